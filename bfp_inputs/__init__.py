@@ -1,0 +1,59 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and bench.py.
+
+This module only draws and samples inputs (random mantissas, the manufactured
+right-hand side, seeded smooth fields, instance sizes).  It holds none of the
+method's arithmetic: no quantisation, no stencil, no multigrid step.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def grid_n(levels_below: int) -> int:
+    """Interior points per side n = 2^J - 1."""
+    return (1 << levels_below) - 1
+
+
+def manufactured_rhs(ndim: int, n: int) -> np.ndarray:
+    """f = d pi^2 prod_i sin(pi x_i) for u = prod_i sin(pi x_i), shape (n,)*ndim, x fastest."""
+    h = 1.0 / (n + 1)
+    s = np.sin(np.pi * np.arange(1, n + 1) * h)
+    u = s
+    for _ in range(ndim - 1):
+        u = np.multiply.outer(s, u)
+    return (ndim * math.pi ** 2) * u
+
+
+def random_mantissas(shape, w: int, seed: int, dist: str = "uniform") -> np.ndarray:
+    """Mantissas in X_w = [-2^(w-1), 2^(w-1)-1] as int64.
+
+    dist: "uniform" over X_w, "small" (a few bits used), "smooth" (a sampled
+    low-frequency field scaled to the range, like a multigrid residual).
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = -(1 << (w - 1)), (1 << (w - 1)) - 1
+    if dist == "uniform":
+        return rng.integers(lo, hi + 1, size=shape, dtype=np.int64)
+    if dist == "small":
+        k = max(1, w // 3)
+        return rng.integers(-(1 << (k - 1)), 1 << (k - 1), size=shape, dtype=np.int64)
+    if dist == "smooth":
+        grids = np.meshgrid(*[np.linspace(0, 1, s) for s in shape], indexing="ij")
+        f = np.zeros(shape)
+        for _ in range(4):
+            k = rng.integers(1, 4, size=len(shape))
+            ph = rng.uniform(0, 2 * np.pi, size=len(shape))
+            term = np.ones(shape)
+            for g, kk, pp in zip(grids, k, ph):
+                term = term * np.sin(np.pi * kk * g + pp)
+            f += rng.uniform(-1, 1) * term
+        f = f / max(np.abs(f).max(), 1e-300)
+        m = np.floor(f * hi).astype(np.int64)
+        return np.clip(m, lo, hi)
+    raise ValueError(dist)
+
+
+def random_exponent(seed: int, lo: int = -40, hi: int = 10) -> int:
+    return int(np.random.default_rng(seed).integers(lo, hi + 1))

@@ -1,0 +1,264 @@
+"""Multigrid reference: FP64 multigrid and the BFP V(2,2) / FMG / IR schedule.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Model problem (Sec. 5, eq. pde-poisson, discretised by finite differences as
+the synthetic workloads require): -Laplace u = f on the unit square / cube,
+zero Dirichlet boundary, n = 2^J - 1 interior points per side, h = 1/(n+1).
+
+Scaling (Alg. solver-setup): the system is multiplied by h^2 / 2^p with 2^p
+the smallest power of two >= 2d, giving A' (centre 2d / 2^p, neighbours
+-1 / 2^p) and b' = (h^2 / 2^p) f.  In 2D this is exactly D^-1 A (D = I after
+setup).  In 3D it keeps A' dyadic; the smoother weight absorbs 2^p / (2d).
+
+V-cycle: the correction scheme of Alg. v-cycle with the paper's signs
+(r_v = A y - r, y <- y - P d), generalised to nu1 pre- and nu2 post-sweeps
+of damped Jacobi; FMG follows Alg. fmg with N IR-V steps per level; IR
+follows Alg. ir with its residual and update in FP64 (r = b - A x, x <- x + y,
+which is the paper's r = A x - b, x <- x - y with both signs flipped).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from . import bfp as B
+
+
+# ---------------------------------------------------------------------------
+# FP64 pieces with a fixed evaluation order (bit-reproducible)
+# ---------------------------------------------------------------------------
+
+def diag_coef(ndim: int) -> float:
+    """Centre of A' = (h^2/2^p) A_h: 1 in 2D, 3/4 in 3D."""
+    return (2.0 * ndim) / pscale(ndim)
+
+
+def pscale(ndim: int) -> float:
+    return 4.0 if ndim == 2 else 8.0
+
+
+def nbr_coef(ndim: int) -> float:
+    return -1.0 / pscale(ndim)
+
+
+def omega_scaled(ndim: int, omega: float) -> float:
+    """Jacobi weight for A': omega * 2^p / (2d)."""
+    return omega * pscale(ndim) / (2.0 * ndim)
+
+
+def neighbours_f64(x: np.ndarray) -> list:
+    """The 2d neighbour arrays in the order W, E, S, N[, B, T], zero outside."""
+    p = np.pad(x, 1)
+    out = []
+    for off in B.shifts(x.ndim):
+        sl = tuple(slice(1 + o, p.shape[i] - 1 + o) for i, o in enumerate(off))
+        out.append(p[sl])
+    return out
+
+
+def apply_f64(x: np.ndarray) -> np.ndarray:
+    """A' x in FP64: s = ((W + E) + S) + N [+ B + T]; A'x = c*x + (nbr*s)."""
+    nd = x.ndim
+    nb = neighbours_f64(x)
+    s = nb[0]
+    for t in nb[1:]:
+        s = s + t
+    return diag_coef(nd) * x + nbr_coef(nd) * s
+
+
+def residual_f64(b: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """IR residual r = b' - A' x (Alg. ir residual line, sign flipped)."""
+    return b - apply_f64(x)
+
+
+def restrict_f64(r: np.ndarray) -> np.ndarray:
+    """Full weighting R~ in FP64, deltas in lexicographic order (outer axis first)."""
+    import itertools
+    nd = r.ndim
+    cs = B.coarse_shape(r.shape)
+    scale = 2.0 ** B.restrict_exponent(nd)
+    acc = np.zeros(cs)
+    for delta in itertools.product((-1, 0, 1), repeat=nd):
+        wgt = 1
+        sl = []
+        for ax, dl in enumerate(delta):
+            wgt *= 2 - abs(dl)
+            sl.append(slice(1 + dl, 1 + dl + 2 * cs[ax], 2))
+        acc = acc + (wgt * scale) * r[tuple(sl)]
+    return acc
+
+
+def prolong_f64(c: np.ndarray, fine_shape) -> np.ndarray:
+    import itertools
+    nd = c.ndim
+    z = np.zeros(tuple(fine_shape))
+    for delta in itertools.product((-1, 0, 1), repeat=nd):
+        wgt = 1.0
+        sl = []
+        for ax, dl in enumerate(delta):
+            wgt *= 1.0 if dl == 0 else 0.5
+            sl.append(slice(1 + dl, 1 + dl + 2 * c.shape[ax], 2))
+        z[tuple(sl)] += wgt * c
+    return z
+
+
+def energy_sq(e: np.ndarray) -> float:
+    """e^T A' e (proportional to the discrete energy norm squared)."""
+    return float(np.sum(e * apply_f64(e)))
+
+
+# ---------------------------------------------------------------------------
+# Manufactured problem (closed forms)
+# ---------------------------------------------------------------------------
+
+def grid_coords(n: int):
+    h = 1.0 / (n + 1)
+    return np.arange(1, n + 1) * h
+
+
+def sin_product(ndim: int, n: int) -> np.ndarray:
+    """u = prod sin(pi x_i) on the interior grid, shape (n,)*ndim (x fastest)."""
+    s = np.sin(np.pi * grid_coords(n))
+    u = s
+    for _ in range(ndim - 1):
+        u = np.multiply.outer(s, u)
+    return u
+
+
+def discrete_solution(ndim: int, n: int) -> np.ndarray:
+    """u_h for f = d pi^2 u: u is an eigenvector of A_h with eigenvalue
+    lambda_h = 4 d sin^2(pi h / 2) / h^2, so u_h = (d pi^2 / lambda_h) u."""
+    h = 1.0 / (n + 1)
+    lam = 4.0 * ndim * math.sin(math.pi * h / 2) ** 2 / h ** 2
+    return (ndim * math.pi ** 2 / lam) * sin_product(ndim, n)
+
+
+def scaled_rhs(f: np.ndarray) -> np.ndarray:
+    """b' = (h^2 / 2^p) f (an exact power-of-two scaling)."""
+    n = f.shape[0]
+    h = 1.0 / (n + 1)
+    return f * (h * h / pscale(f.ndim))
+
+
+# ---------------------------------------------------------------------------
+# FP64 V(nu1, nu2) multigrid (pins the BFP schedule's algebra)
+# ---------------------------------------------------------------------------
+
+def jacobi_f64(y: np.ndarray, r: np.ndarray, om: float) -> np.ndarray:
+    return y + om * (r - apply_f64(y))
+
+
+def vcycle_f64(r: np.ndarray, om: float, nu1=2, nu2=2, coarse_sweeps=32) -> np.ndarray:
+    """FP64 V-cycle for A' y = r with the same schedule as the BFP one."""
+    n = r.shape[0]
+    if n <= 3:
+        y = om * r
+        for _ in range(coarse_sweeps - 1):
+            y = jacobi_f64(y, r, om)
+        return y
+    y = om * r
+    for _ in range(nu1 - 1):
+        y = jacobi_f64(y, r, om)
+    rv = apply_f64(y) - r
+    rc = restrict_f64(rv)
+    d = vcycle_f64(rc, om, nu1, nu2, coarse_sweeps)
+    y = y - prolong_f64(d, r.shape)
+    for _ in range(nu2):
+        y = jacobi_f64(y, r, om)
+    return y
+
+
+# ---------------------------------------------------------------------------
+# BFP multigrid schedule
+# ---------------------------------------------------------------------------
+
+@dataclass
+class BFPSolver:
+    """Schedule of the BFP solver: widths, mode, sweeps and the quantised weight."""
+    ndim: int
+    n: int
+    w: int = 16                      # one width for w_check = w = w_hat (configs)
+    mode: str = "qcomp"
+    nu1: int = 2
+    nu2: int = 2
+    coarse_sweeps: int = 32
+    omega: float = 0.8               # damped-Jacobi weight for A_h's diagonal
+    w_omega: int = 16                # storage width of the weight (w_check)
+    n_fmg: int = 2                   # N of Alg. fmg
+    stats: B.Stats = field(default_factory=B.Stats)
+
+    def __post_init__(self):
+        self.A = B.laplace_stencil(self.ndim)
+        self.om = B.scalar_floor(omega_scaled(self.ndim, self.omega), self.w_omega)
+        sizes = []
+        m = self.n
+        while True:
+            sizes.append(m)
+            if m <= 3:
+                break
+            m = (m - 1) // 2
+        self.sizes = sizes
+
+    @property
+    def q(self) -> B.Quant:
+        return B.Quant(self.w, self.mode)
+
+    def vcycle(self, k: int, r: B.BFP) -> B.BFP:
+        A, om, q, st = self.A, self.om, self.q, self.stats
+        if k == len(self.sizes) - 1:
+            y = B.jacobi(A, om, None, r, q, st)
+            for _ in range(self.coarse_sweeps - 1):
+                y = B.jacobi(A, om, y, r, q, st)
+            return y
+        y = B.jacobi(A, om, None, r, q, st)
+        for _ in range(self.nu1 - 1):
+            y = B.jacobi(A, om, y, r, q, st)
+        rv = B.residual(A, y, r, q, om, st)
+        rc = B.restrict(rv, q, st)
+        d = self.vcycle(k + 1, rc)
+        y = B.prolong(d, y, r.m.shape, q, st)
+        for _ in range(self.nu2):
+            y = B.jacobi(A, om, y, r, q, st)
+        return y
+
+    def ir_step(self, k: int, b: np.ndarray, x: np.ndarray, trace: Optional[list] = None):
+        """One IR-V step (Alg. ir): FP64 residual, quantise, V-cycle, FP64 update."""
+        r64 = residual_f64(b, x)
+        r = B.from_f64(r64, self.w)
+        y = self.vcycle(k, r)
+        if trace is not None:
+            trace.append((r, y))
+        return x + B.to_f64(y)
+
+    def rhs_hierarchy(self, f: np.ndarray):
+        bs = [scaled_rhs(f)]
+        for _ in self.sizes[1:]:
+            bs.append(restrict_f64(bs[-1]))
+        return bs
+
+    def fmg(self, f: np.ndarray, trace: Optional[list] = None) -> np.ndarray:
+        """Alg. fmg: recurse to the coarsest level, interpolate at w (qspmv(P, x)), N IR-V steps."""
+        bs = self.rhs_hierarchy(f)
+        x = None
+        for k in range(len(self.sizes) - 1, -1, -1):
+            if x is None:
+                x = np.zeros(bs[k].shape)
+            else:
+                xq = B.from_f64(x, self.w)
+                xp = B.prolong(xq, None, bs[k].shape, self.q, self.stats)
+                x = B.to_f64(xp)
+            for _ in range(self.n_fmg):
+                x = self.ir_step(k, bs[k], x, trace)
+        return x
+
+
+def accuracy_ratio(ndim: int, x: np.ndarray) -> float:
+    """||u - x||_L / ||u - u_h||_L (Sec. 5.1 acceptance test; <= 1.5 passes)."""
+    n = x.shape[0]
+    u = sin_product(ndim, n)
+    uh = discrete_solution(ndim, n)
+    return math.sqrt(energy_sq(u - x) / energy_sq(u - uh))

@@ -1,0 +1,164 @@
+"""Pins for the multigrid oracle (CPU only): closed forms, O(h^2), local Fourier
+analysis of damped Jacobi, dense-eigensolve V-cycle factors (Sec. 5.2
+conv-rate-v-cycle), and the BFP schedule against the FP64 one."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from bfp_inputs import manufactured_rhs
+from oracle import bfp as B
+from oracle import mg
+
+from test_oracle_bfp import laplacian_matrix, prolong_matrix
+
+
+@pytest.mark.parametrize("nd,n", [(2, 31), (2, 63), (3, 15)])
+def test_discrete_solution_closed_form(nd, n):
+    f = manufactured_rhs(nd, n)
+    b = mg.scaled_rhs(f)
+    uh = mg.discrete_solution(nd, n)
+    r = mg.residual_f64(b, uh)
+    assert np.abs(r).max() <= 1e-12 * np.abs(b).max()
+    # same check with an independently built sparse matrix A_h = L / h^2
+    h = 1.0 / (n + 1)
+    L = laplacian_matrix(nd, n) / h ** 2
+    assert np.allclose(L @ uh.ravel(), f.ravel(), rtol=1e-11, atol=1e-9)
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_discretisation_error_is_second_order(nd):
+    errs = []
+    ns = (15, 31, 63) if nd == 3 else (63, 127, 255)
+    for n in ns:
+        u = mg.sin_product(nd, n)
+        uh = mg.discrete_solution(nd, n)
+        errs.append(np.abs(u - uh).max())
+    for a, b in zip(errs, errs[1:]):
+        assert 3.9 < a / b < 4.1
+    # closed form |1 - d pi^2 / lambda_h| ~ pi^2 h^2 / 12 for the finest grid
+    h = 1.0 / (ns[-1] + 1)
+    assert abs(errs[-1] / (math.pi ** 2 * h ** 2 / 12) - 1) < 1e-3
+
+
+def eigenmode(nd, n, ks):
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    m = np.sin(np.pi * ks[0] * x)
+    for k in ks[1:]:
+        m = np.multiply.outer(np.sin(np.pi * k * x), m)
+    lam = sum(1 - math.cos(math.pi * k * h) for k in ks) * 2.0 / mg.pscale(nd)
+    return m, lam
+
+
+@pytest.mark.parametrize("nd,omega,mu", [(2, 0.8, 3 / 5), (3, 6 / 7, 5 / 7)])
+def test_jacobi_smoothing_factor_lfa(nd, omega, mu):
+    """Damped Jacobi on A': each sine mode is an eigenvector; the worst high-frequency
+    amplification matches the LFA closed form max(|1-2w|, |1-w/d|)."""
+    n = 15 if nd == 2 else 7
+    om = mg.omega_scaled(nd, omega)
+    worst = 0.0
+    import itertools
+    for ks in itertools.product(range(1, n + 1), repeat=nd):
+        m, lam = eigenmode(nd, n, ks)
+        assert np.allclose(mg.apply_f64(m), lam * m, atol=1e-12)
+        y = mg.jacobi_f64(m, np.zeros_like(m), om)
+        amp = 1 - om * lam
+        assert np.allclose(y, amp * m, atol=1e-12)
+        if max(ks) > (n + 1) // 2:
+            worst = max(worst, abs(amp))
+    assert worst <= mu + 1e-12
+    assert worst > mu - 0.15
+    assert abs(mu - max(abs(1 - 2 * omega), abs(1 - omega / nd))) < 1e-12
+
+
+def vcycle_matrix(nd, n, omega):
+    """Error propagation V = I - Vcycle(A') applied to canonical basis vectors."""
+    N = n ** nd
+    om = mg.omega_scaled(nd, omega)
+    V = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        e = e.reshape((n,) * nd)
+        y = mg.vcycle_f64(mg.apply_f64(e), om)
+        V[:, i] = (e - y).ravel()
+    return V
+
+
+def test_vcycle_energy_factor_dense_eigensolve():
+    """rho_v = ||V||_A from V^T A V x = lambda A x (Sec. 5.2), mesh independent,
+    and close to the asymptotic rate seen by iterating."""
+    rhos = []
+    for n in (7, 15):
+        h = 1.0 / (n + 1)
+        A = (laplacian_matrix(2, n) / 4.0).toarray()
+        V = vcycle_matrix(2, n, 0.8)
+        lam = sla.eigh(V.T @ A @ V, A, eigvals_only=True)
+        rhos.append(math.sqrt(lam.max()))
+    assert all(0.05 < r < 0.25 for r in rhos), rhos
+    assert abs(rhos[0] - rhos[1]) < 0.05
+    rng = np.random.default_rng(0)
+    n = 63
+    x = rng.standard_normal((n, n))
+    b = np.zeros((n, n))
+    om = mg.omega_scaled(2, 0.8)
+    e0 = math.sqrt(mg.energy_sq(x))
+    for _ in range(12):
+        x = x + mg.vcycle_f64(mg.residual_f64(b, x), om)
+        e1 = math.sqrt(mg.energy_sq(x))
+        fac, e0 = e1 / e0, e1
+    assert fac <= rhos[1] + 0.02
+
+
+def test_fp64_restriction_matches_matrix():
+    for nd, nc in ((2, 5), (3, 3)):
+        rng = np.random.default_rng(1)
+        nf = 2 * nc + 1
+        r = rng.standard_normal((nf,) * nd)
+        P = prolong_matrix(nd, nc)
+        Rt = P.T * (1.0 if nd == 2 else 0.5)
+        assert np.allclose(mg.restrict_f64(r).ravel(), Rt @ r.ravel(), atol=1e-14)
+        c = rng.standard_normal((nc,) * nd)
+        assert np.allclose(mg.prolong_f64(c, (nf,) * nd).ravel(), P @ c.ravel(), atol=1e-14)
+
+
+@pytest.mark.parametrize("nd,n", [(2, 31), (3, 15)])
+def test_bfp_vcycle_tracks_fp64_vcycle_at_32_bits(nd, n):
+    """The BFP schedule at w = 32 equals the FP64 V-cycle up to quantisation."""
+    omega = 0.8 if nd == 2 else 6 / 7
+    s = mg.BFPSolver(nd, n, w=32, w_omega=32, omega=omega, mode="qcomp")
+    rng = np.random.default_rng(2)
+    r64 = rng.standard_normal((n,) * nd)
+    r = B.from_f64(r64, 32)
+    y = B.to_f64(s.vcycle(0, r))
+    y64 = mg.vcycle_f64(B.to_f64(r), float(s.om.value()))
+    assert np.abs(y - y64).max() <= 1e-7 * np.abs(y64).max()
+
+
+@pytest.mark.parametrize("mode", ["qcomp", "nnqcomp"])
+def test_bfp_fmg_reaches_discretisation_accuracy(mode):
+    """Sec. 5.1 acceptance ||u - x||_L / ||u - u_h||_L <= 1.5 after FMG at w = 16 (63^2)."""
+    f = manufactured_rhs(2, 63)
+    s = mg.BFPSolver(2, 63, w=16, mode=mode)
+    x = s.fmg(f)
+    assert mg.accuracy_ratio(2, x) <= 1.5
+    if mode == "nnqcomp":
+        assert s.stats.recomputed == 0
+
+
+def test_bfp_ir_converges_to_discrete_solution():
+    f = manufactured_rhs(2, 63)
+    s = mg.BFPSolver(2, 63, w=16, mode="qcomp")
+    b = s.rhs_hierarchy(f)[0]
+    x = np.zeros_like(b)
+    uh = mg.discrete_solution(2, 63)
+    errs = []
+    for _ in range(10):
+        x = s.ir_step(0, b, x)
+        errs.append(math.sqrt(mg.energy_sq(x - uh)))
+    facs = [b_ / a_ for a_, b_ in zip(errs, errs[1:])]
+    assert max(facs[:6]) < 0.3
+    assert errs[-1] < 1e-8 * math.sqrt(mg.energy_sq(uh))
