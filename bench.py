@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark: BFP IR-V steps on the 2D Poisson workload (4095^2 interior points, w = 16).
+
+One step is one iteration of FP64 iterative refinement with a BFP V(2,2)
+inner cycle (Alg. ir / v-cycle): FP64 residual r = b' - A'x and its
+normalised BFP quantisation, the V-cycle over 11 levels (damped Jacobi,
+residual, full-weighting restriction, bilinear correction), and the FP64
+update.  Metric: fine-grid DOF x V-cycles per second (GDOF/s), whole job.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle
+instead (the exact reference this library is checked against).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFP V-cycle GDOF/s (IR-V steps, 2D Poisson 4095^2, w=16)"
+UNIT = "GDOF/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="nnqcomp", choices=["nnqcomp", "qcomp"])
+    p.add_argument("--n", type=int, default=4095)
+    p.add_argument("--w", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_step(n, w, mode, nd=2):
+    """Time one oracle IR-V step on an n^2 grid (numpy, exact integers)."""
+    import numpy as np
+    from bfp_inputs import manufactured_rhs
+    from oracle import mg
+    f = manufactured_rhs(nd, n)
+    s = mg.BFPSolver(nd, n, w=w, mode=mode)
+    b = s.rhs_hierarchy(f)[0]
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    s.ir_step(0, b, x)
+    return time.perf_counter() - t0
+
+
+def cpu_threads():
+    try:
+        import numpy as np  # noqa: F401
+        return 1   # the oracle is plain numpy on one core (no threaded BLAS on this path)
+    except Exception:
+        return 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init(args)
+    if rank != 0:
+        return
+    # the oracle on the host cores: each step is one IR-V step on a bounded sample
+    # of the workload (a 1023^2 grid of the same problem; GDOF/s is per fine DOF)
+    n = 1023
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = cpu_oracle_step(n, args.w, args.mode)
+        if i >= args.warmup:
+            times.append(t)
+    tot = sum(times)
+    dof = n * n
+    value = dof * len(times) / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16+f64",
+        "data": "synthetic", "config": {"workload": "2D Poisson 5-point, IR-V(2,2) damped Jacobi, w=%d, %s" % (
+            args.w, args.mode), "sample": "%dx%d grid per step" % (n, n)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                         "sample": "one IR-V step on a %d^2 grid per step" % n},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_init(args)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2307_00124_gb300 as bfp
+    from bfp_inputs import manufactured_rhs
+
+    nd, n, w = 2, args.n, args.w
+    mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
+    o = bfp.bfp_solver_opts_default(nd, n, w)
+    o.mode = mode
+    h = bfp.Hierarchy(o)
+    f_host = manufactured_rhs(nd, n)
+    f = torch.from_numpy(f_host).cuda()
+    x = torch.zeros_like(f)
+    stream = torch.cuda.Stream()
+    dof = n ** nd
+
+    # warm-up (the first call captures one IR step into a CUDA graph)
+    l0 = bfp.bfp_kernel_launches()
+    with torch.cuda.stream(stream):
+        h.ir_iterate(f, x, 1)
+    stream.synchronize()
+    launches_per_step = bfp.bfp_kernel_launches() - l0
+    with torch.cuda.stream(stream):
+        h.ir_iterate(f, x, max(args.warmup - 1, 0))
+    stream.synchronize()
+
+    # timed region: inputs (4 x 134 MB of FP64 plus 33 MB BFP levels) exceed the 129 MB L2
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        h.ir_iterate(f, x, args.steps)
+        e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    value = ws * dof * args.steps / t / 1e9
+
+    # roofline: the dominant kernels timed alone with CUDA events on their stream
+    hbm, peak_kind = peaks()
+    A = bfp.bfp_laplace_stencil(nd, o.omega, o.w_omega)
+    rng = np.random.default_rng(0)
+    ym = rng.integers(-(1 << 12), 1 << 12, size=(n, n))
+    y = bfp.BFPVector.from_mantissas(ym, -20, w)
+    r = bfp.BFPVector.from_mantissas(ym[::-1].copy(), -19, w)
+    yo = bfp.BFPVector((n, n), w)
+    q = bfp.q(w, mode)
+    reps = 30
+    kern = {}
+
+    def timeit(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    mb = 2 if w <= 16 else 4
+    kern["jacobi"] = (timeit(lambda: bfp.bfp_jacobi(A, y, r, yo, q, stream=stream)), 3 * mb * dof)
+    kern["residual"] = (timeit(lambda: bfp.bfp_residual(A, y, r, yo, q, stream=stream)), 3 * mb * dof)
+    kern["ir_residual"] = (timeit(lambda: h.ir_residual(f, x, yo, stream=stream)), 2 * 16 * dof + mb * dof)
+    kern["ir_update"] = (timeit(lambda: bfp.bfp_ir_update(x, y, stream=stream)), (16 + mb) * dof)
+    kern_out = {k: {"ms": 1e3 * v[0], "algorithmic_bytes": v[1], "GBps": v[1] / v[0] / 1e9,
+                    "frac": v[1] / v[0] / 1e9 / hbm} for k, v in kern.items()}
+    dom = "ir_residual"
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern_out[dom]["GBps"], "peak": hbm, "unit": "GB/s",
+            "frac": kern_out[dom]["GBps"] / hbm, "peak_kind": peak_kind, "traffic": None}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(f_host).pin_memory()
+        xh = torch.zeros_like(fh).pin_memory()
+        xd = torch.empty_like(f)
+        fd = torch.empty_like(f)
+        k2 = max(3, args.steps // 2)
+        with torch.cuda.stream(stream):
+            for i in range(2 + k2):
+                if i == 2:
+                    a = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                fd.copy_(fh, non_blocking=True)
+                xd.copy_(xh, non_blocking=True)
+                h.ir_iterate(fd, xd, 1)
+                xh.copy_(xd, non_blocking=True)
+            b = torch.cuda.Event(enable_timing=True)
+            b.record(stream)
+        stream.synchronize()
+        te = a.elapsed_time(b) / 1e3
+        e2e = {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
+               "d2h_bytes_per_step": 8 * dof}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            tc = cpu_oracle_step(n, w, args.mode)
+            cpu = {"value": dof / tc / 1e9, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                   "sample": "one IR-V step of the same %d^2 workload (numpy exact-integer oracle)" % n}
+        except Exception as exc:  # the oracle is a reported baseline, never the product path
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % exc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16+f64" if w <= 16 else "int32+f64",
+            "data": "synthetic",
+            "config": {"workload": "2D Poisson 5-point, %dx%d interior, FP64 IR with BFP V(2,2) damped Jacobi "
+                                   "omega=4/5, 11 levels, w=%d, %s" % (n, n, w, args.mode),
+                       "l2": "inputs larger than L2 (x, f: 134 MB each)", "parallelism": "replicas" if ws > 1
+                       else "single GPU"},
+            "roofline": roof, "kernels": kern_out, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches_per_step * args.steps),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    h.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

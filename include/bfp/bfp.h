@@ -1,0 +1,284 @@
+/*
+ * bfp.h -- C ABI of the GB300 block-floating-point multigrid library.
+ *
+ * Method: Kohl, McCormick, Tamstorf, "Multigrid methods using Block Floating
+ * Point Arithmetic" (arXiv:2307.00124).  A BFP block is x = 2^e * m with
+ * integer mantissas m in X_w = [-2^(w-1), 2^(w-1)-1] sharing one exponent e
+ * (Sec. 2).  Every op computes its exact result z* with the App. B setup
+ * rules and quantises it to w_out bits, either normalised (Alg. qcomp) or
+ * saturated and truncated from a bound gamma (Alg. nnqcomp).
+ *
+ * General conventions
+ *  - Every pointer named "device" is CUDA device memory owned by the caller.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is
+ *    the legacy default stream).  Argument errors are returned synchronously;
+ *    nothing is read back from the device inside an op.
+ *  - Exponents and norms live on the device in the vector's meta block, so a
+ *    sequence of ops never synchronises with the host.
+ *  - Inputs and outputs of one call must not alias (mantissas or meta).
+ *  - Return value: a bfp_status (0 = BFP_OK).
+ */
+#ifndef BFP_BFP_H
+#define BFP_BFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* bfp_stream; /* cudaStream_t */
+
+typedef enum {
+  BFP_OK = 0,
+  BFP_ERR_ARG = -1,       /* null pointer, bad width, aliasing, bad scalar */
+  BFP_ERR_SHAPE = -2,     /* sizes, leading dimension or alignment */
+  BFP_ERR_WIDTH = -3,     /* an exact intermediate would exceed 62 bits per group */
+  BFP_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+  BFP_ERR_NONFINITE = -5, /* NaN or Inf in an FP64 input (reported via meta) */
+  BFP_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
+  BFP_ERR_NOCONV = -7     /* ir_solve reached its iteration limit */
+} bfp_status;
+
+/* Words in a vector's device meta block. */
+#define BFP_META_WORDS 8
+/* meta[0]: shared exponent e.  meta[1]: max_i |m_i| (written by the producer).
+ * meta[2..7]: scratch of the op that writes this vector (mu*, flags). */
+#define BFP_META_EXP 0
+#define BFP_META_NORM 1
+#define BFP_META_MU 2
+#define BFP_META_FLAGS 3
+
+/* One BFP block (Sec. 2: tuple (e, m, w, d)).
+ *   mant : device, int16_t when 1 <= w <= 16, int32_t when 17 <= w <= 32;
+ *          16-byte aligned.
+ *   meta : device, BFP_META_WORDS int64 (see above), 8-byte aligned.
+ *   n    : points per dimension, x fastest; unused dimensions are 1.
+ *   ld   : elements between consecutive x-lines (rows); ld >= n[0] and
+ *          ld % 8 == 0.  Row r = y + n[1]*z starts at mant + r*ld.  Elements
+ *          in [n[0], ld) are ignored on input and written as 0 on output.
+ */
+typedef struct {
+  void* mant;
+  int64_t* meta;
+  int32_t w;
+  int32_t ndim;
+  int64_t n[3];
+  int64_t ld;
+} bfp_vec;
+
+/* An exact dyadic scalar 2^e * m (a BFP block of one element), |m| < 2^31. */
+typedef struct {
+  int64_t m;
+  int64_t e;
+} bfp_scalar;
+
+typedef enum {
+  BFP_QCOMP = 0,  /* Alg. qcomp: exact up to w_out bits, normalised result */
+  BFP_NNQCOMP = 1 /* Alg. nnqcomp: window from gamma, saturate, no normalisation */
+} bfp_mode;
+
+/* Quantisation request of one op.
+ *   w_out     : result width, 1..32 (must equal the output vector's w).
+ *   w_add     : w_tmp - w_out for Alg. qcomp; < 0 selects the op's value
+ *               from Table tab:estimates.
+ *   mode      : bfp_mode.
+ *   has_gamma : 0 -> gamma from the op's rule (Table tab:estimates; the
+ *               damped-Jacobi rows are this library's reading), 1 -> gamma.
+ *   gamma     : the bound on ||z||_inf used when has_gamma = 1 (>= 0).
+ *   tmp       : device int32 scratch with the output's layout (rows * ld
+ *               elements) holding the w_tmp-bit window of Alg. qcomp; NULL
+ *               makes qcomp recompute every element in its second pass (the
+ *               result is identical).  Ignored by nnqcomp.
+ */
+typedef struct {
+  int32_t w_out;
+  int32_t w_add;
+  int32_t mode;
+  int32_t has_gamma;
+  bfp_scalar gamma;
+  void* tmp;
+} bfp_q;
+
+/* Optional device counters (uint64[8]) accumulated with atomics:
+ * [0] quantised ops, [1] qcomp recomputations (overflow or underflow),
+ * [2] overflows, [3] underflows, [4] saturated elements (nnqcomp). */
+typedef struct {
+  uint64_t* counters;
+} bfp_stats;
+
+/* Constant-coefficient star stencil (2*ndim+1 points) as one BFP block, plus
+ * the damped-Jacobi weight paired with it.
+ *   center, nbr : mantissas (|.| < 2^15), e : shared exponent.
+ *   omega       : smoother weight (bfp_jacobi; also the residual gamma rule).
+ * Laplacian of the model problem after setup S (Alg. solver-setup):
+ *   2D: center 4, nbr -1, e -2 (A' = D^-1 A_h); 3D: center 6, nbr -1, e -3
+ *   (A' = h^2/8 A_h; the diagonal 3/4 is folded into omega). */
+typedef struct {
+  int32_t ndim;
+  int32_t reserved;
+  int64_t center;
+  int64_t nbr;
+  int64_t e;
+  bfp_scalar omega;
+} bfp_stencil;
+
+/* ---- helpers --------------------------------------------------------------- */
+
+/* Text for a status code.  Never NULL. */
+const char* bfp_status_str(int32_t status);
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t bfp_version(void);
+/* Number of kernels this library has enqueued in this process so far
+ * (launched directly or recorded into a captured graph). */
+int64_t bfp_kernel_launches(void);
+/* Smallest valid ld for rows of n0 elements. */
+int64_t bfp_pitch(int64_t n0);
+/* Floor-quantise a double to a normalised BFP scalar of w bits (quant(),
+ * read as floor; Alg. ir / v-cycle / fmg).  Host only. */
+int32_t bfp_scalar_from_double(double x, int32_t w, bfp_scalar* out);
+/* The model-problem Laplacian of ndim (2 or 3) with Jacobi weight omega
+ * (for A_h's diagonal) floor-quantised to w_omega bits.  Host only. */
+int32_t bfp_laplace_stencil(int32_t ndim, double omega, int32_t w_omega, bfp_stencil* out);
+
+/* ---- BFP ops (Sec. 4, App. B) ------------------------------------------------ */
+
+/* out = quantisation of x to q->w_out bits (exact z* = x; Sec. 2 normalised
+ * representation).  out has x's shape. */
+int32_t bfp_normalize(const bfp_vec* x, const bfp_vec* out, const bfp_q* q,
+                      const bfp_stats* st, bfp_stream stream);
+
+/* out = floor-quantised normalised BFP of the doubles x (device, dense,
+ * n[0]*n[1]*n[2] values, x fastest) at out->w bits.  The doubles are read as
+ * one exact block with e* = -1074; the result is Alg. qcomp's (quant() of
+ * Alg. ir).  A NaN or Inf sets meta[BFP_META_FLAGS] bit 0 and out is
+ * unspecified. */
+int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream);
+
+/* out (device, dense doubles) = m * 2^e, exact when representable (w <= 32). */
+int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream);
+
+/* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp). */
+int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
+                 const bfp_vec* z, const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+
+/* out = sum_i x_i y_i exactly (Sec. 2 remark on BFP dot products; 128-bit
+ * accumulator), normalised to w_out bits (1..62).  out: device int64[8],
+ * out[0] = mantissa, out[1] = exponent, out[2..7] scratch. */
+int32_t bfp_dot(const bfp_vec* x, const bfp_vec* y, int32_t w_out, int64_t* out,
+                bfp_stream stream);
+
+/* z = A x (Alg. espmv-setup / espmv-row with m_A = 2*ndim+1; qspmv). */
+int32_t bfp_stencil_apply(const bfp_stencil* A, const bfp_vec* x, const bfp_vec* z,
+                          const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+
+/* rv = A y - r (Alg. egemv with alpha = 1, beta = -1; the V-cycle residual
+ * line of Alg. v-cycle, with the paper's sign). */
+int32_t bfp_residual(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r,
+                     const bfp_vec* rv, const bfp_q* q, const bfp_stats* st,
+                     bfp_stream stream);
+
+/* y_out = y + omega (r - A y) = S y + omega r with S = I - omega A (damped
+ * Jacobi in the relaxation slot of Alg. v-cycle; egemv(S, y, r, 1, omega)).
+ * y == NULL means a zero initial guess: y_out = omega r. */
+int32_t bfp_jacobi(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r,
+                   const bfp_vec* y_out, const bfp_q* q, const bfp_stats* st,
+                   bfp_stream stream);
+
+/* r_c = R~ r_f, full weighting R~ = D_c^-1 R_FW D_f (P^T in 2D, P^T/2 in 3D):
+ * the restriction line of Alg. v-cycle (qspmv with m_R = 3^d).
+ * r_f has n = 2*n_c + 1 points per dimension. */
+int32_t bfp_restrict(const bfp_vec* r_f, const bfp_vec* r_c, const bfp_q* q,
+                     const bfp_stats* st, bfp_stream stream);
+
+/* y_out = y - P d (Alg. v-cycle correction line: qgemv(P, d, y, -1, 1)), or
+ * y_out = P d when y == NULL (Alg. fmg interpolation line: qspmv(P, x)).
+ * P is bilinear (2D) / trilinear (3D) interpolation. */
+int32_t bfp_prolong(const bfp_vec* d, const bfp_vec* y, const bfp_vec* y_out,
+                    const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+
+/* ---- multigrid (Alg. v-cycle, fmg, ir) ---------------------------------------- */
+
+typedef struct bfp_hierarchy bfp_hierarchy;
+
+/* Solver set-up for -Laplace u = f on the unit square/cube, zero Dirichlet
+ * boundary, n = 2^J - 1 interior points per side (finite differences). */
+typedef struct {
+  int32_t ndim;          /* 2 or 3 */
+  int32_t w;             /* one mantissa width for all BFP vectors, 1..32 */
+  int64_t n;             /* finest interior points per side, 2^J - 1 >= 3 */
+  int32_t mode;          /* bfp_mode for every op inside the V-cycle */
+  int32_t nu1, nu2;      /* pre- and post-smoothing sweeps (>= 1, >= 0) */
+  int32_t coarse_sweeps; /* Jacobi sweeps on the coarsest level (n = 3) */
+  int32_t n_fmg;         /* N of Alg. fmg: IR-V steps per level */
+  double omega;          /* Jacobi weight for A_h's diagonal (4/5 in 2D, 6/7 in 3D) */
+  int32_t w_omega;       /* storage width of the quantised weight */
+  int32_t use_tmp;       /* 1: qcomp keeps the w_tmp window (Alg. qcomp); 0: recompute */
+  int32_t use_graph;     /* 1: replay IR steps from a captured CUDA graph */
+  int32_t reserved;
+} bfp_solver_opts;
+
+/* Fill opts with the defaults of the 2D/3D model problem. */
+int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_opts* o);
+
+/* Allocate the level hierarchy on the current CUDA device (cudaMalloc; the
+ * hierarchy owns every buffer it allocates). */
+int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** h);
+void bfp_hierarchy_destroy(bfp_hierarchy* h);
+
+/* Copies the hierarchy's device counters (bfp_stats layout, uint64[8]) to
+ * host memory; synchronises the stream.  bfp_hierarchy_reset_stats zeroes
+ * them (asynchronously). */
+int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream);
+int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream);
+
+/* y = V(nu1,nu2)(r) on the finest level: approximate solution of A' y = r
+ * (Alg. v-cycle correction scheme with damped Jacobi).  r and y use the
+ * hierarchy's width and finest shape. */
+int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_stream stream);
+
+/* The FP64 halves of one IR step on the finest level (Alg. ir residual and
+ * correction lines, in FP64 with the signs flipped):
+ *   bfp_ir_residual: r = quant(b' - A' x) at r->w bits, normalised, with
+ *     b' = (h^2/2^p) f; the residual is evaluated in a fixed order with
+ *     correctly rounded operations; f, x: device dense doubles (n^d).
+ *   bfp_ir_update:   x = x + y (y dequantised exactly, one rounding). */
+int32_t bfp_ir_residual(bfp_hierarchy* h, const double* f, const double* x, const bfp_vec* r,
+                        bfp_stream stream);
+int32_t bfp_ir_update(double* x, const bfp_vec* y, bfp_stream stream);
+
+/* FP64 iterative refinement (Alg. ir with FP64 residual and update):
+ * k steps of  r = b' - A' x,  y = V(quant(r)),  x = x + y  on the finest level,
+ * where b' = (h^2 / 2^p) f.  f, x: device dense doubles (n^d).  No host sync. */
+int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k,
+                       bfp_stream stream);
+
+/* Full multigrid (Alg. fmg) from x = 0: on each level from the coarsest,
+ * interpolate the coarser solution at width w (bfp_prolong) and run n_fmg
+ * IR-V steps; the coarse right-hand sides are full-weighting restrictions of
+ * b'.  x: device dense doubles (n^d) receiving the finest solution. */
+int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream);
+
+typedef struct {
+  int32_t max_iter;   /* IR steps at most */
+  int32_t fmg_start;  /* 1: start from FMG, 0: from the given x */
+  double tol;         /* stop when ||b' - A'x||_inf <= tol * ||b'||_inf (checked on the host) */
+} bfp_ir_opts;
+
+typedef struct {
+  int32_t iterations;
+  int32_t converged;
+  double res_inf;     /* final ||b' - A'x||_inf */
+  double res0_inf;    /* ||b'||_inf */
+} bfp_ir_report;
+
+/* IR to a tolerance (Alg. ir): synchronises with the host once per step to
+ * read the residual norm.  Returns BFP_ERR_NOCONV when max_iter is reached. */
+int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts* o,
+                 bfp_ir_report* rep, bfp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFP_BFP_H */

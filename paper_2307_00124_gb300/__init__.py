@@ -1,0 +1,373 @@
+"""Python binding of the GB300 BFP multigrid library (C ABI in include/bfp/bfp.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``lib/libbfpmg.so``.  PyTorch supplies device memory and streams.
+Importing this package without the built library raises ImportError; build
+it with ``python -m paper_2307_00124_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libbfpmg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libbfpmg.so is not built (%s); run paper_2307_00124_gb300/build.py" % LIB_PATH)
+_lib = C.CDLL(LIB_PATH)
+
+META_WORDS = 8
+QCOMP, NNQCOMP = 0, 1
+
+STATUS = {0: "BFP_OK", -1: "BFP_ERR_ARG", -2: "BFP_ERR_SHAPE", -3: "BFP_ERR_WIDTH", -4: "BFP_ERR_CUDA",
+          -5: "BFP_ERR_NONFINITE", -6: "BFP_ERR_TIMEOUT", -7: "BFP_ERR_NOCONV"}
+
+
+class BFPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.bfp_status_str(status).decode()
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), msg))
+
+
+# ---- ctypes mirrors of the C structs ----------------------------------------
+
+class bfp_vec(C.Structure):
+    _fields_ = [("mant", C.c_void_p), ("meta", C.c_void_p), ("w", C.c_int32), ("ndim", C.c_int32),
+                ("n", C.c_int64 * 3), ("ld", C.c_int64)]
+
+
+class bfp_scalar(C.Structure):
+    _fields_ = [("m", C.c_int64), ("e", C.c_int64)]
+
+
+class bfp_q(C.Structure):
+    _fields_ = [("w_out", C.c_int32), ("w_add", C.c_int32), ("mode", C.c_int32), ("has_gamma", C.c_int32),
+                ("gamma", bfp_scalar), ("tmp", C.c_void_p)]
+
+
+class bfp_stats(C.Structure):
+    _fields_ = [("counters", C.c_void_p)]
+
+
+class bfp_stencil(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("reserved", C.c_int32), ("center", C.c_int64), ("nbr", C.c_int64),
+                ("e", C.c_int64), ("omega", bfp_scalar)]
+
+
+class bfp_solver_opts(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("w", C.c_int32), ("n", C.c_int64), ("mode", C.c_int32),
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
+                ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
+                ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bfp_ir_opts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("fmg_start", C.c_int32), ("tol", C.c_double)]
+
+
+class bfp_ir_report(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("res_inf", C.c_double),
+                ("res0_inf", C.c_double)]
+
+
+P = C.POINTER
+_sig = {
+    "bfp_status_str": (C.c_char_p, [C.c_int32]),
+    "bfp_version": (C.c_int32, []),
+    "bfp_pitch": (C.c_int64, [C.c_int64]),
+    "bfp_kernel_launches": (C.c_int64, []),
+    "bfp_scalar_from_double": (C.c_int32, [C.c_double, C.c_int32, P(bfp_scalar)]),
+    "bfp_laplace_stencil": (C.c_int32, [C.c_int32, C.c_double, C.c_int32, P(bfp_stencil)]),
+    "bfp_normalize": (C.c_int32, [P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
+    "bfp_from_f64": (C.c_int32, [C.c_void_p, P(bfp_vec), C.c_void_p]),
+    "bfp_to_f64": (C.c_int32, [P(bfp_vec), C.c_void_p, C.c_void_p]),
+    "bfp_axpy": (C.c_int32, [bfp_scalar, P(bfp_vec), bfp_scalar, P(bfp_vec), P(bfp_vec), P(bfp_q),
+                             P(bfp_stats), C.c_void_p]),
+    "bfp_dot": (C.c_int32, [P(bfp_vec), P(bfp_vec), C.c_int32, C.c_void_p, C.c_void_p]),
+    "bfp_stencil_apply": (C.c_int32, [P(bfp_stencil), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats),
+                                      C.c_void_p]),
+    "bfp_residual": (C.c_int32, [P(bfp_stencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q),
+                                 P(bfp_stats), C.c_void_p]),
+    "bfp_jacobi": (C.c_int32, [P(bfp_stencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats),
+                               C.c_void_p]),
+    "bfp_restrict": (C.c_int32, [P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
+    "bfp_prolong": (C.c_int32, [P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
+    "bfp_solver_opts_default": (C.c_int32, [C.c_int32, C.c_int64, C.c_int32, P(bfp_solver_opts)]),
+    "bfp_hierarchy_create": (C.c_int32, [P(bfp_solver_opts), P(C.c_void_p)]),
+    "bfp_hierarchy_destroy": (None, [C.c_void_p]),
+    "bfp_hierarchy_read_stats": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bfp_hierarchy_reset_stats": (C.c_int32, [C.c_void_p, C.c_void_p]),
+    "bfp_vcycle": (C.c_int32, [C.c_void_p, P(bfp_vec), P(bfp_vec), C.c_void_p]),
+    "bfp_ir_iterate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "bfp_fmg": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bfp_ir_residual": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, P(bfp_vec), C.c_void_p]),
+    "bfp_ir_update": (C.c_int32, [C.c_void_p, P(bfp_vec), C.c_void_p]),
+    "ir_solve": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, P(bfp_ir_opts), P(bfp_ir_report),
+                             C.c_void_p]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise BFPError(rc, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def bfp_kernel_launches() -> int:
+    return int(_lib.bfp_kernel_launches())
+
+
+def pitch(n0: int) -> int:
+    return int(_lib.bfp_pitch(n0))
+
+
+# ---- BFP vectors backed by torch device memory --------------------------------
+
+class BFPVector:
+    """A BFP block in device memory: mantissas (rows x ld, int16 or int32) + meta (int64[8]).
+
+    ``shape`` is the numpy-order logical shape ((n,), (ny, nx) or (nz, ny, nx)).
+    """
+
+    def __init__(self, shape, w: int, device="cuda", mant=None, meta=None):
+        import torch
+        self.shape = tuple(int(s) for s in shape)
+        self.w = int(w)
+        nx = self.shape[-1]
+        self.ld = pitch(nx)
+        self.rows = int(np.prod(self.shape[:-1])) if len(self.shape) > 1 else 1
+        dt = torch.int16 if self.w <= 16 else torch.int32
+        self.mant = mant if mant is not None else torch.zeros((self.rows, self.ld), dtype=dt, device=device)
+        self.meta = meta if meta is not None else torch.zeros(META_WORDS, dtype=torch.int64, device=device)
+
+    @property
+    def ndim(self):
+        return len(self.shape)
+
+    def struct(self) -> bfp_vec:
+        v = bfp_vec()
+        v.mant = self.mant.data_ptr()
+        v.meta = self.meta.data_ptr()
+        v.w = self.w
+        v.ndim = self.ndim
+        n = list(reversed(self.shape)) + [1] * (3 - self.ndim)
+        for i in range(3):
+            v.n[i] = n[i]
+        v.ld = self.ld
+        return v
+
+    @classmethod
+    def from_mantissas(cls, m: np.ndarray, e: int, w: int, device="cuda"):
+        import torch
+        m = np.asarray(m, dtype=np.int64)
+        v = cls(m.shape, w, device)
+        host = np.zeros((v.rows, v.ld), dtype=np.int16 if w <= 16 else np.int32)
+        host[:, : m.shape[-1]] = m.reshape(v.rows, m.shape[-1])
+        v.mant.copy_(torch.from_numpy(host))
+        meta = np.zeros(META_WORDS, dtype=np.int64)
+        meta[0] = e
+        meta[1] = int(np.abs(m).max()) if m.size else 0
+        v.meta.copy_(torch.from_numpy(meta))
+        return v
+
+    def mantissas(self) -> np.ndarray:
+        h = self.mant.cpu().numpy().astype(np.int64)
+        return h[:, : self.shape[-1]].reshape(self.shape)
+
+    def padding(self) -> np.ndarray:
+        return self.mant.cpu().numpy()[:, self.shape[-1]:]
+
+    @property
+    def exponent(self) -> int:
+        return int(self.meta[0].item())
+
+    @property
+    def norm_m(self) -> int:
+        return int(self.meta[1].item())
+
+
+def q(w_out: int, mode: int = QCOMP, w_add: int = -1, gamma=None, tmp=None) -> bfp_q:
+    r = bfp_q()
+    r.w_out = w_out
+    r.w_add = w_add
+    r.mode = mode
+    r.has_gamma = 0 if gamma is None else 1
+    if gamma is not None:
+        r.gamma.m, r.gamma.e = int(gamma[0]), int(gamma[1])
+    r.tmp = None if tmp is None else tmp.data_ptr()
+    return r
+
+
+def stats_of(counters) -> bfp_stats:
+    s = bfp_stats()
+    s.counters = counters.data_ptr()
+    return s
+
+
+def _st(stats):
+    return None if stats is None else C.byref(stats_of(stats) if not isinstance(stats, bfp_stats) else stats)
+
+
+def scalar(m: int, e: int) -> bfp_scalar:
+    s = bfp_scalar()
+    s.m, s.e = int(m), int(e)
+    return s
+
+
+def bfp_scalar_from_double(x: float, w: int) -> bfp_scalar:
+    s = bfp_scalar()
+    _check(_lib.bfp_scalar_from_double(float(x), int(w), C.byref(s)), "bfp_scalar_from_double")
+    return s
+
+
+def bfp_laplace_stencil(ndim: int, omega: float, w_omega: int = 16) -> bfp_stencil:
+    A = bfp_stencil()
+    _check(_lib.bfp_laplace_stencil(ndim, float(omega), w_omega, C.byref(A)), "bfp_laplace_stencil")
+    return A
+
+
+# ---- ops (same names as the C ABI) ---------------------------------------------
+
+def bfp_normalize(x, out, qq, stats=None, stream=None):
+    _check(_lib.bfp_normalize(C.byref(x.struct()), C.byref(out.struct()), C.byref(qq), _st(stats),
+                              _stream(stream)), "bfp_normalize")
+
+
+def bfp_from_f64(x, out, stream=None):
+    assert x.is_cuda and x.dtype.is_floating_point and x.is_contiguous()
+    _check(_lib.bfp_from_f64(C.c_void_p(x.data_ptr()), C.byref(out.struct()), _stream(stream)), "bfp_from_f64")
+
+
+def bfp_to_f64(x, out, stream=None):
+    assert out.is_cuda and out.is_contiguous()
+    _check(_lib.bfp_to_f64(C.byref(x.struct()), C.c_void_p(out.data_ptr()), _stream(stream)), "bfp_to_f64")
+
+
+def bfp_axpy(a, x, b, y, z, qq, stats=None, stream=None):
+    _check(_lib.bfp_axpy(a, C.byref(x.struct()), b, C.byref(y.struct()), C.byref(z.struct()), C.byref(qq),
+                         _st(stats), _stream(stream)), "bfp_axpy")
+
+
+def bfp_dot(x, y, w_out, out, stream=None):
+    _check(_lib.bfp_dot(C.byref(x.struct()), C.byref(y.struct()), int(w_out), C.c_void_p(out.data_ptr()),
+                        _stream(stream)), "bfp_dot")
+
+
+def bfp_stencil_apply(A, x, z, qq, stats=None, stream=None):
+    _check(_lib.bfp_stencil_apply(C.byref(A), C.byref(x.struct()), C.byref(z.struct()), C.byref(qq),
+                                  _st(stats), _stream(stream)), "bfp_stencil_apply")
+
+
+def bfp_residual(A, y, r, rv, qq, stats=None, stream=None):
+    _check(_lib.bfp_residual(C.byref(A), C.byref(y.struct()), C.byref(r.struct()), C.byref(rv.struct()),
+                             C.byref(qq), _st(stats), _stream(stream)), "bfp_residual")
+
+
+def bfp_jacobi(A, y, r, y_out, qq, stats=None, stream=None):
+    yp = None if y is None else C.byref(y.struct())
+    _check(_lib.bfp_jacobi(C.byref(A), yp, C.byref(r.struct()), C.byref(y_out.struct()), C.byref(qq),
+                           _st(stats), _stream(stream)), "bfp_jacobi")
+
+
+def bfp_restrict(rf, rc, qq, stats=None, stream=None):
+    _check(_lib.bfp_restrict(C.byref(rf.struct()), C.byref(rc.struct()), C.byref(qq), _st(stats),
+                             _stream(stream)), "bfp_restrict")
+
+
+def bfp_prolong(d, y, y_out, qq, stats=None, stream=None):
+    yp = None if y is None else C.byref(y.struct())
+    _check(_lib.bfp_prolong(C.byref(d.struct()), yp, C.byref(y_out.struct()), C.byref(qq), _st(stats),
+                            _stream(stream)), "bfp_prolong")
+
+
+# ---- multigrid ---------------------------------------------------------------------
+
+def bfp_solver_opts_default(ndim: int, n: int, w: int) -> bfp_solver_opts:
+    o = bfp_solver_opts()
+    _check(_lib.bfp_solver_opts_default(ndim, n, w, C.byref(o)), "bfp_solver_opts_default")
+    return o
+
+
+class Hierarchy:
+    """Owns a bfp_hierarchy (level buffers, captured graphs) on the current device."""
+
+    def __init__(self, opts: bfp_solver_opts):
+        self.opts = opts
+        h = C.c_void_p()
+        _check(_lib.bfp_hierarchy_create(C.byref(opts), C.byref(h)), "bfp_hierarchy_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.bfp_hierarchy_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self, stream=None) -> dict:
+        host = (C.c_uint64 * 8)()
+        _check(_lib.bfp_hierarchy_read_stats(self.h, host, _stream(stream)), "bfp_hierarchy_read_stats")
+        keys = ("calls", "recomputed", "overflow", "underflow", "saturated")
+        return {k: int(host[i]) for i, k in enumerate(keys)}
+
+    def reset_stats(self, stream=None):
+        _check(_lib.bfp_hierarchy_reset_stats(self.h, _stream(stream)), "bfp_hierarchy_reset_stats")
+
+    def vcycle(self, r, y, stream=None):
+        _check(_lib.bfp_vcycle(self.h, C.byref(r.struct()), C.byref(y.struct()), _stream(stream)), "bfp_vcycle")
+
+    def ir_iterate(self, f, x, k: int, stream=None):
+        _check(_lib.bfp_ir_iterate(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()), int(k),
+                                   _stream(stream)), "bfp_ir_iterate")
+
+    def ir_residual(self, f, x, r, stream=None):
+        _check(_lib.bfp_ir_residual(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()),
+                                    C.byref(r.struct()), _stream(stream)), "bfp_ir_residual")
+
+    def fmg(self, f, x, stream=None):
+        _check(_lib.bfp_fmg(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()), _stream(stream)),
+               "bfp_fmg")
+
+    def ir_solve(self, f, x, max_iter=50, tol=1e-10, fmg_start=True, stream=None):
+        o = bfp_ir_opts()
+        o.max_iter, o.tol, o.fmg_start = int(max_iter), float(tol), int(bool(fmg_start))
+        rep = bfp_ir_report()
+        rc = _lib.ir_solve(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(o), C.byref(rep),
+                           _stream(stream))
+        if rc not in (0, -7):
+            raise BFPError(rc, "ir_solve")
+        return rep
+
+
+def bfp_ir_update(x, y, stream=None):
+    _check(_lib.bfp_ir_update(C.c_void_p(x.data_ptr()), C.byref(y.struct()), _stream(stream)), "bfp_ir_update")
+
+
+def ir_solve(h: Hierarchy, f, x, **kw):
+    return h.ir_solve(f, x, **kw)
+
+
+def exported_symbols():
+    """Names of the C ABI functions this binding declares."""
+    return sorted(_sig)

@@ -1,0 +1,284 @@
+// bfp_capi_point.cu -- C ABI: helpers and the pointwise BFP ops
+// (normalise, axpby, dot, FP64 <-> BFP conversion).
+#include <atomic>
+#include <cmath>
+
+#include "bfp_host.h"
+
+using namespace bfp;
+
+namespace bfp {
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace bfp
+
+namespace {
+
+// ---- FP64 -> BFP (quant() of Alg. ir, read as floor) ---------------------
+
+// Exact split of a double: v = M * 2^E (|M| < 2^53).  Returns false for NaN/Inf.
+__device__ __forceinline__ bool f64_split(double v, int64_t& M, int64_t& E) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const uint64_t fr = b & ((1ull << 52) - 1);
+  if (ex == 0x7ff) return false;
+  if (ex == 0) { M = (int64_t)fr; E = -1074; }
+  else { M = (int64_t)(fr | (1ull << 52)); E = ex - 1075; }
+  if (b >> 63) M = -M;
+  return true;
+}
+
+constexpr int64_t kF64KeyOffset = 4096;   // keeps the msb key positive for atomicMax
+constexpr int64_t kF64EStar = -1074;      // every double is a multiple of 2^-1074
+
+__global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ x, const VOut out,
+                                                  int64_t* meta_out, int w, bool pass1) {
+  const int64_t nvec = out.ld >> 3, rows = out.ny * out.nz, total = rows * nvec;
+  int64_t e_out = 0;
+  if (!pass1) {
+    const int64_t key = meta_out[kMetaMu];
+    const int64_t mu_abs = key > 0 ? key - kF64KeyOffset : kF64EStar + 1;
+    e_out = mu_abs - w;
+  }
+  Red red = {0, 0, 0};
+  bool bad = false;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / nvec, c0 = (idx - row * nvec) << 3;
+    int32_t o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      o[k] = 0;
+      const int64_t c = c0 + k;
+      if (c >= out.nx) continue;
+      int64_t M = 0, E = kF64EStar;
+      if (!f64_split(x[row * out.nx + c], M, E)) { bad = true; continue; }
+      if (pass1) {
+        const int64_t mv = M == 0 ? kF64EStar + 1 : msb64(M) + E;
+        red.key = max(red.key, (long long)(mv + kF64KeyOffset));
+      } else {
+        const int64_t sh = E - e_out;
+        const int64_t v = sh >= 0 ? (int64_t)((uint64_t)M << (sh > 63 ? 63 : sh)) : (M >> (-sh > 63 ? 63 : -sh));
+        o[k] = (int32_t)v;
+        red.nrm = max(red.nrm, (long long)(v < 0 ? -v : v));
+      }
+    }
+    if (!pass1) st8(out, row, c0, o);
+  }
+  if (bad) atomicOr((unsigned long long*)&meta_out[BFP_META_FLAGS], 1ull);
+  block_commit(red, meta_out, nullptr, pass1);
+  if (!pass1 && blockIdx.x == 0 && threadIdx.x == 0) meta_out[0] = e_out;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_to_f64(const VIn x, const int64_t* meta, double* __restrict__ out) {
+  const int64_t rows = x.ny * x.nz, total = rows * x.nx;
+  int64_t e = meta[0];
+  const int ei = (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e));
+  const T* m = reinterpret_cast<const T*>(x.m);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / x.nx, c = idx - row * x.nx;
+    out[idx] = ldexp((double)m[row * x.ld + c], ei);
+  }
+}
+
+// ---- exact dot product (Sec. 2 remark: one wide accumulator, one final shift) ----
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dot(const VIn x, const VIn y, int64_t* out) {
+  const int64_t rows = x.ny * x.nz, total = rows * x.nx;
+  const T* a = reinterpret_cast<const T*>(x.m);
+  const T* b = reinterpret_cast<const T*>(y.m);
+  i128 acc = 0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / x.nx, c = idx - row * x.nx;
+    acc += (i128)((int64_t)a[row * x.ld + c] * (int64_t)b[row * y.ld + c]);
+  }
+  // block reduction of the 128-bit partial sums
+  __shared__ long long s_lo[8], s_hi[8];
+  uint64_t lo = (uint64_t)acc;
+  int64_t hi = (int64_t)(acc >> 64);
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t lo2 = (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)lo, o);
+    int64_t hi2 = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)hi, o);
+    i128 s = (((i128)hi << 64) | (i128)lo) + (((i128)hi2 << 64) | (i128)lo2);
+    lo = (uint64_t)s;
+    hi = (int64_t)(s >> 64);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { s_lo[wid] = (long long)lo; s_hi[wid] = (long long)hi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    i128 s = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += ((i128)s_hi[k] << 64) | (i128)(uint64_t)s_lo[k];
+    // 32-bit limbs: three unsigned, the top one signed (two's complement sums)
+    const u128 u = (u128)s;
+    atomicAdd((unsigned long long*)&out[2], (unsigned long long)(uint32_t)(u));
+    atomicAdd((unsigned long long*)&out[3], (unsigned long long)(uint32_t)(u >> 32));
+    atomicAdd((unsigned long long*)&out[4], (unsigned long long)(uint32_t)(u >> 64));
+    atomicAdd((unsigned long long*)&out[5], (unsigned long long)(int64_t)(s >> 96));
+  }
+}
+
+__global__ void k_dot_finish(const int64_t* mx, const int64_t* my, int64_t* out, int w_out) {
+  const i128 s = (i128)(uint64_t)out[2] + ((i128)(uint64_t)out[3] << 32) + ((i128)(uint64_t)out[4] << 64) +
+                 ((i128)out[5] << 96);
+  const int64_t e_star = mx[0] + my[0];
+  const int mu = msb128(s);
+  const int lam = mu - w_out;   // Alg. qcomp: lambda_out = mu* - w_out
+  i128 m = lam >= 0 ? (s >> lam) : (i128)((u128)s << (-lam));
+  out[0] = (int64_t)m;
+  out[1] = e_star + lam;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* bfp_status_str(int32_t st) {
+  switch (st) {
+    case BFP_OK: return "ok";
+    case BFP_ERR_ARG: return "invalid argument";
+    case BFP_ERR_SHAPE: return "invalid shape, leading dimension or alignment";
+    case BFP_ERR_WIDTH: return "exact intermediate wider than 62 bits";
+    case BFP_ERR_CUDA: return "CUDA runtime error";
+    case BFP_ERR_NONFINITE: return "non-finite FP64 input";
+    case BFP_ERR_TIMEOUT: return "bounded device wait timed out";
+    case BFP_ERR_NOCONV: return "iteration limit reached";
+    default: return "unknown status";
+  }
+}
+
+int32_t bfp_version(void) { return 100; }
+
+int64_t bfp_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int64_t bfp_pitch(int64_t n0) { return n0 <= 0 ? 8 : ((n0 + 7) / 8) * 8; }
+
+int32_t bfp_scalar_from_double(double x, int32_t w, bfp_scalar* out) {
+  if (!out || w < 1 || w > 32 || !std::isfinite(x)) return BFP_ERR_ARG;
+  if (x == 0.0) { out->m = 0; out->e = 0; return BFP_OK; }
+  // exact split x = M 2^E (|M| < 2^53), then the smallest e with floor(x / 2^e) in X_w.
+  // At e0 = msb(M) + E - w - 2 the floor needs >= w + 1 bits, so e0 is below the
+  // minimum; fitting is monotone in e, so the first e that fits is the minimum.
+  int ex = 0;
+  double fm = std::frexp(x, &ex);
+  int64_t M = (int64_t)std::ldexp(fm, 53);
+  int64_t E = ex - 53;
+  int64_t e = (int64_t)hmsb(M) + E - w - 2;
+  int64_t m = 0;
+  for (;;) {
+    int64_t sh = E - e;
+    m = sh >= 0 ? (int64_t)((uint64_t)M << sh) : (sh <= -63 ? (M >> 63) : (M >> (-sh)));
+    if (hmsb(m) <= w) break;
+    ++e;
+  }
+  out->m = m;
+  out->e = e;
+  return BFP_OK;
+}
+
+int32_t bfp_laplace_stencil(int32_t ndim, double omega, int32_t w_omega, bfp_stencil* out) {
+  if (!out || (ndim != 2 && ndim != 3) || !(omega > 0.0)) return BFP_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->ndim = ndim;
+  if (ndim == 2) { out->center = 4; out->nbr = -1; out->e = -2; }
+  else { out->center = 6; out->nbr = -1; out->e = -3; }
+  const double pscale = ndim == 2 ? 4.0 : 8.0;
+  return bfp_scalar_from_double(omega * pscale / (2.0 * ndim), w_omega, &out->omega);
+}
+
+int32_t bfp_normalize(const bfp_vec* x, const bfp_vec* out, const bfp_q* q, const bfp_stats* st,
+                      bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_vec(x)) || (rc = check_vec(out))) return rc;
+  if (!same_shape(x, out)) return BFP_ERR_SHAPE;
+  if (overlaps(x, out)) return BFP_ERR_ARG;
+  QDesc d = blank_desc();
+  if ((rc = fill_q(d, q, out, 2))) return rc;
+  d.meta_a = x->meta;
+  d.meta_out = out->meta;
+  d.stats = st ? st->counters : nullptr;
+  d.ch = 0; d.ha = 1; d.two = 0; d.hbits = x->w;
+  d.ng = 1; d.gv[0] = 0; d.gm[0] = 1; d.ge[0] = 0;   // gamma = ||x||
+  cudaStream_t s = as_stream(stream);
+  if (is32(x)) return launch_quant(OpCopy<int32_t>{vin(x)}, d, out, s);
+  return launch_quant(OpCopy<int16_t>{vin(x)}, d, out, s);
+}
+
+int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y, const bfp_vec* z,
+                 const bfp_q* q, const bfp_stats* st, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_vec(x)) || (rc = check_vec(y)) || (rc = check_vec(z))) return rc;
+  if (!same_shape(x, y) || !same_shape(x, z)) return BFP_ERR_SHAPE;
+  if (is32(x) != is32(y)) return BFP_ERR_ARG;
+  if (overlaps(x, z) || overlaps(y, z)) return BFP_ERR_ARG;
+  if (a.m >= (1ll << 31) || a.m < -(1ll << 31) || b.m >= (1ll << 31) || b.m < -(1ll << 31)) return BFP_ERR_ARG;
+  QDesc d = blank_desc();
+  if ((rc = fill_q(d, q, z, 2))) return rc;
+  d.meta_a = x->meta; d.meta_b = y->meta; d.meta_out = z->meta;
+  d.stats = st ? st->counters : nullptr;
+  d.ch = a.e; d.ha = 1;                 // alpha x at e_alpha + e_x (Alg. eaxpby-setup)
+  d.cl = b.e; d.lb = 1;                 // beta y at e_beta + e_y
+  d.two = 1;
+  d.hbits = hmsb(a.m) + x->w;
+  d.lbits = hmsb(b.m) + y->w;
+  d.ng = 2;                             // gamma = |alpha| ||x|| + |beta| ||y||
+  d.gv[0] = 0; d.gm[0] = (uint64_t)(a.m < 0 ? -a.m : a.m); d.ge[0] = a.e;
+  d.gv[1] = 1; d.gm[1] = (uint64_t)(b.m < 0 ? -b.m : b.m); d.ge[1] = b.e;
+  cudaStream_t s = as_stream(stream);
+  if (is32(x)) return launch_quant(OpAxpy<int32_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
+  return launch_quant(OpAxpy<int16_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
+}
+
+int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream) {
+  int32_t rc;
+  if (!x) return BFP_ERR_ARG;
+  if ((rc = check_vec(out))) return rc;
+  cudaStream_t s = as_stream(stream);
+  VOut o = vout(out);
+  const int64_t items = rows_of(out) * (out->ld / 8);
+  unsigned g = grid_for(items, 256);
+  if (cudaMemsetAsync(out->meta + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess)
+    return BFP_ERR_CUDA;
+  k_from_f64<<<g, 256, 0, s>>>(x, o, out->meta, out->w, true);
+  k_from_f64<<<g, 256, 0, s>>>(x, o, out->meta, out->w, false);
+  note_launches(2);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream) {
+  int32_t rc;
+  if (!out) return BFP_ERR_ARG;
+  if ((rc = check_vec(x))) return rc;
+  cudaStream_t s = as_stream(stream);
+  const int64_t total = rows_of(x) * x->n[0];
+  if (total == 0) return BFP_OK;
+  unsigned g = grid_for(total, 256);
+  if (is32(x)) k_to_f64<int32_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
+  else k_to_f64<int16_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
+  note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_dot(const bfp_vec* x, const bfp_vec* y, int32_t w_out, int64_t* out, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_vec(x)) || (rc = check_vec(y))) return rc;
+  if (!out || w_out < 1 || w_out > 62) return BFP_ERR_ARG;
+  if (!same_shape(x, y) || is32(x) != is32(y)) return BFP_ERR_SHAPE;
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(out, 0, BFP_META_WORDS * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
+  const int64_t total = rows_of(x) * x->n[0];
+  unsigned g = grid_for(total, 256);
+  if (is32(x)) k_dot<int32_t><<<g, 256, 0, s>>>(vin(x), vin(y), out);
+  else k_dot<int16_t><<<g, 256, 0, s>>>(vin(x), vin(y), out);
+  k_dot_finish<<<1, 1, 0, s>>>(x->meta, y->meta, out, w_out);
+  note_launches(2);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+}  // extern "C"

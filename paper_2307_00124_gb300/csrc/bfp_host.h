@@ -1,0 +1,148 @@
+// bfp_host.h -- host-side validation, view construction and launch helpers
+// shared by the C ABI translation units.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "bfp/bfp.h"
+#include "bfp_ops.cuh"
+
+namespace bfp {
+
+// Counts every kernel this library enqueues (directly or into a captured graph).
+void note_launches(int n);
+
+inline cudaStream_t as_stream(bfp_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int hmsb(int64_t z) {  // host msb (Sec. 2 signed width)
+  uint64_t v = (uint64_t)(z ^ (z >> 63));
+  int b = 0;
+  while (v) { ++b; v >>= 1; }
+  return b + 1;
+}
+
+inline int clog2(int64_t m) {
+  int b = 0;
+  uint64_t v = (uint64_t)(m - 1);
+  while (v) { ++b; v >>= 1; }
+  return b;
+}
+
+inline bool is32(const bfp_vec* v) { return v->w > 16; }
+
+inline int32_t check_vec(const bfp_vec* v) {
+  if (!v || !v->mant || !v->meta) return BFP_ERR_ARG;
+  if (v->w < 1 || v->w > 32) return BFP_ERR_ARG;
+  if (v->ndim < 1 || v->ndim > 3) return BFP_ERR_SHAPE;
+  for (int i = 0; i < 3; ++i)
+    if (v->n[i] < 0) return BFP_ERR_SHAPE;
+  for (int i = v->ndim; i < 3; ++i)
+    if (v->n[i] != 1) return BFP_ERR_SHAPE;
+  if (v->ld < v->n[0] || v->ld % 8 != 0 || v->ld <= 0) return BFP_ERR_SHAPE;
+  if (reinterpret_cast<uintptr_t>(v->mant) % 16 != 0) return BFP_ERR_SHAPE;
+  if (reinterpret_cast<uintptr_t>(v->meta) % 8 != 0) return BFP_ERR_SHAPE;
+  return BFP_OK;
+}
+
+inline int64_t rows_of(const bfp_vec* v) { return v->n[1] * v->n[2]; }
+
+inline bool same_shape(const bfp_vec* a, const bfp_vec* b) {
+  return a->ndim == b->ndim && a->n[0] == b->n[0] && a->n[1] == b->n[1] && a->n[2] == b->n[2];
+}
+
+inline bool overlaps(const bfp_vec* a, const bfp_vec* b) {
+  if (!a || !b) return false;
+  const char* a0 = (const char*)a->mant;
+  const char* a1 = a0 + (rows_of(a) * a->ld) * (is32(a) ? 4 : 2);
+  const char* b0 = (const char*)b->mant;
+  const char* b1 = b0 + (rows_of(b) * b->ld) * (is32(b) ? 4 : 2);
+  bool mant = a0 < b1 && b0 < a1 && rows_of(a) > 0 && rows_of(b) > 0;
+  bool meta = (a->meta < b->meta + BFP_META_WORDS) && (b->meta < a->meta + BFP_META_WORDS);
+  return mant || meta;
+}
+
+inline VIn vin(const bfp_vec* v) {
+  VIn r;
+  r.m = v ? v->mant : nullptr;
+  r.ld = v ? v->ld : 8;
+  r.nx = v ? v->n[0] : 0;
+  r.ny = v ? v->n[1] : 1;
+  r.nz = v ? v->n[2] : 1;
+  return r;
+}
+
+inline VOut vout(const bfp_vec* v) {
+  VOut r;
+  r.m = v->mant;
+  r.ld = v->ld;
+  r.nx = v->n[0];
+  r.ny = v->n[1];
+  r.nz = v->n[2];
+  r.is32 = is32(v) ? 1 : 0;
+  return r;
+}
+
+inline int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || cached <= 0)
+      cached = 148;
+  }
+  return cached;
+}
+
+inline unsigned grid_for(int64_t work_items, int threads) {
+  int64_t b = (work_items + threads - 1) / threads;
+  int64_t cap = (int64_t)sm_count() * 8;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// Fills the quantisation fields of a QDesc from a bfp_q; w_add_rule is the
+// op's Table tab:estimates value.
+inline int32_t fill_q(QDesc& d, const bfp_q* q, const bfp_vec* out, int w_add_rule) {
+  if (!q || q->w_out < 1 || q->w_out > 32 || q->w_out != out->w) return BFP_ERR_ARG;
+  if (q->mode != BFP_QCOMP && q->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
+  int w_add = q->w_add < 0 ? w_add_rule : q->w_add;
+  d.mode = q->mode;
+  d.w_out = q->w_out;
+  d.w_tmp = q->w_out + w_add;
+  d.use_tmp = (q->mode == BFP_QCOMP && q->tmp != nullptr && d.w_tmp <= 32) ? 1 : 0;
+  d.tmp = d.use_tmp ? q->tmp : nullptr;
+  if (d.use_tmp && reinterpret_cast<uintptr_t>(q->tmp) % 16 != 0) return BFP_ERR_SHAPE;
+  d.has_gamma = q->has_gamma ? 1 : 0;
+  if (q->has_gamma && q->gamma.m < 0) return BFP_ERR_ARG;
+  d.gamma_m = q->gamma.m;
+  d.gamma_e = q->gamma.e;
+  return BFP_OK;
+}
+
+inline QDesc blank_desc() {
+  QDesc d;
+  std::memset(&d, 0, sizeof(d));
+  return d;
+}
+
+// memset of the output meta's accumulators, then the pass(es) of the op.
+template <class Op>
+inline int32_t launch_quant(const Op& op, const QDesc& q, const bfp_vec* out, cudaStream_t s) {
+  if (q.hbits > 62 || (q.two && q.lbits > 62)) return BFP_ERR_WIDTH;
+  VOut o = vout(out);
+  const int threads = 256;
+  const int64_t items = rows_of(out) * (out->ld / 8);
+  unsigned g = grid_for(items, threads);
+  if (cudaMemsetAsync(q.meta_out + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess)
+    return BFP_ERR_CUDA;
+  if (q.mode == kQcomp) k_quant<Op, true><<<g, threads, 0, s>>>(op, q, o);
+  k_quant<Op, false><<<g, threads, 0, s>>>(op, q, o);
+  note_launches(q.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+}  // namespace bfp

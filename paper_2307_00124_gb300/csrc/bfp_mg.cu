@@ -1,0 +1,543 @@
+// bfp_mg.cu -- BFP multigrid driver: V(nu1,nu2)-cycle (Alg. v-cycle with damped
+// Jacobi), FP64 iterative refinement (Alg. ir with FP64 residual and update),
+// and full multigrid (Alg. fmg).  Host code enqueues stream-ordered launches
+// of the BFP ops; exponents and norms stay on the device.
+#include <cmath>
+#include <cstdlib>
+#include <new>
+#include <vector>
+
+#include "bfp_host.h"
+
+using namespace bfp;
+
+namespace {
+
+// ---- FP64 kernels with a fixed evaluation order --------------------------------
+//
+// The IR residual is r = b' - A' x with b' = s * f (s = h^2 / 2^p, exact) and
+// A'x = c*x + nb*(((W + E) + S) + N [+ B + T]) evaluated with explicitly
+// rounded operations (no contraction), so it is bitwise reproducible on any
+// IEEE-754 machine that evaluates the same sequence.
+
+struct Grid {
+  int64_t nx, ny, nz;
+};
+
+__device__ __forceinline__ double at(const double* __restrict__ x, const Grid& g, int64_t i, int64_t j, int64_t k) {
+  if (i < 0 || i >= g.nx || j < 0 || j >= g.ny || k < 0 || k >= g.nz) return 0.0;
+  return x[i + g.nx * (j + g.ny * k)];
+}
+
+template <int ND>
+__device__ __forceinline__ double ir_res(const double* __restrict__ b, double bscale, const double* __restrict__ x,
+                                         const Grid& g, int64_t i, int64_t j, int64_t k, double cdiag, double cnb) {
+  double s = __dadd_rn(at(x, g, i - 1, j, k), at(x, g, i + 1, j, k));
+  s = __dadd_rn(s, at(x, g, i, j - 1, k));
+  s = __dadd_rn(s, at(x, g, i, j + 1, k));
+  if (ND == 3) {
+    s = __dadd_rn(s, at(x, g, i, j, k - 1));
+    s = __dadd_rn(s, at(x, g, i, j, k + 1));
+  }
+  const int64_t idx = i + g.nx * (j + g.ny * k);
+  const double ax = __dadd_rn(__dmul_rn(cdiag, x[idx]), __dmul_rn(cnb, s));
+  return __dsub_rn(__dmul_rn(b[idx], bscale), ax);
+}
+
+__device__ __forceinline__ bool split_f64(double v, int64_t& M, int64_t& E) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  const uint64_t fr = bits & ((1ull << 52) - 1);
+  if (ex == 0x7ff) return false;
+  if (ex == 0) { M = (int64_t)fr; E = -1074; }
+  else { M = (int64_t)(fr | (1ull << 52)); E = ex - 1075; }
+  if (bits >> 63) M = -M;
+  return true;
+}
+
+constexpr int64_t kKeyOff = 4096;
+
+// Pass 1: max over the residual of msb(M) + E (the quant() normalisation);
+// pass 2: recompute the residual and store floor(r / 2^e_out) as BFP.
+template <int ND, bool PASS1>
+__global__ void __launch_bounds__(256) k_ir_residual(const double* __restrict__ b, double bscale,
+                                                     const double* __restrict__ x, Grid g, double cdiag,
+                                                     double cnb, VOut out, int64_t* meta, int w) {
+  const int64_t nvec = out.ld >> 3, rows = g.ny * g.nz, total = rows * nvec;
+  int64_t e_out = 0;
+  if (!PASS1) {
+    const int64_t key = meta[kMetaMu];
+    e_out = (key > 0 ? key - kKeyOff : -1073) - w;
+  }
+  Red red = {0, 0, 0};
+  bool bad = false;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / nvec, c0 = (idx - row * nvec) << 3;
+    const int64_t j = row % g.ny, k = row / g.ny;
+    int32_t o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      o[q] = 0;
+      const int64_t i = c0 + q;
+      if (i >= g.nx) continue;
+      const double r = ir_res<ND>(b, bscale, x, g, i, j, k, cdiag, cnb);
+      int64_t M = 0, E = -1074;
+      if (!split_f64(r, M, E)) { bad = true; continue; }
+      if (PASS1) {
+        const int64_t mv = M == 0 ? -1073 : msb64(M) + E;
+        red.key = max(red.key, (long long)(mv + kKeyOff));
+      } else {
+        const int64_t sh = E - e_out;
+        const int64_t v = sh >= 0 ? (int64_t)((uint64_t)M << (sh > 63 ? 63 : sh)) : (M >> (-sh > 63 ? 63 : -sh));
+        o[q] = (int32_t)v;
+        red.nrm = max(red.nrm, (long long)(v < 0 ? -v : v));
+      }
+    }
+    if (!PASS1) st8(out, row, c0, o);
+  }
+  if (bad) atomicOr((unsigned long long*)&meta[BFP_META_FLAGS], 1ull);
+  block_commit(red, meta, nullptr, PASS1);
+  if (!PASS1 && blockIdx.x == 0 && threadIdx.x == 0) meta[0] = e_out;
+}
+
+// ||b' - A' x||_inf (for ir_solve's host-side stopping test)
+template <int ND>
+__global__ void __launch_bounds__(256) k_ir_resnorm(const double* __restrict__ b, double bscale,
+                                                    const double* __restrict__ x, Grid g, double cdiag,
+                                                    double cnb, unsigned long long* out) {
+  const int64_t total = g.nx * g.ny * g.nz;
+  double mx = 0.0, mb = 0.0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % g.nx, j = (idx / g.nx) % g.ny, k = idx / (g.nx * g.ny);
+    mx = fmax(mx, fabs(ir_res<ND>(b, bscale, x, g, i, j, k, cdiag, cnb)));
+    mb = fmax(mb, fabs(__dmul_rn(b[idx], bscale)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(mx));   // non-negative doubles order as integers
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(mb));
+  }
+}
+
+// x <- x + m 2^e (the FP64 update of Alg. ir, sign flipped with the residual)
+template <class T>
+__global__ void __launch_bounds__(256) k_ir_update(double* __restrict__ x, const VIn y, const int64_t* meta) {
+  const int64_t total = y.nx * y.ny * y.nz;
+  const int64_t e = meta[0];
+  const int ei = (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e));
+  const T* m = reinterpret_cast<const T*>(y.m);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / y.nx, c = idx - row * y.nx;
+    x[idx] = __dadd_rn(x[idx], ldexp((double)m[row * y.ld + c], ei));
+  }
+}
+
+// b_c = R~ (bscale * b_f), deltas in lexicographic order (outer axis first)
+template <int ND>
+__global__ void __launch_bounds__(256) k_restrict_f64(const double* __restrict__ bf, double bscale, Grid gf,
+                                                      double* __restrict__ bc, Grid gc, double rscale) {
+  const int64_t total = gc.nx * gc.ny * gc.nz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = idx % gc.nx, J = (idx / gc.nx) % gc.ny, K = idx / (gc.nx * gc.ny);
+    double acc = 0.0;
+    const int zr = ND == 3 ? 1 : 0;
+    for (int dz = -zr; dz <= zr; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const double wgt = (double)((2 - abs(dx)) * (2 - abs(dy)) * (ND == 3 ? (2 - abs(dz)) : 1)) * rscale;
+          const int64_t fi = 2 * I + 1 + dx, fj = 2 * J + 1 + dy, fk = ND == 3 ? 2 * K + 1 + dz : 0;
+          const double v = __dmul_rn(bf[fi + gf.nx * (fj + gf.ny * fk)], bscale);
+          acc = __dadd_rn(acc, __dmul_rn(wgt, v));
+        }
+    bc[idx] = acc;
+  }
+}
+
+// ---- hierarchy ---------------------------------------------------------------------
+
+struct Level {
+  int64_t n = 0;
+  bfp_vec r{}, ya{}, yb{}, rv{};  // BFP buffers (mantissa + meta)
+  void* tmp = nullptr;            // qcomp window (int32)
+  double* b = nullptr;            // FP64 right-hand side (levels >= 1)
+  double* x = nullptr;            // FP64 iterate (levels >= 1)
+};
+
+}  // namespace
+
+struct bfp_hierarchy {
+  bfp_solver_opts o;
+  bfp_stencil A;
+  std::vector<Level> lv;
+  std::vector<void*> allocs;
+  uint64_t* stats = nullptr;
+  unsigned long long* norms = nullptr;   // 2 words for the residual norm
+  bfp_vec y0{};                          // spare finest-level buffer for ir steps
+  // captured IR step
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_f = nullptr;
+  double* graph_x = nullptr;
+  cudaStream_t graph_stream = nullptr;
+};
+
+namespace {
+
+void* dalloc(bfp_hierarchy* h, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes < 16 ? 16 : bytes) != cudaSuccess) return nullptr;
+  h->allocs.push_back(p);
+  return p;
+}
+
+bool make_vec(bfp_hierarchy* h, bfp_vec& v, int nd, int64_t n, int w) {
+  std::memset(&v, 0, sizeof(v));
+  v.w = w;
+  v.ndim = nd;
+  v.n[0] = n; v.n[1] = n; v.n[2] = nd == 3 ? n : 1;
+  v.ld = bfp_pitch(n);
+  const size_t bytes = (size_t)(v.n[1] * v.n[2] * v.ld) * (w > 16 ? 4 : 2);
+  v.mant = dalloc(h, bytes);
+  v.meta = (int64_t*)dalloc(h, BFP_META_WORDS * sizeof(int64_t));
+  if (!v.mant || !v.meta) return false;
+  cudaMemset(v.mant, 0, bytes);
+  cudaMemset(v.meta, 0, BFP_META_WORDS * sizeof(int64_t));
+  return true;
+}
+
+inline double pscale(int nd) { return nd == 2 ? 4.0 : 8.0; }
+
+struct Q {
+  bfp_q q;
+  bfp_stats st;
+};
+
+Q make_q(const bfp_hierarchy* h, const Level& L) {
+  Q r;
+  std::memset(&r, 0, sizeof(r));
+  r.q.w_out = h->o.w;
+  r.q.w_add = -1;
+  r.q.mode = h->o.mode;
+  r.q.tmp = (h->o.mode == BFP_QCOMP && h->o.use_tmp) ? L.tmp : nullptr;
+  r.st.counters = h->stats;
+  return r;
+}
+
+#define TRY(x)                         \
+  do {                                 \
+    int32_t _rc = (x);                 \
+    if (_rc != BFP_OK) return _rc;     \
+  } while (0)
+
+// V(nu1, nu2) on level k: y_out receives the approximate solution of A' y = r.
+// Returns which buffer holds the result through *res.
+int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, bfp_vec* bufA, bfp_vec* bufB,
+                   const bfp_vec** res, cudaStream_t s) {
+  Level& L = h->lv[k];
+  Q q = make_q(h, L);
+  const bool coarsest = (k + 1 == (int)h->lv.size());
+  const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
+  // writes per level: 1 (omega r) + (nu1 - 1) sweeps [+ correction + nu2 sweeps]
+  const int writes = coarsest ? nu1 : (nu1 + 1 + h->o.nu2);
+  // choose the first target so that the last write lands in bufA
+  bfp_vec* cur = (writes % 2 == 1) ? bufA : bufB;
+  bfp_vec* oth = (cur == bufA) ? bufB : bufA;
+  TRY(bfp_jacobi(&h->A, nullptr, r, cur, &q.q, &q.st, s));            // relaxation from y = 0
+  for (int i = 1; i < nu1; ++i) {
+    TRY(bfp_jacobi(&h->A, cur, r, oth, &q.q, &q.st, s));
+    std::swap(cur, oth);
+  }
+  if (!coarsest) {
+    Level& C = h->lv[k + 1];
+    TRY(bfp_residual(&h->A, cur, r, &L.rv, &q.q, &q.st, s));           // r_v = A y - r
+    TRY(bfp_restrict(&L.rv, &C.r, &q.q, &q.st, s));                    // r_c = R~ r_v
+    const bfp_vec* d = nullptr;
+    TRY(vcycle_rec(h, k + 1, &C.r, &C.ya, &C.yb, &d, s));              // d = V(r_c)
+    TRY(bfp_prolong(d, cur, oth, &q.q, &q.st, s));                     // y = y - P d
+    std::swap(cur, oth);
+    for (int i = 0; i < h->o.nu2; ++i) {
+      TRY(bfp_jacobi(&h->A, cur, r, oth, &q.q, &q.st, s));
+      std::swap(cur, oth);
+    }
+  }
+  *res = cur;
+  return BFP_OK;
+}
+
+Grid grid_of(int nd, int64_t n) { return Grid{n, n, nd == 3 ? n : 1}; }
+
+// r (BFP, width w, normalised) = quant(b' - A' x) on level k (Alg. ir residual line)
+int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, const double* x, const bfp_vec* r,
+                      cudaStream_t s) {
+  const int nd = h->o.ndim;
+  const Grid g = grid_of(nd, h->lv[k].n);
+  const double cdiag = (2.0 * nd) / pscale(nd), cnb = -1.0 / pscale(nd);
+  VOut o = vout(r);
+  const int64_t items = rows_of(r) * (r->ld / 8);
+  const unsigned gr = grid_for(items, 256);
+  if (cudaMemsetAsync(r->meta + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (nd == 2) {
+    k_ir_residual<2, true><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
+    k_ir_residual<2, false><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
+  } else {
+    k_ir_residual<3, true><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
+    k_ir_residual<3, false><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
+  }
+  note_launches(2);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t ir_update(double* x, const bfp_vec* y, cudaStream_t s) {
+  const int64_t total = y->n[0] * y->n[1] * y->n[2];
+  if (total == 0) return BFP_OK;
+  if (y->w > 16) k_ir_update<int32_t><<<grid_for(total, 256), 256, 0, s>>>(x, vin(y), y->meta);
+  else k_ir_update<int16_t><<<grid_for(total, 256), 256, 0, s>>>(x, vin(y), y->meta);
+  note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double* x, cudaStream_t s) {
+  Level& L = h->lv[k];
+  TRY(ir_residual_q(h, k, b, bscale, x, &L.r, s));
+  bfp_vec* A = (k == 0) ? &h->y0 : &L.ya;
+  bfp_vec* B = &L.yb;
+  const bfp_vec* y = nullptr;
+  TRY(vcycle_rec(h, k, &L.r, A, B, &y, s));
+  return ir_update(x, y, s);
+}
+
+double bscale_of(int nd, int64_t n) {
+  const double hh = 1.0 / (double)(n + 1);
+  return hh * hh / pscale(nd);   // an exact power of two for n + 1 = 2^J
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_opts* o) {
+  if (!o || (ndim != 2 && ndim != 3)) return BFP_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->ndim = ndim;
+  o->n = n;
+  o->w = w;
+  o->mode = BFP_QCOMP;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->coarse_sweeps = 32;
+  o->n_fmg = 2;
+  o->omega = ndim == 2 ? 0.8 : 6.0 / 7.0;
+  o->w_omega = 16;
+  o->use_tmp = 1;
+  o->use_graph = 1;
+  return BFP_OK;
+}
+
+void bfp_hierarchy_destroy(bfp_hierarchy* h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
+  if (!o || !out) return BFP_ERR_ARG;
+  *out = nullptr;
+  if ((o->ndim != 2 && o->ndim != 3) || o->w < 1 || o->w > 32) return BFP_ERR_ARG;
+  if (o->nu1 < 1 || o->nu2 < 0 || o->coarse_sweeps < 1 || o->n_fmg < 1) return BFP_ERR_ARG;
+  if (o->mode != BFP_QCOMP && o->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
+  // n = 2^J - 1 with J >= 2
+  if (o->n < 3 || ((o->n + 1) & o->n) != 0) return BFP_ERR_SHAPE;
+  bfp_hierarchy* h = new (std::nothrow) bfp_hierarchy();
+  if (!h) return BFP_ERR_ARG;
+  h->o = *o;
+  int32_t rc = bfp_laplace_stencil(o->ndim, o->omega, o->w_omega, &h->A);
+  if (rc) { delete h; return rc; }
+  for (int64_t n = o->n; n >= 3; n = (n - 1) / 2) {
+    Level L;
+    L.n = n;
+    h->lv.push_back(L);
+    if (n == 3) break;
+  }
+  const int nd = o->ndim;
+  bool ok = true;
+  for (size_t k = 0; k < h->lv.size() && ok; ++k) {
+    Level& L = h->lv[k];
+    ok = make_vec(h, L.r, nd, L.n, o->w) && make_vec(h, L.ya, nd, L.n, o->w) && make_vec(h, L.yb, nd, L.n, o->w) &&
+         make_vec(h, L.rv, nd, L.n, o->w);
+    const int64_t pts = L.n * L.n * (nd == 3 ? L.n : 1);
+    if (ok && o->mode == BFP_QCOMP && o->use_tmp) {
+      L.tmp = dalloc(h, (size_t)(L.r.n[1] * L.r.n[2] * L.r.ld) * 4);
+      ok = L.tmp != nullptr;
+    }
+    if (ok && k > 0) {
+      L.b = (double*)dalloc(h, pts * sizeof(double));
+      L.x = (double*)dalloc(h, pts * sizeof(double));
+      ok = L.b && L.x;
+    }
+  }
+  ok = ok && make_vec(h, h->y0, nd, o->n, o->w);
+  if (ok) {
+    h->stats = (uint64_t*)dalloc(h, 8 * sizeof(uint64_t));
+    h->norms = (unsigned long long*)dalloc(h, 2 * sizeof(unsigned long long));
+    ok = h->stats && h->norms;
+    if (ok) cudaMemset(h->stats, 0, 8 * sizeof(uint64_t));
+  }
+  if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+    bfp_hierarchy_destroy(h);
+    return BFP_ERR_CUDA;
+  }
+  *out = h;
+  return BFP_OK;
+}
+
+int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream) {
+  if (!h || !host8) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemcpyAsync(host8, h->stats, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return BFP_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream) {
+  if (!h) return BFP_ERR_ARG;
+  return cudaMemsetAsync(h->stats, 0, 8 * sizeof(uint64_t), as_stream(stream)) == cudaSuccess ? BFP_OK
+                                                                                               : BFP_ERR_CUDA;
+}
+
+int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_stream stream) {
+  if (!h || !r || !y) return BFP_ERR_ARG;
+  int32_t rc;
+  if ((rc = check_vec(r)) || (rc = check_vec(y))) return rc;
+  const Level& L = h->lv[0];
+  if (r->w != h->o.w || y->w != h->o.w || r->n[0] != L.n || !same_shape(r, &L.r) || !same_shape(y, &L.r))
+    return BFP_ERR_SHAPE;
+  if (overlaps(r, y)) return BFP_ERR_ARG;
+  bfp_vec yv = *y;
+  const bfp_vec* res = nullptr;
+  return vcycle_rec(h, 0, r, &yv, &h->y0, &res, as_stream(stream));
+}
+
+static int32_t ir_iterate_direct(bfp_hierarchy* h, const double* f, double* x, int32_t k, cudaStream_t s) {
+  const double bs = bscale_of(h->o.ndim, h->o.n);
+  for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));
+  return BFP_OK;
+}
+
+int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k, bfp_stream stream) {
+  if (!h || !f || !x || k < 0) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (k == 0) return BFP_OK;
+  if (!h->o.use_graph || s == nullptr) return ir_iterate_direct(h, f, x, k, s);
+  // one IR step captured once per (f, x, stream) and replayed
+  if (!h->graph || h->graph_f != f || h->graph_x != x || h->graph_stream != s) {
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BFP_ERR_CUDA;
+    int32_t rc = ir_iterate_direct(h, f, x, 1, s);
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (rc != BFP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess) return BFP_ERR_CUDA;
+    ce = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { h->graph = nullptr; return BFP_ERR_CUDA; }
+    h->graph_f = f; h->graph_x = x; h->graph_stream = s;
+  }
+  for (int i = 0; i < k; ++i)
+    if (cudaGraphLaunch(h->graph, s) != cudaSuccess) return BFP_ERR_CUDA;
+  return BFP_OK;
+}
+
+int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream) {
+  if (!h || !f || !x) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  const int nd = h->o.ndim;
+  const int nl = (int)h->lv.size();
+  const double rscale = nd == 2 ? 0.25 : 0.0625;   // R~ = P^T (2D), P^T/2 (3D): weights prod(2-|d|) * 2^e_R
+  const double bs0 = bscale_of(nd, h->o.n);
+  // right-hand sides b_k = R~ b_{k-1}, b_0 = s f
+  for (int k = 1; k < nl; ++k) {
+    const Level& F = h->lv[k - 1];
+    Level& Cc = h->lv[k];
+    const double* bf = (k == 1) ? f : F.b;
+    const double sc = (k == 1) ? bs0 : 1.0;
+    const int64_t tot = Cc.n * Cc.n * (nd == 3 ? Cc.n : 1);
+    if (nd == 2) k_restrict_f64<2><<<grid_for(tot, 256), 256, 0, s>>>(bf, sc, grid_of(nd, F.n), Cc.b, grid_of(nd, Cc.n), rscale);
+    else k_restrict_f64<3><<<grid_for(tot, 256), 256, 0, s>>>(bf, sc, grid_of(nd, F.n), Cc.b, grid_of(nd, Cc.n), rscale);
+    note_launches(1);
+  }
+  for (int k = nl - 1; k >= 0; --k) {
+    Level& L = h->lv[k];
+    double* xk = (k == 0) ? x : L.x;
+    const int64_t tot = L.n * L.n * (nd == 3 ? L.n : 1);
+    if (k == nl - 1) {
+      if (cudaMemsetAsync(xk, 0, tot * sizeof(double), s) != cudaSuccess) return BFP_ERR_CUDA;
+    } else {
+      // x_k = P x_{k+1} at width w (Alg. fmg interpolation line, qspmv)
+      Level& Cc = h->lv[k + 1];
+      TRY(bfp_from_f64(Cc.x, &Cc.ya, s));
+      Q q = make_q(h, L);
+      bfp_vec* xf = (k == 0) ? &h->y0 : &L.ya;
+      TRY(bfp_prolong(&Cc.ya, nullptr, xf, &q.q, &q.st, s));
+      TRY(bfp_to_f64(xf, xk, s));
+    }
+    const double* bk = (k == 0) ? f : L.b;
+    const double sc = (k == 0) ? bs0 : 1.0;
+    for (int i = 0; i < h->o.n_fmg; ++i) TRY(ir_step(h, k, bk, sc, xk, s));
+  }
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_ir_residual(bfp_hierarchy* h, const double* f, const double* x, const bfp_vec* r, bfp_stream stream) {
+  if (!h || !f || !x || !r) return BFP_ERR_ARG;
+  int32_t rc;
+  if ((rc = check_vec(r))) return rc;
+  if (!same_shape(r, &h->lv[0].r)) return BFP_ERR_SHAPE;
+  return ir_residual_q(h, 0, f, bscale_of(h->o.ndim, h->o.n), x, r, as_stream(stream));
+}
+
+int32_t bfp_ir_update(double* x, const bfp_vec* y, bfp_stream stream) {
+  if (!x) return BFP_ERR_ARG;
+  int32_t rc;
+  if ((rc = check_vec(y))) return rc;
+  return ir_update(x, y, as_stream(stream));
+}
+
+int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts* o, bfp_ir_report* rep,
+                 bfp_stream stream) {
+  if (!h || !f || !x || !o || !rep) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  std::memset(rep, 0, sizeof(*rep));
+  if (o->fmg_start) TRY(bfp_fmg(h, f, x, s));
+  const int nd = h->o.ndim;
+  const Grid g = grid_of(nd, h->o.n);
+  const double cdiag = (2.0 * nd) / pscale(nd), cnb = -1.0 / pscale(nd);
+  const double bs = bscale_of(nd, h->o.n);
+  const int64_t tot = g.nx * g.ny * g.nz;
+  for (int it = 0;; ++it) {
+    if (cudaMemsetAsync(h->norms, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return BFP_ERR_CUDA;
+    if (nd == 2) k_ir_resnorm<2><<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, g, cdiag, cnb, h->norms);
+    else k_ir_resnorm<3><<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, g, cdiag, cnb, h->norms);
+    note_launches(1);
+    unsigned long long hn[2] = {0, 0};
+    if (cudaMemcpyAsync(hn, h->norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BFP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BFP_ERR_CUDA;
+    double rn, bn;
+    std::memcpy(&rn, &hn[0], 8);
+    std::memcpy(&bn, &hn[1], 8);
+    rep->iterations = it;
+    rep->res_inf = rn;
+    rep->res0_inf = bn;
+    if (rn <= o->tol * bn) { rep->converged = 1; return BFP_OK; }
+    if (it >= o->max_iter) return BFP_ERR_NOCONV;
+    TRY(ir_step(h, 0, f, bs, x, s));
+  }
+}
+
+}  // extern "C"

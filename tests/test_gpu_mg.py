@@ -1,0 +1,93 @@
+"""Whole-solve parity of the CUDA multigrid (V-cycle, IR, FMG) with the oracle schedule."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import paper_2307_00124_gb300 as bfp  # noqa: E402
+from bfp_inputs import manufactured_rhs, random_mantissas  # noqa: E402
+from oracle import bfp as B  # noqa: E402
+from oracle import mg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def make(nd, n, w, mode, use_tmp=1, use_graph=1):
+    o = bfp.bfp_solver_opts_default(nd, n, w)
+    o.mode = mode
+    o.use_tmp = use_tmp
+    o.use_graph = use_graph
+    h = bfp.Hierarchy(o)
+    s = mg.BFPSolver(nd, n, w=w, mode="qcomp" if mode == bfp.QCOMP else "nnqcomp",
+                     omega=o.omega, w_omega=o.w_omega)
+    return h, s
+
+
+@pytest.mark.parametrize("nd,n", [(2, 63), (2, 31), (3, 15)])
+@pytest.mark.parametrize("w", [8, 16, 32])
+@pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
+def test_vcycle_bit_exact(nd, n, w, mode):
+    h, s = make(nd, n, w, mode)
+    rm = random_mantissas((n,) * nd, w, 5, "smooth")
+    r = bfp.BFPVector.from_mantissas(rm, -30, w)
+    y = bfp.BFPVector((n,) * nd, w)
+    h.vcycle(r, y)
+    ref = s.vcycle(0, B.BFP(rm, -30, w))
+    torch.cuda.synchronize()
+    assert y.exponent == ref.e
+    assert np.array_equal(y.mantissas(), np.asarray(ref.m).astype(np.int64))
+    st = h.stats()
+    assert st["calls"] == s.stats.calls
+    assert (st["recomputed"], st["saturated"]) == (s.stats.recomputed, s.stats.saturated)
+
+
+@pytest.mark.parametrize("nd,n,w", [(2, 63, 16), (2, 63, 8), (2, 127, 24), (3, 15, 16)])
+@pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
+def test_fmg_and_ir_bit_exact(nd, n, w, mode):
+    """C1: FMG then IR-V steps; the FP64 iterate must match the oracle bit for bit."""
+    h, s = make(nd, n, w, mode)
+    f = manufactured_rhs(nd, n)
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.fmg(ft, xt)
+    stream.synchronize()
+    xr = s.fmg(f)
+    assert np.array_equal(xt.cpu().numpy(), xr)
+    b = s.rhs_hierarchy(f)[0]
+    for it in range(3):
+        with torch.cuda.stream(stream):
+            h.ir_iterate(ft, xt, 1)
+        stream.synchronize()
+        xr = s.ir_step(0, b, xr)
+        assert np.array_equal(xt.cpu().numpy(), xr), it
+    if nd == 2 and w >= 16:
+        assert mg.accuracy_ratio(nd, xt.cpu().numpy()) <= 1.5
+
+
+def test_ir_solve_reaches_tolerance():
+    h, s = make(2, 255, 16, bfp.QCOMP)
+    f = manufactured_rhs(2, 255)
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    # the FP64 residual of A' x has a rounding floor near 5e-12 relative to ||b'|| at h = 1/256
+    rep = h.ir_solve(ft, xt, max_iter=30, tol=1e-10)
+    assert rep.converged and rep.iterations <= 12
+    assert rep.res_inf <= 1e-10 * rep.res0_inf
+    uh = mg.discrete_solution(2, 255)
+    x = xt.cpu().numpy()
+    assert np.abs(x - uh).max() <= 1e-6 * np.abs(uh).max()
+    assert mg.accuracy_ratio(2, x) <= 1.001
+
+
+def test_graph_and_direct_ir_agree():
+    hg, _ = make(2, 127, 16, bfp.NNQCOMP, use_graph=1)
+    hd, _ = make(2, 127, 16, bfp.NNQCOMP, use_graph=0)
+    f = torch.from_numpy(manufactured_rhs(2, 127)).cuda()
+    xg, xd = torch.zeros_like(f), torch.zeros_like(f)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        hg.ir_iterate(f, xg, 4)
+        hd.ir_iterate(f, xd, 4)
+    st.synchronize()
+    assert torch.equal(xg, xd)
