@@ -39,6 +39,10 @@ def parse():
     p.add_argument("--w", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--op", default=None, choices=[None, "jacobi", "residual", "restrict", "prolong", "ir_residual",
+                                                  "ir_update", "step"],
+                   help="run one finest-level op --reps times and exit (profiling driver)")
+    p.add_argument("--reps", type=int, default=3)
     return p.parse_args()
 
 
@@ -209,6 +213,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     t = e0.elapsed_time(e1) / 1e3
+    h.reset_stats()
+    with torch.cuda.stream(stream):
+        h.ir_iterate(f, x, 2)
+    stream.synchronize()
+    op_stats = h.stats()
     if ws > 1:
         tt = torch.tensor([t], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -295,6 +304,7 @@ def run_ours(args):
                        else "single GPU"},
             "roofline": roof, "kernels": kern_out, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches_per_step * args.steps),
+            "op_stats_2_steps": op_stats,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -302,8 +312,50 @@ def run_ours(args):
     h.close()
 
 
+def run_op(args):
+    """Runs one op of the finest level --reps times (the launch configuration the step uses)."""
+    import numpy as np
+    import torch
+    import paper_2307_00124_gb300 as bfp
+    from bfp_inputs import manufactured_rhs
+    nd, n, w = 2, args.n, args.w
+    mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
+    o = bfp.bfp_solver_opts_default(nd, n, w)
+    o.mode = mode
+    h = bfp.Hierarchy(o)
+    f = torch.from_numpy(manufactured_rhs(nd, n)).cuda()
+    x = torch.zeros_like(f)
+    A = bfp.bfp_laplace_stencil(nd, o.omega, o.w_omega)
+    rng = np.random.default_rng(0)
+    ym = rng.integers(-(1 << 12), 1 << 12, size=(n, n))
+    y = bfp.BFPVector.from_mantissas(ym, -20, w)
+    r = bfp.BFPVector.from_mantissas(ym[::-1].copy(), -19, w)
+    yo = bfp.BFPVector((n, n), w)
+    nc = (n - 1) // 2
+    yc = bfp.BFPVector((nc, nc), w)
+    d = bfp.BFPVector.from_mantissas(ym[:nc, :nc].copy(), -18, w)
+    q = bfp.q(w, mode)
+    ops = {
+        "jacobi": lambda: bfp.bfp_jacobi(A, y, r, yo, q),
+        "residual": lambda: bfp.bfp_residual(A, y, r, yo, q),
+        "restrict": lambda: bfp.bfp_restrict(y, yc, q),
+        "prolong": lambda: bfp.bfp_prolong(d, y, yo, q),
+        "ir_residual": lambda: h.ir_residual(f, x, yo),
+        "ir_update": lambda: bfp.bfp_ir_update(x, y),
+        "step": lambda: h.ir_iterate(f, x, 1),
+    }
+    for _ in range(args.reps):
+        ops[args.op]()
+    torch.cuda.synchronize()
+    print(json.dumps({"op": args.op, "reps": args.reps, "n": n, "w": w, "mode": args.mode}))
+    h.close()
+
+
 def main():
     args = parse()
+    if args.op:
+        run_op(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

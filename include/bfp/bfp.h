@@ -227,8 +227,10 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
 int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** h);
 void bfp_hierarchy_destroy(bfp_hierarchy* h);
 
-/* Copies the hierarchy's device counters (bfp_stats layout, uint64[8]) to
- * host memory; synchronises the stream.  bfp_hierarchy_reset_stats zeroes
+/* Copies the hierarchy's device counters (bfp_stats layout, uint64[8], plus
+ * [5] FP64 IR residual quantisations and [6] of those that recomputed the
+ * residual because the Alg. qcomp window missed) to host memory;
+ * synchronises the stream.  bfp_hierarchy_reset_stats zeroes
  * them (asynchronously). */
 int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream);
 int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream);

@@ -328,7 +328,7 @@ class Hierarchy:
     def stats(self, stream=None) -> dict:
         host = (C.c_uint64 * 8)()
         _check(_lib.bfp_hierarchy_read_stats(self.h, host, _stream(stream)), "bfp_hierarchy_read_stats")
-        keys = ("calls", "recomputed", "overflow", "underflow", "saturated")
+        keys = ("calls", "recomputed", "overflow", "underflow", "saturated", "ir_residuals", "ir_recomputed")
         return {k: int(host[i]) for i, k in enumerate(keys)}
 
     def reset_stats(self, stream=None):

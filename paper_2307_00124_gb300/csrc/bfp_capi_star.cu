@@ -1,6 +1,6 @@
 // bfp_capi_star.cu -- C ABI: star-stencil ops (Alg. espmv / egemv on the
 // 5- and 7-point Laplacian): bfp_stencil_apply, bfp_residual, bfp_jacobi.
-#include "bfp_host.h"
+#include "bfp_star2d.cuh"
 
 using namespace bfp;
 
@@ -17,6 +17,10 @@ int32_t check_stencil(const bfp_stencil* A, const bfp_vec* v) {
 template <int KIND, int ND>
 int32_t star_launch(const bfp_vec* yv, const bfp_vec* rv, const QDesc& d, const bfp_vec* out, int64_t c,
                     int64_t n, int64_t mw, bool wide_in, cudaStream_t s) {
+  if (ND == 2) {
+    if (wide_in) return launch_star2d<int32_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
+    return launch_star2d<int16_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
+  }
   if (wide_in) {
     OpStar<int32_t, KIND, ND> op{vin(yv), vin(rv), c, n, mw};
     return launch_quant(op, d, out, s);

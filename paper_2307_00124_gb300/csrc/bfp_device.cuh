@@ -211,6 +211,30 @@ __device__ __forceinline__ void plan_from_mu(Plan& p, int64_t key) {
   p.narrow = p.use_tmp && !p.guarded && !p.overflow && !p.underflow;
 }
 
+// Register-resident fast path of one op: valid when the exact integer
+// Z = (H << dh) + (L << dl) fits in int64 (no wide / guarded combine) and the
+// output (or window) exponent is at or above Ez, so every element needs only
+// shifts by uniform amounts, a clamp and a bit width.
+struct Fast {
+  int32_t ok;           // fast path usable
+  int32_t dh, dl;       // left shifts of H and L into Z (one of them is 0)
+  int32_t t;            // Z >> t gives the result (pass 2 / nnqcomp) or the window (pass 1)
+  int32_t w;            // width that result / window is reduced to
+  int32_t clamp;        // nnqcomp saturation (qcomp results fit by construction)
+};
+
+__device__ __forceinline__ Fast make_fast(const Plan& p, bool pass1) {
+  Fast f;
+  const int64_t t = pass1 ? (p.e_tmp - p.Ez) : (p.e_out - p.Ez);
+  f.ok = (!p.wide && !p.guarded && (t >= 0 || (pass1 && !p.use_tmp))) ? 1 : 0;
+  f.dh = (p.two && p.top_is_h) ? p.s_top : 0;
+  f.dl = (p.two && !p.top_is_h) ? p.s_top : 0;
+  f.t = (int32_t)(t < 0 ? 0 : (t > 63 ? 63 : t));
+  f.w = pass1 ? p.w_tmp : p.w_out;
+  f.clamp = (!pass1 && p.mode == kNnqcomp) ? 1 : 0;
+  return f;
+}
+
 // ---------------------------------------------------------------------------
 // Per-element steps
 // ---------------------------------------------------------------------------

@@ -1,0 +1,232 @@
+// bfp_ir2d.cuh -- FP64 iterative-refinement kernels for the 2D finest levels.
+//
+// Residual r = b' - A' x quantised to a normalised BFP block (Alg. ir residual
+// line with FP64 arithmetic): r is evaluated with explicitly rounded
+// operations in a fixed order, so it is bitwise reproducible.  The
+// quantisation follows Alg. qcomp: pass 1 finds mu* = max_i (msb(M_i) + E_i)
+// and stores a w_tmp-bit window guessed from gamma = the previous residual's
+// norm (Table tab:estimates, IR residual row, w_add = 4); pass 2 narrows the
+// window when it captured every significant bit and otherwise recomputes r.
+//
+// Layout: FP64 vectors are dense (row stride n), so a lane owns the
+// interleaved columns cb + 32 k + lane (k < kIrV): every warp access is a
+// contiguous 256-byte line whatever the row alignment.  A warp walks a strip
+// of rows keeping x rows j-1, j, j+1 (and j+2, prefetched) in registers.
+#pragma once
+
+#include "bfp_host.h"
+
+namespace bfp {
+
+constexpr int kIrV = 2;            // doubles per lane
+constexpr int kIrCols = 32 * kIrV;
+constexpr int kIrWarps = 4;
+constexpr int64_t kIrKeyOff = 4096;
+
+struct IrArgs {
+  const double* b;   // right-hand side (scaled by bscale on the fly)
+  double bscale;     // 2^-bshift
+  int32_t bshift;
+  int32_t nbshift;   // nb = -2^-nbshift
+  const double* x;
+  int64_t nx, ny;
+  double cdiag, cnb;
+  VOut out;          // BFP residual
+  int64_t* meta;     // its meta block
+  int32_t* tmp;      // qcomp window (int32, out layout) or null
+  int64_t* gamma_mu; // previous residual's mu* (+ offset; 0 = unknown) in / out
+  uint64_t* stats;   // [5] IR residual quantisations, [6] of which recomputed
+  int w, w_tmp;
+};
+
+__device__ __forceinline__ bool split_double(double v, int64_t& M, int64_t& E) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  const uint64_t fr = bits & ((1ull << 52) - 1);
+  if (ex == 0x7ff) return false;
+  if (ex == 0) { M = (int64_t)fr; E = -1074; }
+  else { M = (int64_t)(fr | (1ull << 52)); E = ex - 1075; }
+  if (bits >> 63) M = -M;
+  return true;
+}
+
+// Rare-case fallbacks kept out of line: inlined, the compiler would evaluate
+// them speculatively and occupy GB300's low-rate FP64 pipe on every element.
+__device__ __noinline__ double dmul_slow(double v, double factor) { return __dmul_rn(v, factor); }
+__device__ __noinline__ double ldexp_slow(int32_t m, int64_t e) {
+  return ldexp((double)m, (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e)));
+}
+
+// v * 2^-k for k >= 0 (exact): exponent-field arithmetic when v and the result
+// are normal, the rounded multiply otherwise (zeros, subnormals, Inf/NaN).
+// Either way the result equals __dmul_rn(v, 2^-k) bit for bit.
+__device__ __forceinline__ double scale_pow2(double v, int k, double factor) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex > k && ex != 0x7ff) return __longlong_as_double((long long)(bits - ((uint64_t)k << 52)));
+  return dmul_slow(v, factor);
+}
+
+// m * 2^e as a double, exact for |m| < 2^31 whenever the result is normal
+// (built from its bits); otherwise ldexp.
+__device__ __forceinline__ double mant_pow2(int32_t m, int64_t e) {
+  if (m == 0) return 0.0;
+  const uint64_t sign = m < 0 ? (1ull << 63) : 0ull;
+  const uint32_t a = m < 0 ? (uint32_t)(-(int64_t)m) : (uint32_t)m;
+  const int lz = __clz(a);                                  // a has 32 - lz significant bits
+  const int64_t be = e + (31 - lz) + 1023;                   // biased exponent of the leading bit
+  if (be >= 1 && be <= 2046) {
+    const uint64_t frac = (((uint64_t)a << (lz + 1)) & 0xffffffffull) << 20;   // bits below the leading one
+    return __longlong_as_double((long long)(sign | ((uint64_t)be << 52) | frac));
+  }
+  return ldexp_slow(m, e);
+}
+
+// floor(M 2^sh) for any sh (caller guarantees the fit when sh > 0)
+__device__ __forceinline__ int64_t fshift(int64_t M, int64_t sh) {
+  if (sh >= 0) return (int64_t)((uint64_t)M << (sh > 63 ? 63 : sh));
+  return M >> (-sh > 63 ? 63 : -sh);
+}
+
+struct IrPlan {
+  int64_t e_out, e_tmp, gam;
+  int32_t window, narrow, recompute;
+};
+
+template <bool PASS1>
+__global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
+  __shared__ IrPlan sp;
+  if (threadIdx.x == 0) {
+    IrPlan p;
+    const int64_t g = PASS1 ? *a.gamma_mu : a.meta[4];
+    p.window = (a.tmp != nullptr && g != 0) ? 1 : 0;
+    p.gam = g - (int64_t(1) << 40);              // msb value of gamma (encoded with an offset)
+    p.e_tmp = p.gam - a.w_tmp;
+    p.e_out = 0;
+    p.narrow = 0;
+    p.recompute = 1;
+    if (!PASS1) {
+      const int64_t key = a.meta[kMetaMu];
+      const int64_t mu_abs = key > 0 ? key - kIrKeyOff : -1073;
+      p.e_out = mu_abs - a.w;
+      const bool ovf = p.gam < mu_abs, unf = (mu_abs - a.w) < (p.gam - a.w_tmp);
+      p.narrow = (p.window && !ovf && !unf) ? 1 : 0;
+      p.recompute = !p.narrow;
+    }
+    sp = p;
+  }
+  __syncthreads();
+  const IrPlan& p = sp;
+  if (PASS1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.meta[4] = *a.gamma_mu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t cb = (int64_t)blockIdx.x * kIrCols;
+  const int64_t j0 = ((int64_t)blockIdx.y * kIrWarps + warp) * rs;
+  const int64_t j1 = j0 + rs < a.ny ? j0 + rs : a.ny;
+  Red red = {0, 0, 0};
+  bool bad = false;
+  const int64_t nx = a.nx;
+
+  if (!PASS1 && p.narrow) {
+    for (int64_t j = j0; j < j1; ++j) {
+#pragma unroll
+      for (int k = 0; k < kIrV; ++k) {
+        const int64_t i = cb + 32 * k + lane;
+        if (i < a.out.ld) {   // padding columns [nx, ld) are written as 0
+          const int32_t v = i < nx ? a.tmp[j * a.out.ld + i] >> (int)(p.e_out - p.e_tmp) : 0;
+          red.nrm = max(red.nrm, (long long)(v < 0 ? -(long long)v : (long long)v));
+          if (a.out.is32) reinterpret_cast<int32_t*>(a.out.m)[j * a.out.ld + i] = v;
+          else reinterpret_cast<int16_t*>(a.out.m)[j * a.out.ld + i] = (int16_t)v;
+        }
+      }
+    }
+  } else if (j0 < j1) {
+    auto ldrow = [&](int64_t j, double (&v)[kIrV]) {
+#pragma unroll
+      for (int k = 0; k < kIrV; ++k) {
+        const int64_t i = cb + 32 * k + lane;
+        v[k] = (j >= 0 && j < a.ny && i < nx) ? __ldg(a.x + j * nx + i) : 0.0;
+      }
+    };
+    double xm[kIrV], xc[kIrV], xp[kIrV], xpp[kIrV];
+    ldrow(j0 - 1, xm);
+    ldrow(j0, xc);
+    ldrow(j0 + 1, xp);
+    for (int64_t j = j0; j < j1; ++j) {
+      ldrow(j + 2, xpp);
+      double bv[kIrV];
+#pragma unroll
+      for (int k = 0; k < kIrV; ++k) {
+        const int64_t i = cb + 32 * k + lane;
+        bv[k] = i < nx ? __ldg(a.b + j * nx + i) : 0.0;
+      }
+      const double wedge = (lane == 0 && cb > 0) ? __ldg(a.x + j * nx + cb - 1) : 0.0;
+      const double eedge = (lane == 31 && cb + kIrCols < nx) ? __ldg(a.x + j * nx + cb + kIrCols) : 0.0;
+#pragma unroll
+      for (int k = 0; k < kIrV; ++k) {
+        const int64_t i = cb + 32 * k + lane;
+        double wv = __shfl_up_sync(0xffffffffu, xc[k], 1);
+        double ev = __shfl_down_sync(0xffffffffu, xc[k], 1);
+        const double wprev = __shfl_sync(0xffffffffu, xc[k > 0 ? k - 1 : 0], 31);
+        const double enext = __shfl_sync(0xffffffffu, xc[k < kIrV - 1 ? k + 1 : kIrV - 1], 0);
+        if (lane == 0) wv = k > 0 ? wprev : wedge;
+        if (lane == 31) ev = k < kIrV - 1 ? enext : eedge;
+        if (i >= nx) {
+          if (!PASS1 && i < a.out.ld) {   // padding columns [nx, ld) are written as 0
+            if (a.out.is32) reinterpret_cast<int32_t*>(a.out.m)[j * a.out.ld + i] = 0;
+            else reinterpret_cast<int16_t*>(a.out.m)[j * a.out.ld + i] = 0;
+          }
+          continue;
+        }
+        // r = b' - A'x, A'x = c x + nb (((W + E) + S) + N): fixed order, explicit rounding.
+        // In 2D c = 1 (1 * x = x exactly) and nb, bscale are powers of two (exact scalings).
+        double s = __dadd_rn(wv, ev);
+        s = __dadd_rn(s, xm[k]);
+        s = __dadd_rn(s, xp[k]);
+        const double ax = __dadd_rn(xc[k], -scale_pow2(s, a.nbshift, -a.cnb));
+        const double r = __dsub_rn(scale_pow2(bv[k], a.bshift, a.bscale), ax);
+        int64_t M = 0, E = -1074;
+        if (!split_double(r, M, E)) { bad = true; continue; }
+        if (PASS1) {
+          const int64_t mv = M == 0 ? -1073 : msb64(M) + E;
+          red.key = max(red.key, (long long)(mv + kIrKeyOff));
+          if (p.window) a.tmp[j * a.out.ld + i] = wrap_bits((uint64_t)fshift(M, E - p.e_tmp), a.w_tmp);
+        } else {
+          const int64_t v = fshift(M, E - p.e_out);
+          red.nrm = max(red.nrm, (long long)(v < 0 ? -v : v));
+          if (a.out.is32) reinterpret_cast<int32_t*>(a.out.m)[j * a.out.ld + i] = (int32_t)v;
+          else reinterpret_cast<int16_t*>(a.out.m)[j * a.out.ld + i] = (int16_t)v;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kIrV; ++k) { xm[k] = xc[k]; xc[k] = xp[k]; xp[k] = xpp[k]; }
+    }
+  }
+  if (bad) atomicOr((unsigned long long*)&a.meta[BFP_META_FLAGS], 1ull);
+  block_commit(red, a.meta, nullptr, PASS1);
+  if (!PASS1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    a.meta[0] = p.e_out;
+    *a.gamma_mu = p.e_out + a.w + (int64_t(1) << 40);   // gamma of the next IR residual
+    if (a.stats) {
+      atomicAdd((unsigned long long*)&a.stats[5], 1ull);
+      if (p.recompute) atomicAdd((unsigned long long*)&a.stats[6], 1ull);
+    }
+  }
+}
+
+// x <- x + m 2^e (FP64 update of Alg. ir): one double per thread, rows over gridDim.y
+template <class T>
+__global__ void __launch_bounds__(256) k_ir_update2(double* __restrict__ x, const VIn y, const int64_t* meta) {
+  const int64_t e = meta[0];
+  const int ei = (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e));
+  const int64_t rows = y.ny * y.nz;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= y.nx) return;
+  const T* m = reinterpret_cast<const T*>(y.m);
+  (void)ei;
+  for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+    double* xr = x + row * y.nx + i;
+    *xr = __dadd_rn(*xr, mant_pow2((int32_t)m[row * y.ld + i], e));
+  }
+}
+
+}  // namespace bfp

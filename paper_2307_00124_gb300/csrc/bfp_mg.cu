@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "bfp_host.h"
+#include "bfp_ir2d.cuh"
 
 using namespace bfp;
 
@@ -179,6 +179,7 @@ struct bfp_hierarchy {
   std::vector<void*> allocs;
   uint64_t* stats = nullptr;
   unsigned long long* norms = nullptr;   // 2 words for the residual norm
+  int64_t* ir_gam = nullptr;             // per level: previous IR residual mu* (+2^40), 0 = unknown
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
   // captured IR step
   cudaGraphExec_t graph = nullptr;
@@ -283,8 +284,24 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
   const unsigned gr = grid_for(items, 256);
   if (cudaMemsetAsync(r->meta + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
   if (nd == 2) {
-    k_ir_residual<2, true><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
-    k_ir_residual<2, false><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
+    IrArgs a;
+    a.b = b; a.bscale = bscale; a.x = x; a.nx = g.nx; a.ny = g.ny; a.cdiag = cdiag; a.cnb = cnb;
+    int bsh = 0;
+    while (std::ldexp(1.0, -bsh) > bscale && bsh < 1100) ++bsh;   // bscale = 2^-bsh (n + 1 = 2^J)
+    if (std::ldexp(1.0, -bsh) != bscale || cdiag != 1.0 || cnb != -0.25) return BFP_ERR_ARG;
+    a.bshift = bsh;
+    a.nbshift = 2;
+    a.out = o; a.meta = r->meta;
+    a.w = r->w;
+    a.w_tmp = r->w + 4;                          // Table tab:estimates, IR residual (i > 1): w_add = 4
+    a.tmp = (h->lv[k].tmp && a.w_tmp <= 32) ? (int32_t*)h->lv[k].tmp : nullptr;
+    a.gamma_mu = h->ir_gam + k;
+    a.stats = h->stats;
+    const int rs = g.ny >= 2048 ? 16 : (g.ny >= 256 ? 8 : 4);
+    const dim3 grid2((unsigned)((g.nx + kIrCols - 1) / kIrCols),
+                     (unsigned)((g.ny + (int64_t)kIrWarps * rs - 1) / ((int64_t)kIrWarps * rs)));
+    k_ir2d<true><<<grid2, 128, 0, s>>>(a, rs);
+    k_ir2d<false><<<grid2, 128, 0, s>>>(a, rs);
   } else {
     k_ir_residual<3, true><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
     k_ir_residual<3, false><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
@@ -296,8 +313,10 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
 int32_t ir_update(double* x, const bfp_vec* y, cudaStream_t s) {
   const int64_t total = y->n[0] * y->n[1] * y->n[2];
   if (total == 0) return BFP_OK;
-  if (y->w > 16) k_ir_update<int32_t><<<grid_for(total, 256), 256, 0, s>>>(x, vin(y), y->meta);
-  else k_ir_update<int16_t><<<grid_for(total, 256), 256, 0, s>>>(x, vin(y), y->meta);
+  const int64_t rows = y->n[1] * y->n[2];
+  const dim3 gu((unsigned)((y->n[0] + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
+  if (y->w > 16) k_ir_update2<int32_t><<<gu, 256, 0, s>>>(x, vin(y), y->meta);
+  else k_ir_update2<int16_t><<<gu, 256, 0, s>>>(x, vin(y), y->meta);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -372,7 +391,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
     ok = make_vec(h, L.r, nd, L.n, o->w) && make_vec(h, L.ya, nd, L.n, o->w) && make_vec(h, L.yb, nd, L.n, o->w) &&
          make_vec(h, L.rv, nd, L.n, o->w);
     const int64_t pts = L.n * L.n * (nd == 3 ? L.n : 1);
-    if (ok && o->mode == BFP_QCOMP && o->use_tmp) {
+    if (ok && o->use_tmp) {
       L.tmp = dalloc(h, (size_t)(L.r.n[1] * L.r.n[2] * L.r.ld) * 4);
       ok = L.tmp != nullptr;
     }
@@ -386,8 +405,10 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if (ok) {
     h->stats = (uint64_t*)dalloc(h, 8 * sizeof(uint64_t));
     h->norms = (unsigned long long*)dalloc(h, 2 * sizeof(unsigned long long));
-    ok = h->stats && h->norms;
+    h->ir_gam = (int64_t*)dalloc(h, h->lv.size() * sizeof(int64_t));
+    ok = h->stats && h->norms && h->ir_gam;
     if (ok) cudaMemset(h->stats, 0, 8 * sizeof(uint64_t));
+    if (ok) cudaMemset(h->ir_gam, 0, h->lv.size() * sizeof(int64_t));
   }
   if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
     bfp_hierarchy_destroy(h);
@@ -472,6 +493,7 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
     else k_restrict_f64<3><<<grid_for(tot, 256), 256, 0, s>>>(bf, sc, grid_of(nd, F.n), Cc.b, grid_of(nd, Cc.n), rscale);
     note_launches(1);
   }
+  if (cudaMemsetAsync(h->ir_gam, 0, nl * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
   for (int k = nl - 1; k >= 0; --k) {
     Level& L = h->lv[k];
     double* xk = (k == 0) ? x : L.x;

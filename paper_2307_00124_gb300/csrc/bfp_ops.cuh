@@ -27,51 +27,70 @@ __device__ __forceinline__ int64_t ld1(const VIn& v, int64_t row, int64_t col) {
   return (int64_t)__ldg(reinterpret_cast<const T*>(v.m) + row * v.ld + col);
 }
 
-// 8 consecutive mantissas of one row starting at c0 (c0 % 8 == 0).  Entries
-// at columns >= nx, rows outside the vector, or vectors past ld read as 0
-// (zero Dirichlet halo and padding).
-template <class T>
-__device__ __forceinline__ void ld8(const VIn& v, int64_t row, int64_t c0, int32_t (&o)[8]) {
+// V consecutive mantissas (V = 4 or 8) of one row starting at c0 (c0 % V == 0).
+// Entries at columns >= nx, rows outside the vector, or chunks past ld read as
+// 0 (zero Dirichlet halo and padding).
+template <class T, int V>
+__device__ __forceinline__ void ldv(const VIn& v, int64_t row, int64_t c0, int32_t (&o)[V]) {
   if (row < 0 || row >= v.ny * v.nz || c0 >= v.ld || c0 >= v.nx) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = 0;
+    for (int k = 0; k < V; ++k) o[k] = 0;
     return;
   }
   const T* p = reinterpret_cast<const T*>(v.m) + row * v.ld + c0;
   if (sizeof(T) == 2) {
-    uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    uint32_t w[V / 2];
+    if (V == 8) {
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+      w[0] = u.x; w[1] = u.y;
+      if (V == 8) { w[V == 8 ? 2 : 0] = u.z; w[V == 8 ? 3 : 1] = u.w; }
+    } else {
+      const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+      w[0] = u.x; w[1] = u.y;
+    }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < V / 2; ++k) {
       o[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
       o[2 * k + 1] = (int32_t)(int16_t)(w[k] >> 16);
     }
   } else {
-    int4 a = __ldg(reinterpret_cast<const int4*>(p));
-    int4 b = __ldg(reinterpret_cast<const int4*>(p) + 1);
+    const int4 a = __ldg(reinterpret_cast<const int4*>(p));
     o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-    o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    if (V == 8) {
+      const int4 b = __ldg(reinterpret_cast<const int4*>(p) + 1);
+      o[V == 8 ? 4 : 0] = b.x; o[V == 8 ? 5 : 1] = b.y; o[V == 8 ? 6 : 2] = b.z; o[V == 8 ? 7 : 3] = b.w;
+    }
   }
-  if (c0 + 8 > v.nx) {
+  if (c0 + V > v.nx) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < V; ++k)
       if (c0 + k >= v.nx) o[k] = 0;
   }
 }
 
-__device__ __forceinline__ void st8(const VOut& v, int64_t row, int64_t c0, const int32_t (&o)[8]) {
+template <class T>
+__device__ __forceinline__ void ld8(const VIn& v, int64_t row, int64_t c0, int32_t (&o)[8]) {
+  ldv<T, 8>(v, row, c0, o);
+}
+
+template <int V>
+__device__ __forceinline__ void stv(const VOut& v, int64_t row, int64_t c0, const int32_t (&o)[V]) {
   if (v.is32) {
     int4* p = reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(v.m) + row * v.ld + c0);
     p[0] = make_int4(o[0], o[1], o[2], o[3]);
-    p[1] = make_int4(o[4], o[5], o[6], o[7]);
+    if (V == 8) p[1] = make_int4(o[V == 8 ? 4 : 0], o[V == 8 ? 5 : 1], o[V == 8 ? 6 : 2], o[V == 8 ? 7 : 3]);
   } else {
-    uint4 u;
-    u.x = (uint32_t)(uint16_t)o[0] | ((uint32_t)(uint16_t)o[1] << 16);
-    u.y = (uint32_t)(uint16_t)o[2] | ((uint32_t)(uint16_t)o[3] << 16);
-    u.z = (uint32_t)(uint16_t)o[4] | ((uint32_t)(uint16_t)o[5] << 16);
-    u.w = (uint32_t)(uint16_t)o[6] | ((uint32_t)(uint16_t)o[7] << 16);
-    *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(v.m) + row * v.ld + c0) = u;
+    uint32_t w[V / 2];
+#pragma unroll
+    for (int k = 0; k < V / 2; ++k) w[k] = (uint32_t)(uint16_t)o[2 * k] | ((uint32_t)(uint16_t)o[2 * k + 1] << 16);
+    int16_t* p = reinterpret_cast<int16_t*>(v.m) + row * v.ld + c0;
+    if (V == 8) *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[V == 8 ? 2 : 0], w[V == 8 ? 3 : 1]);
+    else *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
   }
+}
+
+__device__ __forceinline__ void st8(const VOut& v, int64_t row, int64_t c0, const int32_t (&o)[8]) {
+  stv<8>(v, row, c0, o);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,41 +302,132 @@ struct OpProlong {
 //           recompute, decided once from mu*)
 // ---------------------------------------------------------------------------
 
-template <class Acc, class Op, bool PASS1>
-__device__ __forceinline__ void row_elems(const Op& op, const Plan& p, const VOut& out, int32_t* tmp,
-                                          int64_t row, int64_t c0, Red& red) {
-  int64_t H[8], L[8];
-  op(row, c0, H, L);
-  int32_t o[8];
+// Quantises the 8 exact results of one row chunk; hl(k, H, L) yields the two
+// exponent groups of element k.  The common case (an int64 combine suffices)
+// is unrolled and computes each element on the fly; the rare wide / far-apart
+// exponent case stages the groups in local memory and runs one element at a
+// time in 128-bit, so that its registers do not add to the unrolled path's.
+template <bool PASS1, int V, class HL>
+__device__ __forceinline__ void quantvf(const HL& hl, const Plan& p, const Fast& fq, const VOut& out, int32_t* tmp,
+                                        int64_t row, int64_t c0, Red& red, bool store = true) {
+  int32_t o[V];
   const int64_t nvalid = out.nx - c0;
-  if (PASS1) {
+  int sat = 0;
+  if (fq.ok) {
+    const int64_t hi = (1ll << (fq.w - 1)) - 1, lo = -(1ll << (fq.w - 1));
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      Acc Z = combine<Acc>(H[k], L[k], p);
-      if (k < nvalid) red.key = max(red.key, (long long)mu_key<Acc>(Z, H[k], L[k], p));
-      o[k] = (k < nvalid) ? window<Acc>(Z, p) : 0;
-    }
-    if (tmp) {
-      int4* q = reinterpret_cast<int4*>(tmp + row * out.ld + c0);
-      q[0] = make_int4(o[0], o[1], o[2], o[3]);
-      q[1] = make_int4(o[4], o[5], o[6], o[7]);
+    for (int k = 0; k < V; ++k) {
+      int64_t H, L;
+      hl(k, H, L);
+      const int64_t Z = (int64_t)((uint64_t)H << fq.dh) + (int64_t)((uint64_t)L << fq.dl);
+      const bool valid = k < nvalid;   // padding columns may see a real neighbour: masked
+      if (PASS1) {
+        if (valid) red.key = max(red.key, (long long)(256 + msb64(Z)));
+        o[k] = valid ? wrap_bits((uint64_t)(Z >> fq.t), fq.w) : 0;
+      } else {
+        int64_t v = Z >> fq.t;
+        if (fq.clamp) {
+          const bool c = v > hi || v < lo;
+          v = v > hi ? hi : (v < lo ? lo : v);
+          sat += (c && valid) ? 1 : 0;
+        }
+        o[k] = valid ? (int32_t)v : 0;
+      }
     }
   } else {
-    int sat = 0;
+    // general path (far-apart exponent groups, 128-bit combine, left-shifted
+    // outputs): staged in local memory, one element at a time
+    int64_t Hs[V], Ls[V];
+    int32_t os[V];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      // padding columns (k >= nvalid) may see a real neighbour through the stencil: skip them
+    for (int k = 0; k < V; ++k) hl(k, Hs[k], Ls[k]);
+#pragma unroll 1
+    for (int k = 0; k < V; ++k) {
+      os[k] = 0;
       if (k < nvalid) {
-        Acc Z = combine<Acc>(H[k], L[k], p);
-        o[k] = finish<Acc>(Z, H[k], L[k], p, sat);
-      } else {
-        o[k] = 0;
+        if (p.wide) {
+          const i128 Z = combine<i128>(Hs[k], Ls[k], p);
+          if (PASS1) {
+            red.key = max(red.key, (long long)mu_key<i128>(Z, Hs[k], Ls[k], p));
+            os[k] = window<i128>(Z, p);
+          } else {
+            os[k] = finish<i128>(Z, Hs[k], Ls[k], p, sat);
+          }
+        } else {
+          const int64_t Z = combine<int64_t>(Hs[k], Ls[k], p);
+          if (PASS1) {
+            red.key = max(red.key, (long long)mu_key<int64_t>(Z, Hs[k], Ls[k], p));
+            os[k] = window<int64_t>(Z, p);
+          } else {
+            os[k] = finish<int64_t>(Z, Hs[k], Ls[k], p, sat);
+          }
+        }
       }
-      long long a = o[k] < 0 ? -(long long)o[k] : (long long)o[k];
-      red.nrm = max(red.nrm, a);
     }
+#pragma unroll
+    for (int k = 0; k < V; ++k) o[k] = os[k];
+  }
+  if (PASS1) {
+    if (tmp && store) {
+      int4* q = reinterpret_cast<int4*>(tmp + row * out.ld + c0);
+      q[0] = make_int4(o[0], o[1], o[2], o[3]);
+      if (V == 8) q[1] = make_int4(o[V == 8 ? 4 : 0], o[V == 8 ? 5 : 1], o[V == 8 ? 6 : 2], o[V == 8 ? 7 : 3]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) red.nrm = max(red.nrm, (long long)(o[k] < 0 ? -(long long)o[k] : (long long)o[k]));
     red.sat += sat;
-    st8(out, row, c0, o);
+    if (store) stv<V>(out, row, c0, o);
+  }
+}
+
+template <bool PASS1>
+__device__ __forceinline__ void quant8(const int64_t (&H)[8], const int64_t (&L)[8], const Plan& p,
+                                       const VOut& out, int32_t* tmp, int64_t row, int64_t c0, Red& red,
+                                       bool store = true) {
+  const Fast fq = make_fast(p, PASS1);
+  quantvf<PASS1, 8>([&](int k, int64_t& h, int64_t& l) { h = H[k]; l = L[k]; }, p, fq, out, tmp, row, c0, red, store);
+}
+
+// Alg. qcomp success branch for one row chunk: decr(w_tmp - w_out, tmp >> (lambda_out - lambda_tmp)).
+template <int V>
+__device__ __forceinline__ void narrowv(const int32_t* tmp, const Plan& p, const VOut& out, int64_t row, int64_t c0,
+                                        Red& red) {
+  const int4* src = reinterpret_cast<const int4*>(tmp + row * out.ld + c0);
+  int32_t t[V];
+  const int4 a = src[0];
+  t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w;
+  if (V == 8) {
+    const int4 b = src[1];
+    t[V == 8 ? 4 : 0] = b.x; t[V == 8 ? 5 : 1] = b.y; t[V == 8 ? 6 : 2] = b.z; t[V == 8 ? 7 : 3] = b.w;
+  }
+  const int s = (int)(p.e_out - p.e_tmp);
+  int32_t o[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    o[k] = (c0 + k < out.nx) ? (t[k] >> s) : 0;
+    red.nrm = max(red.nrm, (long long)(o[k] < 0 ? -(long long)o[k] : (long long)o[k]));
+  }
+  stv<V>(out, row, c0, o);
+}
+
+__device__ __forceinline__ void narrow8(const int32_t* tmp, const Plan& p, const VOut& out, int64_t row, int64_t c0,
+                                        Red& red) {
+  narrowv<8>(tmp, p, out, row, c0, red);
+}
+
+// Final bookkeeping of a quantised op: e_out and the counters (block 0 only).
+__device__ __forceinline__ void op_epilogue(const QDesc& q, const Plan& p) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    q.meta_out[0] = p.e_out;
+    if (q.stats) {
+      atomicAdd((unsigned long long*)&q.stats[0], 1ull);
+      if (q.mode == kQcomp) {
+        if (p.overflow || p.underflow) atomicAdd((unsigned long long*)&q.stats[1], 1ull);
+        if (p.overflow) atomicAdd((unsigned long long*)&q.stats[2], 1ull);
+        if (p.underflow) atomicAdd((unsigned long long*)&q.stats[3], 1ull);
+      }
+    }
   }
 }
 
@@ -340,36 +450,15 @@ __global__ void __launch_bounds__(256) k_quant(const Op op, const QDesc q, const
     const int64_t row = idx / nvec;
     const int64_t c0 = (idx - row * nvec) << 3;
     if (!PASS1 && p.narrow) {
-      // Alg. qcomp success branch: decr(w_tmp - w_out, tmp >> (lambda_out - lambda_tmp))
-      const int4* src = reinterpret_cast<const int4*>(reinterpret_cast<const int32_t*>(q.tmp) + row * out.ld + c0);
-      int4 a = src[0], b = src[1];
-      const int32_t t[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-      const int s = (int)(p.e_out - p.e_tmp);
-      int32_t o[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        o[k] = (c0 + k < out.nx) ? (t[k] >> s) : 0;
-        long long av = o[k] < 0 ? -(long long)o[k] : (long long)o[k];
-        red.nrm = max(red.nrm, av);
-      }
-      st8(out, row, c0, o);
+      narrow8(reinterpret_cast<const int32_t*>(q.tmp), p, out, row, c0, red);
       continue;
     }
-    if (p.wide) row_elems<i128, Op, PASS1>(op, p, out, tmp, row, c0, red);
-    else row_elems<int64_t, Op, PASS1>(op, p, out, tmp, row, c0, red);
+    int64_t H[8], L[8];
+    op(row, c0, H, L);
+    quant8<PASS1>(H, L, p, out, tmp, row, c0, red);
   }
   block_commit(red, q.meta_out, q.stats, PASS1);
-  if (!PASS1 && blockIdx.x == 0 && threadIdx.x == 0) {
-    q.meta_out[0] = p.e_out;
-    if (q.stats) {
-      atomicAdd((unsigned long long*)&q.stats[0], 1ull);
-      if (q.mode == kQcomp) {
-        if (p.overflow || p.underflow) atomicAdd((unsigned long long*)&q.stats[1], 1ull);
-        if (p.overflow) atomicAdd((unsigned long long*)&q.stats[2], 1ull);
-        if (p.underflow) atomicAdd((unsigned long long*)&q.stats[3], 1ull);
-      }
-    }
-  }
+  if (!PASS1) op_epilogue(q, p);
 }
 
 }  // namespace bfp

@@ -91,3 +91,31 @@ def test_graph_and_direct_ir_agree():
         hd.ir_iterate(f, xd, 4)
     st.synchronize()
     assert torch.equal(xg, xd)
+
+
+@pytest.mark.parametrize("n", [127, 63])
+def test_ir_residual_window_and_padding(n):
+    """bfp_ir_residual equals quant(b' - A'x) of the oracle; the qcomp window (gamma =
+    previous residual norm) is used from the second call on; padding is zeroed."""
+    h, s = make(2, n, 16, bfp.QCOMP)
+    f = manufactured_rhs(2, n)
+    b = s.rhs_hierarchy(f)[0]
+    rng = np.random.default_rng(n)
+    ft = torch.from_numpy(f).cuda()
+    r = bfp.BFPVector((n, n), 16)
+    x = rng.standard_normal((n, n)) * 1e-3
+    for it in range(4):
+        if it == 3:
+            x = x * 1e6          # far larger residual: the window overflows, pass 2 recomputes
+        xt = torch.from_numpy(x).cuda()
+        r.mant.fill_(-5)
+        h.ir_residual(ft, xt, r)
+        ref = B.from_f64(mg.residual_f64(b, x), 16)
+        torch.cuda.synchronize()
+        assert r.exponent == ref.e
+        assert np.array_equal(r.mantissas(), ref.m)
+        assert np.all(r.padding() == 0)
+        x = x + 1e-9 * rng.standard_normal((n, n))
+    st = h.stats()
+    assert st["ir_residuals"] == 4
+    assert st["ir_recomputed"] == 2       # the first call (no gamma yet) and the overflowing one
