@@ -38,7 +38,8 @@ typedef enum {
   BFP_ERR_CUDA = -4,      /* a CUDA runtime call failed */
   BFP_ERR_NONFINITE = -5, /* NaN or Inf in an FP64 input (reported via meta) */
   BFP_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
-  BFP_ERR_NOCONV = -7     /* ir_solve reached its iteration limit */
+  BFP_ERR_NOCONV = -7,    /* ir_solve reached its iteration limit */
+  BFP_ERR_CAPACITY = -8   /* larger than a fixed-size static scratch area */
 } bfp_status;
 
 /* Words in a vector's device meta block. */
@@ -197,6 +198,27 @@ int32_t bfp_restrict(const bfp_vec* r_f, const bfp_vec* r_c, const bfp_q* q,
  * P is bilinear (2D) / trilinear (3D) interpolation. */
 int32_t bfp_prolong(const bfp_vec* d, const bfp_vec* y, const bfp_vec* y_out,
                     const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+
+/* ---- no-allocation variant ---------------------------------------------------- */
+
+/* bfp_jacobi for callers that cannot allocate device memory at the call site
+ * (inside a host callback or another context where CUDA allocation calls are
+ * not allowed, under a device-memory budget owned by another framework, or
+ * where the implicit device synchronisation of cudaMalloc / cudaFree is not
+ * acceptable).  The paper has no counterpart: this is a deployment variant.
+ * Same arguments and result as bfp_jacobi; q->tmp is ignored.  In qcomp mode
+ * the w_tmp-bit window lives in a static device array of
+ * bfp_noalloc_window_capacity() int32 entries (16 MiB on every GPU that
+ * loads the library, held until exit); nothing is allocated.
+ *  - Outputs with rows * ld larger than the capacity: BFP_ERR_CAPACITY.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - All calls on a device share the array; calls that overlap on the GPU
+ *    (unordered streams) race on it. */
+int64_t bfp_noalloc_window_capacity(void);
+int32_t bfp_jacobi_noalloc(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r,
+                           const bfp_vec* y_out, const bfp_q* q, const bfp_stats* st,
+                           bfp_stream stream);
 
 /* ---- multigrid (Alg. v-cycle, fmg, ir) ---------------------------------------- */
 

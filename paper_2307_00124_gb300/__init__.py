@@ -24,7 +24,7 @@ META_WORDS = 8
 QCOMP, NNQCOMP = 0, 1
 
 STATUS = {0: "BFP_OK", -1: "BFP_ERR_ARG", -2: "BFP_ERR_SHAPE", -3: "BFP_ERR_WIDTH", -4: "BFP_ERR_CUDA",
-          -5: "BFP_ERR_NONFINITE", -6: "BFP_ERR_TIMEOUT", -7: "BFP_ERR_NOCONV"}
+          -5: "BFP_ERR_NONFINITE", -6: "BFP_ERR_TIMEOUT", -7: "BFP_ERR_NOCONV", -8: "BFP_ERR_CAPACITY"}
 
 
 class BFPError(RuntimeError):
@@ -97,6 +97,9 @@ _sig = {
                                C.c_void_p]),
     "bfp_restrict": (C.c_int32, [P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
     "bfp_prolong": (C.c_int32, [P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
+    "bfp_noalloc_window_capacity": (C.c_int64, []),
+    "bfp_jacobi_noalloc": (C.c_int32, [P(bfp_stencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q),
+                                       P(bfp_stats), C.c_void_p]),
     "bfp_solver_opts_default": (C.c_int32, [C.c_int32, C.c_int64, C.c_int32, P(bfp_solver_opts)]),
     "bfp_hierarchy_create": (C.c_int32, [P(bfp_solver_opts), P(C.c_void_p)]),
     "bfp_hierarchy_destroy": (None, [C.c_void_p]),
@@ -284,6 +287,17 @@ def bfp_jacobi(A, y, r, y_out, qq, stats=None, stream=None):
     yp = None if y is None else C.byref(y.struct())
     _check(_lib.bfp_jacobi(C.byref(A), yp, C.byref(r.struct()), C.byref(y_out.struct()), C.byref(qq),
                            _st(stats), _stream(stream)), "bfp_jacobi")
+
+
+def bfp_jacobi_noalloc(A, y, r, y_out, qq, stats=None, stream=None):
+    """bfp_jacobi whose qcomp window lives in the library's static device array (no allocation)."""
+    yp = None if y is None else C.byref(y.struct())
+    _check(_lib.bfp_jacobi_noalloc(C.byref(A), yp, C.byref(r.struct()), C.byref(y_out.struct()), C.byref(qq),
+                                   _st(stats), _stream(stream)), "bfp_jacobi_noalloc")
+
+
+def bfp_noalloc_window_capacity() -> int:
+    return int(_lib.bfp_noalloc_window_capacity())
 
 
 def bfp_restrict(rf, rc, qq, stats=None, stream=None):

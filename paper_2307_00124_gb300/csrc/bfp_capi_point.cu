@@ -149,6 +149,7 @@ const char* bfp_status_str(int32_t st) {
     case BFP_ERR_NONFINITE: return "non-finite FP64 input";
     case BFP_ERR_TIMEOUT: return "bounded device wait timed out";
     case BFP_ERR_NOCONV: return "iteration limit reached";
+    case BFP_ERR_CAPACITY: return "size exceeds the fixed static scratch capacity";
     default: return "unknown status";
   }
 }
