@@ -10,6 +10,10 @@ using namespace bfp;
 namespace bfp {
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool& prezeroed() {
+  static thread_local bool flag = false;
+  return flag;
+}
 }  // namespace bfp
 
 namespace {

@@ -15,6 +15,21 @@ namespace bfp {
 // Counts every kernel this library enqueues (directly or into a captured graph).
 void note_launches(int n);
 
+// When set (by the multigrid driver, for the ops it enqueues), the output meta
+// accumulators have already been zeroed for this op and the per-op memset is
+// skipped.  Thread-local: other host threads calling the C ABI are unaffected.
+bool& prezeroed();
+struct PrezeroedScope {
+  bool saved;
+  PrezeroedScope() : saved(prezeroed()) { prezeroed() = true; }
+  ~PrezeroedScope() { prezeroed() = saved; }
+};
+
+inline cudaError_t zero_accumulators(int64_t* meta_out, cudaStream_t s) {
+  if (prezeroed()) return cudaSuccess;
+  return cudaMemsetAsync(meta_out + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s);
+}
+
 inline cudaStream_t as_stream(bfp_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int hmsb(int64_t z) {  // host msb (Sec. 2 signed width)
@@ -137,8 +152,7 @@ inline int32_t launch_quant(const Op& op, const QDesc& q, const bfp_vec* out, cu
   const int threads = 256;
   const int64_t items = rows_of(out) * (out->ld / 8);
   unsigned g = grid_for(items, threads);
-  if (cudaMemsetAsync(q.meta_out + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess)
-    return BFP_ERR_CUDA;
+  if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (q.mode == kQcomp) k_quant<Op, true><<<g, threads, 0, s>>>(op, q, o);
   k_quant<Op, false><<<g, threads, 0, s>>>(op, q, o);
   note_launches(q.mode == kQcomp ? 2 : 1);

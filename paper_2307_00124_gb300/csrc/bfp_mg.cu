@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(256) k_restrict_f64(const double* __restrict__
 
 struct Level {
   int64_t n = 0;
+  int64_t* slots = nullptr;       // meta blocks of this level's op call sites (zeroed once per step)
+  int nslots = 0;
   bfp_vec r{}, ya{}, yb{}, rv{};  // BFP buffers (mantissa + meta)
   void* tmp = nullptr;            // qcomp window (int32)
   double* b = nullptr;            // FP64 right-hand side (levels >= 1)
@@ -180,6 +182,8 @@ struct bfp_hierarchy {
   uint64_t* stats = nullptr;
   unsigned long long* norms = nullptr;   // 2 words for the residual norm
   int64_t* ir_gam = nullptr;             // per level: previous IR residual mu* (+2^40), 0 = unknown
+  int64_t* arena = nullptr;              // all call-site meta blocks, contiguous
+  size_t arena_words = 0;
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
   // captured IR step
   cudaGraphExec_t graph = nullptr;
@@ -236,39 +240,65 @@ Q make_q(const bfp_hierarchy* h, const Level& L) {
     if (_rc != BFP_OK) return _rc;     \
   } while (0)
 
-// V(nu1, nu2) on level k: y_out receives the approximate solution of A' y = r.
-// Returns which buffer holds the result through *res.
-int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, bfp_vec* bufA, bfp_vec* bufB,
-                   const bfp_vec** res, cudaStream_t s) {
+// V(nu1, nu2) on level k: the approximate solution of A' y = r ends in bufA's
+// mantissas; *res describes it (its meta block is a call-site slot of level k).
+// Every op writes a meta block of its own (zeroed once per step), so the ops
+// skip their per-op memset.
+int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* bufA, const bfp_vec* bufB,
+                   bfp_vec* res, cudaStream_t s) {
   Level& L = h->lv[k];
   Q q = make_q(h, L);
+  int slot = 0;
+  auto at_slot = [&](const bfp_vec* buf) {
+    bfp_vec v = *buf;
+    v.meta = L.slots + BFP_META_WORDS * (slot++);
+    return v;
+  };
   const bool coarsest = (k + 1 == (int)h->lv.size());
   const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
   // writes per level: 1 (omega r) + (nu1 - 1) sweeps [+ correction + nu2 sweeps]
   const int writes = coarsest ? nu1 : (nu1 + 1 + h->o.nu2);
   // choose the first target so that the last write lands in bufA
-  bfp_vec* cur = (writes % 2 == 1) ? bufA : bufB;
-  bfp_vec* oth = (cur == bufA) ? bufB : bufA;
-  TRY(bfp_jacobi(&h->A, nullptr, r, cur, &q.q, &q.st, s));            // relaxation from y = 0
+  const bfp_vec* curb = (writes % 2 == 1) ? bufA : bufB;
+  const bfp_vec* othb = (curb == bufA) ? bufB : bufA;
+  bfp_vec cur = at_slot(curb);
+  TRY(bfp_jacobi(&h->A, nullptr, r, &cur, &q.q, &q.st, s));            // relaxation from y = 0
   for (int i = 1; i < nu1; ++i) {
-    TRY(bfp_jacobi(&h->A, cur, r, oth, &q.q, &q.st, s));
-    std::swap(cur, oth);
+    bfp_vec nx = at_slot(othb);
+    TRY(bfp_jacobi(&h->A, &cur, r, &nx, &q.q, &q.st, s));
+    cur = nx;
+    std::swap(curb, othb);
   }
   if (!coarsest) {
     Level& C = h->lv[k + 1];
-    TRY(bfp_residual(&h->A, cur, r, &L.rv, &q.q, &q.st, s));           // r_v = A y - r
-    TRY(bfp_restrict(&L.rv, &C.r, &q.q, &q.st, s));                    // r_c = R~ r_v
-    const bfp_vec* d = nullptr;
-    TRY(vcycle_rec(h, k + 1, &C.r, &C.ya, &C.yb, &d, s));              // d = V(r_c)
-    TRY(bfp_prolong(d, cur, oth, &q.q, &q.st, s));                     // y = y - P d
-    std::swap(cur, oth);
+    bfp_vec rv = at_slot(&L.rv);
+    TRY(bfp_residual(&h->A, &cur, r, &rv, &q.q, &q.st, s));            // r_v = A y - r
+    bfp_vec rc = at_slot(&C.r);
+    TRY(bfp_restrict(&rv, &rc, &q.q, &q.st, s));                       // r_c = R~ r_v
+    bfp_vec d;
+    TRY(vcycle_rec(h, k + 1, &rc, &C.ya, &C.yb, &d, s));               // d = V(r_c)
+    bfp_vec nx = at_slot(othb);
+    TRY(bfp_prolong(&d, &cur, &nx, &q.q, &q.st, s));                   // y = y - P d
+    cur = nx;
+    std::swap(curb, othb);
     for (int i = 0; i < h->o.nu2; ++i) {
-      TRY(bfp_jacobi(&h->A, cur, r, oth, &q.q, &q.st, s));
-      std::swap(cur, oth);
+      bfp_vec nx2 = at_slot(othb);
+      TRY(bfp_jacobi(&h->A, &cur, r, &nx2, &q.q, &q.st, s));
+      cur = nx2;
+      std::swap(curb, othb);
     }
   }
   *res = cur;
   return BFP_OK;
+}
+
+int slots_needed(const bfp_solver_opts& o, bool coarsest) {
+  // IR residual + relaxations [+ residual, restriction, correction, post-relaxations]
+  return 1 + (coarsest ? o.coarse_sweeps : (o.nu1 + 3 + o.nu2));
+}
+
+cudaError_t zero_arena(bfp_hierarchy* h, cudaStream_t s) {
+  return cudaMemsetAsync(h->arena, 0, h->arena_words * sizeof(int64_t), s);
 }
 
 Grid grid_of(int nd, int64_t n) { return Grid{n, n, nd == 3 ? n : 1}; }
@@ -282,7 +312,7 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
   VOut o = vout(r);
   const int64_t items = rows_of(r) * (r->ld / 8);
   const unsigned gr = grid_for(items, 256);
-  if (cudaMemsetAsync(r->meta + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (zero_accumulators(r->meta, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (nd == 2) {
     IrArgs a;
     a.b = b; a.bscale = bscale; a.x = x; a.nx = g.nx; a.ny = g.ny; a.cdiag = cdiag; a.cnb = cnb;
@@ -297,7 +327,7 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
     a.tmp = (h->lv[k].tmp && a.w_tmp <= 32) ? (int32_t*)h->lv[k].tmp : nullptr;
     a.gamma_mu = h->ir_gam + k;
     a.stats = h->stats;
-    const int rs = g.ny >= 2048 ? 16 : (g.ny >= 256 ? 8 : 4);
+    const int rs = g.ny >= 2048 ? 16 : (g.ny >= 1024 ? 8 : (g.ny >= 256 ? 4 : 2));
     const dim3 grid2((unsigned)((g.nx + kIrCols - 1) / kIrCols),
                      (unsigned)((g.ny + (int64_t)kIrWarps * rs - 1) / ((int64_t)kIrWarps * rs)));
     k_ir2d<true><<<grid2, 128, 0, s>>>(a, rs);
@@ -323,12 +353,16 @@ int32_t ir_update(double* x, const bfp_vec* y, cudaStream_t s) {
 
 int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double* x, cudaStream_t s) {
   Level& L = h->lv[k];
-  TRY(ir_residual_q(h, k, b, bscale, x, &L.r, s));
-  bfp_vec* A = (k == 0) ? &h->y0 : &L.ya;
-  bfp_vec* B = &L.yb;
-  const bfp_vec* y = nullptr;
-  TRY(vcycle_rec(h, k, &L.r, A, B, &y, s));
-  return ir_update(x, y, s);
+  if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;   // every call-site meta of this step
+  PrezeroedScope pz;
+  bfp_vec r = L.r;
+  r.meta = L.slots + BFP_META_WORDS * (L.nslots - 1);         // the IR residual's own slot
+  TRY(ir_residual_q(h, k, b, bscale, x, &r, s));
+  const bfp_vec* A = (k == 0) ? &h->y0 : &L.ya;
+  const bfp_vec* B = &L.yb;
+  bfp_vec y;
+  TRY(vcycle_rec(h, k, &r, A, B, &y, s));
+  return ir_update(x, &y, s);
 }
 
 double bscale_of(int nd, int64_t n) {
@@ -403,6 +437,22 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   }
   ok = ok && make_vec(h, h->y0, nd, o->n, o->w);
   if (ok) {
+    size_t words = 0;
+    for (size_t k = 0; k < h->lv.size(); ++k) {
+      h->lv[k].nslots = slots_needed(*o, k + 1 == h->lv.size());
+      words += (size_t)h->lv[k].nslots * BFP_META_WORDS;
+    }
+    h->arena = (int64_t*)dalloc(h, words * sizeof(int64_t));
+    h->arena_words = words;
+    ok = h->arena != nullptr;
+    size_t off = 0;
+    for (size_t k = 0; ok && k < h->lv.size(); ++k) {
+      h->lv[k].slots = h->arena + off;
+      off += (size_t)h->lv[k].nslots * BFP_META_WORDS;
+    }
+    if (ok) cudaMemset(h->arena, 0, words * sizeof(int64_t));
+  }
+  if (ok) {
     h->stats = (uint64_t*)dalloc(h, 8 * sizeof(uint64_t));
     h->norms = (unsigned long long*)dalloc(h, 2 * sizeof(unsigned long long));
     h->ir_gam = (int64_t*)dalloc(h, h->lv.size() * sizeof(int64_t));
@@ -440,9 +490,15 @@ int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_str
   if (r->w != h->o.w || y->w != h->o.w || r->n[0] != L.n || !same_shape(r, &L.r) || !same_shape(y, &L.r))
     return BFP_ERR_SHAPE;
   if (overlaps(r, y)) return BFP_ERR_ARG;
-  bfp_vec yv = *y;
-  const bfp_vec* res = nullptr;
-  return vcycle_rec(h, 0, r, &yv, &h->y0, &res, as_stream(stream));
+  cudaStream_t s = as_stream(stream);
+  if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;
+  PrezeroedScope pz;
+  bfp_vec res;
+  TRY(vcycle_rec(h, 0, r, y, &h->y0, &res, s));
+  // the result's mantissas are in y; its exponent and norm are in a call-site slot
+  if (cudaMemcpyAsync(y->meta, res.meta, BFP_META_WORDS * sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return BFP_ERR_CUDA;
+  return BFP_OK;
 }
 
 static int32_t ir_iterate_direct(bfp_hierarchy* h, const double* f, double* x, int32_t k, cudaStream_t s) {

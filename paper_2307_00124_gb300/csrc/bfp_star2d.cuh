@@ -12,6 +12,7 @@
 #pragma once
 
 #include "bfp_host.h"
+#include "bfp_star2d16.cuh"
 
 namespace bfp {
 
@@ -247,12 +248,18 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const int32_t c = (int32_t)c64, nb = (int32_t)nb64, mw = (int32_t)mw64;   // checked < 2^31 by the caller
   const VOut o = vout(out);
   const int64_t ny = out->n[1];
-  const int rs = ny >= 2048 ? 16 : (ny >= 256 ? 8 : 4);
+  const int rs = ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2));
   const int64_t chunks = (out->ld + kStarCols - 1) / kStarCols;
   const int64_t strips = (ny + (int64_t)kStarWarps * rs - 1) / ((int64_t)kStarWarps * rs);
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
-  if (cudaMemsetAsync(q.meta_out + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess)
-    return BFP_ERR_CUDA;
+  if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (sizeof(T) == 2) {
+    const dim3 g16((unsigned)((out->ld + kS16Cols - 1) / kS16Cols), grid.y);
+    if (q.mode == kQcomp) k_star2d16<KIND, true><<<g16, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
+    k_star2d16<KIND, false><<<g16, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
+    note_launches(q.mode == kQcomp ? 2 : 1);
+    return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+  }
   if (q.mode == kQcomp) k_star2d<T, KIND, true><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
   k_star2d<T, KIND, false><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
   note_launches(q.mode == kQcomp ? 2 : 1);
