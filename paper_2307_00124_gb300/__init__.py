@@ -63,7 +63,7 @@ class bfp_solver_opts(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("w", C.c_int32), ("n", C.c_int64), ("mode", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
                 ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
-                ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+                ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32)]
 
 
 class bfp_ir_opts(C.Structure):

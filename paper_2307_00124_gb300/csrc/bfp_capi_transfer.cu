@@ -1,6 +1,7 @@
 // bfp_capi_transfer.cu -- C ABI: grid transfers of the V-cycle and FMG
 // (full-weighting restriction R~, bilinear/trilinear prolongation P).
-#include "bfp_host.h"
+#include "bfp_desc.h"
+#include "bfp_transfer2d.cuh"
 
 using namespace bfp;
 
@@ -13,14 +14,54 @@ bool coarse_of(const bfp_vec* f, const bfp_vec* c) {
   return true;
 }
 
+int rows_per_warp(int64_t rows) { return rows >= 1024 ? 8 : (rows >= 256 ? 4 : (rows >= 64 ? 2 : 1)); }
+
+int32_t launch_checks(const QDesc& d) {
+  if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;
+  return BFP_OK;
+}
+
+int32_t restrict2d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaStream_t s) {
+  int32_t e = launch_checks(d);
+  if (e) return e;
+  const int64_t ny = rc->n[1];
+  const int rs = rows_per_warp(ny);
+  const dim3 grid((unsigned)((rc->ld + 255) / 256), (unsigned)((ny + 4 * rs - 1) / (4 * rs)));
+  const VOut o = vout(rc);
+  if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (d.mode == kQcomp) k_restrict2d16<true><<<grid, 128, 0, s>>>(vin(rf), d, o, rs);
+  k_restrict2d16<false><<<grid, 128, 0, s>>>(vin(rf), d, o, rs);
+  note_launches(d.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+template <bool CORR>
+int32_t prolong2d16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
+  int32_t e = launch_checks(d);
+  if (e) return e;
+  const int64_t pairs = (out->n[1] + 1) / 2;
+  const int rs = rows_per_warp(pairs);
+  const dim3 grid((unsigned)((out->ld + 255) / 256), (unsigned)((pairs + 4 * rs - 1) / (4 * rs)));
+  const VOut o = vout(out);
+  VIn yv = vin(y ? y : out);
+  if (!CORR) yv.m = nullptr;
+  if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (d.mode == kQcomp) k_prolong2d16<CORR, true><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
+  k_prolong2d16<CORR, false><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
+  note_launches(d.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
 template <int ND>
 int32_t restrict_launch(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaStream_t s) {
+  if (ND == 2 && !is32(rf)) return restrict2d16(rf, rc, d, s);
   if (is32(rf)) return launch_quant(OpRestrict<int32_t, ND>{vin(rf), rc->n[1]}, d, rc, s);
   return launch_quant(OpRestrict<int16_t, ND>{vin(rf), rc->n[1]}, d, rc, s);
 }
 
 template <int ND, bool CORR>
 int32_t prolong_launch(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
+  if (ND == 2 && !is32(dc)) return prolong2d16<CORR>(dc, y, out, d, s);
   VIn yv = vin(y ? y : out);   // carries the fine shape; not read when CORR is false
   if (!CORR) yv.m = nullptr;
   if (is32(dc)) return launch_quant(OpProlong<int32_t, ND, CORR>{vin(dc), yv}, d, out, s);
@@ -38,16 +79,10 @@ int32_t bfp_restrict(const bfp_vec* r_f, const bfp_vec* r_c, const bfp_q* q, con
   if (!coarse_of(r_f, r_c)) return BFP_ERR_SHAPE;
   if (overlaps(r_f, r_c)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
-  if ((rc = fill_q(d, q, r_c, 6))) return rc;    // Table tab:estimates, restriction: w_add = 6
   const int nd = r_f->ndim;
-  const int64_t eR = nd == 2 ? -2 : -4;           // R~ = P^T (2D), P^T / 2 (3D)
-  int mR = 1;
-  for (int i = 0; i < nd; ++i) mR *= 3;
+  int rule = 0;
+  if ((rc = desc_restrict(nd, r_f->w, d, &rule)) || (rc = fill_q(d, q, r_c, rule))) return rc;
   d.meta_a = r_f->meta; d.meta_out = r_c->meta; d.stats = st ? st->counters : nullptr;
-  d.ch = eR; d.ha = 1; d.two = 0;
-  d.hbits = hmsb(1ll << nd) + r_f->w + clog2(mR);  // Alg. espmv-setup with m_R = 3^d
-  d.ng = 1; d.gv[0] = 0;                           // gamma = ||R~||_inf ||r_v||  (||R~|| = 4)
-  d.gm[0] = nd == 2 ? 16 : 64; d.ge[0] = eR;
   cudaStream_t s = as_stream(stream);
   return nd == 2 ? restrict_launch<2>(r_f, r_c, d, s) : restrict_launch<3>(r_f, r_c, d, s);
 }
@@ -65,28 +100,12 @@ int32_t bfp_prolong(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* y_out, c
     if (overlaps(y, y_out)) return BFP_ERR_ARG;
   }
   QDesc d = blank_desc();
-  // Table tab:estimates: V correction w_add = 1, FMG interpolation w_add = 0
-  if ((rc = fill_q(d, q, y_out, y ? 1 : 0))) return rc;
   const int nd = dc->ndim;
-  const int64_t eP = -nd;                          // P mantissas prod(2 or 1) at e = -d
-  const int wP = hmsb(1ll << nd);
+  int rule = 0;
+  if ((rc = desc_prolong(nd, dc->w, y ? y->w : 0, d, &rule)) || (rc = fill_q(d, q, y_out, rule))) return rc;
   d.meta_out = y_out->meta; d.stats = st ? st->counters : nullptr;
   d.meta_a = dc->meta;
-  d.ch = eP; d.ha = 1;
-  d.hbits = wP + dc->w + nd + 1;                   // w_P + w_d + ceil(log2 m_P), sign of -P d
-  // ||P||_inf = 1 = 2^d * 2^-d
-  if (y) {
-    d.meta_b = y->meta;
-    d.cl = 0; d.lb = 1; d.two = 1;
-    d.lbits = y->w + 1;
-    d.ng = 2;                                      // gamma = ||y|| + ||P|| ||d||
-    d.gv[0] = 1; d.gm[0] = 1; d.ge[0] = 0;
-    d.gv[1] = 0; d.gm[1] = 1ull << nd; d.ge[1] = eP;
-  } else {
-    d.two = 0;
-    d.ng = 1;                                      // gamma = ||P|| ||x||
-    d.gv[0] = 0; d.gm[0] = 1ull << nd; d.ge[0] = eP;
-  }
+  if (y) d.meta_b = y->meta;
   cudaStream_t s = as_stream(stream);
   if (nd == 2) return y ? prolong_launch<2, true>(dc, y, y_out, d, s) : prolong_launch<2, false>(dc, y, y_out, d, s);
   return y ? prolong_launch<3, true>(dc, y, y_out, d, s) : prolong_launch<3, false>(dc, y, y_out, d, s);

@@ -127,18 +127,25 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
   const int64_t nx = a.nx;
 
   if (!PASS1 && p.narrow) {
-    for (int64_t j = j0; j < j1; ++j) {
+    // window hit: 8 consecutive columns per lane, 4 rows of the warp's tile at a time
+    const int sh = (int)(p.e_out - p.e_tmp);
+    const int64_t col = cb + (lane & 7) * 8;
+    uint32_t nrm = 0;
+    if (col < a.out.ld) {
+      for (int64_t j = j0 + (lane >> 3); j < j1; j += 4) {
+        const int4* src = reinterpret_cast<const int4*>(a.tmp + j * a.out.ld + col);
+        const int4 u0 = src[0], u1 = src[1];
+        int32_t o[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-      for (int k = 0; k < kIrV; ++k) {
-        const int64_t i = cb + 32 * k + lane;
-        if (i < a.out.ld) {   // padding columns [nx, ld) are written as 0
-          const int32_t v = i < nx ? a.tmp[j * a.out.ld + i] >> (int)(p.e_out - p.e_tmp) : 0;
-          red.nrm = max(red.nrm, (long long)(v < 0 ? -(long long)v : (long long)v));
-          if (a.out.is32) reinterpret_cast<int32_t*>(a.out.m)[j * a.out.ld + i] = v;
-          else reinterpret_cast<int16_t*>(a.out.m)[j * a.out.ld + i] = (int16_t)v;
+        for (int k = 0; k < 8; ++k) {
+          o[k] = col + k < nx ? (o[k] >> sh) : 0;   // padding columns [nx, ld) are written as 0
+          const uint32_t av = (uint32_t)(o[k] < 0 ? -o[k] : o[k]);
+          nrm = av > nrm ? av : nrm;
         }
+        stv<8>(a.out, j, col, o);
       }
     }
+    red.nrm = max(red.nrm, (long long)nrm);
   } else if (j0 < j1) {
     auto ldrow = [&](int64_t j, double (&v)[kIrV]) {
 #pragma unroll

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include "bfp_coarse.cuh"
+#include "bfp_desc.h"
 #include "bfp_ir2d.cuh"
 
 using namespace bfp;
@@ -184,6 +186,14 @@ struct bfp_hierarchy {
   int64_t* ir_gam = nullptr;             // per level: previous IR residual mu* (+2^40), 0 = unknown
   int64_t* arena = nullptr;              // all call-site meta blocks, contiguous
   size_t arena_words = 0;
+  // on-chip coarse V-cycle: levels kc.. run in one CTA (kc = nlevels: disabled)
+  int kc = 0;
+  CoarseBuf* d_bufs = nullptr;
+  int nbufs = 0;
+  int smem_bytes = 0;
+  int meta_off = 0, ops_off = 0, bufs_off = 0;
+  std::vector<CoarseOp*> d_ops;          // per start level k >= kc
+  std::vector<int> nops, rbuf, ybuf;
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
   // captured IR step
   cudaGraphExec_t graph = nullptr;
@@ -240,6 +250,150 @@ Q make_q(const bfp_hierarchy* h, const Level& L) {
     if (_rc != BFP_OK) return _rc;     \
   } while (0)
 
+// ---- on-chip coarse V-cycle -------------------------------------------------
+
+struct CoarseLevelBufs {
+  int r, y0, y1;
+};
+
+// Flattens the V-cycle schedule of levels l.. (the same op order as vcycle_rec)
+int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vector<CoarseLevelBufs>& lb,
+                       std::vector<CoarseOp>& ops, int* res) {
+  const bool coarsest = (l + 1 == (int)h->lv.size());
+  const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
+  const CoarseLevelBufs& B = lb[l - h->kc];
+  int cur = B.y0, oth = B.y1;
+  const int w = h->o.w, nd = h->o.ndim;
+  auto push = [&](int kind, int a, int b, int out) -> int32_t {
+    CoarseOp op;
+    std::memset(&op, 0, sizeof(op));
+    op.kind = kind; op.a = a; op.b = b; op.out = out;
+    QDesc& d = op.q;
+    int rule = 0;
+    int32_t rc = BFP_OK;
+    switch (kind) {
+      case cJac0: rc = desc_jacobi(&h->A, 0, w, d, &rule); op.mw = h->A.omega.m; break;
+      case cJac: {
+        int64_t Sc, Sn, eS;
+        rc = desc_jacobi(&h->A, w, w, d, &rule);
+        if (!rc) rc = jacobi_operator(&h->A, &Sc, &Sn, &eS);
+        op.c = Sc; op.nb = Sn; op.mw = h->A.omega.m;
+        break;
+      }
+      case cRes: rc = desc_residual(&h->A, w, w, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
+      case cRestrict: rc = desc_restrict(nd, w, d, &rule); break;
+      default: rc = desc_prolong(nd, w, w, d, &rule); break;
+    }
+    if (rc) return rc;
+    if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;
+    d.mode = h->o.mode;
+    d.w_out = w;
+    d.w_tmp = w + rule;
+    d.use_tmp = 0;
+    ops.push_back(op);
+    return BFP_OK;
+  };
+  TRY(push(cJac0, -1, rbuf, cur));
+  for (int i = 1; i < nu1; ++i) { TRY(push(cJac, cur, rbuf, oth)); std::swap(cur, oth); }
+  if (!coarsest) {
+    const int rnext = lb[l + 1 - h->kc].r;
+    TRY(push(cRes, cur, rbuf, oth));                   // r_v (kept in the free ping-pong buffer)
+    TRY(push(cRestrict, oth, -1, rnext));
+    int d = -1;
+    TRY(coarse_flatten(h, l + 1, rnext, lb, ops, &d));
+    TRY(push(cProlong, d, cur, oth)); std::swap(cur, oth);
+    for (int i = 0; i < h->o.nu2; ++i) { TRY(push(cJac, cur, rbuf, oth)); std::swap(cur, oth); }
+  }
+  *res = cur;
+  return BFP_OK;
+}
+
+// Chooses kc and uploads the op lists; kc = nlevels disables the on-chip path.
+int32_t coarse_setup(bfp_hierarchy* h) {
+  const int nl = (int)h->lv.size();
+  h->kc = nl;
+  if (h->o.ndim != 2) return BFP_OK;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return BFP_OK;
+  const int budget = optin - 1024;
+  const int eb = h->o.w > 16 ? 4 : 2;
+  // the largest start level (n <= 127) whose levels, schedule and tables fit in shared memory
+  for (int k = 0; k < nl; ++k) {
+    if (h->lv[k].n > 127) continue;
+    const int64_t nops = (int64_t)(nl - 1 - k) * (h->o.nu1 + 3 + h->o.nu2) + h->o.coarse_sweeps;
+    int64_t bytes = (int64_t)(nl - k) * 3 * (BFP_META_WORDS * 8 + (int64_t)sizeof(CoarseBuf)) + nops * (int64_t)sizeof(CoarseOp) + 64;
+    for (int l = k; l < nl; ++l) bytes += 3 * (((int64_t)h->lv[l].n * h->lv[l].n * eb + 15) / 16 * 16);
+    if (bytes <= budget) { h->kc = k; break; }
+  }
+  if (h->kc == nl) return BFP_OK;
+  const int nb = (nl - h->kc) * 3;
+  const int max_ops = (nl - 1 - h->kc) * (h->o.nu1 + 3 + h->o.nu2) + h->o.coarse_sweeps;
+  // layout: meta blocks | buffer table | op list | mantissa buffers (16-byte aligned)
+  h->meta_off = 0;
+  h->bufs_off = nb * BFP_META_WORDS * 8;
+  h->ops_off = (int)(((int64_t)h->bufs_off + nb * (int64_t)sizeof(CoarseBuf) + 15) / 16 * 16);
+  int off = (int)(((int64_t)h->ops_off + max_ops * (int64_t)sizeof(CoarseOp) + 15) / 16 * 16);
+  std::vector<CoarseLevelBufs> lb;
+  std::vector<CoarseBuf> bufs;
+  for (int l = h->kc; l < nl; ++l) {
+    CoarseLevelBufs B;
+    int* ids[3] = {&B.r, &B.y0, &B.y1};
+    for (int t = 0; t < 3; ++t) {
+      *ids[t] = (int)bufs.size();
+      bufs.push_back(CoarseBuf{off, (int32_t)h->lv[l].n});
+      off += (int)(((int64_t)h->lv[l].n * h->lv[l].n * eb + 15) / 16 * 16);
+    }
+    lb.push_back(B);
+  }
+  h->smem_bytes = off;
+  h->nbufs = nb;
+  h->d_bufs = (CoarseBuf*)dalloc(h, bufs.size() * sizeof(CoarseBuf));
+  if (!h->d_bufs) return BFP_ERR_CUDA;
+  cudaMemcpy(h->d_bufs, bufs.data(), bufs.size() * sizeof(CoarseBuf), cudaMemcpyHostToDevice);
+  for (int k = h->kc; k < nl; ++k) {
+    std::vector<CoarseOp> ops;
+    int res = -1;
+    TRY(coarse_flatten(h, k, lb[k - h->kc].r, lb, ops, &res));
+    if ((int)ops.size() > max_ops) return BFP_ERR_ARG;
+    CoarseOp* d = (CoarseOp*)dalloc(h, ops.size() * sizeof(CoarseOp));
+    if (!d) return BFP_ERR_CUDA;
+    cudaMemcpy(d, ops.data(), ops.size() * sizeof(CoarseOp), cudaMemcpyHostToDevice);
+    h->d_ops.push_back(d);
+    h->nops.push_back((int)ops.size());
+    h->rbuf.push_back(lb[k - h->kc].r);
+    h->ybuf.push_back(res);
+  }
+  if (cudaFuncSetAttribute(k_coarse_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_bytes) !=
+      cudaSuccess)
+    return BFP_ERR_CUDA;
+  return BFP_OK;
+}
+
+int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* out, cudaStream_t s) {
+  const int i = k - h->kc;
+  CoarseArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.ops = h->d_ops[i];
+  a.nops = h->nops[i];
+  a.bufs = h->d_bufs;
+  a.nbufs = h->nbufs;
+  a.is32 = h->o.w > 16 ? 1 : 0;
+  a.meta_off = h->meta_off;
+  a.ops_off = h->ops_off;
+  a.bufs_off = h->bufs_off;
+  a.rin = vin(r);
+  a.rin_meta = r->meta;
+  a.rin_buf = h->rbuf[i];
+  a.yout = vout(out);
+  a.yout_meta = out->meta;
+  a.yout_buf = h->ybuf[i];
+  a.stats = h->stats;
+  k_coarse_vcycle<<<1, 1024, h->smem_bytes, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
 // V(nu1, nu2) on level k: the approximate solution of A' y = r ends in bufA's
 // mantissas; *res describes it (its meta block is a call-site slot of level k).
 // Every op writes a meta block of its own (zeroed once per step), so the ops
@@ -254,6 +408,12 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
     v.meta = L.slots + BFP_META_WORDS * (slot++);
     return v;
   };
+  if (k >= h->kc) {                       // the rest of the cycle on one SM
+    bfp_vec y = at_slot(bufA);
+    TRY(coarse_vcycle(h, k, r, &y, s));
+    *res = y;
+    return BFP_OK;
+  }
   const bool coarsest = (k + 1 == (int)h->lv.size());
   const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
   // writes per level: 1 (omega r) + (nu1 - 1) sweeps [+ correction + nu2 sweeps]
@@ -389,6 +549,7 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
   o->w_omega = 16;
   o->use_tmp = 1;
   o->use_graph = 1;
+  o->coarse_onchip = 1;
   return BFP_OK;
 }
 
@@ -451,6 +612,11 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
       off += (size_t)h->lv[k].nslots * BFP_META_WORDS;
     }
     if (ok) cudaMemset(h->arena, 0, words * sizeof(int64_t));
+  }
+  h->kc = (int)h->lv.size();
+  if (ok && o->coarse_onchip) {
+    int32_t crc = coarse_setup(h);
+    if (crc) { bfp_hierarchy_destroy(h); return crc; }
   }
   if (ok) {
     h->stats = (uint64_t*)dalloc(h, 8 * sizeof(uint64_t));

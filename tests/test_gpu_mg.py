@@ -11,22 +11,24 @@ from oracle import mg  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def make(nd, n, w, mode, use_tmp=1, use_graph=1):
+def make(nd, n, w, mode, use_tmp=1, use_graph=1, coarse_onchip=1):
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
     o.use_tmp = use_tmp
     o.use_graph = use_graph
+    o.coarse_onchip = coarse_onchip
     h = bfp.Hierarchy(o)
     s = mg.BFPSolver(nd, n, w=w, mode="qcomp" if mode == bfp.QCOMP else "nnqcomp",
                      omega=o.omega, w_omega=o.w_omega)
     return h, s
 
 
-@pytest.mark.parametrize("nd,n", [(2, 63), (2, 31), (3, 15)])
+@pytest.mark.parametrize("nd,n", [(2, 63), (2, 31), (2, 255), (3, 15)])
 @pytest.mark.parametrize("w", [8, 16, 32])
 @pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
-def test_vcycle_bit_exact(nd, n, w, mode):
-    h, s = make(nd, n, w, mode)
+@pytest.mark.parametrize("onchip", [1, 0])
+def test_vcycle_bit_exact(nd, n, w, mode, onchip):
+    h, s = make(nd, n, w, mode, coarse_onchip=onchip)
     rm = random_mantissas((n,) * nd, w, 5, "smooth")
     r = bfp.BFPVector.from_mantissas(rm, -30, w)
     y = bfp.BFPVector((n,) * nd, w)
