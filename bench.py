@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--op", default=None, choices=[None, "jacobi", "residual", "restrict", "prolong", "ir_residual",
-                                                  "ir_update", "step"],
+                                                  "ir_update", "step", "vcycle"],
                    help="run one finest-level op --reps times and exit (profiling driver)")
     p.add_argument("--reps", type=int, default=3)
     return p.parse_args()
@@ -343,6 +343,7 @@ def run_op(args):
         "ir_residual": lambda: h.ir_residual(f, x, yo),
         "ir_update": lambda: bfp.bfp_ir_update(x, y),
         "step": lambda: h.ir_iterate(f, x, 1),
+        "vcycle": lambda: h.vcycle(r, yo),
     }
     for _ in range(args.reps):
         ops[args.op]()

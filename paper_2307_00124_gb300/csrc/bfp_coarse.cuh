@@ -5,13 +5,23 @@
 // launches.  One CTA instead runs every level from n_c (<= 127) down to 3 in
 // shared memory: the host flattens the recursive schedule of Alg. v-cycle
 // (exactly the order the global driver uses) into a list of ops; the CTA
-// executes the list with __syncthreads between passes.  Each op builds its
-// plan from the same QDesc the C ABI op would use and quantises through the
-// same device arithmetic (combine / mu_key / finish), so the result is
-// bit-identical to running the ops one by one.  qcomp's second pass always
-// recomputes (the window is only a cache); its overflow / underflow counts
-// are still those of Alg. qcomp.
+// executes the list.  Each op builds its plan from the same QDesc the C ABI op
+// would use and quantises through the same device arithmetic (combine /
+// mu_key / finish), so the result is bit-identical to running the ops one by
+// one.  qcomp's second pass always recomputes (the window is only a cache);
+// its overflow / underflow counts are still those of Alg. qcomp.
+//
+// Synchronisation: every thread plans each op in registers, so an nnqcomp op
+// costs one block barrier (qcomp two).  Ops on levels with n <= 15 run on warp
+// 0 alone with warp reductions while the other warps wait at the next
+// full-block op.
+//
+// Buffers are stored with a zero halo: point (i, j) of an n x n level sits at
+// (j + 1)(n + 2) + i + 1, so no neighbour, restriction or interpolation read
+// needs a bounds test.
 #pragma once
+
+#include <type_traits>
 
 #include "bfp_host.h"
 
@@ -22,12 +32,14 @@ enum CoarseKind : int32_t { cJac0 = 0, cJac = 1, cRes = 2, cRestrict = 3, cProlo
 struct CoarseOp {
   int32_t kind;
   int32_t a, b, out;     // buffer ids (-1: none)
+  int32_t solo;          // run by warp 0 alone
+  int32_t sync_before;   // first full-block op after a run of solo ops
   int64_t c, nb, mw;     // stencil / smoother coefficients
-  QDesc q;               // static description; meta pointers are set on the device
+  QDesc q;               // static description (meta pointers unused)
 };
 
 struct CoarseBuf {
-  int32_t off;           // byte offset of the mantissas in dynamic shared memory
+  int32_t off;           // byte offset of the (n + 2)^2 padded buffer in dynamic shared memory
   int32_t n;             // points per side
 };
 
@@ -35,10 +47,11 @@ struct CoarseArgs {
   const CoarseOp* ops;
   const CoarseBuf* bufs;
   int32_t nops, nbufs;
-  int32_t is32;          // mantissa storage: int32 (else int16)
   int32_t meta_off;      // byte offsets in dynamic shared memory: meta blocks,
-  int32_t ops_off;       // the op list (copied in at start) and
+  int32_t ops_off;       // the op list (copied in at start),
   int32_t bufs_off;      // the buffer table
+  int32_t data_off;      // and the mantissa buffers (up to smem_bytes)
+  int32_t smem_bytes;
   VIn rin;               // level n_c right-hand side (global) ...
   const int64_t* rin_meta;
   int32_t rin_buf;       // ... and the buffer it is loaded into
@@ -48,210 +61,486 @@ struct CoarseArgs {
   uint64_t* stats;
 };
 
-struct CoarseMem {
-  unsigned char* base;
-  int32_t is32;
-  __device__ __forceinline__ int32_t get(const CoarseBuf& b, int i, int j) const {
-    if (i < 0 || j < 0 || i >= b.n || j >= b.n) return 0;
-    const int idx = j * b.n + i;
-    return is32 ? reinterpret_cast<const int32_t*>(base + b.off)[idx]
-                : (int32_t)reinterpret_cast<const int16_t*>(base + b.off)[idx];
+// W: a type wide enough for sums of 16 mantissas of T
+template <class T>
+struct CoarseView {
+  using W = typename std::conditional<sizeof(T) == 2, int32_t, int64_t>::type;
+  T* p;
+  int s;                 // row stride n + 2
+  __device__ __forceinline__ W operator()(int i, int j) const { return (W)p[(j + 1) * s + i + 1]; }
+  __device__ __forceinline__ void put(int i, int j, int32_t v) const { p[(j + 1) * s + i + 1] = (T)v; }
+};
+
+template <class T>
+__device__ __forceinline__ CoarseView<T> cview(unsigned char* sm, const CoarseBuf& b) {
+  return CoarseView<T>{reinterpret_cast<T*>(sm + b.off), b.n + 2};
+}
+
+// General (wide / guarded / below-Ez) quantisation of one element, out of line.
+__device__ __noinline__ long long coarse_key_general(int64_t H, int64_t L, const Plan* pp) {
+  const Plan& p = *pp;
+  if (p.wide) {
+    const i128 Z = combine<i128>(H, L, p);
+    return mu_key<i128>(Z, H, L, p);
   }
-  __device__ __forceinline__ void put(const CoarseBuf& b, int idx, int32_t v) const {
-    if (is32) reinterpret_cast<int32_t*>(base + b.off)[idx] = v;
-    else reinterpret_cast<int16_t*>(base + b.off)[idx] = (int16_t)v;
+  const int64_t Z = combine<int64_t>(H, L, p);
+  return mu_key<int64_t>(Z, H, L, p);
+}
+
+// value in the low 32 bits, saturation count above
+__device__ __noinline__ int64_t coarse_val_general(int64_t H, int64_t L, const Plan* pp) {
+  const Plan& p = *pp;
+  int sat = 0;
+  int32_t v;
+  if (p.wide) {
+    const i128 Z = combine<i128>(H, L, p);
+    v = finish<i128>(Z, H, L, p, sat);
+  } else {
+    const int64_t Z = combine<int64_t>(H, L, p);
+    v = finish<int64_t>(Z, H, L, p, sat);
+  }
+  return (int64_t)(uint32_t)v | ((int64_t)sat << 32);
+}
+
+// int16 register path: Z is a sum of at most three products k_s * P_s of int32
+// multipliers (the op's coefficients with the group shifts dh / dl folded in)
+// and int32 partial sums P_s of mantissas, each one mul.wide; the result is
+// the low word of Z >> t, saturated through one range test on Z.
+struct CoarseMul {
+  int32_t ok;
+  int32_t k0, k1, k2;   // multipliers of the partial sums (see coarse_pass16)
+  int32_t t;            // Z >> t gives the result
+  int32_t clamp;        // nnqcomp saturation test active
+  int32_t vlo, vhi;     // X_w bounds
+  int64_t zmin;         // vlo 2^t
+  uint64_t zrange;      // 2^(w + t): Z in range iff Z - zmin < zrange (unsigned)
+};
+
+// k = c 2^sh when that fits in int32 (c itself fits in int32 by construction)
+__device__ __forceinline__ bool fold_mul(int32_t c, int32_t sh, int32_t& k) {
+  const int32_t s = sh & 31;
+  const int32_t v = (int32_t)((uint32_t)c << s);
+  k = v;
+  return c == 0 || (sh <= 30 && (v >> s) == c);
+}
+
+__device__ __forceinline__ CoarseMul make_mul(int kind, const Fast& f, const CoarseOp& op) {
+  CoarseMul m;
+  m.k0 = m.k1 = m.k2 = 0;
+  m.t = f.t;
+  const int32_t w = f.w > 32 ? 32 : f.w;
+  m.vhi = (int32_t)((1u << (w - 1)) - 1u);
+  m.vlo = -m.vhi - 1;
+  const int32_t e = f.w + f.t;                // the range is [vlo 2^t, (vhi + 1) 2^t)
+  m.clamp = f.clamp && e <= 63;               // beyond that every int64 Z is in range
+  const uint32_t lo = e < 32 ? (1u << (e & 31)) : 0u, hi = e < 32 ? 0u : (1u << ((e - 32) & 31));
+  m.zrange = m.clamp ? (((uint64_t)hi << 32) | lo) : 0;
+  m.zmin = -(int64_t)(m.zrange >> 1);
+  const int32_t c = (int32_t)op.c, nb = (int32_t)op.nb, mw = (int32_t)op.mw;
+  bool ok;
+  if (kind == cJac0) ok = fold_mul(mw, f.dh, m.k0);
+  else if (kind == cJac) ok = fold_mul(c, f.dh, m.k0) & fold_mul(nb, f.dh, m.k1) & fold_mul(mw, f.dl, m.k2);
+  else if (kind == cRes) ok = fold_mul(c, f.dh, m.k0) & fold_mul(nb, f.dh, m.k1) & fold_mul(-1, f.dl, m.k2);
+  else if (kind == cRestrict) ok = fold_mul(1, f.dh, m.k0);
+  else ok = fold_mul(-1, f.dh, m.k0) & fold_mul(1, f.dl, m.k2);
+  m.ok = (ok && f.ok && f.w <= 32) ? 1 : 0;
+  return m;
+}
+
+// What every thread needs to run one pass of an op (built once per pass by one thread).
+struct CoarseExec {
+  Fast f;
+  CoarseMul m;
+};
+
+// Columns per thread and row: n <= 127 with 32 lanes, or n <= 15 with 16.
+constexpr int kCoarseCols = 4;
+constexpr int kCoarseThreads = 512;
+
+struct CoarseRes {
+  long long key, nrm;
+  int sat;
+};
+
+// The general pass (any storage type, any plan), kept out of line: it runs only
+// for int32 storage or when the int16 register path does not apply.
+template <class T, int KIND, bool PASS1>
+__device__ __noinline__ CoarseRes coarse_pass_any(unsigned char* sm, const CoarseOp& op, const CoarseBuf bo,
+                                                  const CoarseBuf* bufs, const Fast f, const Plan* pp, int i0,
+                                                  int istep, int j0, int jstep) {
+  long long key = 0, nrm = 0;
+  int sat = 0;
+  const int n = bo.n;
+  const CoarseView<T> O = cview<T>(sm, bo);
+  const CoarseView<T> A = cview<T>(sm, bufs[op.a >= 0 ? op.a : op.out]);
+  const CoarseView<T> B = cview<T>(sm, bufs[op.b >= 0 ? op.b : op.out]);
+  const int64_t c = op.c, nbc = op.nb, mw = op.mw;
+  const int64_t hi = (1ll << (f.w - 1)) - 1, lo = -(1ll << (f.w - 1));
+  using W = typename CoarseView<T>::W;
+  for (int j = j0; j < n; j += jstep) {
+    for (int u = 0; u < kCoarseCols; ++u) {
+      const int i = i0 + u * istep;
+      if (i >= n) break;
+      int64_t H, L;
+      if (KIND == cJac0) {
+        H = mw * B(i, j);
+        L = 0;
+      } else if (KIND == cJac || KIND == cRes) {
+        const int64_t ns = (int64_t)(A(i - 1, j) + A(i + 1, j)) + (A(i, j - 1) + A(i, j + 1));
+        H = c * A(i, j) + nbc * ns;
+        L = KIND == cJac ? mw * B(i, j) : -(int64_t)B(i, j);
+      } else if (KIND == cRestrict) {
+        const int fi = 2 * i + 1, fj = 2 * j + 1;
+        const W r0 = A(fi - 1, fj - 1) + 2 * A(fi, fj - 1) + A(fi + 1, fj - 1);
+        const W r1 = A(fi - 1, fj) + 2 * A(fi, fj) + A(fi + 1, fj);
+        const W r2 = A(fi - 1, fj + 1) + 2 * A(fi, fj + 1) + A(fi + 1, fj + 1);
+        H = (int64_t)r0 + 2 * (int64_t)r1 + r2;
+        L = 0;
+      } else {
+        auto g = [&](int J) -> W {
+          return (i & 1) ? 2 * A((i - 1) >> 1, J) : A((i >> 1) - 1, J) + A(i >> 1, J);
+        };
+        const W pd = (j & 1) ? 2 * g((j - 1) >> 1) : g((j >> 1) - 1) + g(j >> 1);
+        H = -(int64_t)pd;
+        L = B(i, j);
+      }
+      if (f.ok) {
+        const int64_t Z = (int64_t)((uint64_t)H << f.dh) + (int64_t)((uint64_t)L << f.dl);
+        if (PASS1) {
+          key = max(key, (long long)(256 + msb64(Z)));
+        } else {
+          int64_t t = Z >> f.t;
+          if (f.clamp) {
+            if (t > hi) { t = hi; ++sat; } else if (t < lo) { t = lo; ++sat; }
+          }
+          O.put(i, j, (int32_t)t);
+          nrm = max(nrm, (long long)(t < 0 ? -t : t));
+        }
+      } else if (PASS1) {
+        key = max(key, coarse_key_general(H, L, pp));
+      } else {
+        const int64_t r = coarse_val_general(H, L, pp);
+        const int32_t v = (int32_t)(uint32_t)r;
+        sat += (int)(r >> 32);
+        O.put(i, j, v);
+        nrm = max(nrm, (long long)(v < 0 ? -(long long)v : (long long)v));
+      }
+    }
+  }
+  return CoarseRes{key, nrm, sat};
+}
+
+// One pass of one op over points (i0 + istep u, j0 + jstep v), u < kCoarseCols.
+template <class T, int KIND, bool PASS1>
+__device__ __forceinline__ void coarse_pass(unsigned char* sm, const CoarseOp& op, const CoarseBuf* bufs,
+                                            const CoarseExec& ex, const Plan* pp, int i0, int istep, int j0,
+                                            int jstep, long long& key, long long& nrm, int& sat) {
+  const CoarseBuf bo = bufs[op.out];
+  const int n = bo.n;
+  if (sizeof(T) == 2 && ex.m.ok) {
+    const CoarseMul& m = ex.m;
+    const CoarseView<int16_t> O = cview<int16_t>(sm, bo);
+    const CoarseView<int16_t> A = cview<int16_t>(sm, bufs[op.a >= 0 ? op.a : op.out]);
+    const CoarseView<int16_t> B = cview<int16_t>(sm, bufs[op.b >= 0 ? op.b : op.out]);
+    uint64_t ormag = 0;
+    bool any = false;
+    uint32_t nr = 0;
+    for (int j = j0; j < n; j += jstep) {
+#pragma unroll
+      for (int u = 0; u < kCoarseCols; ++u) {
+        const int i = i0 + u * istep;
+        if (i >= n) break;
+        int64_t z;
+        if (KIND == cJac0) {
+          z = (int64_t)m.k0 * B(i, j);
+        } else if (KIND == cJac || KIND == cRes) {
+          const int32_t ns = (A(i - 1, j) + A(i + 1, j)) + (A(i, j - 1) + A(i, j + 1));
+          z = (int64_t)m.k0 * A(i, j) + (int64_t)m.k1 * ns + (int64_t)m.k2 * B(i, j);
+        } else if (KIND == cRestrict) {
+          // coarse (i, j) gathers fine (2i+1+dx, 2j+1+dy) with weights (2-|dx|)(2-|dy|)
+          const int fi = 2 * i + 1, fj = 2 * j + 1;
+          const int32_t r0 = A(fi - 1, fj - 1) + 2 * A(fi, fj - 1) + A(fi + 1, fj - 1);
+          const int32_t r1 = A(fi - 1, fj) + 2 * A(fi, fj) + A(fi + 1, fj);
+          const int32_t r2 = A(fi - 1, fj + 1) + 2 * A(fi, fj + 1) + A(fi + 1, fj + 1);
+          z = (int64_t)m.k0 * (r0 + 2 * r1 + r2);
+        } else {  // cProlong with correction: Z = -P_m d 2^dh + y 2^dl
+          // fine i odd sits on coarse (i-1)/2 (weight 2); even i between i/2-1 and i/2
+          auto g = [&](int J) -> int32_t {
+            return (i & 1) ? 2 * A((i - 1) >> 1, J) : A((i >> 1) - 1, J) + A(i >> 1, J);
+          };
+          const int32_t pd = (j & 1) ? 2 * g((j - 1) >> 1) : g((j >> 1) - 1) + g(j >> 1);
+          z = (int64_t)m.k0 * pd + (int64_t)m.k2 * B(i, j);
+        }
+        if (PASS1) {
+          ormag |= (uint64_t)(z ^ (z >> 63));
+          any = true;
+        } else {
+          const uint32_t zl = (uint32_t)z, zh = (uint32_t)((uint64_t)z >> 32);
+          int32_t v = m.t < 32 ? (int32_t)__funnelshift_r(zl, zh, m.t) : ((int32_t)zh >> (m.t - 32));
+          if (m.clamp && (uint64_t)(z - m.zmin) >= m.zrange) {
+            v = z < 0 ? m.vlo : m.vhi;
+            ++sat;
+          }
+          O.put(i, j, v);
+          const uint32_t a = (uint32_t)(v < 0 ? -v : v);
+          nr = a > nr ? a : nr;
+        }
+      }
+    }
+    if (PASS1 && any) key = max(key, (long long)(256 + (64 - __clzll((long long)ormag)) + 1));
+    nrm = max(nrm, (long long)nr);
+    return;
+  }
+  const CoarseRes r = coarse_pass_any<T, KIND, PASS1>(sm, op, bo, bufs, ex.f, pp, i0, istep, j0, jstep);
+  key = max(key, r.key);
+  nrm = max(nrm, r.nrm);
+  sat += r.sat;
+}
+
+template <class T, bool PASS1>
+__device__ __forceinline__ void coarse_dispatch(unsigned char* sm, const CoarseOp& op, const CoarseBuf* bufs,
+                                                const CoarseExec& ex, const Plan* pp, int i0, int istep, int j0,
+                                                int jstep, long long& key, long long& nrm, int& sat) {
+  switch (op.kind) {
+    case cJac0: coarse_pass<T, cJac0, PASS1>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat); break;
+    case cJac: coarse_pass<T, cJac, PASS1>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat); break;
+    case cRes: coarse_pass<T, cRes, PASS1>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat); break;
+    case cRestrict: coarse_pass<T, cRestrict, PASS1>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat); break;
+    default: coarse_pass<T, cProlong, PASS1>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat); break;
+  }
+}
+
+// Register plan of one op for the fast paths: the part of the full Plan that
+// the passes and the meta block need, computed by every thread that runs the
+// op (no shared-memory round trip, no barrier).  Exponents are handled in
+// int32 (inputs within +-2^28).  Whenever the full plan would not take the
+// fast path (wide or guarded groups, a result exponent below Ez) lean_first /
+// lean_second return false and the op runs from the full Plan instead.
+struct CoarseLean {
+  int32_t Ez, Gam, e_out;
+  int32_t D, top, two;
+  int32_t ov, un;               // qcomp overflow / underflow of the second pass
+};
+
+__device__ __forceinline__ void lean_exec(const CoarseOp& op, const CoarseLean& L, int32_t t, int32_t w, bool pass1,
+                                          bool clamp, CoarseExec& ex) {
+  ex.f.ok = 1;
+  ex.f.dh = (L.two && L.top) ? L.D : 0;
+  ex.f.dl = (L.two && !L.top) ? L.D : 0;
+  ex.f.t = t < 0 ? 0 : (t > 63 ? 63 : t);
+  ex.f.w = w;
+  ex.f.clamp = (!pass1 && clamp) ? 1 : 0;
+  ex.m = make_mul(op.kind, ex.f, op);
+}
+
+__device__ __forceinline__ bool lean_first(const CoarseOp& op, int64_t ea64, int64_t na, int64_t eb64, int64_t nb,
+                                           CoarseLean& L, CoarseExec& ex) {
+  const QDesc& q = op.q;
+  const int64_t lim = 1ll << 28;
+  if (ea64 <= -lim || ea64 >= lim || eb64 <= -lim || eb64 >= lim) return false;
+  const int32_t ea = (int32_t)ea64, eb = (int32_t)eb64;
+  const int32_t Eh = (int32_t)q.ch + (q.ha ? ea : 0) + (q.hb ? eb : 0);
+  const int32_t El = (int32_t)q.cl + (q.la ? ea : 0) + (q.lb ? eb : 0);
+  L.two = q.two;
+  const int32_t d = q.two ? Eh - El : 0;
+  L.top = d >= 0;
+  L.D = d >= 0 ? d : -d;
+  L.Ez = (q.two && d > 0) ? El : Eh;
+  const bool wide = q.two && ((L.top ? q.hbits : q.lbits) + L.D > 62);
+  // gamma (Table tab:estimates rule) exactly as build_plan_v
+  const uint64_t a0 = q.gm[0] * (uint64_t)(q.gv[0] == 0 ? na : nb);
+  const int64_t e0 = q.ge[0] + (q.gv[0] == 0 ? ea : eb);
+  uint64_t a1 = 0;
+  int64_t e1 = 0;
+  if (q.ng > 1) {
+    a1 = q.gm[1] * (uint64_t)(q.gv[1] == 0 ? na : nb);
+    e1 = q.ge[1] + (q.gv[1] == 0 ? ea : eb);
+  }
+  int64_t G = 0;
+  const bool nz = gamma_msb(a0, e0, a1, e1, &G);
+  L.Gam = nz ? (int32_t)G : L.Ez + 1;
+  L.e_out = L.Gam - q.w_out;
+  L.ov = L.un = 0;
+  const bool qc = q.mode == kQcomp;
+  const int32_t t = qc ? (L.Gam - q.w_tmp) - L.Ez : L.e_out - L.Ez;
+  if (wide || (!qc && t < 0) || q.has_gamma || q.use_tmp) return false;
+  lean_exec(op, L, t, qc ? q.w_tmp : q.w_out, qc, q.mode == kNnqcomp, ex);
+  return true;
+}
+
+// qcomp: the second pass from the block maximum key (plan_from_mu with Eb = e* = Ez)
+__device__ __forceinline__ bool lean_second(const CoarseOp& op, int32_t key, CoarseLean& L, CoarseExec& ex) {
+  const QDesc& q = op.q;
+  const int32_t mu = key >= 256 ? L.Ez + (key - 256) : (key > 0 ? L.Ez + key : L.Ez + 1);
+  L.e_out = mu - q.w_out;
+  L.ov = L.Gam < mu;
+  L.un = L.e_out < L.Gam - q.w_tmp;
+  const int32_t t = L.e_out - L.Ez;
+  if (t < 0) return false;
+  lean_exec(op, L, t, q.w_out, false, false, ex);
+  return true;
+}
+
+struct CoarseCounts {
+  unsigned long long calls, recomputed, overflow, underflow;
+  __device__ __forceinline__ void add(bool ov, bool un, bool qc) {
+    calls += 1;
+    if (qc) {
+      if (ov || un) recomputed += 1;
+      if (ov) overflow += 1;
+      if (un) underflow += 1;
+    }
   }
 };
 
-// exact groups (H, L) of one output element of a coarse op
-__device__ __forceinline__ void coarse_elem(const CoarseOp& op, const CoarseMem& m, const CoarseBuf& ba,
-                                            const CoarseBuf& bb, int i, int j, int64_t& H, int64_t& L) {
-  switch (op.kind) {
-    case cJac0:
-      H = op.mw * (int64_t)m.get(bb, i, j);
-      L = 0;
-      break;
-    case cJac:
-    case cRes: {
-      const int64_t ns = (int64_t)m.get(ba, i - 1, j) + m.get(ba, i + 1, j) + m.get(ba, i, j - 1) + m.get(ba, i, j + 1);
-      H = op.c * (int64_t)m.get(ba, i, j) + op.nb * ns;
-      const int64_t rv = m.get(bb, i, j);
-      L = op.kind == cJac ? op.mw * rv : -rv;
-      break;
-    }
-    case cRestrict: {
-      // coarse (i, j) gathers fine (2i+1+dx, 2j+1+dy) with weights (2-|dx|)(2-|dy|)
-      int64_t acc = 0;
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx)
-          acc += (int64_t)((2 - (dx < 0 ? -dx : dx)) * (2 - (dy < 0 ? -dy : dy))) *
-                 m.get(ba, 2 * i + 1 + dx, 2 * j + 1 + dy);
-      H = acc;
-      L = 0;
-      break;
-    }
-    default: {  // cProlong with correction: H = -P_m d, L = y
-      int64_t acc = 0;
-      int Jy[2], wy[2], ny = 0, Ix[2], wx[2], nx = 0;
-      if (j & 1) { Jy[0] = (j - 1) / 2; wy[0] = 2; ny = 1; } else { Jy[0] = j / 2 - 1; wy[0] = 1; Jy[1] = j / 2; wy[1] = 1; ny = 2; }
-      if (i & 1) { Ix[0] = (i - 1) / 2; wx[0] = 2; nx = 1; } else { Ix[0] = i / 2 - 1; wx[0] = 1; Ix[1] = i / 2; wx[1] = 1; nx = 2; }
-      for (int u = 0; u < ny; ++u)
-        for (int v = 0; v < nx; ++v) acc += (int64_t)(wy[u] * wx[v]) * m.get(ba, Ix[v], Jy[u]);
-      H = -acc;
-      L = m.get(bb, i, j);
-      break;
-    }
-  }
-}
-
-// One element's result in the register fast path (see Fast) or the general path.
-template <bool PASS1>
-__device__ __forceinline__ void coarse_quant(int64_t H, int64_t L, const Plan& p, const Fast& f, long long& key,
-                                             int32_t& v, int& sat) {
-  if (f.ok) {
-    const int64_t Z = (int64_t)((uint64_t)H << f.dh) + (int64_t)((uint64_t)L << f.dl);
-    if (PASS1) {
-      key = max(key, (long long)(256 + msb64(Z)));
-    } else {
-      int64_t t = Z >> f.t;
-      if (f.clamp) {
-        const int64_t hi = (1ll << (f.w - 1)) - 1, lo = -(1ll << (f.w - 1));
-        if (t > hi) { t = hi; ++sat; } else if (t < lo) { t = lo; ++sat; }
-      }
-      v = (int32_t)t;
-    }
-    return;
-  }
-  if (p.wide) {
-    const i128 Z = combine<i128>(H, L, p);
-    if (PASS1) key = max(key, (long long)mu_key<i128>(Z, H, L, p));
-    else v = finish<i128>(Z, H, L, p, sat);
-  } else {
-    const int64_t Z = combine<int64_t>(H, L, p);
-    if (PASS1) key = max(key, (long long)mu_key<int64_t>(Z, H, L, p));
-    else v = finish<int64_t>(Z, H, L, p, sat);
-  }
-}
-
-__global__ void __launch_bounds__(1024, 1) k_coarse_vcycle(const CoarseArgs a) {
+// Every thread that runs an op plans it in registers; a full-block op then
+// costs one barrier (qcomp two) for its block maximum, a solo op (warp 0
+// alone) only warp reductions.  Thread 0 writes every meta block; the output
+// meta of the previous op stays in registers (prev / pe / pn) until then.
+// Block maxima rotate over three slots (full-block op c uses slot c mod 3 and
+// clears slot c + 1 before its first barrier).
+template <class T>
+__global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const CoarseArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ Plan sp;
-  __shared__ Fast sf;
-  __shared__ long long s_key, s_nrm, s_sat;
-  __shared__ unsigned long long s_cnt[5];
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const CoarseMem m{sm, a.is32};
+  __shared__ Plan s_plan[kCoarseThreads / 32];   // full plans (general path only)
+  __shared__ unsigned int s_key[3], s_nrm[3];
+  __shared__ unsigned long long s_sat;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
   int64_t* metas = reinterpret_cast<int64_t*>(sm + a.meta_off);
-  // the schedule and buffer table live in shared memory for the whole cycle
   CoarseOp* ops = reinterpret_cast<CoarseOp*>(sm + a.ops_off);
   CoarseBuf* bufs = reinterpret_cast<CoarseBuf*>(sm + a.bufs_off);
+  // zero the meta blocks and the buffers (halo included); copy the schedule in
   {
+    int4* mz = reinterpret_cast<int4*>(sm + a.meta_off);
+    for (int i = tid; i < a.nbufs * BFP_META_WORDS / 2; i += nth) mz[i] = make_int4(0, 0, 0, 0);
+    int4* dz = reinterpret_cast<int4*>(sm + a.data_off);
+    for (int i = tid; i < (a.smem_bytes - a.data_off) / 16; i += nth) dz[i] = make_int4(0, 0, 0, 0);
     const int n4 = (int)(a.nops * sizeof(CoarseOp) / 4);
     for (int i = tid; i < n4; i += nth) reinterpret_cast<int32_t*>(ops)[i] = reinterpret_cast<const int32_t*>(a.ops)[i];
     for (int i = tid; i < a.nbufs; i += nth) bufs[i] = a.bufs[i];
+    if (tid < 3) { s_key[tid] = 0; s_nrm[tid] = 0; }
+    if (tid == 0) s_sat = 0;
   }
-  if (tid < 5) s_cnt[tid] = 0;
   __syncthreads();
-  // load the level-n_c right-hand side and its meta
+  // the level-n_c right-hand side and its meta
   {
-    const CoarseBuf rb = bufs[a.rin_buf];
-    const int tot = rb.n * rb.n;
-    for (int idx = tid; idx < tot; idx += nth) {
-      const int i = idx % rb.n, j = idx / rb.n;
-      const int64_t off = (int64_t)j * a.rin.ld + i;
-      const int32_t v = a.is32 ? reinterpret_cast<const int32_t*>(a.rin.m)[off]
-                               : (int32_t)reinterpret_cast<const int16_t*>(a.rin.m)[off];
-      m.put(rb, idx, v);
-    }
+    const CoarseView<T> R = cview<T>(sm, bufs[a.rin_buf]);
+    const int n = bufs[a.rin_buf].n;
+    for (int j = warp; j < n; j += nw)
+      for (int i = lane; i < n; i += 32) R.p[(j + 1) * R.s + i + 1] = reinterpret_cast<const T*>(a.rin.m)[(int64_t)j * a.rin.ld + i];
     if (tid < BFP_META_WORDS) metas[a.rin_buf * BFP_META_WORDS + tid] = a.rin_meta[tid];
   }
   __syncthreads();
-  for (int oi = 0; oi < a.nops; ++oi) {
-    const CoarseOp& op = ops[oi];
-    const CoarseBuf bo = bufs[op.out];
-    const CoarseBuf ba = op.a >= 0 ? bufs[op.a] : bo;
-    const CoarseBuf bb = op.b >= 0 ? bufs[op.b] : bo;
+  int prev = -1;                 // output buffer of the previous op, meta in (pe, pn)
+  int64_t pe = 0, pn = 0;
+  int c = 0;                     // full-block ops so far
+  int sat = 0;
+  CoarseCounts cnt = {0, 0, 0, 0};
+  Plan* pp = &s_plan[warp];
+  for (int k = 0; k < a.nops; ++k) {
+    const CoarseOp& op = ops[k];
+    const bool solo = op.solo != 0;
+    if (solo && warp != 0) continue;
+    if (op.sync_before) {
+      __syncthreads();           // the solo ops' results and meta blocks
+      prev = -1;
+    }
+    int64_t ea = 0, na = 0, eb = 0, nb = 0;
+    if (op.a >= 0) {
+      if (op.a == prev) { ea = pe; na = pn; }
+      else { ea = metas[op.a * BFP_META_WORDS]; na = metas[op.a * BFP_META_WORDS + 1]; }
+    }
+    if (op.b >= 0) {
+      if (op.b == prev) { eb = pe; nb = pn; }
+      else { eb = metas[op.b * BFP_META_WORDS]; nb = metas[op.b * BFP_META_WORDS + 1]; }
+    }
     const bool qc = op.q.mode == kQcomp;
-    if (tid == 0) {
-      QDesc q = op.q;
-      q.meta_a = op.a >= 0 ? metas + op.a * BFP_META_WORDS : nullptr;
-      q.meta_b = op.b >= 0 ? metas + op.b * BFP_META_WORDS : nullptr;
-      q.meta_out = metas + op.out * BFP_META_WORDS;
-      build_plan(q, sp);
-      sf = make_fast(sp, qc);
-      s_key = 0;
-      s_nrm = 0;
-      s_sat = 0;
+    CoarseLean L;
+    CoarseExec ex;
+    bool lean = lean_first(op, ea, na, eb, nb, L, ex);
+    bool built = false;
+    if (!lean) {                 // full plan (uniform decision)
+      __syncwarp();
+      if (lane == 0) {
+        Plan p;
+        build_plan_v(op.q, ea, na, eb, nb, p);
+        *pp = p;
+      }
+      __syncwarp();
+      built = true;
+      ex.f = make_fast(*pp, qc);
+      ex.m = make_mul(op.kind, ex.f, op);
     }
-    __syncthreads();
-    const int tot = bo.n * bo.n;
+    const int i0 = solo ? (lane & 15) : lane, istep = solo ? 16 : 32;
+    const int j0 = solo ? (lane >> 4) : warp, jstep = solo ? 2 : nw;
+    const int slot = c % 3;
+    if (!solo && tid == 0) {
+      s_key[(c + 1) % 3] = 0u;
+      s_nrm[(c + 1) % 3] = 0u;
+    }
+    long long key = 0, nrm = 0;
     if (qc) {
-      long long key = 0;
-      const Fast f = sf;
-      for (int idx = tid; idx < tot; idx += nth) {
-        int64_t H, L;
-        coarse_elem(op, m, ba, bb, idx % bo.n, idx / bo.n, H, L);
-        int32_t v;
-        int s = 0;
-        coarse_quant<true>(H, L, sp, f, key, v, s);
+      coarse_dispatch<T, true>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat);
+      unsigned kk = __reduce_max_sync(0xffffffffu, (unsigned)key);
+      if (!solo) {
+        if (lane == 0) atomicMax(&s_key[slot], kk);
+        __syncthreads();
+        kk = s_key[slot];
       }
-      key = warp_max(key);
-      if ((tid & 31) == 0) atomicMax(&s_key, key);
+      if (lean) lean = lean_second(op, (int32_t)kk, L, ex);
+      if (!lean) {
+        __syncwarp();
+        if (lane == 0) {
+          Plan p;
+          if (built) p = *pp;
+          else build_plan_v(op.q, ea, na, eb, nb, p);
+          plan_from_mu(p, (int64_t)kk);
+          *pp = p;
+        }
+        __syncwarp();
+        ex.f = make_fast(*pp, false);
+        ex.m = make_mul(op.kind, ex.f, op);
+      }
+    }
+    coarse_dispatch<T, false>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat);
+    unsigned nn = __reduce_max_sync(0xffffffffu, (unsigned)nrm);
+    if (!solo) {
+      if (lane == 0) atomicMax(&s_nrm[slot], nn);
       __syncthreads();
-      if (tid == 0) {
-        plan_from_mu(sp, s_key);
-        sf = make_fast(sp, false);
-      }
-      __syncthreads();
+      nn = s_nrm[slot];
+      ++c;
+    } else {
+      __syncwarp();              // this op's results before the next op reads them
     }
-    long long nrm = 0, sat = 0;
-    {
-      const Fast f = sf;
-      long long key = 0;
-      for (int idx = tid; idx < tot; idx += nth) {
-        int64_t H, L;
-        coarse_elem(op, m, ba, bb, idx % bo.n, idx / bo.n, H, L);
-        int s = 0;
-        int32_t v = 0;
-        coarse_quant<false>(H, L, sp, f, key, v, s);
-        m.put(bo, idx, v);
-        nrm = max(nrm, (long long)(v < 0 ? -(long long)v : (long long)v));
-        sat += s;
-      }
-    }
-    nrm = warp_max(nrm);
-    sat = warp_sum(sat);
-    if ((tid & 31) == 0) {
-      atomicMax(&s_nrm, nrm);
-      if (sat) atomicAdd((unsigned long long*)&s_sat, (unsigned long long)sat);
-    }
-    __syncthreads();
+    const int64_t eo = lean ? (int64_t)L.e_out : pp->e_out;
+    prev = op.out;
+    pe = eo;
+    pn = (int64_t)nn;
     if (tid == 0) {
-      int64_t* mo = metas + op.out * BFP_META_WORDS;
-      mo[0] = sp.e_out;
-      mo[1] = s_nrm;
-      s_cnt[0] += 1;
-      if (qc) {
-        if (sp.overflow || sp.underflow) s_cnt[1] += 1;
-        if (sp.overflow) s_cnt[2] += 1;
-        if (sp.underflow) s_cnt[3] += 1;
-      }
-      s_cnt[4] += (unsigned long long)s_sat;
+      metas[op.out * BFP_META_WORDS] = eo;
+      metas[op.out * BFP_META_WORDS + 1] = (int64_t)nn;
+      cnt.add(lean ? L.ov != 0 : pp->overflow != 0, lean ? L.un != 0 : pp->underflow != 0, qc);
     }
-    __syncthreads();
   }
+  {
+    const long long s = warp_sum((long long)sat);
+    if (lane == 0 && s) atomicAdd(&s_sat, (unsigned long long)s);
+  }
+  __syncthreads();
   // the level-n_c result back to global memory (padding columns written as 0)
   {
     const CoarseBuf yb = bufs[a.yout_buf];
-    const int64_t rows = yb.n, ld = a.yout.ld;
-    for (int64_t idx = tid; idx < rows * ld; idx += nth) {
-      const int64_t j = idx / ld, i = idx - j * ld;
-      const int32_t v = i < yb.n ? m.get(yb, (int)i, (int)j) : 0;
-      if (a.yout.is32) reinterpret_cast<int32_t*>(a.yout.m)[idx] = v;
-      else reinterpret_cast<int16_t*>(a.yout.m)[idx] = (int16_t)v;
-    }
+    const CoarseView<T> Y = cview<T>(sm, yb);
+    const int64_t ld = a.yout.ld;
+    T* dst = reinterpret_cast<T*>(a.yout.m);
+    for (int j = warp; j < yb.n; j += nw)
+      for (int64_t i = lane; i < ld; i += 32) dst[(int64_t)j * ld + i] = (T)(i < yb.n ? Y((int)i, j) : 0);
     if (tid < BFP_META_WORDS) a.yout_meta[tid] = metas[a.yout_buf * BFP_META_WORDS + tid];
-    if (tid < 5 && a.stats && s_cnt[tid]) atomicAdd((unsigned long long*)&a.stats[tid], s_cnt[tid]);
+    if (tid == 0 && a.stats) {
+      const unsigned long long cc[5] = {cnt.calls, cnt.recomputed, cnt.overflow, cnt.underflow, s_sat};
+      for (int t = 0; t < 5; ++t)
+        if (cc[t]) atomicAdd((unsigned long long*)&a.stats[t], cc[t]);
+    }
   }
 }
 

@@ -149,9 +149,8 @@ __device__ __forceinline__ bool gamma_msb(uint64_t a1, int64_t e1, uint64_t a2, 
   return true;
 }
 
-__device__ __forceinline__ void build_plan(const QDesc& q, Plan& p) {
-  int64_t ea = q.meta_a ? q.meta_a[0] : 0, eb = q.meta_b ? q.meta_b[0] : 0;
-  int64_t na = q.meta_a ? q.meta_a[1] : 0, nb = q.meta_b ? q.meta_b[1] : 0;
+// Plan from the input exponents (ea, eb) and max-|m| norms (na, nb).
+__device__ __forceinline__ void build_plan_v(const QDesc& q, int64_t ea, int64_t na, int64_t eb, int64_t nb, Plan& p) {
   int64_t Eh = group_exp(q.ch, q.ha, q.hb, ea, eb);
   p.two = q.two;
   p.mode = q.mode;
@@ -188,17 +187,25 @@ __device__ __forceinline__ void build_plan(const QDesc& q, Plan& p) {
   } else {
     uint64_t a[2] = {0, 0};
     int64_t e[2] = {0, 0};
-    for (int k = 0; k < q.ng; ++k) {
-      uint64_t nrm = (uint64_t)(q.gv[k] == 0 ? na : nb);
-      int64_t ev = q.gv[k] == 0 ? ea : eb;
-      a[k] = q.gm[k] * nrm;
-      e[k] = q.ge[k] + ev;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (k < q.ng) {
+        uint64_t nrm = (uint64_t)(q.gv[k] == 0 ? na : nb);
+        int64_t ev = q.gv[k] == 0 ? ea : eb;
+        a[k] = q.gm[k] * nrm;
+        e[k] = q.ge[k] + ev;
+      }
     }
     nz = gamma_msb(a[0], e[0], a[1], e[1], &G);
   }
   p.Gam = nz ? G : p.e_star + 1;   // gamma = 0 read as the zero scalar with exponent e*
   p.e_out = p.Gam - q.w_out;       // Alg. nnqcomp: lambda_out = mu_out - w_out
   p.e_tmp = p.Gam - q.w_tmp;       // Alg. qcomp: lambda_tmp = mu_tmp - w_tmp
+}
+
+__device__ __forceinline__ void build_plan(const QDesc& q, Plan& p) {
+  build_plan_v(q, q.meta_a ? q.meta_a[0] : 0, q.meta_a ? q.meta_a[1] : 0, q.meta_b ? q.meta_b[0] : 0,
+               q.meta_b ? q.meta_b[1] : 0, p);
 }
 
 // Completes the plan of qcomp's second pass from mu* (the atomic max key).

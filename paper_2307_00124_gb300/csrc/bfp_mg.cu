@@ -191,7 +191,7 @@ struct bfp_hierarchy {
   CoarseBuf* d_bufs = nullptr;
   int nbufs = 0;
   int smem_bytes = 0;
-  int meta_off = 0, ops_off = 0, bufs_off = 0;
+  int meta_off = 0, ops_off = 0, bufs_off = 0, data_off = 0;
   std::vector<CoarseOp*> d_ops;          // per start level k >= kc
   std::vector<int> nops, rbuf, ybuf;
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
@@ -286,10 +286,12 @@ int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vecto
     }
     if (rc) return rc;
     if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;
+    if (op.c != (int32_t)op.c || op.nb != (int32_t)op.nb || op.mw != (int32_t)op.mw) return BFP_ERR_WIDTH;
     d.mode = h->o.mode;
     d.w_out = w;
     d.w_tmp = w + rule;
     d.use_tmp = 0;
+    op.solo = h->lv[l + (kind == cRestrict ? 1 : 0)].n <= 15 ? 1 : 0;   // output level size
     ops.push_back(op);
     return BFP_OK;
   };
@@ -316,14 +318,16 @@ int32_t coarse_setup(bfp_hierarchy* h) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return BFP_OK;
-  const int budget = optin - 1024;
+  const int budget = optin - 2048;   // the kernel's static shared memory is a few hundred bytes
   const int eb = h->o.w > 16 ? 4 : 2;
+  const int nmax = h->o.coarse_onchip == 1 || h->o.coarse_onchip > 127 ? 127 : h->o.coarse_onchip;   // 4 columns per lane
+  auto buf_bytes = [&](int64_t n) { return ((n + 2) * (n + 2) * eb + 15) / 16 * 16; };
   // the largest start level (n <= 127) whose levels, schedule and tables fit in shared memory
   for (int k = 0; k < nl; ++k) {
-    if (h->lv[k].n > 127) continue;
+    if (h->lv[k].n > nmax) continue;
     const int64_t nops = (int64_t)(nl - 1 - k) * (h->o.nu1 + 3 + h->o.nu2) + h->o.coarse_sweeps;
     int64_t bytes = (int64_t)(nl - k) * 3 * (BFP_META_WORDS * 8 + (int64_t)sizeof(CoarseBuf)) + nops * (int64_t)sizeof(CoarseOp) + 64;
-    for (int l = k; l < nl; ++l) bytes += 3 * (((int64_t)h->lv[l].n * h->lv[l].n * eb + 15) / 16 * 16);
+    for (int l = k; l < nl; ++l) bytes += 3 * buf_bytes(h->lv[l].n);
     if (bytes <= budget) { h->kc = k; break; }
   }
   if (h->kc == nl) return BFP_OK;
@@ -334,6 +338,7 @@ int32_t coarse_setup(bfp_hierarchy* h) {
   h->bufs_off = nb * BFP_META_WORDS * 8;
   h->ops_off = (int)(((int64_t)h->bufs_off + nb * (int64_t)sizeof(CoarseBuf) + 15) / 16 * 16);
   int off = (int)(((int64_t)h->ops_off + max_ops * (int64_t)sizeof(CoarseOp) + 15) / 16 * 16);
+  h->data_off = off;
   std::vector<CoarseLevelBufs> lb;
   std::vector<CoarseBuf> bufs;
   for (int l = h->kc; l < nl; ++l) {
@@ -342,7 +347,7 @@ int32_t coarse_setup(bfp_hierarchy* h) {
     for (int t = 0; t < 3; ++t) {
       *ids[t] = (int)bufs.size();
       bufs.push_back(CoarseBuf{off, (int32_t)h->lv[l].n});
-      off += (int)(((int64_t)h->lv[l].n * h->lv[l].n * eb + 15) / 16 * 16);
+      off += (int)buf_bytes(h->lv[l].n);
     }
     lb.push_back(B);
   }
@@ -355,6 +360,7 @@ int32_t coarse_setup(bfp_hierarchy* h) {
     std::vector<CoarseOp> ops;
     int res = -1;
     TRY(coarse_flatten(h, k, lb[k - h->kc].r, lb, ops, &res));
+    for (size_t i = 1; i < ops.size(); ++i) ops[i].sync_before = (ops[i - 1].solo && !ops[i].solo) ? 1 : 0;
     if ((int)ops.size() > max_ops) return BFP_ERR_ARG;
     CoarseOp* d = (CoarseOp*)dalloc(h, ops.size() * sizeof(CoarseOp));
     if (!d) return BFP_ERR_CUDA;
@@ -364,9 +370,11 @@ int32_t coarse_setup(bfp_hierarchy* h) {
     h->rbuf.push_back(lb[k - h->kc].r);
     h->ybuf.push_back(res);
   }
-  if (cudaFuncSetAttribute(k_coarse_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_bytes) !=
-      cudaSuccess)
-    return BFP_ERR_CUDA;
+  const cudaError_t ae =
+      h->o.w > 16
+          ? cudaFuncSetAttribute(k_coarse_vcycle<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_bytes)
+          : cudaFuncSetAttribute(k_coarse_vcycle<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_bytes);
+  if (ae != cudaSuccess) return BFP_ERR_CUDA;
   return BFP_OK;
 }
 
@@ -378,10 +386,11 @@ int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* 
   a.nops = h->nops[i];
   a.bufs = h->d_bufs;
   a.nbufs = h->nbufs;
-  a.is32 = h->o.w > 16 ? 1 : 0;
   a.meta_off = h->meta_off;
   a.ops_off = h->ops_off;
   a.bufs_off = h->bufs_off;
+  a.data_off = h->data_off;
+  a.smem_bytes = h->smem_bytes;
   a.rin = vin(r);
   a.rin_meta = r->meta;
   a.rin_buf = h->rbuf[i];
@@ -389,7 +398,8 @@ int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* 
   a.yout_meta = out->meta;
   a.yout_buf = h->ybuf[i];
   a.stats = h->stats;
-  k_coarse_vcycle<<<1, 1024, h->smem_bytes, s>>>(a);
+  if (h->o.w > 16) k_coarse_vcycle<int32_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
+  else k_coarse_vcycle<int16_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
