@@ -239,7 +239,8 @@ typedef struct {
   int32_t use_tmp;       /* 1: qcomp keeps the w_tmp window (Alg. qcomp); 0: recompute */
   int32_t use_graph;     /* 1: replay IR steps from a captured CUDA graph */
   int32_t coarse_onchip; /* 2D: the levels from the first with n <= N run as one shared-memory
-                            kernel; N = 127 for 1, N = the value itself for values > 1, 0: off */
+                            kernel; N = 127 for 1, N = min(value, 127) for values > 1, 0: off
+                            (default 63) */
 } bfp_solver_opts;
 
 /* Fill opts with the defaults of the 2D/3D model problem. */

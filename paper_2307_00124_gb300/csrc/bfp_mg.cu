@@ -559,7 +559,7 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
   o->w_omega = 16;
   o->use_tmp = 1;
   o->use_graph = 1;
-  o->coarse_onchip = 1;
+  o->coarse_onchip = 63;
   return BFP_OK;
 }
 

@@ -253,7 +253,13 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const int64_t strips = (ny + (int64_t)kStarWarps * rs - 1) / ((int64_t)kStarWarps * rs);
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
-  if (sizeof(T) == 2) {
+  if (sizeof(T) == 2 && !o.is32) {
+    static bool carved = false;   // the staging ring wants the shared-memory carveout for 7 CTAs / SM
+    if (!carved) {
+      cudaFuncSetAttribute(k_star2d16<KIND, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_star2d16<KIND, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      carved = true;
+    }
     const dim3 g16((unsigned)((out->ld + kS16Cols - 1) / kS16Cols), grid.y);
     if (q.mode == kQcomp) k_star2d16<KIND, true><<<g16, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
     k_star2d16<KIND, false><<<g16, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);

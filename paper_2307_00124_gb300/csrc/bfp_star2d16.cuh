@@ -1,20 +1,26 @@
 // bfp_star2d16.cuh -- five-point stencil ops on int16 mantissas (w <= 16), the
 // finest-level hot path of the V-cycle.
 //
-// A warp owns a 256-column chunk: each lane 8 consecutive mantissas (one
-// 16-byte load per row and input), kept packed as int16 pairs.  The warp walks
-// a strip of rows with the rows above and below in registers, prefetching
-// the next two rows of y (and the edge mantissas lanes 0 and 31 need) and the
-// next row of r, so three rows of loads are in flight per warp.
+// A warp owns a 256-column chunk of a strip of rows: each lane 8 consecutive
+// mantissas (16 bytes per row and input).  Rows are staged through a per-lane
+// ring of kStages slots in shared memory with cp.async (16-byte copies,
+// zero-filled outside the grid), issued kStages - 3 rows ahead of the
+// three-row window the lane reads back (rows j-1, j, j+1 of y and row j of r).
+// Every lane reads only what it copied itself, so a per-thread wait on the
+// copy groups is the only synchronisation; the west / east neighbours at the
+// chunk edges come from shuffles, lanes 0 and 31 copying the one extra
+// mantissa pair they need.
 //
 // Fast path (the exact integer Z fits in int64 and the output exponent is at
 // or above Z's): Z = cy*y + cn*(W+E+S+N) + cr*r with the App. B exponent
-// alignment folded into three 32-bit coefficients, the result is one funnel
-// shift, and nnqcomp saturation is detected with one unsigned range test per
-// element; a warp that sees a value outside X_w (or a plan outside the fast
-// regime) recomputes that row through the general quantiser, kept out of line
-// so that it costs no registers on the fast path.  qcomp pass 1 takes the bit
-// width of the OR of |Z| (the max msb) and stores the w_tmp window.
+// alignment folded into three 32-bit coefficients; the result is one funnel
+// shift.  For nnqcomp the fast path also requires |Z| < 2^(31 + t) (from the
+// op's msb bounds), so the saturation test runs on the 32-bit results: the OR
+// of v + 2^(w-1) over a row has no bit at or above w iff every v is in X_w.
+// A warp that sees a value outside X_w (or a plan outside the fast regime)
+// recomputes that row through the general quantiser, kept out of line.  qcomp
+// pass 1 takes the bit width of the OR of |Z| (the max msb) and stores the
+// w_tmp window.  max |m| is kept on the packed results with 16x2 max / min.
 #pragma once
 
 #include "bfp_host.h"
@@ -22,6 +28,7 @@
 namespace bfp {
 
 constexpr int kS16Cols = 256;   // columns per warp chunk (32 lanes x 8)
+constexpr int kStages = 6;      // ring slots per lane: the 3-row window + 3 rows in flight
 
 struct Pk8 {
   uint32_t w[4];
@@ -29,40 +36,36 @@ struct Pk8 {
 
 __device__ __forceinline__ int32_t pk_get(const Pk8& p, int k) {
   const uint32_t word = p.w[k >> 1];
-  return (k & 1) ? ((int32_t)word >> 16) : ((int32_t)(word << 16) >> 16);
+  return (k & 1) ? ((int32_t)word >> 16) : (int32_t)(int16_t)(word & 0xffffu);
 }
 
-struct Loader16 {
-  const int16_t* col;   // row 0 of this lane's 8 columns
-  int64_t ld;
-  int ny;
-  bool ok;              // any valid column in this lane
-  uint32_t mask[4];     // zeroes the columns >= nx
-  __device__ __forceinline__ Pk8 operator()(int j) const {
-    Pk8 p;
-    if (ok && j >= 0 && j < ny) {
-      const uint4 u = __ldg(reinterpret_cast<const uint4*>(col + (int64_t)j * ld));
-      p.w[0] = u.x & mask[0]; p.w[1] = u.y & mask[1]; p.w[2] = u.z & mask[2]; p.w[3] = u.w & mask[3];
-    } else {
-      p.w[0] = p.w[1] = p.w[2] = p.w[3] = 0u;
-    }
-    return p;
-  }
-};
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
 
-__device__ __forceinline__ Loader16 loader16(const VIn& v, int64_t c0) {
-  Loader16 L;
-  L.col = reinterpret_cast<const int16_t*>(v.m) + c0;
-  L.ld = v.ld;
-  L.ny = (int)(v.ny * v.nz);
-  L.ok = v.m != nullptr && c0 < v.nx && c0 < v.ld;
-  const int64_t nv = v.nx - c0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint32_t lo = (2 * i < nv) ? 0xffffu : 0u, hi = (2 * i + 1 < nv) ? 0xffff0000u : 0u;
-    L.mask[i] = lo | hi;
-  }
-  return L;
+// Asynchronous copies global -> shared; src_bytes 0 fills zeros (the source
+// address is then not read; callers still pass an address inside the buffer).
+__device__ __forceinline__ void cp16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp4(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ uint32_t max_s16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t min_s16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
 }
 
 // Inputs of one lane's 8 outputs, for the out-of-line general path.
@@ -89,10 +92,18 @@ __device__ __noinline__ void slow_row8(const Row8& in, const Plan& p, const Fast
   quantvf<PASS1, 8>(hl, p, fq, out, tmp, row, c0, red);
 }
 
+// Per-warp staging ring: y rows, r rows and the two edge pairs, per stage.
+struct Stage16 {
+  uint4 y[kStages][32];
+  uint4 r[kStages][32];
+  uint32_t e[kStages][2];     // [0]: lane 0's west pair, [1]: lane 31's east pair
+};
+
 template <int KIND, bool PASS1>
 __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, const int32_t c, const int32_t nb,
                                                      const int32_t mw, const QDesc q, const VOut out, const int rs) {
   __shared__ Plan sp;
+  __shared__ Stage16 stg[4];
   if (threadIdx.x == 0) {
     build_plan(q, sp);
     if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
@@ -108,6 +119,7 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const bool act = c0 < out.ld;
   Red red = {0, 0, 0};
   int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
+  constexpr bool kUseY = KIND != kJacobi0, kUseR = KIND != kApply;
 
   // Z = cy*y + cn*ns + cr*r, the group shifts folded into the coefficients
   int64_t cy, cn, cr;
@@ -118,88 +130,98 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
     cn = (int64_t)((uint64_t)(int64_t)nb << fq.dh);
     cr = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)(1ull << fq.dl) : (int64_t)((uint64_t)(int64_t)mw << fq.dl));
   }
-  const bool fast = fq.ok && fq.t < 32 && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr;
   const int32_t cy32 = (int32_t)cy, cn32 = (int32_t)cn, cr32 = (int32_t)cr;
   const uint32_t t = (uint32_t)fq.t;
+  // |Z| <= 2^zb from the msb bounds of the two groups
+  const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
+  const bool fast = fq.ok && fq.t < 32 && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr &&
+                    (PASS1 || !fq.clamp || zb - (int)fq.t <= 30);
   const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
-  // nnqcomp range: the result fits in X_w iff zmin <= Z <= zmax
-  const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << t);
-  const uint64_t zrange = (uint64_t)(((uint64_t)1 << (fq.w - 1 + t)) * 2 - 1);
-  const int64_t nvalid = out.nx - c0;
+  const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
+  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
+  const bool partial = nvalid < 8;
 
-  const Loader16 ly = loader16(y, c0), lr = loader16(r, c0);
-  // lane 0 needs the west neighbour of its first column, lane 31 the east one of its last
-  const int16_t* yb = reinterpret_cast<const int16_t*>(y.m);
-  const int64_t ecol = lane == 0 ? c0 - 1 : c0 + 8;
-  const bool eok = (lane == 0 || lane == 31) && KIND != kJacobi0 && y.m != nullptr && ecol >= 0 && ecol < y.nx;
-  auto ledge = [&](int j) -> int32_t {
-    return (eok && j >= 0 && j < ny) ? (int32_t)__ldg(yb + (int64_t)j * y.ld + ecol) : 0;
+  // staging: stage s holds y row j0 - 1 + s and r row j0 - 2 + s
+  Stage16& S = stg[warp];
+  const int nyin = kUseY ? (int)(y.ny * y.nz) : 0, nrin = kUseR ? (int)(r.ny * r.nz) : 0;
+  const bool ycol = kUseY && c0 < y.nx && c0 < y.ld, rcol = kUseR && c0 < r.nx && c0 < r.ld;
+  const int16_t* ybase = kUseY ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
+  const int16_t* rbase = kUseR ? reinterpret_cast<const int16_t*>(r.m) : nullptr;
+  // edge pairs: lane 0 the pair (c0-2, c0-1), lane 31 the pair (c0+8, c0+9)
+  const int64_t ecol = lane == 0 ? c0 - 2 : c0 + 8;
+  const bool eok = kUseY && (lane == 0 ? (c0 >= 2 && c0 - 1 < y.nx) : (lane == 31 && c0 + 8 < y.nx));
+  auto issue = [&](int s, int slot) {
+    if (kUseY) {
+      const int jy = j0 - 1 + s;
+      const bool in = jy >= 0 && jy < nyin;
+      const bool ok = ycol && in;
+      cp16(&S.y[slot][lane], ybase + (ok ? (int64_t)jy * y.ld + c0 : 0), ok ? 16u : 0u);
+      if (lane == 0 || lane == 31) {
+        const bool ek = eok && in;
+        cp4(&S.e[slot][lane == 0 ? 0 : 1], ybase + (ek ? (int64_t)jy * y.ld + ecol : 0), ek ? 4u : 0u);
+      }
+    }
+    if (kUseR) {
+      const int jr = j0 - 2 + s;
+      const bool ok = rcol && jr >= 0 && jr < nrin;
+      cp16(&S.r[slot][lane], rbase + (ok ? (int64_t)jr * r.ld + c0 : 0), ok ? 16u : 0u);
+    }
+    cp_commit();
   };
 
-  uint32_t nrm = 0;
+  // the lane's columns at or beyond nx read as 0 (partial chunk only)
+  uint32_t cmask[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    cmask[i] = ((2 * i < nvalid) ? 0xffffu : 0u) | ((2 * i + 1 < nvalid) ? 0xffff0000u : 0u);
+  auto rd = [&](const uint4& u) {
+    Pk8 v;
+    v.w[0] = u.x; v.w[1] = u.y; v.w[2] = u.z; v.w[3] = u.w;
+    if (partial) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v.w[i] &= cmask[i];
+    }
+    return v;
+  };
+
+  uint32_t vmax = 0, vmin = 0;                  // packed 16x2 extremes of the results
   uint64_t ormag = 0;
-
-  auto emit_row = [&](int j, int32_t (&o)[8]) {
-    if (nvalid < 8) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (k >= nvalid) o[k] = 0;
-    }
-    if (PASS1) {
-      if (tmp) {
-        int4* d = reinterpret_cast<int4*>(tmp + (int64_t)j * out.ld + c0);
-        d[0] = make_int4(o[0], o[1], o[2], o[3]);
-        d[1] = make_int4(o[4], o[5], o[6], o[7]);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t a = (uint32_t)(o[k] < 0 ? -o[k] : o[k]);
-        nrm = a > nrm ? a : nrm;
-      }
-      uint4 u;
-      u.x = (uint32_t)(uint16_t)o[0] | ((uint32_t)(uint16_t)o[1] << 16);
-      u.y = (uint32_t)(uint16_t)o[2] | ((uint32_t)(uint16_t)o[3] << 16);
-      u.z = (uint32_t)(uint16_t)o[4] | ((uint32_t)(uint16_t)o[5] << 16);
-      u.w = (uint32_t)(uint16_t)o[6] | ((uint32_t)(uint16_t)o[7] << 16);
-      if (out.is32) {
-        stv<8>(out, j, c0, o);
-      } else {
-        *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (int64_t)j * out.ld + c0) = u;
-      }
-    }
-  };
-
   if (!PASS1 && p.narrow) {
     for (int j = j0; j < j1; ++j)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
   } else if (j0 < j1) {
-    Pk8 ym, yc, yp, rc;
-    int32_t ec = 0, ep = 0;
-    if (KIND != kJacobi0) {
-      ym = ly(j0 - 1); yc = ly(j0); yp = ly(j0 + 1);
-      ec = ledge(j0); ep = ledge(j0 + 1);
-    }
-    if (KIND != kApply) rc = lr(j0);
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) issue(s, s);
+    // ring slots of stages i, i + 1, i + 2 and i + kStages - 1 (= i - 1 mod kStages)
+    int s0 = 0, s1 = 1, s2 = 2, sn = kStages - 1;
     for (int j = j0; j < j1; ++j) {
-      Pk8 ypp, rn;
-      int32_t epp = 0;
-      if (KIND != kJacobi0) { ypp = ly(j + 2); epp = ledge(j + 2); }
-      if (KIND != kApply) rn = lr(j + 1);
+      const int i = j - j0;
+      issue(i + kStages - 1, sn);               // into the slot of row j - 2
+      cp_wait<kStages - 3>();                   // stages <= i + 2 have landed
+      Pk8 ym, yc, yp, rc;
       int32_t yv[8], wv = 0, ev = 0;
-      if (KIND != kJacobi0) {
+      if (kUseY) {
+        ym = rd(S.y[s0][lane]);
+        yc = rd(S.y[s1][lane]);
+        yp = rd(S.y[s2][lane]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
+        uint32_t ew = 0;
+        if (lane == 0 || lane == 31) ew = S.e[s1][lane == 0 ? 0 : 1];
         wv = __shfl_up_sync(0xffffffffu, yv[7], 1);
         ev = __shfl_down_sync(0xffffffffu, yv[0], 1);
-        if (lane == 0) wv = ec;
-        if (lane == 31) ev = ec;
+        if (lane == 0) wv = (int32_t)ew >> 16;
+        if (lane == 31) ev = (int32_t)(int16_t)(ew & 0xffffu);
       }
+      if (kUseR) rc = rd(S.r[s2][lane]);
+      sn = s0;
+      s0 = s1;
+      s1 = s2;
+      s2 = s2 + 1 == kStages ? 0 : s2 + 1;
       if (act) {
         bool redo = !fast;
         int32_t o[8];
         if (fast) {
-          bool ovf = false;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             int64_t Z;
@@ -217,36 +239,61 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
               if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
               o[k] = (int32_t)((uint32_t)v << sh) >> sh;
             } else {
-              if (fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)zmin > zrange) && (k < nvalid);
               o[k] = v;
             }
           }
-          if (!PASS1 && fq.clamp) redo = ovf;
+          if (partial) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (k >= nvalid) o[k] = 0;
+          }
+          if (!PASS1 && fq.clamp) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc |= (uint32_t)o[k] + half;
+            redo = (acc >> fq.w) != 0u;
+          }
         }
         if (!PASS1 && fq.clamp && fast) redo = __any_sync(__activemask(), redo);
         if (redo) {
           Row8 in;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            in.y[k] = KIND == kJacobi0 ? 0 : pk_get(yc, k);
-            in.ym[k] = KIND == kJacobi0 ? 0 : pk_get(ym, k);
-            in.yp[k] = KIND == kJacobi0 ? 0 : pk_get(yp, k);
-            in.r[k] = KIND == kApply ? 0 : pk_get(rc, k);
+            in.y[k] = kUseY ? pk_get(yc, k) : 0;
+            in.ym[k] = kUseY ? pk_get(ym, k) : 0;
+            in.yp[k] = kUseY ? pk_get(yp, k) : 0;
+            in.r[k] = kUseR ? pk_get(rc, k) : 0;
           }
           in.wv = wv;
           in.ev = ev;
           slow_row8<PASS1, KIND>(in, p, fq, out, tmp, j, c0, red, c, nb, mw);
+        } else if (PASS1) {
+          if (tmp) {
+            int4* d = reinterpret_cast<int4*>(tmp + (int64_t)j * out.ld + c0);
+            d[0] = make_int4(o[0], o[1], o[2], o[3]);
+            d[1] = make_int4(o[4], o[5], o[6], o[7]);
+          }
         } else {
-          emit_row(j, o);
+          uint4 u;
+          u.x = __byte_perm((uint32_t)o[0], (uint32_t)o[1], 0x5410);
+          u.y = __byte_perm((uint32_t)o[2], (uint32_t)o[3], 0x5410);
+          u.z = __byte_perm((uint32_t)o[4], (uint32_t)o[5], 0x5410);
+          u.w = __byte_perm((uint32_t)o[6], (uint32_t)o[7], 0x5410);
+          vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
+          vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
+          *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (int64_t)j * out.ld + c0) = u;
         }
       }
-      if (KIND != kJacobi0) { ym = yc; yc = yp; yp = ypp; ec = ep; ep = epp; }
-      if (KIND != kApply) rc = rn;
     }
+    cp_wait<0>();
+  }
+  if (!PASS1) {
+    const int32_t mx = max((int32_t)vmax >> 16, (int32_t)(int16_t)(vmax & 0xffffu));
+    const int32_t mn = min((int32_t)vmin >> 16, (int32_t)(int16_t)(vmin & 0xffffu));
+    red.nrm = max(red.nrm, (long long)max(mx, -mn));
   }
   if (PASS1 && ormag) red.key = max(red.key, (long long)(256 + (64 - __clzll((long long)ormag)) + 1));
-  if (PASS1 && fast && j0 < j1 && act && ormag == 0) red.key = max(red.key, 257ll);   // all-zero chunk: msb 1
-  red.nrm = max(red.nrm, (long long)nrm);
+  if (PASS1 && fast && j0 < j1 && act && ormag == 0 && nvalid > 0) red.key = max(red.key, 257ll);   // all-zero chunk: msb 1
   block_commit(red, q.meta_out, q.stats, PASS1);
   if (!PASS1) op_epilogue(q, p);
 }

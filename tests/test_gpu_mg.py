@@ -26,7 +26,7 @@ def make(nd, n, w, mode, use_tmp=1, use_graph=1, coarse_onchip=1):
 @pytest.mark.parametrize("nd,n", [(2, 63), (2, 31), (2, 255), (3, 15)])
 @pytest.mark.parametrize("w", [8, 16, 32])
 @pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
-@pytest.mark.parametrize("onchip", [1, 0])
+@pytest.mark.parametrize("onchip", [1, 63, 15, 0])
 def test_vcycle_bit_exact(nd, n, w, mode, onchip):
     h, s = make(nd, n, w, mode, coarse_onchip=onchip)
     rm = random_mantissas((n,) * nd, w, 5, "smooth")
