@@ -49,9 +49,25 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, uint32_t src_by
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp4(void* dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-               : "memory");
+// predicated 4-byte copy (no branch: only lanes with p set issue it)
+__device__ __forceinline__ void cp4_if(bool p, void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q cp.async.ca.shared.global [%0], [%1], 4, %2;\n}\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(src_bytes), "r"((int)p)
+      : "memory");
+}
+
+// Z = a*b + c with a 64-bit accumulator (one mad.wide)
+__device__ __forceinline__ int64_t madw(int32_t a, int32_t b, int64_t c) {
+  int64_t d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ int64_t mulw(int32_t a, int32_t b) {
+  int64_t d;
+  asm("mul.wide.s32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+  return d;
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -74,9 +90,21 @@ struct Row8 {
   int32_t wv, ev;
 };
 
+// The general path for one lane's 8 outputs of row `row`: reloads its inputs
+// from global memory (zero outside the grid) and quantises through quantvf.
 template <bool PASS1, int KIND>
-__device__ __noinline__ void slow_row8(const Row8& in, const Plan& p, const Fast& fq, const VOut& out, int32_t* tmp,
-                                       int64_t row, int64_t c0, Red& red, int32_t c, int32_t nb, int32_t mw) {
+__device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p, const Fast& fq, const VOut& out,
+                                       int32_t* tmp, int64_t row, int64_t c0, Red& red, int32_t c, int32_t nb,
+                                       int32_t mw) {
+  Row8 in;
+  if (KIND != kJacobi0) {
+    ldv<int16_t, 8>(y, row, c0, in.y);
+    ldv<int16_t, 8>(y, row - 1, c0, in.ym);
+    ldv<int16_t, 8>(y, row + 1, c0, in.yp);
+    in.wv = (int32_t)ld1<int16_t>(y, row, c0 - 1);
+    in.ev = (int32_t)ld1<int16_t>(y, row, c0 + 8);
+  }
+  if (KIND != kApply) ldv<int16_t, 8>(r, row, c0, in.r);
   auto hl = [&](int k, int64_t& H, int64_t& L) {
     if (KIND == kJacobi0) {
       H = (int64_t)mw * (int64_t)in.r[k];
@@ -92,11 +120,14 @@ __device__ __noinline__ void slow_row8(const Row8& in, const Plan& p, const Fast
   quantvf<PASS1, 8>(hl, p, fq, out, tmp, row, c0, red);
 }
 
-// Per-warp staging ring: y rows, r rows and the two edge pairs, per stage.
-struct Stage16 {
-  uint4 y[kStages][32];
+// Per-warp staging ring.  A y row is 136 words: 3 pad words, the west halo
+// pair (columns c-2, c-1 of the chunk start c), 32 lane slots of 4 words, the
+// east halo pair (columns c+256, c+257), 3 pad words; lane slots stay 16-byte
+// aligned, and every west / east neighbour is one int16 load from the row.
+constexpr int kRowWords = 136;
+struct __align__(16) Stage16 {
+  uint32_t y[kStages][kRowWords];
   uint4 r[kStages][32];
-  uint32_t e[kStages][2];     // [0]: lane 0's west pair, [1]: lane 31's east pair
 };
 
 template <int KIND, bool PASS1>
@@ -147,25 +178,30 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const bool ycol = kUseY && c0 < y.nx && c0 < y.ld, rcol = kUseR && c0 < r.nx && c0 < r.ld;
   const int16_t* ybase = kUseY ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
   const int16_t* rbase = kUseR ? reinterpret_cast<const int16_t*>(r.m) : nullptr;
-  // edge pairs: lane 0 the pair (c0-2, c0-1), lane 31 the pair (c0+8, c0+9)
+  // halo pairs: lane 0 copies (c0-2, c0-1) into word 3, lane 31 (c0+8, c0+9) into word 132
   const int64_t ecol = lane == 0 ? c0 - 2 : c0 + 8;
   const bool eok = kUseY && (lane == 0 ? (c0 >= 2 && c0 - 1 < y.nx) : (lane == 31 && c0 + 8 < y.nx));
-  auto issue = [&](int s, int slot) {
+  const int eword = lane == 0 ? 3 : kRowWords - 4;
+  // the next stage to issue: y row jy at element offset oy, r row jy - 1 at offset orr
+  int jy = j0 - 1;
+  int64_t oy = kUseY ? (int64_t)jy * y.ld + c0 : 0, orr = kUseR ? (int64_t)(jy - 1) * r.ld + c0 : 0;
+  const int64_t edelta = ecol - c0;
+  const bool edge_lane = lane == 0 || lane == 31;
+  auto issue = [&](int slot) {
     if (kUseY) {
-      const int jy = j0 - 1 + s;
-      const bool in = jy >= 0 && jy < nyin;
+      const bool in = (unsigned)jy < (unsigned)nyin;
       const bool ok = ycol && in;
-      cp16(&S.y[slot][lane], ybase + (ok ? (int64_t)jy * y.ld + c0 : 0), ok ? 16u : 0u);
-      if (lane == 0 || lane == 31) {
-        const bool ek = eok && in;
-        cp4(&S.e[slot][lane == 0 ? 0 : 1], ybase + (ek ? (int64_t)jy * y.ld + ecol : 0), ek ? 4u : 0u);
-      }
+      cp16(&S.y[slot][4 + 4 * lane], ybase + (ok ? oy : 0), ok ? 16u : 0u);
+      const bool ek = eok && in;
+      cp4_if(edge_lane, &S.y[slot][eword], ybase + (ek ? oy + edelta : 0), ek ? 4u : 0u);
+      oy += y.ld;
     }
     if (kUseR) {
-      const int jr = j0 - 2 + s;
-      const bool ok = rcol && jr >= 0 && jr < nrin;
-      cp16(&S.r[slot][lane], rbase + (ok ? (int64_t)jr * r.ld + c0 : 0), ok ? 16u : 0u);
+      const bool ok = rcol && (unsigned)(jy - 1) < (unsigned)nrin;
+      cp16(&S.r[slot][lane], rbase + (ok ? orr : 0), ok ? 16u : 0u);
+      orr += r.ld;
     }
+    ++jy;
     cp_commit();
   };
 
@@ -185,33 +221,32 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   };
 
   uint32_t vmax = 0, vmin = 0;                  // packed 16x2 extremes of the results
+  uint32_t redo_rows = 0;
   uint64_t ormag = 0;
   if (!PASS1 && p.narrow) {
     for (int j = j0; j < j1; ++j)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
   } else if (j0 < j1) {
 #pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) issue(s, s);
+    for (int s = 0; s < kStages - 1; ++s) issue(s);
     // ring slots of stages i, i + 1, i + 2 and i + kStages - 1 (= i - 1 mod kStages)
     int s0 = 0, s1 = 1, s2 = 2, sn = kStages - 1;
     for (int j = j0; j < j1; ++j) {
       const int i = j - j0;
-      issue(i + kStages - 1, sn);               // into the slot of row j - 2
-      cp_wait<kStages - 3>();                   // stages <= i + 2 have landed
+      issue(sn);                                // stage i + kStages - 1, into the slot of row j - 2
+      cp_wait<kStages - 3>();                   // stages <= i + 2 have landed (own copies)
+      __syncwarp();                             // ... and the other lanes' (neighbours, halo)
       Pk8 ym, yc, yp, rc;
       int32_t yv[8], wv = 0, ev = 0;
       if (kUseY) {
-        ym = rd(S.y[s0][lane]);
-        yc = rd(S.y[s1][lane]);
-        yp = rd(S.y[s2][lane]);
+        ym = rd(*reinterpret_cast<const uint4*>(&S.y[s0][4 + 4 * lane]));
+        yc = rd(*reinterpret_cast<const uint4*>(&S.y[s1][4 + 4 * lane]));
+        yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
 #pragma unroll
         for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
-        uint32_t ew = 0;
-        if (lane == 0 || lane == 31) ew = S.e[s1][lane == 0 ? 0 : 1];
-        wv = __shfl_up_sync(0xffffffffu, yv[7], 1);
-        ev = __shfl_down_sync(0xffffffffu, yv[0], 1);
-        if (lane == 0) wv = (int32_t)ew >> 16;
-        if (lane == 31) ev = (int32_t)(int16_t)(ew & 0xffffu);
+        const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
+        wv = row[7 + 8 * lane];                 // column c0 - 1
+        ev = row[16 + 8 * lane];                // column c0 + 8
       }
       if (kUseR) rc = rd(S.r[s2][lane]);
       sn = s0;
@@ -226,13 +261,13 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
           for (int k = 0; k < 8; ++k) {
             int64_t Z;
             if (KIND == kJacobi0) {
-              Z = (int64_t)cr32 * pk_get(rc, k);
+              Z = mulw(cr32, pk_get(rc, k));
             } else {
               const int32_t wk = k == 0 ? wv : yv[k - 1];
               const int32_t ek = k == 7 ? ev : yv[k + 1];
               const int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
-              Z = (int64_t)cy32 * yv[k] + (int64_t)cn32 * ns;
-              if (KIND != kApply) Z += (int64_t)cr32 * pk_get(rc, k);
+              Z = madw(cn32, ns, mulw(cy32, yv[k]));
+              if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
             }
             const int32_t v = (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), t);
             if (PASS1) {
@@ -256,17 +291,7 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
         }
         if (!PASS1 && fq.clamp && fast) redo = __any_sync(__activemask(), redo);
         if (redo) {
-          Row8 in;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            in.y[k] = kUseY ? pk_get(yc, k) : 0;
-            in.ym[k] = kUseY ? pk_get(ym, k) : 0;
-            in.yp[k] = kUseY ? pk_get(yp, k) : 0;
-            in.r[k] = kUseR ? pk_get(rc, k) : 0;
-          }
-          in.wv = wv;
-          in.ev = ev;
-          slow_row8<PASS1, KIND>(in, p, fq, out, tmp, j, c0, red, c, nb, mw);
+          redo_rows |= 1u << i;                 // recomputed after the loop
         } else if (PASS1) {
           if (tmp) {
             int4* d = reinterpret_cast<int4*>(tmp + (int64_t)j * out.ld + c0);
@@ -286,6 +311,11 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
       }
     }
     cp_wait<0>();
+    // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
+    for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
+      const int j = j0 + __ffs(m) - 1;
+      if (act) slow_row8<PASS1, KIND>(y, r, p, fq, out, tmp, j, c0, red, c, nb, mw);
+    }
   }
   if (!PASS1) {
     const int32_t mx = max((int32_t)vmax >> 16, (int32_t)(int16_t)(vmax & 0xffffu));
