@@ -14,6 +14,7 @@ bool coarse_of(const bfp_vec* f, const bfp_vec* c) {
   return true;
 }
 
+// rows per warp strip (<= 16: the kernels keep a per-strip mask of general-path rows)
 int rows_per_warp(int64_t rows) { return rows >= 1024 ? 8 : (rows >= 256 ? 4 : (rows >= 64 ? 2 : 1)); }
 
 int32_t launch_checks(const QDesc& d) {
@@ -28,6 +29,12 @@ int32_t restrict2d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaS
   const int rs = rows_per_warp(ny);
   const dim3 grid((unsigned)((rc->ld + 255) / 256), (unsigned)((ny + 4 * rs - 1) / (4 * rs)));
   const VOut o = vout(rc);
+  static bool carved = false;   // the staging rings want the shared-memory carveout
+  if (!carved) {
+    cudaFuncSetAttribute(k_restrict2d16<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    carved = true;
+  }
   if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (d.mode == kQcomp) k_restrict2d16<true><<<grid, 128, 0, s>>>(vin(rf), d, o, rs);
   k_restrict2d16<false><<<grid, 128, 0, s>>>(vin(rf), d, o, rs);
@@ -45,6 +52,12 @@ int32_t prolong2d16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, con
   const VOut o = vout(out);
   VIn yv = vin(y ? y : out);
   if (!CORR) yv.m = nullptr;
+  static bool carved = false;
+  if (!carved) {
+    cudaFuncSetAttribute(k_prolong2d16<CORR, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_prolong2d16<CORR, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    carved = true;
+  }
   if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (d.mode == kQcomp) k_prolong2d16<CORR, true><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
   k_prolong2d16<CORR, false><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);

@@ -132,17 +132,31 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
     const int64_t col = cb + (lane & 7) * 8;
     uint32_t nrm = 0;
     if (col < a.out.ld) {
-      for (int64_t j = j0 + (lane >> 3); j < j1; j += 4) {
-        const int4* src = reinterpret_cast<const int4*>(a.tmp + j * a.out.ld + col);
-        const int4 u0 = src[0], u1 = src[1];
-        int32_t o[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      // four rows per lane in flight: all loads of a group before any store
+      for (int64_t jb = j0 + (lane >> 3); jb < j1; jb += 16) {
+        int4 u[4][2];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          o[k] = col + k < nx ? (o[k] >> sh) : 0;   // padding columns [nx, ld) are written as 0
-          const uint32_t av = (uint32_t)(o[k] < 0 ? -o[k] : o[k]);
-          nrm = av > nrm ? av : nrm;
+        for (int g = 0; g < 4; ++g) {
+          const int64_t j = jb + 4 * g;
+          if (j < j1) {
+            const int4* src = reinterpret_cast<const int4*>(a.tmp + j * a.out.ld + col);
+            u[g][0] = src[0];
+            u[g][1] = src[1];
+          }
         }
-        stv<8>(a.out, j, col, o);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int64_t j = jb + 4 * g;
+          if (j >= j1) break;
+          int32_t o[8] = {u[g][0].x, u[g][0].y, u[g][0].z, u[g][0].w, u[g][1].x, u[g][1].y, u[g][1].z, u[g][1].w};
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            o[k] = col + k < nx ? (o[k] >> sh) : 0;   // padding columns [nx, ld) are written as 0
+            const uint32_t av = (uint32_t)(o[k] < 0 ? -o[k] : o[k]);
+            nrm = av > nrm ? av : nrm;
+          }
+          stv<8>(a.out, j, col, o);
+        }
       }
     }
     red.nrm = max(red.nrm, (long long)nrm);
@@ -220,19 +234,32 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
   }
 }
 
-// x <- x + m 2^e (FP64 update of Alg. ir): one double per thread, rows over gridDim.y
+// x <- x + m 2^e (FP64 update of Alg. ir): a thread owns one column of
+// kUpdRows consecutive rows and issues all of their loads before any add.
+constexpr int kUpdRows = 8;
 template <class T>
 __global__ void __launch_bounds__(256) k_ir_update2(double* __restrict__ x, const VIn y, const int64_t* meta) {
   const int64_t e = meta[0];
-  const int ei = (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e));
   const int64_t rows = y.ny * y.nz;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= y.nx) return;
   const T* m = reinterpret_cast<const T*>(y.m);
-  (void)ei;
-  for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
-    double* xr = x + row * y.nx + i;
-    *xr = __dadd_rn(*xr, mant_pow2((int32_t)m[row * y.ld + i], e));
+  for (int64_t r0 = (int64_t)blockIdx.y * kUpdRows; r0 < rows; r0 += (int64_t)gridDim.y * kUpdRows) {
+    double xv[kUpdRows];
+    int32_t mv[kUpdRows];
+#pragma unroll
+    for (int k = 0; k < kUpdRows; ++k) {
+      const int64_t row = r0 + k;
+      if (row < rows) {
+        xv[k] = x[row * y.nx + i];
+        mv[k] = (int32_t)__ldg(m + row * y.ld + i);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUpdRows; ++k) {
+      const int64_t row = r0 + k;
+      if (row < rows) x[row * y.nx + i] = __dadd_rn(xv[k], mant_pow2(mv[k], e));
+    }
   }
 }
 

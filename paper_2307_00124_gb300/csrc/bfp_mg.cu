@@ -514,7 +514,8 @@ int32_t ir_update(double* x, const bfp_vec* y, cudaStream_t s) {
   const int64_t total = y->n[0] * y->n[1] * y->n[2];
   if (total == 0) return BFP_OK;
   const int64_t rows = y->n[1] * y->n[2];
-  const dim3 gu((unsigned)((y->n[0] + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
+  const int64_t rblocks = (rows + kUpdRows - 1) / kUpdRows;
+  const dim3 gu((unsigned)((y->n[0] + 255) / 256), (unsigned)(rblocks < 65535 ? rblocks : 65535));
   if (y->w > 16) k_ir_update2<int32_t><<<gu, 256, 0, s>>>(x, vin(y), y->meta);
   else k_ir_update2<int16_t><<<gu, 256, 0, s>>>(x, vin(y), y->meta);
   note_launches(1);

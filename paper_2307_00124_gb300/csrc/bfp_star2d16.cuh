@@ -14,14 +14,17 @@
 // Fast path (the exact integer Z fits in int64 and the output exponent is at
 // or above Z's): Z = cy*y + cn*(W+E+S+N) + cr*r with the App. B exponent
 // alignment folded into three 32-bit coefficients; the result is one funnel
-// shift.  For nnqcomp the fast path also requires |Z| < 2^(31 + t) (from the
-// op's msb bounds), so the saturation test runs on the 32-bit results: the OR
-// of v + 2^(w-1) over a row has no bit at or above w iff every v is in X_w.
+// shift.  When |Z| < 2^(31 + t) (from the op's msb bounds) the nnqcomp
+// saturation test runs on the 32-bit results: the OR of v + 2^(w-1) over a
+// row has no bit at or above w iff every v is in X_w; otherwise it is one
+// unsigned range test on Z per element.
 // A warp that sees a value outside X_w (or a plan outside the fast regime)
 // recomputes that row through the general quantiser, kept out of line.  qcomp
 // pass 1 takes the bit width of the OR of |Z| (the max msb) and stores the
 // w_tmp window.  max |m| is kept on the packed results with 16x2 max / min.
 #pragma once
+
+#include <type_traits>
 
 #include "bfp_host.h"
 
@@ -165,8 +168,11 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const uint32_t t = (uint32_t)fq.t;
   // |Z| <= 2^zb from the msb bounds of the two groups
   const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
-  const bool fast = fq.ok && fq.t < 32 && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr &&
-                    (PASS1 || !fq.clamp || zb - (int)fq.t <= 30);
+  const bool fast = fq.ok && fq.t < 32 && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr;
+  // saturation test on the 32-bit results when Z >> t is exact in int32, else on Z
+  const bool v32 = zb - (int)fq.t <= 30;
+  const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << t);
+  const uint64_t zrange = (uint64_t)(((uint64_t)1 << (fq.w - 1 + t)) * 2 - 1);
   const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
   const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
   const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
 
   // staging: stage s holds y row j0 - 1 + s and r row j0 - 2 + s
   Stage16& S = stg[warp];
-  const int nyin = kUseY ? (int)(y.ny * y.nz) : 0, nrin = kUseR ? (int)(r.ny * r.nz) : 0;
+  const int nyin = kUseY ? (int)(y.ny * y.nz) : 1, nrin = kUseR ? (int)(r.ny * r.nz) : 1;
   const bool ycol = kUseY && c0 < y.nx && c0 < y.ld, rcol = kUseR && c0 < r.nx && c0 < r.ld;
   const int16_t* ybase = kUseY ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
   const int16_t* rbase = kUseR ? reinterpret_cast<const int16_t*>(r.m) : nullptr;
@@ -227,90 +233,102 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
     for (int j = j0; j < j1; ++j)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
   } else if (j0 < j1) {
-#pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) issue(s);
-    // ring slots of stages i, i + 1, i + 2 and i + kStages - 1 (= i - 1 mod kStages)
-    int s0 = 0, s1 = 1, s2 = 2, sn = kStages - 1;
-    for (int j = j0; j < j1; ++j) {
-      const int i = j - j0;
-      issue(sn);                                // stage i + kStages - 1, into the slot of row j - 2
-      cp_wait<kStages - 3>();                   // stages <= i + 2 have landed (own copies)
-      __syncwarp();                             // ... and the other lanes' (neighbours, halo)
-      Pk8 ym, yc, yp, rc;
-      int32_t yv[8], wv = 0, ev = 0;
-      if (kUseY) {
-        ym = rd(*reinterpret_cast<const uint4*>(&S.y[s0][4 + 4 * lane]));
-        yc = rd(*reinterpret_cast<const uint4*>(&S.y[s1][4 + 4 * lane]));
-        yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
-#pragma unroll
-        for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
-        const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
-        wv = row[7 + 8 * lane];                 // column c0 - 1
-        ev = row[16 + 8 * lane];                // column c0 + 8
-      }
-      if (kUseR) rc = rd(S.r[s2][lane]);
-      sn = s0;
-      s0 = s1;
-      s1 = s2;
-      s2 = s2 + 1 == kStages ? 0 : s2 + 1;
-      if (act) {
-        bool redo = !fast;
-        int32_t o[8];
-        if (fast) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            int64_t Z;
-            if (KIND == kJacobi0) {
-              Z = mulw(cr32, pk_get(rc, k));
-            } else {
-              const int32_t wk = k == 0 ? wv : yv[k - 1];
-              const int32_t ek = k == 7 ? ev : yv[k + 1];
-              const int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
-              Z = madw(cn32, ns, mulw(cy32, yv[k]));
-              if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
+    // the row walk, instantiated for both saturation tests (a uniform choice per CTA)
+    auto walk = [&](auto v32tag) {
+      constexpr bool V32 = decltype(v32tag)::value;
+  #pragma unroll
+      for (int s = 0; s < kStages - 1; ++s) issue(s);
+      // ring slots of stages i, i + 1, i + 2 and i + kStages - 1 (= i - 1 mod kStages)
+      int s0 = 0, s1 = 1, s2 = 2, sn = kStages - 1;
+      for (int j = j0; j < j1; ++j) {
+        const int i = j - j0;
+        issue(sn);                                // stage i + kStages - 1, into the slot of row j - 2
+        cp_wait<kStages - 3>();                   // stages <= i + 2 have landed (own copies)
+        __syncwarp();                             // ... and the other lanes' (neighbours, halo)
+        Pk8 ym, yc, yp, rc;
+        int32_t yv[8], wv = 0, ev = 0;
+        if (kUseY) {
+          ym = rd(*reinterpret_cast<const uint4*>(&S.y[s0][4 + 4 * lane]));
+          yc = rd(*reinterpret_cast<const uint4*>(&S.y[s1][4 + 4 * lane]));
+          yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
+  #pragma unroll
+          for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
+          const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
+          wv = row[7 + 8 * lane];                 // column c0 - 1
+          ev = row[16 + 8 * lane];                // column c0 + 8
+        }
+        if (kUseR) rc = rd(S.r[s2][lane]);
+        sn = s0;
+        s0 = s1;
+        s1 = s2;
+        s2 = s2 + 1 == kStages ? 0 : s2 + 1;
+        if (act) {
+          bool redo = !fast;
+          int32_t o[8];
+          bool ovf = false;
+          if (fast) {
+  #pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              int64_t Z;
+              if (KIND == kJacobi0) {
+                Z = mulw(cr32, pk_get(rc, k));
+              } else {
+                const int32_t wk = k == 0 ? wv : yv[k - 1];
+                const int32_t ek = k == 7 ? ev : yv[k + 1];
+                const int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
+                Z = madw(cn32, ns, mulw(cy32, yv[k]));
+                if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
+              }
+              const int32_t v = (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), t);
+              if (PASS1) {
+                if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
+                o[k] = (int32_t)((uint32_t)v << sh) >> sh;
+              } else {
+                o[k] = v;
+                if (!V32 && fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)zmin > zrange) && (k < nvalid);
+              }
             }
-            const int32_t v = (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), t);
-            if (PASS1) {
-              if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
-              o[k] = (int32_t)((uint32_t)v << sh) >> sh;
-            } else {
-              o[k] = v;
+            if (partial) {
+  #pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (k >= nvalid) o[k] = 0;
+            }
+            if (!PASS1 && fq.clamp) {
+              if (V32) {
+                uint32_t acc = 0;
+  #pragma unroll
+                for (int k = 0; k < 8; ++k) acc |= (uint32_t)o[k] + half;
+                redo = (acc >> fq.w) != 0u;
+              } else {
+                redo = ovf;
+              }
             }
           }
-          if (partial) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (k >= nvalid) o[k] = 0;
-          }
-          if (!PASS1 && fq.clamp) {
-            uint32_t acc = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc |= (uint32_t)o[k] + half;
-            redo = (acc >> fq.w) != 0u;
+          if (!PASS1 && fq.clamp && fast) redo = __any_sync(__activemask(), redo);
+          if (redo) {
+            redo_rows |= 1u << i;                 // recomputed after the loop
+          } else if (PASS1) {
+            if (tmp) {
+              int4* d = reinterpret_cast<int4*>(tmp + (int64_t)j * out.ld + c0);
+              d[0] = make_int4(o[0], o[1], o[2], o[3]);
+              d[1] = make_int4(o[4], o[5], o[6], o[7]);
+            }
+          } else {
+            uint4 u;
+            u.x = __byte_perm((uint32_t)o[0], (uint32_t)o[1], 0x5410);
+            u.y = __byte_perm((uint32_t)o[2], (uint32_t)o[3], 0x5410);
+            u.z = __byte_perm((uint32_t)o[4], (uint32_t)o[5], 0x5410);
+            u.w = __byte_perm((uint32_t)o[6], (uint32_t)o[7], 0x5410);
+            vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
+            vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
+            *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (int64_t)j * out.ld + c0) = u;
           }
         }
-        if (!PASS1 && fq.clamp && fast) redo = __any_sync(__activemask(), redo);
-        if (redo) {
-          redo_rows |= 1u << i;                 // recomputed after the loop
-        } else if (PASS1) {
-          if (tmp) {
-            int4* d = reinterpret_cast<int4*>(tmp + (int64_t)j * out.ld + c0);
-            d[0] = make_int4(o[0], o[1], o[2], o[3]);
-            d[1] = make_int4(o[4], o[5], o[6], o[7]);
-          }
-        } else {
-          uint4 u;
-          u.x = __byte_perm((uint32_t)o[0], (uint32_t)o[1], 0x5410);
-          u.y = __byte_perm((uint32_t)o[2], (uint32_t)o[3], 0x5410);
-          u.z = __byte_perm((uint32_t)o[4], (uint32_t)o[5], 0x5410);
-          u.w = __byte_perm((uint32_t)o[6], (uint32_t)o[7], 0x5410);
-          vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
-          vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
-          *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (int64_t)j * out.ld + c0) = u;
-        }
       }
-    }
-    cp_wait<0>();
+      cp_wait<0>();
+    };
+    if (v32) walk(std::true_type{});
+    else walk(std::false_type{});
     // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = j0 + __ffs(m) - 1;

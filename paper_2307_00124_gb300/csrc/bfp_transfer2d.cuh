@@ -1,9 +1,19 @@
-// bfp_transfer2d.cuh -- 2D grid transfers on int16 mantissas as row-walking
-// kernels: full-weighting restriction (Alg. v-cycle restriction line) and
-// bilinear interpolation with or without the correction y - P d (Alg. v-cycle
-// correction line, Alg. fmg interpolation line).  Same structure and the same
-// register fast path / out-of-line general path as bfp_star2d16.cuh.
+// bfp_transfer2d.cuh -- 2D grid transfers on int16 mantissas: full-weighting
+// restriction (Alg. v-cycle restriction line) and bilinear interpolation with
+// or without the correction y - P d (Alg. v-cycle correction line, Alg. fmg
+// interpolation line).
+//
+// Same structure as bfp_star2d16.cuh: a warp owns a 256-column chunk of a
+// strip of output rows, input rows are staged per warp through a cp.async
+// ring in shared memory (with halo words for the one neighbour mantissa a
+// chunk needs from the next / previous chunk), the exact groups H (the
+// transfer stencil) and L (the correction's y) are combined as
+// Z = kh*H + kl*L with the App. B exponent alignment folded into kh, kl, and
+// rows a warp cannot finish on the register path are recomputed after the
+// walk through the general quantiser.
 #pragma once
+
+#include <type_traits>
 
 #include "bfp_star2d16.cuh"
 
@@ -13,23 +23,8 @@ __device__ __forceinline__ void unpack8(const uint4 u, int32_t (&o)[8]) {
   const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    o[2 * k] = (int32_t)(w[k] << 16) >> 16;
+    o[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
     o[2 * k + 1] = (int32_t)w[k] >> 16;
-  }
-}
-
-// int16 row chunk of 8 at (row, c0) with zeros outside the grid
-__device__ __forceinline__ void ldrow16(const VIn& v, int64_t row, int64_t c0, int32_t (&o)[8]) {
-  if (row < 0 || row >= v.ny * v.nz || c0 >= v.nx || c0 >= v.ld) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = 0;
-    return;
-  }
-  unpack8(__ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const int16_t*>(v.m) + row * v.ld + c0)), o);
-  if (c0 + 8 > v.nx) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (c0 + k >= v.nx) o[k] = 0;
   }
 }
 
@@ -38,8 +33,11 @@ __device__ __forceinline__ int32_t ld1_16(const VIn& v, int64_t row, int64_t col
   return (int32_t)__ldg(reinterpret_cast<const int16_t*>(v.m) + row * v.ld + col);
 }
 
-// Emits one 8-wide output chunk from exact groups (H, L) through the fast path when the
-// plan allows (no value outside X_w in the warp), else through the general quantiser.
+__device__ __forceinline__ void cp8(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
 // General-path fallback for one chunk (kept out of line).
 template <bool PASS1>
 __device__ __noinline__ void slow_hl8(const int32_t (&H)[8], const int32_t (&L)[8], const Plan& p, const VOut& out,
@@ -50,49 +48,109 @@ __device__ __noinline__ void slow_hl8(const int32_t (&H)[8], const int32_t (&L)[
   quant8<PASS1>(H64, L64, p, out, tmp, row, c0, red);
 }
 
-template <bool PASS1>
-__device__ __forceinline__ void emit_hl8(const int32_t (&H)[8], const int32_t (&L)[8], const Plan& p, const Fast& fq,
-                                         bool fast, const VOut& out, int32_t* tmp, int64_t row, int64_t c0, Red& red,
-                                         uint32_t& nrm, uint64_t& ormag) {
-  const int64_t nvalid = out.nx - c0;
+// Uniform per-CTA constants of the register path: Z = kh H + kl L, v = Z >> t.
+struct EmitC {
+  bool fast;          // register path usable
+  bool v32;           // |Z| < 2^(31 + t): saturation tested on the 32-bit results
+  int32_t kh, kl;
+  uint32_t t;
+  int w, sh;          // result width, 32 - w (pass 1 window decr)
+  uint32_t half;      // 2^(w-1)
+  int64_t zmin;
+  uint64_t zrange;
+};
+
+__device__ __forceinline__ EmitC make_emit(const Fast& fq, const QDesc& q, int32_t hsign, bool pass1) {
+  EmitC e;
+  const bool dh_ok = fq.dh <= 30, dl_ok = fq.dl <= 30;
+  e.kh = dh_ok ? hsign * (int32_t)(1u << (fq.dh & 31)) : 0;
+  e.kl = dl_ok ? (int32_t)(1u << (fq.dl & 31)) : 0;
+  e.fast = fq.ok && fq.t < 32 && dh_ok && dl_ok && fq.w <= 32;
+  e.t = (uint32_t)fq.t;
+  const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
+  e.v32 = zb - fq.t <= 30;
+  e.w = fq.w;
+  e.sh = 32 - fq.w;
+  e.half = 1u << ((fq.w - 1) & 31);
+  e.zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << (fq.t & 63));
+  e.zrange = (uint64_t)(((uint64_t)1 << ((fq.w - 1 + fq.t) & 63)) * 2 - 1);
+  (void)pass1;
+  return e;
+}
+
+// One lane's 8 outputs on the register path; returns true when the warp must
+// recompute the row on the general path (nnqcomp saturation, or no fast path).
+template <bool PASS1, bool V32>
+__device__ __forceinline__ bool emit8(const EmitC& e, const Fast& fq, const int32_t (&H)[8], const int32_t (&L)[8],
+                                      bool two, int nvalid, bool partial, const VOut& out, int32_t* tmp, int64_t row,
+                                      int64_t c0, uint64_t& ormag, uint32_t& vmax, uint32_t& vmin) {
   int32_t o[8];
-  bool redo = !fast;
-  if (fast) {
-    const int64_t hi = (1ll << (fq.w - 1)) - 1, lo = -(1ll << (fq.w - 1));
-    bool ovf = false;
+  bool ovf = false;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t Z = (int64_t)((uint64_t)(int64_t)H[k] << fq.dh) + (int64_t)((uint64_t)(int64_t)L[k] << fq.dl);
-      const int64_t v = Z >> fq.t;
-      const bool valid = k < nvalid;
-      if (PASS1) {
-        if (valid) ormag |= (uint64_t)(Z ^ (Z >> 63));
-        o[k] = valid ? wrap_bits((uint64_t)v, fq.w) : 0;
-      } else {
-        if (fq.clamp) ovf |= (v > hi || v < lo) && valid;
-        o[k] = valid ? (int32_t)v : 0;
-      }
+  for (int k = 0; k < 8; ++k) {
+    const int64_t Z = two ? madw(e.kl, L[k], mulw(e.kh, H[k])) : mulw(e.kh, H[k]);
+    const int32_t v = (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), e.t);
+    if (PASS1) {
+      if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
+      o[k] = (int32_t)((uint32_t)v << e.sh) >> e.sh;
+    } else {
+      o[k] = v;
+      if (!V32 && fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)e.zmin > e.zrange) && (k < nvalid);
     }
-    if (!PASS1 && fq.clamp) redo = __any_sync(__activemask(), ovf);
   }
-  if (redo) {
-    slow_hl8<PASS1>(H, L, p, out, tmp, row, c0, red);
-    return;
+  if (partial) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k >= nvalid) o[k] = 0;
   }
+  bool redo = false;
+  if (!PASS1 && fq.clamp) {
+    if (V32) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc |= (uint32_t)o[k] + e.half;
+      redo = (acc >> e.w) != 0u;
+    } else {
+      redo = ovf;
+    }
+    redo = __any_sync(__activemask(), redo);
+  }
+  if (redo) return true;
   if (PASS1) {
     if (tmp) {
       int4* d = reinterpret_cast<int4*>(tmp + row * out.ld + c0);
       d[0] = make_int4(o[0], o[1], o[2], o[3]);
       d[1] = make_int4(o[4], o[5], o[6], o[7]);
     }
-  } else {
+  } else if (out.is32) {
+    int4* d = reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(out.m) + row * out.ld + c0);
+    d[0] = make_int4(o[0], o[1], o[2], o[3]);
+    d[1] = make_int4(o[4], o[5], o[6], o[7]);
+    uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const uint32_t a = (uint32_t)(o[k] < 0 ? -o[k] : o[k]);
-      nrm = a > nrm ? a : nrm;
+      m = a > m ? a : m;
     }
-    stv<8>(out, row, c0, o);
+    vmax = max(vmax, m);   // (int32 outputs: vmax holds max |v| directly, vmin unused)
+  } else {
+    uint4 u;
+    u.x = __byte_perm((uint32_t)o[0], (uint32_t)o[1], 0x5410);
+    u.y = __byte_perm((uint32_t)o[2], (uint32_t)o[3], 0x5410);
+    u.z = __byte_perm((uint32_t)o[4], (uint32_t)o[5], 0x5410);
+    u.w = __byte_perm((uint32_t)o[6], (uint32_t)o[7], 0x5410);
+    vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
+    vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
+    *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + row * out.ld + c0) = u;
   }
+  return false;
+}
+
+__device__ __forceinline__ long long packed_norm(uint32_t vmax, uint32_t vmin, bool is32) {
+  if (is32) return (long long)vmax;
+  const int32_t mx = max((int32_t)vmax >> 16, (int32_t)(int16_t)(vmax & 0xffffu));
+  const int32_t mn = min((int32_t)vmin >> 16, (int32_t)(int16_t)(vmin & 0xffffu));
+  return (long long)max(mx, -mn);
 }
 
 __device__ __forceinline__ void fold_key(Red& red, uint64_t ormag, bool any) {
@@ -100,11 +158,44 @@ __device__ __forceinline__ void fold_key(Red& red, uint64_t ormag, bool any) {
   else if (any) red.key = max(red.key, 257ll);
 }
 
-// r_c = R~ r_f: a warp owns 256 coarse columns (8 per lane: fine columns 2c0 .. 2c0+16)
-// and walks coarse rows, keeping the horizontally weighted fine row 2J+2 for the next row.
+// ---------------------------------------------------------------------------
+// Restriction r_c = R~ r_f.  A lane owns 8 coarse columns c0.. (fine columns
+// 2c0 .. 2c0+16); a stage is one fine row: 32 lane slots of 32 bytes, then the
+// east halo pair (the next chunk's first fine pair).
+// ---------------------------------------------------------------------------
+constexpr int kRStages = 8;
+constexpr int kRRowWords = 4 + 256 + 4;
+struct __align__(16) StageR {
+  uint32_t f[kRStages][kRRowWords];
+};
+
+// H of coarse row J from global memory (general path)
+__device__ __forceinline__ void restrict_hl_global(const VIn& f, int64_t J, int64_t c0, int32_t (&H)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t fi = 2 * (c0 + k) + 1, fj = 2 * J + 1;
+    int32_t acc = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        acc += (2 - (dx < 0 ? -dx : dx)) * (2 - (dy < 0 ? -dy : dy)) * ld1_16(f, fj + dy, fi + dx);
+    H[k] = acc;
+  }
+}
+
 template <bool PASS1>
-__global__ void __launch_bounds__(128, 8) k_restrict2d16(const VIn f, const QDesc q, const VOut out, const int rs) {
+__device__ __noinline__ void restrict_slow(const VIn& f, const Plan& p, const VOut& out, int32_t* tmp, int64_t J,
+                                           int64_t c0, Red& red) {
+  int32_t H[8], L[8];
+  restrict_hl_global(f, J, c0, H);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) L[k] = 0;
+  slow_hl8<PASS1>(H, L, p, out, tmp, J, c0, red);
+}
+
+template <bool PASS1>
+__global__ void __launch_bounds__(128, 6) k_restrict2d16(const VIn f, const QDesc q, const VOut out, const int rs) {
   __shared__ Plan sp;
+  __shared__ StageR stg[4];
   if (threadIdx.x == 0) {
     build_plan(q, sp);
     if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
@@ -112,62 +203,160 @@ __global__ void __launch_bounds__(128, 8) k_restrict2d16(const VIn f, const QDes
   __syncthreads();
   const Plan& p = sp;
   const Fast fq = make_fast(p, PASS1);
-  const bool fast = fq.ok;
+  const EmitC ec = make_emit(fq, q, 1, PASS1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * 256 + lane * 8;
-  const int64_t ny = out.ny;
-  const int64_t J0 = ((int64_t)blockIdx.y * 4 + warp) * rs;
-  const int64_t J1 = J0 + rs < ny ? J0 + rs : ny;
+  const int64_t fc = 2 * c0;
+  const int ny = (int)out.ny;
+  const int J0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);
+  const int J1 = J0 + rs < ny ? J0 + rs : ny;
   const bool act = c0 < out.ld;
-  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
   Red red = {0, 0, 0};
-  uint32_t nrm = 0;
+  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
+  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
+  const bool partial = nvalid < 8;
+  // fine columns fc + m, m < 16, beyond nx read as 0 (partial chunks only)
+  const int fvalid = (int)(f.nx - fc < 16 ? (f.nx - fc < 0 ? 0 : f.nx - fc) : 16);
+  uint32_t fmask[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    fmask[i] = ((2 * i < fvalid) ? 0xffffu : 0u) | ((2 * i + 1 < fvalid) ? 0xffff0000u : 0u);
+  const bool fpartial = fvalid < 16;
+
+  StageR& S = stg[warp];
+  const int nfin = (int)(f.ny * f.nz);
+  const int16_t* fb = reinterpret_cast<const int16_t*>(f.m);
+  const bool seg0 = fc < f.nx && fc < f.ld, seg1 = fc + 8 < f.nx && fc + 8 < f.ld;
+  const bool hok = lane == 31 && fc + 16 < f.nx;
+  // the next stage to issue: fine row jf (stage s holds fine row 2 J0 + s)
+  int jf = 2 * J0;
+  int64_t of = (int64_t)jf * f.ld + fc;
+  auto issue = [&](int slot) {
+    const bool in = (unsigned)jf < (unsigned)nfin;
+    cp16(&S.f[slot][4 + 8 * lane], fb + ((in && seg0) ? of : 0), (in && seg0) ? 16u : 0u);
+    cp16(&S.f[slot][8 + 8 * lane], fb + ((in && seg1) ? of + 8 : 0), (in && seg1) ? 16u : 0u);
+    const bool hk = hok && in;
+    cp4_if(lane == 31, &S.f[slot][kRRowWords - 4], fb + (hk ? of + 16 : 0), hk ? 4u : 0u);
+    of += f.ld;
+    ++jf;
+  };
+  // h_k = f[2c] + 2 f[2c+1] + f[2c+2] for c = c0 + k of the fine row in `slot`
+  auto hrow = [&](int slot, int32_t (&h)[8]) {
+    const uint4 a = *reinterpret_cast<const uint4*>(&S.f[slot][4 + 8 * lane]);
+    const uint4 b = *reinterpret_cast<const uint4*>(&S.f[slot][8 + 8 * lane]);
+    uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    if (fpartial) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[i] &= fmask[i];
+    }
+    const int32_t nxt = reinterpret_cast<const int16_t*>(&S.f[slot][0])[8 + 16 * (lane + 1)];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int32_t v0 = (int32_t)(int16_t)(w[k] & 0xffffu), v1 = (int32_t)w[k] >> 16;
+      const int32_t v2 = k < 7 ? (int32_t)(int16_t)(w[k + 1] & 0xffffu) : nxt;
+      h[k] = v0 + 2 * v1 + v2;
+    }
+  };
+
+  uint32_t vmax = 0, vmin = 0, redo_rows = 0;
   uint64_t ormag = 0;
   bool any = false;
-  // h_k = f[2c] + 2 f[2c+1] + f[2c+2] for c = c0 + k of fine row fr
-  auto hrow = [&](int64_t fr, int32_t (&h)[8]) {
-    int32_t a[8], b[8];
-    ldrow16(f, fr, 2 * c0, a);
-    ldrow16(f, fr, 2 * c0 + 8, b);
-    int32_t nxt = __shfl_down_sync(0xffffffffu, a[0], 1);
-    if (lane == 31) nxt = ld1_16(f, fr, 2 * c0 + 16);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) h[k] = a[2 * k] + 2 * a[2 * k + 1] + (k < 3 ? a[2 * k + 2] : b[0]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) h[4 + k] = b[2 * k] + 2 * b[2 * k + 1] + (k < 3 ? b[2 * k + 2] : nxt);
-  };
   if (!PASS1 && p.narrow) {
-    for (int64_t J = J0; J < J1; ++J)
+    for (int J = J0; J < J1; ++J)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, J, c0, red);
   } else if (J0 < J1) {
-    int32_t hp[8];
-    hrow(2 * J0, hp);
-    for (int64_t J = J0; J < J1; ++J) {
-      int32_t hm[8], hn[8];
-      hrow(2 * J + 1, hm);
-      hrow(2 * J + 2, hn);
-      int32_t H[8], L[8];
+    auto walk = [&](auto v32tag) {
+      constexpr bool V32 = decltype(v32tag)::value;
+      // prologue: fine rows 2 J0 .. 2 J0 + 5 in three groups of two
 #pragma unroll
-      for (int k = 0; k < 8; ++k) { H[k] = hp[k] + 2 * hm[k] + hn[k]; L[k] = 0; hp[k] = hn[k]; }
-      if (act) {
-        emit_hl8<PASS1>(H, L, p, fq, fast, out, tmp, J, c0, red, nrm, ormag);
-        any = any || (out.nx - c0 > 0);
+      for (int g = 0; g < 3; ++g) {
+        issue(2 * g);
+        issue(2 * g + 1);
+        cp_commit();
       }
+      cp_wait<2>();
+      __syncwarp();
+      int32_t hp[8];
+      hrow(0, hp);
+      for (int J = J0; J < J1; ++J) {
+        const int i = J - J0;
+        __syncwarp();                           // every lane is done with the slots reused below
+        issue((2 * i + 6) & (kRStages - 1));    // fine rows 2J + 6, 2J + 7 into the slots of 2J - 2, 2J - 1
+        issue((2 * i + 7) & (kRStages - 1));
+        cp_commit();
+        cp_wait<2>();                           // fine rows <= 2J + 3 have landed
+        __syncwarp();
+        int32_t hm[8], hn[8];
+        hrow((2 * i + 1) & (kRStages - 1), hm);
+        hrow((2 * i + 2) & (kRStages - 1), hn);
+        int32_t H[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { H[k] = hp[k] + 2 * hm[k] + hn[k]; hp[k] = hn[k]; }
+        if (act) {
+          bool redo = !ec.fast;
+          if (ec.fast)   // one exact group: the L argument is not read
+            redo = emit8<PASS1, V32>(ec, fq, H, H, false, nvalid, partial, out, tmp, J, c0, ormag, vmax, vmin);
+          if (redo) redo_rows |= 1u << i;
+          any = any || nvalid > 0;
+        }
+      }
+      cp_wait<0>();
+    };
+    if (ec.v32) walk(std::true_type{});
+    else walk(std::false_type{});
+    for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
+      const int J = J0 + __ffs(m) - 1;
+      if (act) restrict_slow<PASS1>(f, p, out, tmp, J, c0, red);
     }
   }
-  if (PASS1) fold_key(red, ormag, any);
-  red.nrm = max(red.nrm, (long long)nrm);
+  if (PASS1) fold_key(red, ormag, any && ec.fast);
+  else red.nrm = max(red.nrm, packed_norm(vmax, vmin, out.is32 != 0));
   block_commit(red, q.meta_out, q.stats, PASS1);
   if (!PASS1) op_epilogue(q, p);
 }
 
-// y' = y - P d (CORR) or P d: a warp owns 256 fine columns (8 per lane: coarse
-// columns c0/2 - 1 .. c0/2 + 3) and walks pairs of fine rows (2J, 2J+1), keeping
-// the interpolated coarse row J - 1.
+// ---------------------------------------------------------------------------
+// Interpolation: y' = y - P d (CORR) or P d.  A lane owns 8 fine columns c0..
+// (coarse columns C = c0/2 .. C+3 and C-1 from the previous lane); a stage is
+// coarse row P (lane slots of 8 bytes after the west halo pair) and fine rows
+// 2P, 2P+1 of y.
+// ---------------------------------------------------------------------------
+constexpr int kPStages = 4;
+constexpr int kPRowWords = 4 + 64;
+struct __align__(16) StageP {
+  uint32_t d[kPStages][kPRowWords];
+  uint4 y[kPStages][2][32];
+};
+
+// H (= P_m d) and L (= y) of fine row j from global memory (general path)
+template <bool CORR>
+__device__ __forceinline__ void prolong_hl_global(const VIn& d, const VIn& y, int64_t j, int64_t c0, int32_t (&H)[8],
+                                                  int32_t (&L)[8]) {
+  auto gx = [&](int64_t J, int64_t i) -> int32_t {   // horizontal interpolation of coarse row J at fine column i
+    return (i & 1) ? 2 * ld1_16(d, J, (i - 1) >> 1) : ld1_16(d, J, (i >> 1) - 1) + ld1_16(d, J, i >> 1);
+  };
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t i = c0 + k;
+    const int32_t pd = (j & 1) ? 2 * gx((j - 1) >> 1, i) : gx((j >> 1) - 1, i) + gx(j >> 1, i);
+    H[k] = CORR ? -pd : pd;
+    L[k] = CORR ? ld1_16(y, j, i) : 0;
+  }
+}
+
 template <bool CORR, bool PASS1>
-__global__ void __launch_bounds__(128, 8) k_prolong2d16(const VIn d, const VIn y, const QDesc q, const VOut out,
+__device__ __noinline__ void prolong_slow(const VIn& d, const VIn& y, const Plan& p, const VOut& out, int32_t* tmp,
+                                          int64_t j, int64_t c0, Red& red) {
+  int32_t H[8], L[8];
+  prolong_hl_global<CORR>(d, y, j, c0, H, L);
+  slow_hl8<PASS1>(H, L, p, out, tmp, j, c0, red);
+}
+
+template <bool CORR, bool PASS1>
+__global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y, const QDesc q, const VOut out,
                                                         const int rs) {
   __shared__ Plan sp;
+  __shared__ StageP stg[4];
   if (threadIdx.x == 0) {
     build_plan(q, sp);
     if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
@@ -175,71 +364,127 @@ __global__ void __launch_bounds__(128, 8) k_prolong2d16(const VIn d, const VIn y
   __syncthreads();
   const Plan& p = sp;
   const Fast fq = make_fast(p, PASS1);
-  const bool fast = fq.ok;
+  const EmitC ec = make_emit(fq, q, CORR ? -1 : 1, PASS1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * 256 + lane * 8;
-  const int64_t ny = out.ny;                     // fine rows
-  const int64_t P0 = ((int64_t)blockIdx.y * 4 + warp) * rs;   // first row pair (fine rows 2P0, 2P0+1)
-  const int64_t P1 = P0 + rs;
-  const bool act = c0 < out.ld;
-  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
-  Red red = {0, 0, 0};
-  uint32_t nrm = 0;
-  uint64_t ormag = 0;
-  bool any = false;
   const int64_t C = c0 >> 1;                     // first coarse column of this lane (multiple of 4)
-  // g_k: horizontal interpolation of coarse row J at fine columns c0 + k (mantissas at exponent -1)
-  auto grow = [&](int64_t J, int32_t (&g)[8]) {
-    int32_t dv[5];
-    if (J >= 0 && J < d.ny && C < d.nx) {
-      const uint2 u = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const int16_t*>(d.m) + J * d.ld + C));
-      dv[1] = (int32_t)(u.x << 16) >> 16; dv[2] = (int32_t)u.x >> 16;
-      dv[3] = (int32_t)(u.y << 16) >> 16; dv[4] = (int32_t)u.y >> 16;
+  const int ny = (int)out.ny;                    // fine rows
+  const int P0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);   // first row pair (fine rows 2P0, 2P0+1)
+  const int P1 = min(P0 + rs, (ny + 1) / 2);
+  const bool act = c0 < out.ld;
+  Red red = {0, 0, 0};
+  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
+  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
+  const bool partial = nvalid < 8;
+  // coarse columns C + m (m < 4) beyond d.nx, fine y columns beyond nx: 0 (partial chunks only)
+  const int cvalid = (int)(d.nx - C < 4 ? (d.nx - C < 0 ? 0 : d.nx - C) : 4);
+  const uint32_t cm0 = ((0 < cvalid) ? 0xffffu : 0u) | ((1 < cvalid) ? 0xffff0000u : 0u);
+  const uint32_t cm1 = ((2 < cvalid) ? 0xffffu : 0u) | ((3 < cvalid) ? 0xffff0000u : 0u);
+  uint32_t ymask[4];
 #pragma unroll
-      for (int k = 1; k < 5; ++k)
-        if (C + k - 1 >= d.nx) dv[k] = 0;
-    } else {
-      dv[1] = dv[2] = dv[3] = dv[4] = 0;
+  for (int i = 0; i < 4; ++i)
+    ymask[i] = ((2 * i < nvalid) ? 0xffffu : 0u) | ((2 * i + 1 < nvalid) ? 0xffff0000u : 0u);
+
+  StageP& S = stg[warp];
+  const int ncr = (int)(d.ny * d.nz), nyr = CORR ? (int)(y.ny * y.nz) : 1;
+  const int16_t* db = reinterpret_cast<const int16_t*>(d.m);
+  const int16_t* yb = CORR ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
+  const bool dseg = C < d.nx && C < d.ld;
+  const bool hok = lane == 0 && C >= 2 && C - 1 < d.nx;
+  const bool yseg = CORR && c0 < y.nx && c0 < y.ld;
+  // the next stage: coarse row jc (stage s holds coarse row P0 - 1 + s, y rows 2 jc, 2 jc + 1)
+  int jc = P0 - 1;
+  int64_t od = (int64_t)jc * d.ld + C, oy = CORR ? (int64_t)(2 * jc) * y.ld + c0 : 0;
+  auto issue = [&](int slot, bool with_y) {
+    const bool in = (unsigned)jc < (unsigned)ncr;
+    cp8(&S.d[slot][4 + 2 * lane], db + ((in && dseg) ? od : 0), (in && dseg) ? 8u : 0u);
+    const bool hk = hok && in;
+    cp4_if(lane == 0, &S.d[slot][3], db + (hk ? od - 2 : 0), hk ? 4u : 0u);
+    if (CORR && with_y) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool yin = yseg && (unsigned)(2 * jc + h) < (unsigned)nyr;
+        cp16(&S.y[slot][h][lane], yb + (yin ? oy + h * y.ld : 0), yin ? 16u : 0u);
+      }
     }
-    dv[0] = __shfl_up_sync(0xffffffffu, dv[4], 1);
-    if (lane == 0) dv[0] = (J >= 0 && J < d.ny) ? ld1_16(d, J, C - 1) : 0;
+    od += d.ld;
+    if (CORR) oy += 2 * y.ld;
+    ++jc;
+    cp_commit();
+  };
+  // g_k: horizontal interpolation of the coarse row in `slot` at fine columns c0 + k
+  auto grow = [&](int slot, int32_t (&g)[8]) {
+    const uint2 u = *reinterpret_cast<const uint2*>(&S.d[slot][4 + 2 * lane]);
+    const uint32_t u0 = u.x & cm0, u1 = u.y & cm1;
+    int32_t dv[5];
+    dv[0] = reinterpret_cast<const int16_t*>(&S.d[slot][0])[7 + 4 * lane];   // coarse column C - 1
+    dv[1] = (int32_t)(int16_t)(u0 & 0xffffu); dv[2] = (int32_t)u0 >> 16;
+    dv[3] = (int32_t)(int16_t)(u1 & 0xffffu); dv[4] = (int32_t)u1 >> 16;
 #pragma unroll
     for (int k = 0; k < 8; ++k) g[k] = (k & 1) ? 2 * dv[(k + 1) / 2] : dv[k / 2] + dv[k / 2 + 1];
   };
+
+  uint32_t vmax = 0, vmin = 0, redo_rows = 0;
+  uint64_t ormag = 0;
+  bool any = false;
   if (!PASS1 && p.narrow) {
-    for (int64_t j = 2 * P0; j < 2 * P1 && j < ny; ++j)
+    for (int j = 2 * P0; j < 2 * P1 && j < ny; ++j)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
-  } else if (2 * P0 < ny) {
-    int32_t gm[8];
-    grow(P0 - 1, gm);
-    for (int64_t P = P0; P < P1 && 2 * P < ny; ++P) {
-      int32_t gc[8];
-      grow(P, gc);
-      // fine row 2P: coarse rows P-1, P (weights 1, 1); fine row 2P+1: coarse row P (weight 2)
+  } else if (P0 < P1) {
+    auto walk = [&](auto v32tag) {
+      constexpr bool V32 = decltype(v32tag)::value;
+      issue(0, false);                           // coarse row P0 - 1 only
+      issue(1, true);
+      issue(2, true);
+      cp_wait<2>();
+      __syncwarp();
+      int32_t gm[8];
+      grow(0, gm);
+      for (int P = P0; P < P1; ++P) {
+        const int i = P - P0;
+        issue((i + 3) & (kPStages - 1), true);   // stage i + 3 into the slot of stage i - 1
+        cp_wait<2>();                            // stage i + 1 (coarse row P, y rows 2P, 2P+1) has landed
+        __syncwarp();
+        const int slot = (i + 1) & (kPStages - 1);
+        int32_t gc[8];
+        grow(slot, gc);
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int64_t j = 2 * P + half;
-        if (j >= ny) break;
-        int32_t yv[8];
-        if (CORR) ldrow16(y, j, c0, yv);
-        int32_t H[8], L[8];
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * P + h;
+          if (j >= ny) break;
+          int32_t H[8], L[8];
+          if (CORR) {
+            uint4 u = S.y[slot][h][lane];
+            if (partial) { u.x &= ymask[0]; u.y &= ymask[1]; u.z &= ymask[2]; u.w &= ymask[3]; }
+            unpack8(u, L);
+          } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int32_t pd = half == 0 ? gm[k] + gc[k] : 2 * gc[k];
-          H[k] = CORR ? -pd : pd;
-          L[k] = CORR ? yv[k] : 0;
+            for (int k = 0; k < 8; ++k) L[k] = 0;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) H[k] = h == 0 ? gm[k] + gc[k] : 2 * gc[k];
+          if (act) {
+            bool redo = !ec.fast;
+            if (ec.fast)
+              redo = emit8<PASS1, V32>(ec, fq, H, L, CORR, nvalid, partial, out, tmp, j, c0, ormag, vmax, vmin);
+            if (redo) redo_rows |= 1u << (2 * i + h);
+            any = any || nvalid > 0;
+          }
         }
-        if (act) {
-          emit_hl8<PASS1>(H, L, p, fq, fast, out, tmp, j, c0, red, nrm, ormag);
-          any = any || (out.nx - c0 > 0);
-        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gm[k] = gc[k];
       }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) gm[k] = gc[k];
+      cp_wait<0>();
+    };
+    if (ec.v32) walk(std::true_type{});
+    else walk(std::false_type{});
+    for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
+      const int j = 2 * P0 + __ffs(m) - 1;
+      if (act) prolong_slow<CORR, PASS1>(d, y, p, out, tmp, j, c0, red);
     }
   }
-  if (PASS1) fold_key(red, ormag, any);
-  red.nrm = max(red.nrm, (long long)nrm);
+  if (PASS1) fold_key(red, ormag, any && ec.fast);
+  else red.nrm = max(red.nrm, packed_norm(vmax, vmin, out.is32 != 0));
   block_commit(red, q.meta_out, q.stats, PASS1);
   if (!PASS1) op_epilogue(q, p);
 }
