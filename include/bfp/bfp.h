@@ -241,7 +241,12 @@ typedef struct {
   int32_t coarse_onchip; /* 2D: the levels from the first with n <= N run as one shared-memory
                             kernel; N = 127 for 1, N = min(value, 127) for values > 1, 0: off
                             (default 63) */
+  int32_t arith;         /* bfp_arith: the V-cycle's vectors and arithmetic (default BFP) */
 } bfp_solver_opts;
+
+/* BFP_ARITH_BFP is the paper's method; FP32 and BF16 (storage, with FP32
+ * arithmetic) are float baselines of the same schedule for comparison. */
+typedef enum { BFP_ARITH_BFP = 0, BFP_ARITH_FP32 = 1, BFP_ARITH_BF16 = 2 } bfp_arith;
 
 /* Fill opts with the defaults of the 2D/3D model problem. */
 int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_opts* o);
@@ -276,7 +281,9 @@ int32_t bfp_ir_update(double* x, const bfp_vec* y, bfp_stream stream);
 
 /* FP64 iterative refinement (Alg. ir with FP64 residual and update):
  * k steps of  r = b' - A' x,  y = V(quant(r)),  x = x + y  on the finest level,
- * where b' = (h^2 / 2^p) f.  f, x: device dense doubles (n^d).  No host sync. */
+ * where b' = (h^2 / 2^p) f.  f, x: device dense doubles (n^d).  No host sync.
+ * With opts.arith FP32 / BF16, quant(r) is r rounded to FP32 (then to BF16)
+ * and V is the float V-cycle; bfp_fmg and ir_solve follow the same rule. */
 int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k,
                        bfp_stream stream);
 
@@ -303,6 +310,43 @@ typedef struct {
  * read the residual norm.  Returns BFP_ERR_NOCONV when max_iter is reached. */
 int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts* o,
                  bfp_ir_report* rep, bfp_stream stream);
+
+/* ---- float baselines (not in the paper) ------------------------------------------ */
+/* FP32 and BF16-storage / FP32-arithmetic versions of the V-cycle ops, for the
+ * comparison the paper's method is measured against.  Arithmetic is FP32 with
+ * round-to-nearest and no contraction, in the order stated per op; BF16
+ * vectors hold the upper half of an FP32 value (loads widen exactly, stores
+ * round to nearest-even).  The coefficients come from a bfp_stencil:
+ * c = center 2^e, nb = nbr 2^e, om = omega.m 2^omega.e (dyadic, exact in FP32).
+ * Neighbours outside the grid are 0; padding columns of outputs are written
+ * as 0.  Status codes and stream behaviour as for the BFP ops. */
+typedef enum { FLT_F32 = 0, FLT_BF16 = 1 } flt_dtype;
+
+typedef struct {
+  void* data;          /* device pointer (float, or BF16 bit patterns as uint16), 16-byte aligned */
+  int32_t dtype;       /* flt_dtype */
+  int32_t ndim;        /* 2 or 3 */
+  int64_t n[3];        /* points per dimension, x fastest (unused dimensions 1) */
+  int64_t ld;          /* row stride in elements: >= n[0], multiple of 8 */
+} flt_vec;
+
+/* out = y + om (r - a), a = c y + nb s, s = (W + E) + (S + N) [+ (B + T)];
+ * y == NULL: out = om r.  y, r, out: same shape and dtype, out distinct. */
+int32_t flt_jacobi(const bfp_stencil* A, const flt_vec* y, const flt_vec* r, const flt_vec* out,
+                   bfp_stream stream);
+/* out = a - r (the V-cycle residual r_v = A'y - r). */
+int32_t flt_residual(const bfp_stencil* A, const flt_vec* y, const flt_vec* r, const flt_vec* out,
+                     bfp_stream stream);
+/* Full weighting r_c = R~ r_f (coarse n_c = (n_f - 1)/2): along x (f0 + 2 f1) + f2
+ * with fine index 2I + 1 of coarse I in the middle, then the same along y [and z],
+ * times 2^-2 (2D) or 2^-4 (3D). */
+int32_t flt_restrict(const flt_vec* r_f, const flt_vec* r_c, bfp_stream stream);
+/* out = y - P d (y != NULL) or P d: interpolation along x, then y [then z];
+ * on a coarse point its value, between two coarse points 0.5 a + 0.5 b. */
+int32_t flt_prolong(const flt_vec* d, const flt_vec* y, const flt_vec* out, bfp_stream stream);
+/* y = V(nu1,nu2)(r) on the finest level of a hierarchy created with
+ * opts.arith FP32 (dtype F32) or BF16 (dtype BF16). */
+int32_t flt_vcycle(bfp_hierarchy* h, const flt_vec* r, const flt_vec* y, bfp_stream stream);
 
 #ifdef __cplusplus
 }

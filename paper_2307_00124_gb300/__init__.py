@@ -22,6 +22,8 @@ _lib = C.CDLL(LIB_PATH)
 
 META_WORDS = 8
 QCOMP, NNQCOMP = 0, 1
+ARITH_BFP, ARITH_FP32, ARITH_BF16 = 0, 1, 2
+F32, BF16 = 0, 1
 
 STATUS = {0: "BFP_OK", -1: "BFP_ERR_ARG", -2: "BFP_ERR_SHAPE", -3: "BFP_ERR_WIDTH", -4: "BFP_ERR_CUDA",
           -5: "BFP_ERR_NONFINITE", -6: "BFP_ERR_TIMEOUT", -7: "BFP_ERR_NOCONV", -8: "BFP_ERR_CAPACITY"}
@@ -63,7 +65,12 @@ class bfp_solver_opts(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("w", C.c_int32), ("n", C.c_int64), ("mode", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
                 ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
-                ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32)]
+                ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32), ("arith", C.c_int32)]
+
+
+class flt_vec(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("ndim", C.c_int32), ("n", C.c_int64 * 3),
+                ("ld", C.c_int64)]
 
 
 class bfp_ir_opts(C.Structure):
@@ -112,6 +119,11 @@ _sig = {
     "bfp_ir_update": (C.c_int32, [C.c_void_p, P(bfp_vec), C.c_void_p]),
     "ir_solve": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, P(bfp_ir_opts), P(bfp_ir_report),
                              C.c_void_p]),
+    "flt_jacobi": (C.c_int32, [P(bfp_stencil), P(flt_vec), P(flt_vec), P(flt_vec), C.c_void_p]),
+    "flt_residual": (C.c_int32, [P(bfp_stencil), P(flt_vec), P(flt_vec), P(flt_vec), C.c_void_p]),
+    "flt_restrict": (C.c_int32, [P(flt_vec), P(flt_vec), C.c_void_p]),
+    "flt_prolong": (C.c_int32, [P(flt_vec), P(flt_vec), P(flt_vec), C.c_void_p]),
+    "flt_vcycle": (C.c_int32, [C.c_void_p, P(flt_vec), P(flt_vec), C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -204,6 +216,63 @@ class BFPVector:
     @property
     def norm_m(self) -> int:
         return int(self.meta[1].item())
+
+
+class FltVector:
+    """A float-baseline vector in device memory: FP32 or BF16 (as int16 bit patterns), rows x ld.
+
+    ``shape`` is the numpy-order logical shape ((ny, nx) or (nz, ny, nx)).
+    """
+
+    def __init__(self, shape, dtype: int = F32, device="cuda", data=None):
+        import torch
+        self.shape = tuple(int(s) for s in shape)
+        self.dtype = int(dtype)
+        self.ld = pitch(self.shape[-1])
+        self.rows = int(np.prod(self.shape[:-1]))
+        td = torch.float32 if self.dtype == F32 else torch.int16
+        self.data = data if data is not None else torch.zeros((self.rows, self.ld), dtype=td, device=device)
+
+    @property
+    def ndim(self):
+        return len(self.shape)
+
+    def struct(self) -> flt_vec:
+        v = flt_vec()
+        v.data = self.data.data_ptr()
+        v.dtype = self.dtype
+        v.ndim = self.ndim
+        n = list(reversed(self.shape)) + [1] * (3 - self.ndim)
+        for i in range(3):
+            v.n[i] = n[i]
+        v.ld = self.ld
+        return v
+
+    @classmethod
+    def from_array(cls, a: np.ndarray, dtype: int = F32, device="cuda"):
+        """a: float32 values (BF16: float32 values whose low 16 bits are zero)."""
+        import torch
+        a = np.asarray(a, dtype=np.float32)
+        v = cls(a.shape, dtype, device)
+        host = np.zeros((v.rows, v.ld), dtype=np.float32)
+        host[:, : a.shape[-1]] = a.reshape(v.rows, a.shape[-1])
+        if dtype == F32:
+            v.data.copy_(torch.from_numpy(host))
+        else:
+            bits = host.view(np.uint32) >> 16
+            v.data.copy_(torch.from_numpy(bits.astype(np.uint16).view(np.int16)))
+        return v
+
+    def values(self) -> np.ndarray:
+        """float32 values of the logical shape."""
+        h = self.data.cpu().numpy()
+        if self.dtype == BF16:
+            h = (h.view(np.uint16).astype(np.uint32) << 16).view(np.float32)
+        return h[:, : self.shape[-1]].reshape(self.shape)
+
+    def padding(self) -> np.ndarray:
+        h = self.data.cpu().numpy()
+        return h[:, self.shape[-1]:]
 
 
 def q(w_out: int, mode: int = QCOMP, w_add: int = -1, gamma=None, tmp=None) -> bfp_q:
@@ -311,6 +380,28 @@ def bfp_prolong(d, y, y_out, qq, stats=None, stream=None):
                             _stream(stream)), "bfp_prolong")
 
 
+# ---- float baselines (not in the paper) ----------------------------------------------
+
+def flt_jacobi(A, y, r, out, stream=None):
+    yp = None if y is None else C.byref(y.struct())
+    _check(_lib.flt_jacobi(C.byref(A), yp, C.byref(r.struct()), C.byref(out.struct()), _stream(stream)),
+           "flt_jacobi")
+
+
+def flt_residual(A, y, r, out, stream=None):
+    _check(_lib.flt_residual(C.byref(A), C.byref(y.struct()), C.byref(r.struct()), C.byref(out.struct()),
+                             _stream(stream)), "flt_residual")
+
+
+def flt_restrict(rf, rc, stream=None):
+    _check(_lib.flt_restrict(C.byref(rf.struct()), C.byref(rc.struct()), _stream(stream)), "flt_restrict")
+
+
+def flt_prolong(d, y, out, stream=None):
+    yp = None if y is None else C.byref(y.struct())
+    _check(_lib.flt_prolong(C.byref(d.struct()), yp, C.byref(out.struct()), _stream(stream)), "flt_prolong")
+
+
 # ---- multigrid ---------------------------------------------------------------------
 
 def bfp_solver_opts_default(ndim: int, n: int, w: int) -> bfp_solver_opts:
@@ -349,6 +440,10 @@ class Hierarchy:
         _check(_lib.bfp_hierarchy_reset_stats(self.h, _stream(stream)), "bfp_hierarchy_reset_stats")
 
     def vcycle(self, r, y, stream=None):
+        if isinstance(r, FltVector):
+            _check(_lib.flt_vcycle(self.h, C.byref(r.struct()), C.byref(y.struct()), _stream(stream)),
+                   "flt_vcycle")
+            return
         _check(_lib.bfp_vcycle(self.h, C.byref(r.struct()), C.byref(y.struct()), _stream(stream)), "bfp_vcycle")
 
     def ir_iterate(self, f, x, k: int, stream=None):

@@ -9,6 +9,7 @@
 
 #include "bfp_coarse.cuh"
 #include "bfp_desc.h"
+#include "bfp_flt_host.h"
 #include "bfp_ir2d.cuh"
 
 using namespace bfp;
@@ -126,6 +127,80 @@ __global__ void __launch_bounds__(256) k_ir_resnorm(const double* __restrict__ b
   }
 }
 
+// ---- float baselines: FP64 IR residual rounded to FP32 (then BF16), update, conversions ----
+
+template <class S>
+__device__ __forceinline__ void fstore_f64(void* p, int64_t o, double v) {
+  const float f = __double2float_rn(v);
+  if (sizeof(S) == 4) reinterpret_cast<float*>(p)[o] = f;
+  else reinterpret_cast<unsigned short*>(p)[o] = (unsigned short)f32_to_bf16(f);
+}
+
+template <class S>
+__device__ __forceinline__ double fload_f64(const void* p, int64_t o) {
+  if (sizeof(S) == 4) return (double)reinterpret_cast<const float*>(p)[o];
+  return (double)bf16_to_f32(reinterpret_cast<const unsigned short*>(p)[o]);
+}
+
+// r = storage(RN32(b' - A'x)) with the FP64 residual of ir_res (fixed order)
+template <int ND, class S>
+__global__ void __launch_bounds__(256) k_fir_residual(const double* __restrict__ b, double bscale,
+                                                      const double* __restrict__ x, Grid g, double cdiag, double cnb,
+                                                      FVOut out) {
+  const int64_t total = out.ld * g.ny * g.nz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % out.ld, row = idx / out.ld, j = row % g.ny, k = row / g.ny;
+    const double r = i < g.nx ? ir_res<ND>(b, bscale, x, g, i, j, k, cdiag, cnb) : 0.0;
+    fstore_f64<S>(out.p, idx, r);
+  }
+}
+
+// x <- x + y (y widened exactly, one FP64 rounding); kUpdRows rows of loads in flight
+template <class S>
+__global__ void __launch_bounds__(256) k_fir_update(double* __restrict__ x, const FVIn y) {
+  const int64_t rows = y.ny * y.nz;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= y.nx) return;
+  for (int64_t r0 = (int64_t)blockIdx.y * kUpdRows; r0 < rows; r0 += (int64_t)gridDim.y * kUpdRows) {
+    double xv[kUpdRows], yv[kUpdRows];
+#pragma unroll
+    for (int k = 0; k < kUpdRows; ++k) {
+      const int64_t row = r0 + k;
+      if (row < rows) {
+        xv[k] = x[row * y.nx + i];
+        yv[k] = fload_f64<S>(y.p, row * y.ld + i);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUpdRows; ++k) {
+      const int64_t row = r0 + k;
+      if (row < rows) x[row * y.nx + i] = __dadd_rn(xv[k], yv[k]);
+    }
+  }
+}
+
+// dense doubles (n^d) <-> float vectors (padding written as 0)
+template <class S>
+__global__ void __launch_bounds__(256) k_f64_to_flt(const double* __restrict__ x, FVOut out) {
+  const int64_t total = out.ld * out.ny * out.nz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % out.ld, row = idx / out.ld;
+    fstore_f64<S>(out.p, idx, i < out.nx ? x[row * out.nx + i] : 0.0);
+  }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_flt_to_f64(const FVIn v, double* __restrict__ x) {
+  const int64_t total = v.nx * v.ny * v.nz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % v.nx, row = idx / v.nx;
+    x[idx] = fload_f64<S>(v.p, row * v.ld + i);
+  }
+}
+
 // x <- x + m 2^e (the FP64 update of Alg. ir, sign flipped with the residual)
 template <class T>
 __global__ void __launch_bounds__(256) k_ir_update(double* __restrict__ x, const VIn y, const int64_t* meta) {
@@ -172,6 +247,7 @@ struct Level {
   void* tmp = nullptr;            // qcomp window (int32)
   double* b = nullptr;            // FP64 right-hand side (levels >= 1)
   double* x = nullptr;            // FP64 iterate (levels >= 1)
+  flt_vec fr{}, fya{}, fyb{}, frv{};   // float baselines: the same buffers as float vectors
 };
 
 }  // namespace
@@ -195,6 +271,7 @@ struct bfp_hierarchy {
   std::vector<CoarseOp*> d_ops;          // per start level k >= kc
   std::vector<int> nops, rbuf, ybuf;
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
+  flt_vec fy0{};                         // its float counterpart (float hierarchies)
   // captured IR step
   cudaGraphExec_t graph = nullptr;
   const double* graph_f = nullptr;
@@ -225,6 +302,22 @@ bool make_vec(bfp_hierarchy* h, bfp_vec& v, int nd, int64_t n, int w) {
   cudaMemset(v.meta, 0, BFP_META_WORDS * sizeof(int64_t));
   return true;
 }
+
+bool make_fvec(bfp_hierarchy* h, flt_vec& v, int nd, int64_t n, int dtype) {
+  std::memset(&v, 0, sizeof(v));
+  v.dtype = dtype;
+  v.ndim = nd;
+  v.n[0] = n; v.n[1] = n; v.n[2] = nd == 3 ? n : 1;
+  v.ld = bfp_pitch(n);
+  const size_t bytes = (size_t)(v.n[1] * v.n[2] * v.ld) * (dtype == FLT_BF16 ? 2 : 4);
+  v.data = dalloc(h, bytes);
+  if (!v.data) return false;
+  cudaMemset(v.data, 0, bytes);
+  return true;
+}
+
+inline bool is_float(const bfp_hierarchy* h) { return h->o.arith != BFP_ARITH_BFP; }
+inline int fdtype(const bfp_hierarchy* h) { return h->o.arith == BFP_ARITH_BF16 ? FLT_BF16 : FLT_F32; }
 
 inline double pscale(int nd) { return nd == 2 ? 4.0 : 8.0; }
 
@@ -522,7 +615,69 @@ int32_t ir_update(double* x, const bfp_vec* y, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
+// ---- float baselines: the same V(nu1, nu2) schedule on float vectors ----
+
+int32_t flt_vcycle_rec(bfp_hierarchy* h, int k, const flt_vec* r, const flt_vec* bufA, const flt_vec* bufB,
+                       flt_vec* res, cudaStream_t s) {
+  Level& L = h->lv[k];
+  const bool coarsest = (k + 1 == (int)h->lv.size());
+  const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
+  const int writes = coarsest ? nu1 : (nu1 + 1 + h->o.nu2);
+  const flt_vec* curb = (writes % 2 == 1) ? bufA : bufB;   // the last write lands in bufA
+  const flt_vec* othb = (curb == bufA) ? bufB : bufA;
+  TRY(flt_jacobi_impl(&h->A, nullptr, r, curb, s));
+  for (int i = 1; i < nu1; ++i) {
+    TRY(flt_jacobi_impl(&h->A, curb, r, othb, s));
+    std::swap(curb, othb);
+  }
+  if (!coarsest) {
+    Level& C = h->lv[k + 1];
+    TRY(flt_residual_impl(&h->A, curb, r, &L.frv, s));        // r_v = A'y - r
+    TRY(flt_restrict_impl(&L.frv, &C.fr, s));
+    flt_vec d;
+    TRY(flt_vcycle_rec(h, k + 1, &C.fr, &C.fya, &C.fyb, &d, s));
+    TRY(flt_prolong_impl(&d, curb, othb, s));                 // y - P d
+    std::swap(curb, othb);
+    for (int i = 0; i < h->o.nu2; ++i) {
+      TRY(flt_jacobi_impl(&h->A, curb, r, othb, s));
+      std::swap(curb, othb);
+    }
+  }
+  *res = *curb;
+  return BFP_OK;
+}
+
+int32_t flt_ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double* x, cudaStream_t s) {
+  Level& L = h->lv[k];
+  const int nd = h->o.ndim;
+  const Grid g = grid_of(nd, L.n);
+  const double cdiag = (2.0 * nd) / pscale(nd), cnb = -1.0 / pscale(nd);
+  const FVOut ro = fvout(&L.fr);
+  const unsigned gr = grid_for(L.fr.ld * g.ny * g.nz, 256);
+  const bool bf = L.fr.dtype == FLT_BF16;
+#define BFP_FIR(ND)                                                                             \
+  do {                                                                                          \
+    if (bf) k_fir_residual<ND, uint16_t><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, ro);   \
+    else k_fir_residual<ND, float><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, ro);         \
+  } while (0)
+  if (nd == 2) BFP_FIR(2);
+  else BFP_FIR(3);
+#undef BFP_FIR
+  note_launches(1);
+  const flt_vec* A = (k == 0) ? &h->fy0 : &L.fya;
+  flt_vec y;
+  TRY(flt_vcycle_rec(h, k, &L.fr, A, &L.fyb, &y, s));
+  const int64_t rows = y.n[1] * y.n[2];
+  const int64_t rblocks = (rows + kUpdRows - 1) / kUpdRows;
+  const dim3 gu((unsigned)((y.n[0] + 255) / 256), (unsigned)(rblocks < 65535 ? rblocks : 65535));
+  if (bf) k_fir_update<uint16_t><<<gu, 256, 0, s>>>(x, fvin(&y));
+  else k_fir_update<float><<<gu, 256, 0, s>>>(x, fvin(&y));
+  note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
 int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double* x, cudaStream_t s) {
+  if (is_float(h)) return flt_ir_step(h, k, b, bscale, x, s);
   Level& L = h->lv[k];
   if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;   // every call-site meta of this step
   PrezeroedScope pz;
@@ -561,6 +716,7 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
   o->use_tmp = 1;
   o->use_graph = 1;
   o->coarse_onchip = 63;
+  o->arith = BFP_ARITH_BFP;
   return BFP_OK;
 }
 
@@ -577,6 +733,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if ((o->ndim != 2 && o->ndim != 3) || o->w < 1 || o->w > 32) return BFP_ERR_ARG;
   if (o->nu1 < 1 || o->nu2 < 0 || o->coarse_sweeps < 1 || o->n_fmg < 1) return BFP_ERR_ARG;
   if (o->mode != BFP_QCOMP && o->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
+  if (o->arith != BFP_ARITH_BFP && o->arith != BFP_ARITH_FP32 && o->arith != BFP_ARITH_BF16) return BFP_ERR_ARG;
   // n = 2^J - 1 with J >= 2
   if (o->n < 3 || ((o->n + 1) & o->n) != 0) return BFP_ERR_SHAPE;
   bfp_hierarchy* h = new (std::nothrow) bfp_hierarchy();
@@ -592,12 +749,19 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   }
   const int nd = o->ndim;
   bool ok = true;
+  const bool flt = is_float(h);
   for (size_t k = 0; k < h->lv.size() && ok; ++k) {
     Level& L = h->lv[k];
-    ok = make_vec(h, L.r, nd, L.n, o->w) && make_vec(h, L.ya, nd, L.n, o->w) && make_vec(h, L.yb, nd, L.n, o->w) &&
-         make_vec(h, L.rv, nd, L.n, o->w);
+    if (flt) {
+      const int dt = fdtype(h);
+      ok = make_fvec(h, L.fr, nd, L.n, dt) && make_fvec(h, L.fya, nd, L.n, dt) && make_fvec(h, L.fyb, nd, L.n, dt) &&
+           make_fvec(h, L.frv, nd, L.n, dt);
+    } else {
+      ok = make_vec(h, L.r, nd, L.n, o->w) && make_vec(h, L.ya, nd, L.n, o->w) &&
+           make_vec(h, L.yb, nd, L.n, o->w) && make_vec(h, L.rv, nd, L.n, o->w);
+    }
     const int64_t pts = L.n * L.n * (nd == 3 ? L.n : 1);
-    if (ok && o->use_tmp) {
+    if (ok && o->use_tmp && !flt) {
       L.tmp = dalloc(h, (size_t)(L.r.n[1] * L.r.n[2] * L.r.ld) * 4);
       ok = L.tmp != nullptr;
     }
@@ -607,7 +771,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
       ok = L.b && L.x;
     }
   }
-  ok = ok && make_vec(h, h->y0, nd, o->n, o->w);
+  ok = ok && (flt ? make_fvec(h, h->fy0, nd, o->n, fdtype(h)) : make_vec(h, h->y0, nd, o->n, o->w));
   if (ok) {
     size_t words = 0;
     for (size_t k = 0; k < h->lv.size(); ++k) {
@@ -625,7 +789,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
     if (ok) cudaMemset(h->arena, 0, words * sizeof(int64_t));
   }
   h->kc = (int)h->lv.size();
-  if (ok && o->coarse_onchip) {
+  if (ok && o->coarse_onchip && !flt) {
     int32_t crc = coarse_setup(h);
     if (crc) { bfp_hierarchy_destroy(h); return crc; }
   }
@@ -660,7 +824,7 @@ int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream) {
 }
 
 int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_stream stream) {
-  if (!h || !r || !y) return BFP_ERR_ARG;
+  if (!h || !r || !y || is_float(h)) return BFP_ERR_ARG;
   int32_t rc;
   if ((rc = check_vec(r)) || (rc = check_vec(y))) return rc;
   const Level& L = h->lv[0];
@@ -734,13 +898,27 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
     if (k == nl - 1) {
       if (cudaMemsetAsync(xk, 0, tot * sizeof(double), s) != cudaSuccess) return BFP_ERR_CUDA;
     } else {
-      // x_k = P x_{k+1} at width w (Alg. fmg interpolation line, qspmv)
       Level& Cc = h->lv[k + 1];
-      TRY(bfp_from_f64(Cc.x, &Cc.ya, s));
-      Q q = make_q(h, L);
-      bfp_vec* xf = (k == 0) ? &h->y0 : &L.ya;
-      TRY(bfp_prolong(&Cc.ya, nullptr, xf, &q.q, &q.st, s));
-      TRY(bfp_to_f64(xf, xk, s));
+      if (is_float(h)) {
+        // float baselines: x_k = P x_{k+1} in the vectors' format
+        const flt_vec* xf = (k == 0) ? &h->fy0 : &L.fya;
+        const bool bf = xf->dtype == FLT_BF16;
+        const unsigned g1 = grid_for(Cc.fya.ld * Cc.fya.n[1] * Cc.fya.n[2], 256);
+        if (bf) k_f64_to_flt<uint16_t><<<g1, 256, 0, s>>>(Cc.x, fvout(&Cc.fya));
+        else k_f64_to_flt<float><<<g1, 256, 0, s>>>(Cc.x, fvout(&Cc.fya));
+        TRY(flt_prolong_impl(&Cc.fya, nullptr, xf, s));
+        const unsigned g2 = grid_for(tot, 256);
+        if (bf) k_flt_to_f64<uint16_t><<<g2, 256, 0, s>>>(fvin(xf), xk);
+        else k_flt_to_f64<float><<<g2, 256, 0, s>>>(fvin(xf), xk);
+        note_launches(2);
+      } else {
+        // x_k = P x_{k+1} at width w (Alg. fmg interpolation line, qspmv)
+        TRY(bfp_from_f64(Cc.x, &Cc.ya, s));
+        Q q = make_q(h, L);
+        bfp_vec* xf = (k == 0) ? &h->y0 : &L.ya;
+        TRY(bfp_prolong(&Cc.ya, nullptr, xf, &q.q, &q.st, s));
+        TRY(bfp_to_f64(xf, xk, s));
+      }
     }
     const double* bk = (k == 0) ? f : L.b;
     const double sc = (k == 0) ? bs0 : 1.0;
@@ -750,11 +928,24 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
 }
 
 int32_t bfp_ir_residual(bfp_hierarchy* h, const double* f, const double* x, const bfp_vec* r, bfp_stream stream) {
-  if (!h || !f || !x || !r) return BFP_ERR_ARG;
+  if (!h || !f || !x || !r || is_float(h)) return BFP_ERR_ARG;
   int32_t rc;
   if ((rc = check_vec(r))) return rc;
   if (!same_shape(r, &h->lv[0].r)) return BFP_ERR_SHAPE;
   return ir_residual_q(h, 0, f, bscale_of(h->o.ndim, h->o.n), x, r, as_stream(stream));
+}
+
+int32_t flt_vcycle(bfp_hierarchy* h, const flt_vec* r, const flt_vec* y, bfp_stream stream) {
+  if (!h || !r || !y || !is_float(h)) return BFP_ERR_ARG;
+  int32_t rc;
+  if ((rc = check_fvec(r)) || (rc = check_fvec(y))) return rc;
+  const Level& L = h->lv[0];
+  if (!same_fshape(r, &L.fr) || !same_fshape(y, &L.fr) || r->dtype != fdtype(h) || y->dtype != fdtype(h))
+    return BFP_ERR_SHAPE;
+  if (foverlaps(r, y)) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  flt_vec res;
+  return flt_vcycle_rec(h, 0, r, y, &h->fy0, &res, s);   // the result lands in y (bufA)
 }
 
 int32_t bfp_ir_update(double* x, const bfp_vec* y, bfp_stream stream) {
