@@ -168,11 +168,16 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const uint32_t t = (uint32_t)fq.t;
   // |Z| <= 2^zb from the msb bounds of the two groups
   const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
-  const bool fast = fq.ok && fq.t < 32 && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr;
+  // fast: Z exact in int64 (the plan's fast regime); fold: the group shifts folded into 32-bit
+  // coefficients and t < 32, so Z is three mad.wide and the result one funnel shift (else
+  // Z = (H << dh) + (L << dl) from the plain coefficients and the result Z >> t)
+  const bool fast = fq.ok;
+  const bool fold = cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr && fq.t < 32;
+  const uint32_t dh = (uint32_t)fq.dh, dl = (uint32_t)fq.dl;
   // saturation test on the 32-bit results when Z >> t is exact in int32, else on Z
   const bool v32 = zb - (int)fq.t <= 30;
-  const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << t);
-  const uint64_t zrange = (uint64_t)(((uint64_t)1 << (fq.w - 1 + t)) * 2 - 1);
+  const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << (t & 63));   // used only when t < 32
+  const uint64_t zrange = (uint64_t)(((uint64_t)1 << ((fq.w - 1 + t) & 63)) * 2 - 1);
   const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
   const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
   const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
@@ -234,8 +239,8 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
   } else if (j0 < j1) {
     // the row walk, instantiated for both saturation tests (a uniform choice per CTA)
-    auto walk = [&](auto v32tag) {
-      constexpr bool V32 = decltype(v32tag)::value;
+    auto walk = [&](auto v32tag, auto foldtag) {
+      constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
   #pragma unroll
       for (int s = 0; s < kStages - 1; ++s) issue(s);
       // ring slots of stages i, i + 1, i + 2 and i + kStages - 1 (= i - 1 mod kStages)
@@ -271,15 +276,23 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
             for (int k = 0; k < 8; ++k) {
               int64_t Z;
               if (KIND == kJacobi0) {
-                Z = mulw(cr32, pk_get(rc, k));
+                Z = FOLD ? mulw(cr32, pk_get(rc, k)) : (int64_t)((uint64_t)mulw(mw, pk_get(rc, k)) << dh);
               } else {
                 const int32_t wk = k == 0 ? wv : yv[k - 1];
                 const int32_t ek = k == 7 ? ev : yv[k + 1];
                 const int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
-                Z = madw(cn32, ns, mulw(cy32, yv[k]));
-                if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
+                if (FOLD) {
+                  Z = madw(cn32, ns, mulw(cy32, yv[k]));
+                  if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
+                } else {
+                  const int64_t H = madw(nb, ns, mulw(c, yv[k]));
+                  const int64_t L = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)pk_get(rc, k)
+                                                                              : mulw(mw, pk_get(rc, k)));
+                  Z = (int64_t)((uint64_t)H << dh) + (int64_t)((uint64_t)L << dl);
+                }
               }
-              const int32_t v = (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), t);
+              const int32_t v = FOLD ? (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), t)
+                                   : (int32_t)(Z >> t);
               if (PASS1) {
                 if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
                 o[k] = (int32_t)((uint32_t)v << sh) >> sh;
@@ -327,8 +340,13 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
       }
       cp_wait<0>();
     };
-    if (v32) walk(std::true_type{});
-    else walk(std::false_type{});
+    if (fold) {
+      if (v32) walk(std::true_type{}, std::true_type{});
+      else walk(std::false_type{}, std::true_type{});
+    } else {
+      if (v32) walk(std::true_type{}, std::false_type{});
+      else walk(std::false_type{}, std::false_type{});
+    }
     // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = j0 + __ffs(m) - 1;

@@ -51,6 +51,8 @@ __device__ __noinline__ void slow_hl8(const int32_t (&H)[8], const int32_t (&L)[
 // Uniform per-CTA constants of the register path: Z = kh H + kl L, v = Z >> t.
 struct EmitC {
   bool fast;          // register path usable
+  bool fold;          // Z = kh H + kl L with 32-bit kh, kl (else (H << dh) + (L << dl))
+  uint32_t dh, dl;
   bool v32;           // |Z| < 2^(31 + t): saturation tested on the 32-bit results
   int32_t kh, kl;
   uint32_t t;
@@ -65,7 +67,11 @@ __device__ __forceinline__ EmitC make_emit(const Fast& fq, const QDesc& q, int32
   const bool dh_ok = fq.dh <= 30, dl_ok = fq.dl <= 30;
   e.kh = dh_ok ? hsign * (int32_t)(1u << (fq.dh & 31)) : 0;
   e.kl = dl_ok ? (int32_t)(1u << (fq.dl & 31)) : 0;
-  e.fast = fq.ok && fq.t < 32 && dh_ok && dl_ok && fq.w <= 32;
+  e.fast = fq.ok && fq.w <= 32;
+  e.fold = dh_ok && dl_ok && fq.t < 32;
+  e.dh = (uint32_t)fq.dh;
+  e.dl = (uint32_t)fq.dl;
+  e.kh = e.fold ? e.kh : hsign;   // unfolded: H carries its sign, Z = (hsign H << dh) + (L << dl)
   e.t = (uint32_t)fq.t;
   const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
   e.v32 = zb - fq.t <= 30;
@@ -80,7 +86,7 @@ __device__ __forceinline__ EmitC make_emit(const Fast& fq, const QDesc& q, int32
 
 // One lane's 8 outputs on the register path; returns true when the warp must
 // recompute the row on the general path (nnqcomp saturation, or no fast path).
-template <bool PASS1, bool V32>
+template <bool PASS1, bool V32, bool FOLD>
 __device__ __forceinline__ bool emit8(const EmitC& e, const Fast& fq, const int32_t (&H)[8], const int32_t (&L)[8],
                                       bool two, int nvalid, bool partial, const VOut& out, int32_t* tmp, int64_t row,
                                       int64_t c0, uint64_t& ormag, uint32_t& vmax, uint32_t& vmin) {
@@ -88,8 +94,15 @@ __device__ __forceinline__ bool emit8(const EmitC& e, const Fast& fq, const int3
   bool ovf = false;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int64_t Z = two ? madw(e.kl, L[k], mulw(e.kh, H[k])) : mulw(e.kh, H[k]);
-    const int32_t v = (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), e.t);
+    int64_t Z;
+    if (FOLD) {
+      Z = two ? madw(e.kl, L[k], mulw(e.kh, H[k])) : mulw(e.kh, H[k]);
+    } else {
+      Z = (int64_t)((uint64_t)(int64_t)(e.kh * H[k]) << e.dh);
+      if (two) Z += (int64_t)((uint64_t)(int64_t)L[k] << e.dl);
+    }
+    const int32_t v = FOLD ? (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), e.t)
+                           : (int32_t)(Z >> e.t);
     if (PASS1) {
       if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
       o[k] = (int32_t)((uint32_t)v << e.sh) >> e.sh;
@@ -265,8 +278,8 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const VIn f, const QDes
     for (int J = J0; J < J1; ++J)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, J, c0, red);
   } else if (J0 < J1) {
-    auto walk = [&](auto v32tag) {
-      constexpr bool V32 = decltype(v32tag)::value;
+    auto walk = [&](auto v32tag, auto foldtag) {
+      constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
       // prologue: fine rows 2 J0 .. 2 J0 + 5 in three groups of two
 #pragma unroll
       for (int g = 0; g < 3; ++g) {
@@ -295,15 +308,20 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const VIn f, const QDes
         if (act) {
           bool redo = !ec.fast;
           if (ec.fast)   // one exact group: the L argument is not read
-            redo = emit8<PASS1, V32>(ec, fq, H, H, false, nvalid, partial, out, tmp, J, c0, ormag, vmax, vmin);
+            redo = emit8<PASS1, V32, FOLD>(ec, fq, H, H, false, nvalid, partial, out, tmp, J, c0, ormag, vmax, vmin);
           if (redo) redo_rows |= 1u << i;
           any = any || nvalid > 0;
         }
       }
       cp_wait<0>();
     };
-    if (ec.v32) walk(std::true_type{});
-    else walk(std::false_type{});
+    if (ec.fold) {
+      if (ec.v32) walk(std::true_type{}, std::true_type{});
+      else walk(std::false_type{}, std::true_type{});
+    } else {
+      if (ec.v32) walk(std::true_type{}, std::false_type{});
+      else walk(std::false_type{}, std::false_type{});
+    }
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int J = J0 + __ffs(m) - 1;
       if (act) restrict_slow<PASS1>(f, p, out, tmp, J, c0, red);
@@ -431,8 +449,8 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
     for (int j = 2 * P0; j < 2 * P1 && j < ny; ++j)
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
   } else if (P0 < P1) {
-    auto walk = [&](auto v32tag) {
-      constexpr bool V32 = decltype(v32tag)::value;
+    auto walk = [&](auto v32tag, auto foldtag) {
+      constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
       issue(0, false);                           // coarse row P0 - 1 only
       issue(1, true);
       issue(2, true);
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
           if (act) {
             bool redo = !ec.fast;
             if (ec.fast)
-              redo = emit8<PASS1, V32>(ec, fq, H, L, CORR, nvalid, partial, out, tmp, j, c0, ormag, vmax, vmin);
+              redo = emit8<PASS1, V32, FOLD>(ec, fq, H, L, CORR, nvalid, partial, out, tmp, j, c0, ormag, vmax, vmin);
             if (redo) redo_rows |= 1u << (2 * i + h);
             any = any || nvalid > 0;
           }
@@ -476,8 +494,13 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
       }
       cp_wait<0>();
     };
-    if (ec.v32) walk(std::true_type{});
-    else walk(std::false_type{});
+    if (ec.fold) {
+      if (ec.v32) walk(std::true_type{}, std::true_type{});
+      else walk(std::false_type{}, std::true_type{});
+    } else {
+      if (ec.v32) walk(std::true_type{}, std::false_type{});
+      else walk(std::false_type{}, std::false_type{});
+    }
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = 2 * P0 + __ffs(m) - 1;
       if (act) prolong_slow<CORR, PASS1>(d, y, p, out, tmp, j, c0, red);
