@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BFP V-cycle GDOF/s (IR-V steps, 2D Poisson 4095^2, w=16)"
-JACOBI_TRAFFIC = None   # bytes per launch of the 4095^2 Jacobi sweep (ncu dram__bytes read + write)
+JACOBI_TRAFFIC = 97467904   # bytes per launch of the 4095^2 Jacobi sweep (ncu dram__bytes read + write)
 UNIT = "GDOF/s"
 
 
