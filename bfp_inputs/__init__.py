@@ -57,3 +57,19 @@ def random_mantissas(shape, w: int, seed: int, dist: str = "uniform") -> np.ndar
 
 def random_exponent(seed: int, lo: int = -40, hi: int = 10) -> int:
     return int(np.random.default_rng(seed).integers(lo, hi + 1))
+
+
+def batch_sizes(count: int = 256, seed: int = 3, sides=(127, 255, 511, 1023)) -> list:
+    """Grid sides of a batch of independent instances, drawn uniformly from `sides`."""
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.choice(np.asarray(sides), size=count)]
+
+
+def smoothed_random_rhs(n: int, seed: int, sweeps: int = 4) -> np.ndarray:
+    """A seeded n x n right-hand side: uniform in [-1, 1], then `sweeps` passes of
+    f <- f/2 + (W + E + S + N)/8 with zeros outside (rough but not white noise)."""
+    f = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, n))
+    for _ in range(sweeps):
+        p = np.pad(f, 1)
+        f = 0.5 * f + 0.125 * (p[1:-1, :-2] + p[1:-1, 2:] + p[:-2, 1:-1] + p[2:, 1:-1])
+    return f

@@ -242,6 +242,8 @@ typedef struct {
                             kernel; N = 127 for 1, N = min(value, 127) for values > 1, 0: off
                             (default 63) */
   int32_t arith;         /* bfp_arith: the V-cycle's vectors and arithmetic (default BFP) */
+  int32_t tile_rows;     /* rows per warp strip of the row-walking kernels for this solver's
+                            ops (0: the launchers' size heuristic); set by an autotuner */
 } bfp_solver_opts;
 
 /* BFP_ARITH_BFP is the paper's method; FP32 and BF16 (storage, with FP32
@@ -310,6 +312,26 @@ typedef struct {
  * read the residual norm.  Returns BFP_ERR_NOCONV when max_iter is reached. */
 int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts* o,
                  bfp_ir_report* rep, bfp_stream stream);
+
+/* ---- batched solves (many independent instances, one graph launch) ------------ */
+/* count independent hierarchies (opts[i]: size, width, mode, schedule of
+ * instance i), solved together: bfp_batch_solve captures, for every instance
+ * on a branch of its own, [FMG] + ir_steps[i] IR-V steps into one CUDA graph
+ * (re-captured only when the arguments change) and launches it once on
+ * stream (which must not be the legacy default stream).  f[i], x[i]: device
+ * dense doubles of instance i (x[i] is the initial iterate when fmg == 0).
+ * bfp_batch_times waits for the last launch and writes, per instance, the ms
+ * from the launch start to the end of that instance's branch. */
+typedef struct bfp_batch bfp_batch;
+int32_t bfp_batch_create(const bfp_solver_opts* opts, int32_t count, bfp_batch** out);
+int32_t bfp_batch_solve(bfp_batch* b, const double* const* f, double* const* x, const int32_t* ir_steps,
+                        int32_t fmg, bfp_stream stream);
+/* The same work for instance i alone, as its own graph launch (the comparison
+ * the batched launch is measured against). */
+int32_t bfp_batch_solve_one(bfp_batch* b, int32_t i, const double* f, double* x, int32_t ir_steps, int32_t fmg,
+                            bfp_stream stream);
+int32_t bfp_batch_times(bfp_batch* b, float* ms);
+void bfp_batch_destroy(bfp_batch* b);
 
 /* ---- float baselines (not in the paper) ------------------------------------------ */
 /* FP32 and BF16-storage / FP32-arithmetic versions of the V-cycle ops, for the

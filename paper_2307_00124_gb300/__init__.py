@@ -65,7 +65,8 @@ class bfp_solver_opts(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("w", C.c_int32), ("n", C.c_int64), ("mode", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
                 ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
-                ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32), ("arith", C.c_int32)]
+                ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32), ("arith", C.c_int32),
+                ("tile_rows", C.c_int32)]
 
 
 class flt_vec(C.Structure):
@@ -124,6 +125,13 @@ _sig = {
     "flt_restrict": (C.c_int32, [P(flt_vec), P(flt_vec), C.c_void_p]),
     "flt_prolong": (C.c_int32, [P(flt_vec), P(flt_vec), P(flt_vec), C.c_void_p]),
     "flt_vcycle": (C.c_int32, [C.c_void_p, P(flt_vec), P(flt_vec), C.c_void_p]),
+    "bfp_batch_create": (C.c_int32, [P(bfp_solver_opts), C.c_int32, P(C.c_void_p)]),
+    "bfp_batch_solve": (C.c_int32, [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(C.c_int32), C.c_int32,
+                                    C.c_void_p]),
+    "bfp_batch_times": (C.c_int32, [C.c_void_p, P(C.c_float)]),
+    "bfp_batch_solve_one": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                        C.c_void_p]),
+    "bfp_batch_destroy": (None, [C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -467,6 +475,47 @@ class Hierarchy:
         if rc not in (0, -7):
             raise BFPError(rc, "ir_solve")
         return rep
+
+
+class Batch:
+    """Owns a bfp_batch: independent hierarchies solved together in one graph launch."""
+
+    def __init__(self, opts_list):
+        n = len(opts_list)
+        arr = (bfp_solver_opts * n)(*opts_list)
+        b = C.c_void_p()
+        _check(_lib.bfp_batch_create(arr, n, C.byref(b)), "bfp_batch_create")
+        self.b, self.count = b, n
+
+    def close(self):
+        if self.b:
+            _lib.bfp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, fs, xs, ir_steps, fmg=True, stream=None):
+        """[FMG] + ir_steps[i] IR-V steps for every instance, one graph launch on stream."""
+        n = self.count
+        fa = (C.c_void_p * n)(*[f.data_ptr() for f in fs])
+        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ka = (C.c_int32 * n)(*[int(k) for k in ir_steps])
+        _check(_lib.bfp_batch_solve(self.b, fa, xa, ka, int(bool(fmg)), _stream(stream)), "bfp_batch_solve")
+
+    def solve_one(self, i, f, x, ir_steps, fmg=True, stream=None):
+        """Instance i alone, as its own graph launch."""
+        _check(_lib.bfp_batch_solve_one(self.b, int(i), C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()),
+                                        int(ir_steps), int(bool(fmg)), _stream(stream)), "bfp_batch_solve_one")
+
+    def times(self):
+        """ms from the launch start to the end of each instance's branch (waits for the launch)."""
+        ms = (C.c_float * self.count)()
+        _check(_lib.bfp_batch_times(self.b, ms), "bfp_batch_times")
+        return [float(v) for v in ms]
 
 
 def bfp_ir_update(x, y, stream=None):

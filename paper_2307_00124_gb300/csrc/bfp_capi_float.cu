@@ -38,7 +38,7 @@ int32_t fstar(const bfp_stencil* A, const flt_vec* y, const flt_vec* r, const fl
   if (out->ndim == 2) {
     const int64_t ny = out->n[1];
     if (ny == 0) return BFP_OK;
-    const int rs = ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2));
+    const int rs = pick_rows(ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2)), 64);
     const dim3 g((unsigned)((out->ld + 255) / 256), (unsigned)((ny + 4 * rs - 1) / (4 * rs)));
     if (bf) k_fstar2d<uint16_t, KIND><<<g, 128, 0, s>>>(yv, rv, c, nb, om, o, rs);
     else k_fstar2d<float, KIND><<<g, 128, 0, s>>>(yv, rv, c, nb, om, o, rs);

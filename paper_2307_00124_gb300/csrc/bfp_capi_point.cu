@@ -14,6 +14,10 @@ bool& prezeroed() {
   static thread_local bool flag = false;
   return flag;
 }
+int& tile_rows_override() {
+  static thread_local int rows = 0;
+  return rows;
+}
 }  // namespace bfp
 
 namespace {

@@ -15,7 +15,9 @@ bool coarse_of(const bfp_vec* f, const bfp_vec* c) {
 }
 
 // rows per warp strip (<= 16: the kernels keep a per-strip mask of general-path rows)
-int rows_per_warp(int64_t rows) { return rows >= 1024 ? 8 : (rows >= 256 ? 4 : (rows >= 64 ? 2 : 1)); }
+int rows_per_warp(int64_t rows) {
+  return pick_rows(rows >= 1024 ? 8 : (rows >= 256 ? 4 : (rows >= 64 ? 2 : 1)), 16);
+}
 
 int32_t launch_checks(const QDesc& d) {
   if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;

@@ -25,6 +25,20 @@ struct PrezeroedScope {
   ~PrezeroedScope() { prezeroed() = saved; }
 };
 
+// Rows per warp strip of the row-walking kernels: the launchers' size
+// heuristic unless a solver with a tuned schedule set an override for the ops
+// it enqueues (thread-local, like PrezeroedScope).
+int& tile_rows_override();
+struct TileScope {
+  int saved;
+  explicit TileScope(int rows) : saved(tile_rows_override()) { if (rows > 0) tile_rows_override() = rows; }
+  ~TileScope() { tile_rows_override() = saved; }
+};
+inline int pick_rows(int heuristic, int cap) {
+  const int v = tile_rows_override();
+  return v > 0 ? (v < cap ? v : cap) : heuristic;
+}
+
 inline cudaError_t zero_accumulators(int64_t* meta_out, cudaStream_t s) {
   if (prezeroed()) return cudaSuccess;
   return cudaMemsetAsync(meta_out + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s);

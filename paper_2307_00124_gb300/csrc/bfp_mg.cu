@@ -403,6 +403,18 @@ int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vecto
   return BFP_OK;
 }
 
+bool allow_coarse_smem(bool is32, int optin) {
+  cudaFuncAttributes fa;
+  const cudaError_t e0 = is32 ? cudaFuncGetAttributes(&fa, k_coarse_vcycle<int32_t>)
+                              : cudaFuncGetAttributes(&fa, k_coarse_vcycle<int16_t>);
+  if (e0 != cudaSuccess) return false;
+  const int dyn = optin - (int)fa.sharedSizeBytes;
+  const cudaError_t e1 =
+      is32 ? cudaFuncSetAttribute(k_coarse_vcycle<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)
+           : cudaFuncSetAttribute(k_coarse_vcycle<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  return e1 == cudaSuccess;
+}
+
 // Chooses kc and uploads the op lists; kc = nlevels disables the on-chip path.
 int32_t coarse_setup(bfp_hierarchy* h) {
   const int nl = (int)h->lv.size();
@@ -463,12 +475,9 @@ int32_t coarse_setup(bfp_hierarchy* h) {
     h->rbuf.push_back(lb[k - h->kc].r);
     h->ybuf.push_back(res);
   }
-  const cudaError_t ae =
-      h->o.w > 16
-          ? cudaFuncSetAttribute(k_coarse_vcycle<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_bytes)
-          : cudaFuncSetAttribute(k_coarse_vcycle<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_bytes);
-  if (ae != cudaSuccess) return BFP_ERR_CUDA;
-  return BFP_OK;
+  // the attribute is per kernel, shared by every hierarchy: allow the device maximum once rather than
+  // this hierarchy's size (a later hierarchy with a smaller on-chip part must not shrink it)
+  return allow_coarse_smem(h->o.w > 16, optin) ? BFP_OK : BFP_ERR_CUDA;
 }
 
 int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* out, cudaStream_t s) {
@@ -590,7 +599,7 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
     a.tmp = (h->lv[k].tmp && a.w_tmp <= 32) ? (int32_t*)h->lv[k].tmp : nullptr;
     a.gamma_mu = h->ir_gam + k;
     a.stats = h->stats;
-    const int rs = g.ny >= 2048 ? 16 : (g.ny >= 1024 ? 8 : (g.ny >= 256 ? 4 : 2));
+    const int rs = pick_rows(g.ny >= 2048 ? 16 : (g.ny >= 1024 ? 8 : (g.ny >= 256 ? 4 : 2)), 64);
     const dim3 grid2((unsigned)((g.nx + kIrCols - 1) / kIrCols),
                      (unsigned)((g.ny + (int64_t)kIrWarps * rs - 1) / ((int64_t)kIrWarps * rs)));
     k_ir2d<true><<<grid2, 128, 0, s>>>(a, rs);
@@ -717,6 +726,7 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
   o->use_graph = 1;
   o->coarse_onchip = 63;
   o->arith = BFP_ARITH_BFP;
+  o->tile_rows = 0;
   return BFP_OK;
 }
 
@@ -734,6 +744,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if (o->nu1 < 1 || o->nu2 < 0 || o->coarse_sweeps < 1 || o->n_fmg < 1) return BFP_ERR_ARG;
   if (o->mode != BFP_QCOMP && o->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
   if (o->arith != BFP_ARITH_BFP && o->arith != BFP_ARITH_FP32 && o->arith != BFP_ARITH_BF16) return BFP_ERR_ARG;
+  if (o->tile_rows < 0 || o->tile_rows > 64) return BFP_ERR_ARG;
   // n = 2^J - 1 with J >= 2
   if (o->n < 3 || ((o->n + 1) & o->n) != 0) return BFP_ERR_SHAPE;
   bfp_hierarchy* h = new (std::nothrow) bfp_hierarchy();
@@ -834,6 +845,7 @@ int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_str
   cudaStream_t s = as_stream(stream);
   if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;
   PrezeroedScope pz;
+  TileScope ts(h->o.tile_rows);
   bfp_vec res;
   TRY(vcycle_rec(h, 0, r, y, &h->y0, &res, s));
   // the result's mantissas are in y; its exponent and norm are in a call-site slot
@@ -843,6 +855,7 @@ int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_str
 }
 
 static int32_t ir_iterate_direct(bfp_hierarchy* h, const double* f, double* x, int32_t k, cudaStream_t s) {
+  TileScope ts(h->o.tile_rows);
   const double bs = bscale_of(h->o.ndim, h->o.n);
   for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));
   return BFP_OK;
@@ -875,6 +888,7 @@ int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k, 
 int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream) {
   if (!h || !f || !x) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
+  TileScope ts(h->o.tile_rows);
   const int nd = h->o.ndim;
   const int nl = (int)h->lv.size();
   const double rscale = nd == 2 ? 0.25 : 0.0625;   // R~ = P^T (2D), P^T/2 (3D): weights prod(2-|d|) * 2^e_R
@@ -944,6 +958,7 @@ int32_t flt_vcycle(bfp_hierarchy* h, const flt_vec* r, const flt_vec* y, bfp_str
     return BFP_ERR_SHAPE;
   if (foverlaps(r, y)) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
+  TileScope ts(h->o.tile_rows);
   flt_vec res;
   return flt_vcycle_rec(h, 0, r, y, &h->fy0, &res, s);   // the result lands in y (bufA)
 }
@@ -959,6 +974,7 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
                  bfp_stream stream) {
   if (!h || !f || !x || !o || !rep) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
+  TileScope ts(h->o.tile_rows);
   std::memset(rep, 0, sizeof(*rep));
   if (o->fmg_start) TRY(bfp_fmg(h, f, x, s));
   const int nd = h->o.ndim;
@@ -984,6 +1000,170 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
     if (it >= o->max_iter) return BFP_ERR_NOCONV;
     TRY(ir_step(h, 0, f, bs, x, s));
   }
+}
+
+}  // extern "C"
+
+// ---- batched solve: many independent instances in one graph launch ----------------
+
+struct bfp_batch {
+  std::vector<bfp_hierarchy*> h;
+  std::vector<cudaStream_t> st;        // one capture branch per instance
+  std::vector<cudaEvent_t> join, tend;
+  cudaEvent_t fork = nullptr, tstart = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const double*> gf;       // the arguments the graph was captured with
+  std::vector<double*> gx;
+  std::vector<int32_t> gk;
+  int32_t gfmg = -1;
+  cudaStream_t gs = nullptr;
+  // per-instance graphs (one launch per instance)
+  struct One {
+    cudaGraphExec_t g = nullptr;
+    const double* f = nullptr;
+    double* x = nullptr;
+    int32_t k = -1, fmg = -1;
+    cudaStream_t s = nullptr;
+  };
+  std::vector<One> one;
+};
+
+namespace {
+
+// FMG (optional) then k IR-V steps of one instance on stream s (direct launches)
+int32_t instance_solve(bfp_hierarchy* h, const double* f, double* x, int32_t k, int32_t fmg, cudaStream_t s) {
+  TileScope ts(h->o.tile_rows);
+  if (fmg) TRY(bfp_fmg(h, f, x, s));
+  const double bs = bscale_of(h->o.ndim, h->o.n);
+  for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));
+  return BFP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bfp_batch_destroy(bfp_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& o : b->one)
+    if (o.g) cudaGraphExecDestroy(o.g);
+  for (bfp_hierarchy* h : b->h) bfp_hierarchy_destroy(h);
+  for (cudaStream_t s : b->st) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->tend) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->tstart) cudaEventDestroy(b->tstart);
+  delete b;
+}
+
+int32_t bfp_batch_create(const bfp_solver_opts* opts, int32_t count, bfp_batch** out) {
+  if (!opts || !out || count < 1) return BFP_ERR_ARG;
+  *out = nullptr;
+  bfp_batch* b = new (std::nothrow) bfp_batch();
+  if (!b) return BFP_ERR_ARG;
+  for (int32_t i = 0; i < count; ++i) {
+    bfp_hierarchy* h = nullptr;
+    const int32_t rc = bfp_hierarchy_create(&opts[i], &h);
+    if (rc) { bfp_batch_destroy(b); return rc; }
+    b->h.push_back(h);
+    cudaStream_t s = nullptr;
+    cudaEvent_t j = nullptr, t = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess || cudaEventCreate(&t) != cudaSuccess) {
+      if (s) cudaStreamDestroy(s);
+      if (j) cudaEventDestroy(j);
+      bfp_batch_destroy(b);
+      return BFP_ERR_CUDA;
+    }
+    b->st.push_back(s);
+    b->join.push_back(j);
+    b->tend.push_back(t);
+  }
+  b->one.resize(count);
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->tstart) != cudaSuccess) {
+    bfp_batch_destroy(b);
+    return BFP_ERR_CUDA;
+  }
+  *out = b;
+  return BFP_OK;
+}
+
+int32_t bfp_batch_solve(bfp_batch* b, const double* const* f, double* const* x, const int32_t* ir_steps, int32_t fmg,
+                        bfp_stream stream) {
+  if (!b || !f || !x || !ir_steps) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (s == nullptr) return BFP_ERR_ARG;   // capture needs a created stream
+  const size_t n = b->h.size();
+  for (size_t i = 0; i < n; ++i)
+    if (!f[i] || !x[i] || ir_steps[i] < 0) return BFP_ERR_ARG;
+  bool same = b->graph && b->gs == s && b->gfmg == fmg;
+  for (size_t i = 0; same && i < n; ++i) same = b->gf[i] == f[i] && b->gx[i] == x[i] && b->gk[i] == ir_steps[i];
+  if (!same) {
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return BFP_ERR_CUDA;
+    int32_t rc = BFP_OK;
+    if (cudaEventRecordWithFlags(b->tstart, s, cudaEventRecordExternal) != cudaSuccess ||
+        cudaEventRecord(b->fork, s) != cudaSuccess)
+      rc = BFP_ERR_CUDA;
+    for (size_t i = 0; rc == BFP_OK && i < n; ++i) {
+      if (cudaStreamWaitEvent(b->st[i], b->fork, 0) != cudaSuccess) { rc = BFP_ERR_CUDA; break; }
+      rc = instance_solve(b->h[i], f[i], x[i], ir_steps[i], fmg, b->st[i]);
+      if (rc) break;
+      if (cudaEventRecordWithFlags(b->tend[i], b->st[i], cudaEventRecordExternal) != cudaSuccess ||
+          cudaEventRecord(b->join[i], b->st[i]) != cudaSuccess || cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess)
+        rc = BFP_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (rc != BFP_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != BFP_OK ? rc : BFP_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { b->graph = nullptr; return BFP_ERR_CUDA; }
+    b->gf.assign(f, f + n);
+    b->gx.assign(x, x + n);
+    b->gk.assign(ir_steps, ir_steps + n);
+    b->gfmg = fmg;
+    b->gs = s;
+  }
+  return cudaGraphLaunch(b->graph, s) == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_batch_solve_one(bfp_batch* b, int32_t i, const double* f, double* x, int32_t ir_steps, int32_t fmg,
+                            bfp_stream stream) {
+  if (!b || i < 0 || i >= (int32_t)b->h.size() || !f || !x || ir_steps < 0) return BFP_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (s == nullptr) return BFP_ERR_ARG;
+  bfp_batch::One& o = b->one[i];
+  if (!o.g || o.f != f || o.x != x || o.k != ir_steps || o.fmg != fmg || o.s != s) {
+    if (o.g) { cudaGraphExecDestroy(o.g); o.g = nullptr; }
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return BFP_ERR_CUDA;
+    const int32_t rc = instance_solve(b->h[i], f, x, ir_steps, fmg, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (rc != BFP_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != BFP_OK ? rc : BFP_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&o.g, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { o.g = nullptr; return BFP_ERR_CUDA; }
+    o.f = f; o.x = x; o.k = ir_steps; o.fmg = fmg; o.s = s;
+  }
+  return cudaGraphLaunch(o.g, s) == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_batch_times(bfp_batch* b, float* ms) {
+  if (!b || !ms || !b->graph) return BFP_ERR_ARG;
+  for (size_t i = 0; i < b->h.size(); ++i) {
+    if (cudaEventSynchronize(b->tend[i]) != cudaSuccess) return BFP_ERR_CUDA;
+    if (cudaEventElapsedTime(&ms[i], b->tstart, b->tend[i]) != cudaSuccess) return BFP_ERR_CUDA;
+  }
+  return BFP_OK;
 }
 
 }  // extern "C"

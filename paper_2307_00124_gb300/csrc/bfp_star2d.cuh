@@ -248,7 +248,7 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const int32_t c = (int32_t)c64, nb = (int32_t)nb64, mw = (int32_t)mw64;   // checked < 2^31 by the caller
   const VOut o = vout(out);
   const int64_t ny = out->n[1];
-  const int rs = ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2));   // <= 32 (row masks of k_star2d16)
+  const int rs = pick_rows(ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2)), 32);   // <= 32: row masks
   const int64_t chunks = (out->ld + kStarCols - 1) / kStarCols;
   const int64_t strips = (ny + (int64_t)kStarWarps * rs - 1) / ((int64_t)kStarWarps * rs);
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
