@@ -72,6 +72,16 @@ __device__ __forceinline__ int64_t mulw(int32_t a, int32_t b) {
   asm("mul.wide.s32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
   return d;
 }
+// the same with 32-bit shared-state-space destination addresses
+__device__ __forceinline__ void cp16u(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp4u_if(bool p, uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q cp.async.ca.shared.global [%0], [%1], 4, %2;\n}\n" ::"r"(dst),
+      "l"(src), "r"(src_bytes), "r"((int)p)
+      : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -193,41 +203,39 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const int64_t ecol = lane == 0 ? c0 - 2 : c0 + 8;
   const bool eok = kUseY && (lane == 0 ? (c0 >= 2 && c0 - 1 < y.nx) : (lane == 31 && c0 + 8 < y.nx));
   const int eword = lane == 0 ? 3 : kRowWords - 4;
-  // the next stage to issue: y row jy at element offset oy, r row jy - 1 at offset orr
+  // the next stage to issue: y row jy at byte offset oy, r row jy - 1 at byte offset orr (rows
+  // outside the grid and lanes past the row are zero-filled)
   int jy = j0 - 1;
-  int64_t oy = kUseY ? (int64_t)jy * y.ld + c0 : 0, orr = kUseR ? (int64_t)(jy - 1) * r.ld + c0 : 0;
-  const int64_t edelta = ecol - c0;
+  int64_t oy = kUseY ? ((int64_t)jy * y.ld + c0) * 2 : 0, orr = kUseR ? ((int64_t)(jy - 1) * r.ld + c0) * 2 : 0;
+  const int64_t ystride = kUseY ? y.ld * 2 : 0, rstride = kUseR ? r.ld * 2 : 0;
+  const int64_t edelta = (ecol - c0) * 2;
   const bool edge_lane = lane == 0 || lane == 31;
+  const uint32_t ybytes = 16u, rbytes = 16u;
+  const char* yb = reinterpret_cast<const char*>(ybase);
+  const char* rb = reinterpret_cast<const char*>(rbase);
+  constexpr uint32_t kYRowBytes = kRowWords * 4, kRRowBytes = 32 * 16;
+  const uint32_t ydst = smem_u32(&S.y[0][4 + 4 * lane]), edst = smem_u32(&S.y[0][eword]);
+  const uint32_t rdst = smem_u32(&S.r[0][lane]);
   auto issue = [&](int slot) {
     if (kUseY) {
       const bool in = (unsigned)jy < (unsigned)nyin;
-      const bool ok = ycol && in;
-      cp16(&S.y[slot][4 + 4 * lane], ybase + (ok ? oy : 0), ok ? 16u : 0u);
+      const bool ok = in && ycol;
+      cp16u(ydst + (uint32_t)slot * kYRowBytes, yb + (ok ? oy : 0), ok ? ybytes : 0u);
       const bool ek = eok && in;
-      cp4_if(edge_lane, &S.y[slot][eword], ybase + (ek ? oy + edelta : 0), ek ? 4u : 0u);
-      oy += y.ld;
+      cp4u_if(edge_lane, edst + (uint32_t)slot * kYRowBytes, yb + (ek ? oy + edelta : 0), ek ? 4u : 0u);
+      oy += ystride;
     }
     if (kUseR) {
       const bool ok = rcol && (unsigned)(jy - 1) < (unsigned)nrin;
-      cp16(&S.r[slot][lane], rbase + (ok ? orr : 0), ok ? 16u : 0u);
-      orr += r.ld;
+      cp16u(rdst + (uint32_t)slot * kRRowBytes, rb + (ok ? orr : 0), ok ? rbytes : 0u);
+      orr += rstride;
     }
     ++jy;
     cp_commit();
   };
-
-  // the lane's columns at or beyond nx read as 0 (partial chunk only)
-  uint32_t cmask[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    cmask[i] = ((2 * i < nvalid) ? 0xffffu : 0u) | ((2 * i + 1 < nvalid) ? 0xffff0000u : 0u);
   auto rd = [&](const uint4& u) {
     Pk8 v;
     v.w[0] = u.x; v.w[1] = u.y; v.w[2] = u.z; v.w[3] = u.w;
-    if (partial) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) v.w[i] &= cmask[i];
-    }
     return v;
   };
 
@@ -258,6 +266,11 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
           yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
   #pragma unroll
           for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
+          if (partial) {   // padding columns may hold anything: the east neighbour of the last column is 0
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (k >= nvalid) yv[k] = 0;
+          }
           const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
           wv = row[7 + 8 * lane];                 // column c0 - 1
           ev = row[16 + 8 * lane];                // column c0 + 8
