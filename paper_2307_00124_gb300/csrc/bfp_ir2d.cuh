@@ -93,28 +93,42 @@ struct IrPlan {
   int32_t window, narrow, recompute;
 };
 
+// Pass 1: the window exponent from gamma = the previous residual's mu (0: none);
+// pass 2: e_out from mu* and the narrow / recompute decision of Alg. qcomp.
+__device__ __forceinline__ IrPlan ir_plan(const IrArgs& a, bool pass1) {
+  IrPlan p;
+  const int64_t g = pass1 ? *a.gamma_mu : a.meta[4];
+  p.window = (a.tmp != nullptr && g != 0) ? 1 : 0;
+  p.gam = g - (int64_t(1) << 40);              // msb value of gamma (encoded with an offset)
+  p.e_tmp = p.gam - a.w_tmp;
+  p.e_out = 0;
+  p.narrow = 0;
+  p.recompute = 1;
+  if (!pass1) {
+    const int64_t key = a.meta[kMetaMu];
+    const int64_t mu_abs = key > 0 ? key - kIrKeyOff : -1073;
+    p.e_out = mu_abs - a.w;
+    const bool ovf = p.gam < mu_abs, unf = (mu_abs - a.w) < (p.gam - a.w_tmp);
+    p.narrow = (p.window && !ovf && !unf) ? 1 : 0;
+    p.recompute = !p.narrow;
+  }
+  return p;
+}
+
+// after pass 2 (one thread): the result exponent, the next residual's gamma, the counters
+__device__ __forceinline__ void ir_finish(const IrArgs& a, const IrPlan& p) {
+  a.meta[0] = p.e_out;
+  *a.gamma_mu = p.e_out + a.w + (int64_t(1) << 40);   // gamma of the next IR residual
+  if (a.stats) {
+    atomicAdd((unsigned long long*)&a.stats[5], 1ull);
+    if (p.recompute) atomicAdd((unsigned long long*)&a.stats[6], 1ull);
+  }
+}
+
 template <bool PASS1>
 __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
   __shared__ IrPlan sp;
-  if (threadIdx.x == 0) {
-    IrPlan p;
-    const int64_t g = PASS1 ? *a.gamma_mu : a.meta[4];
-    p.window = (a.tmp != nullptr && g != 0) ? 1 : 0;
-    p.gam = g - (int64_t(1) << 40);              // msb value of gamma (encoded with an offset)
-    p.e_tmp = p.gam - a.w_tmp;
-    p.e_out = 0;
-    p.narrow = 0;
-    p.recompute = 1;
-    if (!PASS1) {
-      const int64_t key = a.meta[kMetaMu];
-      const int64_t mu_abs = key > 0 ? key - kIrKeyOff : -1073;
-      p.e_out = mu_abs - a.w;
-      const bool ovf = p.gam < mu_abs, unf = (mu_abs - a.w) < (p.gam - a.w_tmp);
-      p.narrow = (p.window && !ovf && !unf) ? 1 : 0;
-      p.recompute = !p.narrow;
-    }
-    sp = p;
-  }
+  if (threadIdx.x == 0) sp = ir_plan(a, PASS1);
   __syncthreads();
   const IrPlan& p = sp;
   if (PASS1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.meta[4] = *a.gamma_mu;
@@ -224,14 +238,7 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
   }
   if (bad) atomicOr((unsigned long long*)&a.meta[BFP_META_FLAGS], 1ull);
   block_commit(red, a.meta, nullptr, PASS1);
-  if (!PASS1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-    a.meta[0] = p.e_out;
-    *a.gamma_mu = p.e_out + a.w + (int64_t(1) << 40);   // gamma of the next IR residual
-    if (a.stats) {
-      atomicAdd((unsigned long long*)&a.stats[5], 1ull);
-      if (p.recompute) atomicAdd((unsigned long long*)&a.stats[6], 1ull);
-    }
-  }
+  if (!PASS1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ir_finish(a, p);
 }
 
 // x <- x + m 2^e (FP64 update of Alg. ir): a thread owns one column of

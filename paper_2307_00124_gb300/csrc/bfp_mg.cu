@@ -104,6 +104,69 @@ __global__ void __launch_bounds__(256) k_ir_residual(const double* __restrict__ 
   if (!PASS1 && blockIdx.x == 0 && threadIdx.x == 0) meta[0] = e_out;
 }
 
+// 3D IR residual with the Alg. qcomp window (as k_ir2d): pass 1 max msb + w_tmp window
+// from the previous residual's gamma, pass 2 narrows the window or recomputes.  The residual is
+// ir_res<3>'s sequence with the power-of-two scalings done on the exponent field (bit-identical).
+template <bool PASS1>
+__global__ void __launch_bounds__(256) k_ir3d(const IrArgs a, const Grid g) {
+  __shared__ IrPlan sp;
+  if (threadIdx.x == 0) sp = ir_plan(a, PASS1);
+  __syncthreads();
+  const IrPlan& p = sp;
+  if (PASS1 && blockIdx.x == 0 && threadIdx.x == 0) a.meta[4] = *a.gamma_mu;
+  const int64_t nvec = a.out.ld >> 3, rows = g.ny * g.nz, total = rows * nvec;
+  Red red = {0, 0, 0};
+  bool bad = false;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / nvec, c0 = (idx - row * nvec) << 3;
+    const int64_t j = row % g.ny, k = row / g.ny;
+    int32_t o[8];
+    if (!PASS1 && p.narrow) {
+      const int sh = (int)(p.e_out - p.e_tmp);
+      const int4* src = reinterpret_cast<const int4*>(a.tmp + row * a.out.ld + c0);
+      const int4 u0 = src[0], u1 = src[1];
+      const int32_t t[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        o[q] = c0 + q < g.nx ? (t[q] >> sh) : 0;
+        red.nrm = max(red.nrm, (long long)(o[q] < 0 ? -o[q] : o[q]));
+      }
+      st8(a.out, row, c0, o);
+      continue;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      o[q] = 0;
+      const int64_t i = c0 + q;
+      if (i >= g.nx) continue;
+      double s = __dadd_rn(at(a.x, g, i - 1, j, k), at(a.x, g, i + 1, j, k));
+      s = __dadd_rn(s, at(a.x, g, i, j - 1, k));
+      s = __dadd_rn(s, at(a.x, g, i, j + 1, k));
+      s = __dadd_rn(s, at(a.x, g, i, j, k - 1));
+      s = __dadd_rn(s, at(a.x, g, i, j, k + 1));
+      const int64_t xi = i + g.nx * (j + g.ny * k);
+      const double ax = __dadd_rn(__dmul_rn(a.cdiag, a.x[xi]), -scale_pow2(s, a.nbshift, -a.cnb));
+      const double r = __dsub_rn(scale_pow2(a.b[xi], a.bshift, a.bscale), ax);
+      int64_t M = 0, E = -1074;
+      if (!split_double(r, M, E)) { bad = true; continue; }
+      if (PASS1) {
+        const int64_t mv = M == 0 ? -1073 : msb64(M) + E;
+        red.key = max(red.key, (long long)(mv + kIrKeyOff));
+        if (p.window) a.tmp[row * a.out.ld + i] = wrap_bits((uint64_t)fshift(M, E - p.e_tmp), a.w_tmp);
+      } else {
+        const int64_t v = fshift(M, E - p.e_out);
+        o[q] = (int32_t)v;
+        red.nrm = max(red.nrm, (long long)(v < 0 ? -v : v));
+      }
+    }
+    if (!PASS1) st8(a.out, row, c0, o);
+  }
+  if (bad) atomicOr((unsigned long long*)&a.meta[BFP_META_FLAGS], 1ull);
+  block_commit(red, a.meta, nullptr, PASS1);
+  if (!PASS1 && blockIdx.x == 0 && threadIdx.x == 0) ir_finish(a, p);
+}
+
 // ||b' - A' x||_inf (for ir_solve's host-side stopping test)
 template <int ND>
 __global__ void __launch_bounds__(256) k_ir_resnorm(const double* __restrict__ b, double bscale,
@@ -585,28 +648,29 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
   const int64_t items = rows_of(r) * (r->ld / 8);
   const unsigned gr = grid_for(items, 256);
   if (zero_accumulators(r->meta, s) != cudaSuccess) return BFP_ERR_CUDA;
+  IrArgs a;
+  a.b = b; a.bscale = bscale; a.x = x; a.nx = g.nx; a.ny = g.ny; a.cdiag = cdiag; a.cnb = cnb;
+  int bsh = 0;
+  while (std::ldexp(1.0, -bsh) > bscale && bsh < 1100) ++bsh;   // bscale = 2^-bsh (n + 1 = 2^J)
+  if (std::ldexp(1.0, -bsh) != bscale || cnb != -1.0 / pscale(nd)) return BFP_ERR_ARG;
+  a.bshift = bsh;
+  a.nbshift = nd == 2 ? 2 : 3;                   // nb = -2^-nbshift
+  a.out = o; a.meta = r->meta;
+  a.w = r->w;
+  a.w_tmp = r->w + 4;                            // Table tab:estimates, IR residual (i > 1): w_add = 4
+  a.tmp = (h->lv[k].tmp && a.w_tmp <= 32) ? (int32_t*)h->lv[k].tmp : nullptr;
+  a.gamma_mu = h->ir_gam + k;
+  a.stats = h->stats;
   if (nd == 2) {
-    IrArgs a;
-    a.b = b; a.bscale = bscale; a.x = x; a.nx = g.nx; a.ny = g.ny; a.cdiag = cdiag; a.cnb = cnb;
-    int bsh = 0;
-    while (std::ldexp(1.0, -bsh) > bscale && bsh < 1100) ++bsh;   // bscale = 2^-bsh (n + 1 = 2^J)
-    if (std::ldexp(1.0, -bsh) != bscale || cdiag != 1.0 || cnb != -0.25) return BFP_ERR_ARG;
-    a.bshift = bsh;
-    a.nbshift = 2;
-    a.out = o; a.meta = r->meta;
-    a.w = r->w;
-    a.w_tmp = r->w + 4;                          // Table tab:estimates, IR residual (i > 1): w_add = 4
-    a.tmp = (h->lv[k].tmp && a.w_tmp <= 32) ? (int32_t*)h->lv[k].tmp : nullptr;
-    a.gamma_mu = h->ir_gam + k;
-    a.stats = h->stats;
+    if (cdiag != 1.0) return BFP_ERR_ARG;
     const int rs = pick_rows(g.ny >= 2048 ? 16 : (g.ny >= 1024 ? 8 : (g.ny >= 256 ? 4 : 2)), 64);
     const dim3 grid2((unsigned)((g.nx + kIrCols - 1) / kIrCols),
                      (unsigned)((g.ny + (int64_t)kIrWarps * rs - 1) / ((int64_t)kIrWarps * rs)));
     k_ir2d<true><<<grid2, 128, 0, s>>>(a, rs);
     k_ir2d<false><<<grid2, 128, 0, s>>>(a, rs);
   } else {
-    k_ir_residual<3, true><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
-    k_ir_residual<3, false><<<gr, 256, 0, s>>>(b, bscale, x, g, cdiag, cnb, o, r->meta, r->w);
+    k_ir3d<true><<<gr, 256, 0, s>>>(a, g);
+    k_ir3d<false><<<gr, 256, 0, s>>>(a, g);
   }
   note_launches(2);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;

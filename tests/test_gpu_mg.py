@@ -95,17 +95,18 @@ def test_graph_and_direct_ir_agree():
     assert torch.equal(xg, xd)
 
 
-@pytest.mark.parametrize("n", [127, 63])
-def test_ir_residual_window_and_padding(n):
+@pytest.mark.parametrize("nd,n", [(2, 127), (2, 63), (3, 31), (3, 15)])
+def test_ir_residual_window_and_padding(nd, n):
     """bfp_ir_residual equals quant(b' - A'x) of the oracle; the qcomp window (gamma =
     previous residual norm) is used from the second call on; padding is zeroed."""
-    h, s = make(2, n, 16, bfp.QCOMP)
-    f = manufactured_rhs(2, n)
+    h, s = make(nd, n, 16, bfp.QCOMP)
+    f = manufactured_rhs(nd, n)
     b = s.rhs_hierarchy(f)[0]
     rng = np.random.default_rng(n)
     ft = torch.from_numpy(f).cuda()
-    r = bfp.BFPVector((n, n), 16)
-    x = rng.standard_normal((n, n)) * 1e-3
+    shape = (n,) * nd
+    r = bfp.BFPVector(shape, 16)
+    x = rng.standard_normal(shape) * 1e-3
     for it in range(4):
         if it == 3:
             x = x * 1e6          # far larger residual: the window overflows, pass 2 recomputes
@@ -117,7 +118,7 @@ def test_ir_residual_window_and_padding(n):
         assert r.exponent == ref.e
         assert np.array_equal(r.mantissas(), ref.m)
         assert np.all(r.padding() == 0)
-        x = x + 1e-9 * rng.standard_normal((n, n))
+        x = x + 1e-9 * rng.standard_normal(shape)
     st = h.stats()
     assert st["ir_residuals"] == 4
     assert st["ir_recomputed"] == 2       # the first call (no gamma yet) and the overflowing one
