@@ -37,6 +37,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="nnqcomp", choices=["nnqcomp", "qcomp"])
     p.add_argument("--n", type=int, default=4095)
+    p.add_argument("--nd", type=int, default=2, choices=[2, 3], help="dimension of the --op problem")
     p.add_argument("--w", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -252,7 +253,7 @@ def run_ours(args):
     import paper_2307_00124_gb300 as bfp
     from bfp_inputs import manufactured_rhs
 
-    nd, n, w = 2, args.n, args.w
+    nd, n, w = args.nd, args.n, args.w
     mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
@@ -503,7 +504,7 @@ def run_op(args):
     import torch
     import paper_2307_00124_gb300 as bfp
     from bfp_inputs import manufactured_rhs
-    nd, n, w = 2, args.n, args.w
+    nd, n, w = args.nd, args.n, args.w
     mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
@@ -512,13 +513,13 @@ def run_op(args):
     x = torch.zeros_like(f)
     A = bfp.bfp_laplace_stencil(nd, o.omega, o.w_omega)
     rng = np.random.default_rng(0)
-    ym = rng.integers(-(1 << 12), 1 << 12, size=(n, n))
+    ym = rng.integers(-(1 << 12), 1 << 12, size=(n,) * nd, dtype=np.int32)
     y = bfp.BFPVector.from_mantissas(ym, -20, w)
     r = bfp.BFPVector.from_mantissas(ym[::-1].copy(), -19, w)
-    yo = bfp.BFPVector((n, n), w)
+    yo = bfp.BFPVector((n,) * nd, w)
     nc = (n - 1) // 2
-    yc = bfp.BFPVector((nc, nc), w)
-    d = bfp.BFPVector.from_mantissas(ym[:nc, :nc].copy(), -18, w)
+    yc = bfp.BFPVector((nc,) * nd, w)
+    d = bfp.BFPVector.from_mantissas(ym[(slice(0, nc),) * nd].copy(), -18, w)
     q = bfp.q(w, mode)
     ops = {
         "jacobi": lambda: bfp.bfp_jacobi(A, y, r, yo, q),
@@ -536,7 +537,7 @@ def run_op(args):
     for _ in range(args.reps):
         ops[args.op]()
     torch.cuda.synchronize()
-    print(json.dumps({"op": args.op, "reps": args.reps, "n": n, "w": w, "mode": args.mode}))
+    print(json.dumps({"op": args.op, "reps": args.reps, "nd": nd, "n": n, "w": w, "mode": args.mode}))
     h.close()
 
 

@@ -22,6 +22,7 @@ int32_t star_launch(const bfp_vec* yv, const bfp_vec* rv, const QDesc& d, const 
     if (wide_in) return launch_star2d<int32_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
     return launch_star2d<int16_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
   }
+  if (!wide_in && !is32(out)) return launch_star3d16<KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
   if (wide_in) {
     OpStar<int32_t, KIND, ND> op{vin(yv), vin(rv), c, n, mw};
     return launch_quant(op, d, out, s);

@@ -416,9 +416,9 @@ __device__ __forceinline__ void narrow8(const int32_t* tmp, const Plan& p, const
   narrowv<8>(tmp, p, out, row, c0, red);
 }
 
-// Final bookkeeping of a quantised op: e_out and the counters (block 0 only).
+// Final bookkeeping of a quantised op: e_out and the counters (block (0, 0, 0) only).
 __device__ __forceinline__ void op_epilogue(const QDesc& q, const Plan& p) {
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
     q.meta_out[0] = p.e_out;
     if (q.stats) {
       atomicAdd((unsigned long long*)&q.stats[0], 1ull);

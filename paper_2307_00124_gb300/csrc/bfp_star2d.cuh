@@ -241,6 +241,47 @@ __global__ void __launch_bounds__(128, 8) k_star2d(const VIn y, const VIn r, con
   if (!PASS1) op_epilogue(q, p);
 }
 
+// int16 staged kernel, 2D or 3D (zero_accumulators already issued); rs rows per warp
+template <int KIND, int ND>
+inline int32_t launch_star16(const VIn& y, const VIn& r, int32_t c, int32_t nb, int32_t mw, const QDesc& q,
+                             const VOut& o, int rs, cudaStream_t s) {
+  static bool carved = false;   // the staging ring wants the shared-memory carveout (7 CTAs / SM in 2D, 5 in 3D)
+  if (!carved) {
+    cudaFuncSetAttribute(k_star16<KIND, true, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_star16<KIND, false, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    carved = true;
+  }
+  const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
+  const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;
+  const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1),
+               (unsigned)(ND == 3 ? o.nz : 1));
+  if (q.mode == kQcomp) k_star16<KIND, true, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
+  k_star16<KIND, false, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
+  note_launches(q.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+// 3D seven-point op on int16 mantissas through the staged kernel
+template <int KIND>
+inline int32_t launch_star3d16(const VIn& y, const VIn& r, int64_t c64, int64_t nb64, int64_t mw64, const QDesc& q,
+                               const bfp_vec* out, cudaStream_t s) {
+  if (q.hbits > 62 || (q.two && q.lbits > 62)) return BFP_ERR_WIDTH;
+  const VOut o = vout(out);
+  if (o.nz > 65535) return BFP_ERR_SHAPE;
+  const int64_t ny = out->n[1];
+  const int rs = pick_rows(ny >= 256 ? 16 : (ny >= 64 ? 8 : 2), 32);   // <= 32: row masks
+  if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  VOut oo = o;
+  if (KIND == kJacobi0) {   // no neighbours: all ny * nz rows as one plane
+    oo.ny = o.ny * o.nz;
+    oo.nz = 1;
+    const int rs2 = pick_rows(oo.ny >= 2048 ? 16 : (oo.ny >= 1024 ? 8 : (oo.ny >= 256 ? 4 : 2)), 32);
+    return launch_star16<KIND, 2>(y, r, 0, 0, (int32_t)mw64, q, oo, rs2, s);
+  }
+  if (oo.nz == 0) { oo.ny = 0; oo.nz = 1; }   // no planes: one (empty) plane still publishes the meta
+  return launch_star16<KIND, 3>(y, r, (int32_t)c64, (int32_t)nb64, (int32_t)mw64, q, oo, rs, s);
+}
+
 template <class T, int KIND>
 inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb64, int64_t mw64, const QDesc& q,
                              const bfp_vec* out, cudaStream_t s) {
@@ -253,19 +294,7 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const int64_t strips = (ny + (int64_t)kStarWarps * rs - 1) / ((int64_t)kStarWarps * rs);
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
-  if (sizeof(T) == 2 && !o.is32) {
-    static bool carved = false;   // the staging ring wants the shared-memory carveout for 7 CTAs / SM
-    if (!carved) {
-      cudaFuncSetAttribute(k_star2d16<KIND, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      cudaFuncSetAttribute(k_star2d16<KIND, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      carved = true;
-    }
-    const dim3 g16((unsigned)((out->ld + kS16Cols - 1) / kS16Cols), grid.y);
-    if (q.mode == kQcomp) k_star2d16<KIND, true><<<g16, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
-    k_star2d16<KIND, false><<<g16, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
-    note_launches(q.mode == kQcomp ? 2 : 1);
-    return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
-  }
+  if (sizeof(T) == 2 && !o.is32) return launch_star16<KIND, 2>(y, r, c, nb, mw, q, o, rs, s);
   if (q.mode == kQcomp) k_star2d<T, KIND, true><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
   k_star2d<T, KIND, false><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
   note_launches(q.mode == kQcomp ? 2 : 1);

@@ -1,11 +1,13 @@
-// bfp_star2d16.cuh -- five-point stencil ops on int16 mantissas (w <= 16), the
-// finest-level hot path of the V-cycle.
+// bfp_star2d16.cuh -- five- and seven-point stencil ops on int16 mantissas
+// (w <= 16), the finest-level hot path of the V-cycle.
 //
-// A warp owns a 256-column chunk of a strip of rows: each lane 8 consecutive
-// mantissas (16 bytes per row and input).  Rows are staged through a per-lane
-// ring of kStages slots in shared memory with cp.async (16-byte copies,
-// zero-filled outside the grid), issued kStages - 3 rows ahead of the
-// three-row window the lane reads back (rows j-1, j, j+1 of y and row j of r).
+// A warp owns a 256-column chunk of a strip of rows of one plane: each lane 8
+// consecutive mantissas (16 bytes per row and input).  Rows are staged through
+// a per-lane ring of NS slots in shared memory with cp.async (16-byte copies,
+// zero-filled outside the grid), issued NS - 3 rows ahead of the three-row
+// window the lane reads back (rows j-1, j, j+1 of y and row j of r; in 3D also
+// row j of the planes below and above, which the CTAs of those planes, resident
+// at the same time, bring into L2).
 // Every lane reads only what it copied itself, so a per-thread wait on the
 // copy groups is the only synchronisation; the west / east neighbours at the
 // chunk edges come from shuffles, lanes 0 and 31 copying the one extra
@@ -31,7 +33,8 @@
 namespace bfp {
 
 constexpr int kS16Cols = 256;   // columns per warp chunk (32 lanes x 8)
-constexpr int kStages = 6;      // ring slots per lane: the 3-row window + 3 rows in flight
+constexpr int kStages = 6;      // ring slots per lane (2D): the 3-row window + 3 rows in flight
+constexpr int kStages3 = 5;     // 3D (four rows per stage): the window + 2 rows in flight
 
 struct Pk8 {
   uint32_t w[4];
@@ -99,21 +102,24 @@ __device__ __forceinline__ uint32_t min_s16x2(uint32_t a, uint32_t b) {
 
 // Inputs of one lane's 8 outputs, for the out-of-line general path.
 struct Row8 {
-  int32_t y[8], ym[8], yp[8], r[8];
+  int32_t y[8], ym[8], yp[8], r[8], zm[8], zp[8];
   int32_t wv, ev;
 };
 
-// The general path for one lane's 8 outputs of row `row`: reloads its inputs
-// from global memory (zero outside the grid) and quantises through quantvf.
-template <bool PASS1, int KIND>
+// The general path for one lane's 8 outputs of row j of plane kz: reloads its
+// inputs from global memory (zero outside the grid) and quantises through quantvf.
+template <bool PASS1, int KIND, int ND>
 __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p, const Fast& fq, const VOut& out,
-                                       int32_t* tmp, int64_t row, int64_t c0, Red& red, int32_t c, int32_t nb,
-                                       int32_t mw) {
+                                       int32_t* tmp, int64_t j, int64_t kz, int64_t c0, Red& red, int32_t c,
+                                       int32_t nb, int32_t mw) {
   Row8 in;
+  const int64_t ny = out.ny, row = kz * ny + j;
   if (KIND != kJacobi0) {
     ldv<int16_t, 8>(y, row, c0, in.y);
-    ldv<int16_t, 8>(y, row - 1, c0, in.ym);
-    ldv<int16_t, 8>(y, row + 1, c0, in.yp);
+    ldv<int16_t, 8>(y, j > 0 ? row - 1 : -1, c0, in.ym);
+    ldv<int16_t, 8>(y, j + 1 < ny ? row + 1 : -1, c0, in.yp);
+    ldv<int16_t, 8>(y, ND == 3 && kz > 0 ? row - ny : -1, c0, in.zm);
+    ldv<int16_t, 8>(y, ND == 3 && kz + 1 < out.nz ? row + ny : -1, c0, in.zp);
     in.wv = (int32_t)ld1<int16_t>(y, row, c0 - 1);
     in.ev = (int32_t)ld1<int16_t>(y, row, c0 + 8);
   }
@@ -126,7 +132,7 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
     }
     const int64_t wk = k == 0 ? in.wv : in.y[k - 1];
     const int64_t ek = k == 7 ? in.ev : in.y[k + 1];
-    const int64_t ns = wk + ek + in.ym[k] + in.yp[k];
+    const int64_t ns = wk + ek + in.ym[k] + in.yp[k] + in.zm[k] + in.zp[k];
     H = (int64_t)c * (int64_t)in.y[k] + (int64_t)nb * ns;
     L = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)in.r[k] : (int64_t)mw * (int64_t)in.r[k]);
   };
@@ -137,17 +143,30 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
 // pair (columns c-2, c-1 of the chunk start c), 32 lane slots of 4 words, the
 // east halo pair (columns c+256, c+257), 3 pad words; lane slots stay 16-byte
 // aligned, and every west / east neighbour is one int16 load from the row.
+// In 3D a stage also holds row j of the planes below (zm) and above (zp).
 constexpr int kRowWords = 136;
+template <int ND>
 struct __align__(16) Stage16 {
-  uint32_t y[kStages][kRowWords];
-  uint4 r[kStages][32];
+  static constexpr int N = kStages;
+  uint32_t y[N][kRowWords];
+  uint4 r[N][32];
+};
+template <>
+struct __align__(16) Stage16<3> {
+  static constexpr int N = kStages3;
+  uint32_t y[N][kRowWords];
+  uint4 r[N][32];
+  uint4 zm[N][32], zp[N][32];
 };
 
-template <int KIND, bool PASS1>
-__global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, const int32_t c, const int32_t nb,
-                                                     const int32_t mw, const QDesc q, const VOut out, const int rs) {
+// grid: (256-column chunks, strips of 4 * rs rows, planes)
+template <int KIND, bool PASS1, int ND>
+__global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, const VIn r, const int32_t c,
+                                                                 const int32_t nb, const int32_t mw, const QDesc q,
+                                                                 const VOut out, const int rs) {
+  constexpr int NS = Stage16<ND>::N;
   __shared__ Plan sp;
-  __shared__ Stage16 stg[4];
+  __shared__ Stage16<ND> stg[4];
   if (threadIdx.x == 0) {
     build_plan(q, sp);
     if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
@@ -158,6 +177,8 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * kS16Cols + lane * 8;
   const int ny = (int)out.ny;
+  const int kz = ND == 3 ? (int)blockIdx.z : 0;
+  const int64_t rowoff = (int64_t)kz * ny;        // global row of the plane's row 0
   const int j0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);
   const int j1 = j0 + rs < ny ? j0 + rs : ny;
   const bool act = c0 < out.ld;
@@ -193,9 +214,9 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
   const bool partial = nvalid < 8;
 
-  // staging: stage s holds y row j0 - 1 + s and r row j0 - 2 + s
-  Stage16& S = stg[warp];
-  const int nyin = kUseY ? (int)(y.ny * y.nz) : 1, nrin = kUseR ? (int)(r.ny * r.nz) : 1;
+  // staging: stage s holds y row j0 - 1 + s and r (zm, zp) row j0 - 2 + s
+  Stage16<ND>& S = stg[warp];
+  const int nyin = kUseY ? ny : 1, nrin = kUseR ? ny : 1;
   const bool ycol = kUseY && c0 < y.nx && c0 < y.ld, rcol = kUseR && c0 < r.nx && c0 < r.ld;
   const int16_t* ybase = kUseY ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
   const int16_t* rbase = kUseR ? reinterpret_cast<const int16_t*>(r.m) : nullptr;
@@ -206,8 +227,12 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   // the next stage to issue: y row jy at byte offset oy, r row jy - 1 at byte offset orr (rows
   // outside the grid and lanes past the row are zero-filled)
   int jy = j0 - 1;
-  int64_t oy = kUseY ? ((int64_t)jy * y.ld + c0) * 2 : 0, orr = kUseR ? ((int64_t)(jy - 1) * r.ld + c0) * 2 : 0;
+  int64_t oy = kUseY ? ((rowoff + jy) * y.ld + c0) * 2 : 0, orr = kUseR ? ((rowoff + jy - 1) * r.ld + c0) * 2 : 0;
   const int64_t ystride = kUseY ? y.ld * 2 : 0, rstride = kUseR ? r.ld * 2 : 0;
+  // 3D: row jy - 1 of planes kz - 1 and kz + 1 (offsets used only when that plane exists)
+  const bool zmok = ND == 3 && kUseY && kz > 0, zpok = ND == 3 && kUseY && kz + 1 < (int)out.nz;
+  int64_t ozm = ND == 3 && kUseY ? ((rowoff - ny + jy - 1) * y.ld + c0) * 2 : 0;
+  const int64_t zdelta = 2 * (int64_t)ny * y.ld * 2;
   const int64_t edelta = (ecol - c0) * 2;
   const bool edge_lane = lane == 0 || lane == 31;
   const uint32_t ybytes = 16u, rbytes = 16u;
@@ -216,6 +241,11 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   constexpr uint32_t kYRowBytes = kRowWords * 4, kRRowBytes = 32 * 16;
   const uint32_t ydst = smem_u32(&S.y[0][4 + 4 * lane]), edst = smem_u32(&S.y[0][eword]);
   const uint32_t rdst = smem_u32(&S.r[0][lane]);
+  uint32_t zmdst = 0, zpdst = 0;
+  if constexpr (ND == 3) {
+    zmdst = smem_u32(&S.zm[0][lane]);
+    zpdst = smem_u32(&S.zp[0][lane]);
+  }
   auto issue = [&](int slot) {
     if (kUseY) {
       const bool in = (unsigned)jy < (unsigned)nyin;
@@ -229,6 +259,13 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
       const bool ok = rcol && (unsigned)(jy - 1) < (unsigned)nrin;
       cp16u(rdst + (uint32_t)slot * kRRowBytes, rb + (ok ? orr : 0), ok ? rbytes : 0u);
       orr += rstride;
+    }
+    if (ND == 3 && kUseY) {
+      const bool in = ycol && (unsigned)(jy - 1) < (unsigned)nyin;
+      const bool okm = in && zmok, okp = in && zpok;
+      cp16u(zmdst + (uint32_t)slot * kRRowBytes, yb + (okm ? ozm : 0), okm ? 16u : 0u);
+      cp16u(zpdst + (uint32_t)slot * kRRowBytes, yb + (okp ? ozm + zdelta : 0), okp ? 16u : 0u);
+      ozm += ystride;
     }
     ++jy;
     cp_commit();
@@ -244,21 +281,21 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
   uint64_t ormag = 0;
   if (!PASS1 && p.narrow) {
     for (int j = j0; j < j1; ++j)
-      if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
+      if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, rowoff + j, c0, red);
   } else if (j0 < j1) {
     // the row walk, instantiated for both saturation tests (a uniform choice per CTA)
     auto walk = [&](auto v32tag, auto foldtag) {
       constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
   #pragma unroll
-      for (int s = 0; s < kStages - 1; ++s) issue(s);
-      // ring slots of stages i, i + 1, i + 2 and i + kStages - 1 (= i - 1 mod kStages)
-      int s0 = 0, s1 = 1, s2 = 2, sn = kStages - 1;
+      for (int s = 0; s < NS - 1; ++s) issue(s);
+      // ring slots of stages i, i + 1, i + 2 and i + NS - 1 (= i - 1 mod NS)
+      int s0 = 0, s1 = 1, s2 = 2, sn = NS - 1;
       for (int j = j0; j < j1; ++j) {
         const int i = j - j0;
-        issue(sn);                                // stage i + kStages - 1, into the slot of row j - 2
-        cp_wait<kStages - 3>();                   // stages <= i + 2 have landed (own copies)
+        issue(sn);                                // stage i + NS - 1, into the slot of row j - 2
+        cp_wait<NS - 3>();                        // stages <= i + 2 have landed (own copies)
         __syncwarp();                             // ... and the other lanes' (neighbours, halo)
-        Pk8 ym, yc, yp, rc;
+        Pk8 ym, yc, yp, rc, zm, zp;
         int32_t yv[8], wv = 0, ev = 0;
         if (kUseY) {
           ym = rd(*reinterpret_cast<const uint4*>(&S.y[s0][4 + 4 * lane]));
@@ -274,12 +311,16 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
           const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
           wv = row[7 + 8 * lane];                 // column c0 - 1
           ev = row[16 + 8 * lane];                // column c0 + 8
+          if constexpr (ND == 3) {
+            zm = rd(S.zm[s2][lane]);
+            zp = rd(S.zp[s2][lane]);
+          }
         }
         if (kUseR) rc = rd(S.r[s2][lane]);
         sn = s0;
         s0 = s1;
         s1 = s2;
-        s2 = s2 + 1 == kStages ? 0 : s2 + 1;
+        s2 = s2 + 1 == NS ? 0 : s2 + 1;
         if (act) {
           bool redo = !fast;
           int32_t o[8];
@@ -293,7 +334,8 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
               } else {
                 const int32_t wk = k == 0 ? wv : yv[k - 1];
                 const int32_t ek = k == 7 ? ev : yv[k + 1];
-                const int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
+                int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
+                if (ND == 3) ns += pk_get(zm, k) + pk_get(zp, k);
                 if (FOLD) {
                   Z = madw(cn32, ns, mulw(cy32, yv[k]));
                   if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
@@ -335,7 +377,7 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
             redo_rows |= 1u << i;                 // recomputed after the loop
           } else if (PASS1) {
             if (tmp) {
-              int4* d = reinterpret_cast<int4*>(tmp + (int64_t)j * out.ld + c0);
+              int4* d = reinterpret_cast<int4*>(tmp + (rowoff + j) * out.ld + c0);
               d[0] = make_int4(o[0], o[1], o[2], o[3]);
               d[1] = make_int4(o[4], o[5], o[6], o[7]);
             }
@@ -347,7 +389,7 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
             u.w = __byte_perm((uint32_t)o[6], (uint32_t)o[7], 0x5410);
             vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
             vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
-            *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (int64_t)j * out.ld + c0) = u;
+            *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (rowoff + j) * out.ld + c0) = u;
           }
         }
       }
@@ -363,7 +405,7 @@ __global__ void __launch_bounds__(128, 7) k_star2d16(const VIn y, const VIn r, c
     // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = j0 + __ffs(m) - 1;
-      if (act) slow_row8<PASS1, KIND>(y, r, p, fq, out, tmp, j, c0, red, c, nb, mw);
+      if (act) slow_row8<PASS1, KIND, ND>(y, r, p, fq, out, tmp, j, kz, c0, red, c, nb, mw);
     }
   }
   if (!PASS1) {

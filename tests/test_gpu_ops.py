@@ -141,7 +141,8 @@ def test_laplace_stencil_matches_oracle():
         assert (om.m, om.e) == (ref.m, ref.e)
 
 
-STAR_SHAPES = [(37, 45), (1, 1), (2, 3), (63, 63), (5, 6, 7), (3, 3, 3)]
+# 3D: several strips of rows per plane, two column chunks, ragged tails in x and y
+STAR_SHAPES = [(37, 45), (1, 1), (2, 3), (63, 63), (5, 6, 7), (3, 3, 3), (9, 70, 300), (3, 260, 17)]
 
 
 @pytest.mark.parametrize("shape", STAR_SHAPES)
@@ -232,10 +233,10 @@ def test_prolong(nc, w, mode, correct):
 
 @pytest.mark.parametrize("gshift", [-12, -3, 0, 2, 9])
 @pytest.mark.parametrize("w_add", [0, 2, 6])
-def test_qcomp_forced_overflow_underflow(gshift, w_add):
+@pytest.mark.parametrize("shape", [(33, 40), (6, 33, 270)])
+def test_qcomp_forced_overflow_underflow(gshift, w_add, shape):
     """A gamma too small forces overflow, too large forces underflow; the result never changes."""
-    shape = (33, 40)
-    A, OA, om = lap(2)
+    A, OA, om = lap(len(shape))
     ym = random_mantissas(shape, 16, 51)
     rm = random_mantissas(shape, 16, 52)
     gamma = (1, 10 + gshift)
@@ -251,9 +252,9 @@ def test_qcomp_forced_overflow_underflow(gshift, w_add):
 
 
 @pytest.mark.parametrize("gshift", [-20, -4, -1, 0, 3])
-def test_nnqcomp_saturation(gshift):
-    shape = (31, 31)
-    A, OA, om = lap(2)
+@pytest.mark.parametrize("shape", [(31, 31), (7, 31, 290)])
+def test_nnqcomp_saturation(gshift, shape):
+    A, OA, om = lap(len(shape))
     ym = random_mantissas(shape, 16, 61)
     rm = random_mantissas(shape, 16, 62)
     gamma = (1, 14 + gshift)
