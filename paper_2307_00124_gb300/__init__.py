@@ -177,7 +177,8 @@ class BFPVector:
         self.ld = pitch(nx)
         self.rows = int(np.prod(self.shape[:-1])) if len(self.shape) > 1 else 1
         dt = torch.int16 if self.w <= 16 else torch.int32
-        self.mant = mant if mant is not None else torch.zeros((self.rows, self.ld), dtype=dt, device=device)
+        # at least one row of storage: the C ABI wants a non-null mantissa pointer, also for an empty grid
+        self.mant = mant if mant is not None else torch.zeros((max(self.rows, 1), self.ld), dtype=dt, device=device)
         self.meta = meta if meta is not None else torch.zeros(META_WORDS, dtype=torch.int64, device=device)
 
     @property
@@ -201,8 +202,8 @@ class BFPVector:
         import torch
         m = np.asarray(m, dtype=np.int64)
         v = cls(m.shape, w, device)
-        host = np.zeros((v.rows, v.ld), dtype=np.int16 if w <= 16 else np.int32)
-        host[:, : m.shape[-1]] = m.reshape(v.rows, m.shape[-1])
+        host = np.zeros(tuple(v.mant.shape), dtype=np.int16 if w <= 16 else np.int32)
+        host[: v.rows, : m.shape[-1]] = m.reshape(v.rows, m.shape[-1])
         v.mant.copy_(torch.from_numpy(host))
         meta = np.zeros(META_WORDS, dtype=np.int64)
         meta[0] = e
@@ -212,10 +213,10 @@ class BFPVector:
 
     def mantissas(self) -> np.ndarray:
         h = self.mant.cpu().numpy().astype(np.int64)
-        return h[:, : self.shape[-1]].reshape(self.shape)
+        return h[: self.rows, : self.shape[-1]].reshape(self.shape)
 
     def padding(self) -> np.ndarray:
-        return self.mant.cpu().numpy()[:, self.shape[-1]:]
+        return self.mant.cpu().numpy()[: self.rows, self.shape[-1]:]
 
     @property
     def exponent(self) -> int:

@@ -29,7 +29,8 @@ int32_t restrict2d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaS
   if (e) return e;
   const int64_t ny = rc->n[1];
   const int rs = rows_per_warp(ny);
-  const dim3 grid((unsigned)((rc->ld + 255) / 256), (unsigned)((ny + 4 * rs - 1) / (4 * rs)));
+  const int64_t strips = (ny + 4 * rs - 1) / (4 * rs);
+  const dim3 grid((unsigned)((rc->ld + 255) / 256), (unsigned)(strips > 0 ? strips : 1));
   const VOut o = vout(rc);
   static bool carved = false;   // the staging rings want the shared-memory carveout
   if (!carved) {
@@ -44,25 +45,52 @@ int32_t restrict2d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaS
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
-template <bool CORR>
-int32_t prolong2d16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
+int32_t restrict3d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaStream_t s) {
+  int32_t e = launch_checks(d);
+  if (e) return e;
+  const int64_t ny = rc->n[1], nz = rc->n[2];
+  if (nz > 65535) return BFP_ERR_SHAPE;
+  const int rs = pick_rows(ny >= 128 ? 8 : (ny >= 32 ? 4 : 2), 16);
+  const int64_t strips = (ny + kR3Warps * rs - 1) / (kR3Warps * rs);
+  const dim3 grid((unsigned)((rc->ld + 255) / 256), (unsigned)(strips > 0 ? strips : 1), (unsigned)(nz > 0 ? nz : 1));
+  VOut o = vout(rc);
+  if (nz == 0) o.ny = 0;
+  static bool carved = false;
+  if (!carved) {
+    cudaFuncSetAttribute(k_restrict3d16<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict3d16<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    carved = true;
+  }
+  if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (d.mode == kQcomp) k_restrict3d16<true><<<grid, 32 * kR3Warps, 0, s>>>(vin(rf), d, o, rs);
+  k_restrict3d16<false><<<grid, 32 * kR3Warps, 0, s>>>(vin(rf), d, o, rs);
+  note_launches(d.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+// staged int16 interpolation, 2D or 3D (grid z: fine planes)
+template <bool CORR, int ND>
+int32_t prolong16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
   int32_t e = launch_checks(d);
   if (e) return e;
   const int64_t pairs = (out->n[1] + 1) / 2;
-  const int rs = rows_per_warp(pairs);
-  const dim3 grid((unsigned)((out->ld + 255) / 256), (unsigned)((pairs + 4 * rs - 1) / (4 * rs)));
+  const int rs = rows_per_warp(ND == 3 ? 4 * pairs : pairs);
+  const int64_t nzf = ND == 3 ? out->n[2] : 1;
+  if (nzf > 65535) return BFP_ERR_SHAPE;
+  const int64_t strips = (pairs + 4 * rs - 1) / (4 * rs);
+  const dim3 grid((unsigned)((out->ld + 255) / 256), (unsigned)(strips > 0 ? strips : 1), (unsigned)nzf);
   const VOut o = vout(out);
   VIn yv = vin(y ? y : out);
   if (!CORR) yv.m = nullptr;
   static bool carved = false;
   if (!carved) {
-    cudaFuncSetAttribute(k_prolong2d16<CORR, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_prolong2d16<CORR, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_prolong16<CORR, true, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_prolong16<CORR, false, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     carved = true;
   }
   if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
-  if (d.mode == kQcomp) k_prolong2d16<CORR, true><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
-  k_prolong2d16<CORR, false><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
+  if (d.mode == kQcomp) k_prolong16<CORR, true, ND><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
+  k_prolong16<CORR, false, ND><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
   note_launches(d.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -70,13 +98,14 @@ int32_t prolong2d16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, con
 template <int ND>
 int32_t restrict_launch(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaStream_t s) {
   if (ND == 2 && !is32(rf)) return restrict2d16(rf, rc, d, s);
+  if (ND == 3 && !is32(rf)) return restrict3d16(rf, rc, d, s);
   if (is32(rf)) return launch_quant(OpRestrict<int32_t, ND>{vin(rf), rc->n[1]}, d, rc, s);
   return launch_quant(OpRestrict<int16_t, ND>{vin(rf), rc->n[1]}, d, rc, s);
 }
 
 template <int ND, bool CORR>
 int32_t prolong_launch(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
-  if (ND == 2 && !is32(dc)) return prolong2d16<CORR>(dc, y, out, d, s);
+  if (!is32(dc)) return prolong16<CORR, ND>(dc, y, out, d, s);
   VIn yv = vin(y ? y : out);   // carries the fine shape; not read when CORR is false
   if (!CORR) yv.m = nullptr;
   if (is32(dc)) return launch_quant(OpProlong<int32_t, ND, CORR>{vin(dc), yv}, d, out, s);

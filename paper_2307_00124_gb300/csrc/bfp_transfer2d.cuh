@@ -334,47 +334,240 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const VIn f, const QDes
 }
 
 // ---------------------------------------------------------------------------
+// 3D restriction.  A warp owns a 256-column chunk of coarse rows J0.. of coarse
+// plane K; a stage is fine row jf of the fine planes 2K, 2K+1, 2K+2, combined
+// as v = f0 + 2 f1 + f2 before the horizontal sums.  Stages are three times the
+// 2D size, so a CTA has two warps and a ring of six fine rows: rows 2J+1 ..
+// 2J+3 in use or landed, rows 2J+4, 2J+5 in flight.
+// ---------------------------------------------------------------------------
+constexpr int kR3Slots = 6;
+constexpr int kR3Warps = 2;
+struct __align__(16) StageR3 {
+  uint32_t f[kR3Slots][3][kRRowWords];
+};
+
+template <bool PASS1>
+__device__ __noinline__ void restrict3_slow(const VIn& f, const Plan& p, const VOut& out, int32_t* tmp, int64_t J,
+                                            int64_t K, int64_t c0, Red& red) {
+  int32_t H[8], L[8];
+  const int64_t fny = f.ny;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t fi = 2 * (c0 + k) + 1, fj = 2 * J + 1, fk = 2 * K + 1;
+    int32_t acc = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx)
+          acc += (2 - (dx < 0 ? -dx : dx)) * (2 - (dy < 0 ? -dy : dy)) * (2 - (dz < 0 ? -dz : dz)) *
+                 ld1_16(f, (fk + dz) * fny + fj + dy, fi + dx);
+    H[k] = acc;
+    L[k] = 0;
+  }
+  slow_hl8<PASS1>(H, L, p, out, tmp, K * out.ny + J, c0, red);
+}
+
+// grid: (256-column chunks, strips of kR3Warps * rs coarse rows, coarse planes)
+template <bool PASS1>
+__global__ void __launch_bounds__(64) k_restrict3d16(const VIn f, const QDesc q, const VOut out, const int rs) {
+  __shared__ Plan sp;
+  __shared__ StageR3 stg[kR3Warps];
+  if (threadIdx.x == 0) {
+    build_plan(q, sp);
+    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
+  }
+  __syncthreads();
+  const Plan& p = sp;
+  const Fast fq = make_fast(p, PASS1);
+  const EmitC ec = make_emit(fq, q, 1, PASS1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = (int64_t)blockIdx.x * 256 + lane * 8;
+  const int64_t fc = 2 * c0;
+  const int ny = (int)out.ny;                    // coarse rows per plane
+  const int K = (int)blockIdx.z;
+  const int64_t crow0 = (int64_t)K * ny;
+  const int J0 = (int)(((int64_t)blockIdx.y * kR3Warps + warp) * rs);
+  const int J1 = J0 + rs < ny ? J0 + rs : ny;
+  const bool act = c0 < out.ld;
+  Red red = {0, 0, 0};
+  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
+  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
+  const bool partial = nvalid < 8;
+  const int fvalid = (int)(f.nx - fc < 16 ? (f.nx - fc < 0 ? 0 : f.nx - fc) : 16);
+  uint32_t fmask[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    fmask[i] = ((2 * i < fvalid) ? 0xffffu : 0u) | ((2 * i + 1 < fvalid) ? 0xffff0000u : 0u);
+  const bool fpartial = fvalid < 16;
+
+  StageR3& S = stg[warp];
+  const int fny = (int)f.ny;
+  const int16_t* fb = reinterpret_cast<const int16_t*>(f.m);
+  const bool seg0 = fc < f.nx && fc < f.ld, seg1 = fc + 8 < f.nx && fc + 8 < f.ld;
+  const bool hok = lane == 31 && fc + 16 < f.nx;
+  const int64_t pdelta = (int64_t)fny * f.ld;    // one fine plane
+  // the next fine row to issue: jf of planes 2K, 2K+1, 2K+2 (planes 2K + 2 <= 2 nz_c < nz_f always exist)
+  int jf = 2 * J0;
+  int64_t of = ((int64_t)2 * K * fny + jf) * f.ld + fc;
+  auto issue = [&](int slot) {
+    const bool in = (unsigned)jf < (unsigned)fny;
+    const bool i0 = in && seg0, i1 = in && seg1, hk = hok && in;
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+      const int64_t o = of + pl * pdelta;
+      cp16(&S.f[slot][pl][4 + 8 * lane], fb + (i0 ? o : 0), i0 ? 16u : 0u);
+      cp16(&S.f[slot][pl][8 + 8 * lane], fb + (i1 ? o + 8 : 0), i1 ? 16u : 0u);
+      cp4_if(lane == 31, &S.f[slot][pl][kRRowWords - 4], fb + (hk ? o + 16 : 0), hk ? 4u : 0u);
+    }
+    of += f.ld;
+    ++jf;
+  };
+  // h_k = v[2c] + 2 v[2c+1] + v[2c+2] (c = c0 + k) of the plane-combined fine row in `slot`
+  auto hrow = [&](int slot, int32_t (&h)[8]) {
+    int32_t v[17];
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+      const uint4 a = *reinterpret_cast<const uint4*>(&S.f[slot][pl][4 + 8 * lane]);
+      const uint4 b = *reinterpret_cast<const uint4*>(&S.f[slot][pl][8 + 8 * lane]);
+      uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      if (fpartial) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] &= fmask[i];
+      }
+      const int32_t nxt = reinterpret_cast<const int16_t*>(&S.f[slot][pl][0])[8 + 16 * (lane + 1)];
+      const int32_t m = pl == 1 ? 2 : 1;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int32_t lo = (int32_t)(int16_t)(w[i] & 0xffffu), hi = (int32_t)w[i] >> 16;
+        v[2 * i] = pl == 0 ? lo : v[2 * i] + m * lo;
+        v[2 * i + 1] = pl == 0 ? hi : v[2 * i + 1] + m * hi;
+      }
+      v[16] = pl == 0 ? nxt : v[16] + m * nxt;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = v[2 * k] + 2 * v[2 * k + 1] + v[2 * k + 2];
+  };
+
+  uint32_t vmax = 0, vmin = 0, redo_rows = 0;
+  uint64_t ormag = 0;
+  bool any = false;
+  if (!PASS1 && p.narrow) {
+    for (int J = J0; J < J1; ++J)
+      if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, crow0 + J, c0, red);
+  } else if (J0 < J1) {
+    auto walk = [&](auto v32tag, auto foldtag) {
+      constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
+      // prologue: fine rows 2 J0 .. 2 J0 + 3 in two groups of two (ring slot = (row - 2 J0) mod 6)
+      issue(0);
+      issue(1);
+      cp_commit();
+      issue(2);
+      issue(3);
+      cp_commit();
+      cp_wait<1>();
+      __syncwarp();
+      int32_t hp[8];
+      hrow(0, hp);
+      int b = 0;                                 // slot of fine row 2J
+      for (int J = J0; J < J1; ++J) {
+        const int i = J - J0;
+        auto sl = [&](int d) { return b + d >= kR3Slots ? b + d - kR3Slots : b + d; };
+        __syncwarp();                            // every lane is done with the slots of rows 2J-2, 2J-1
+        issue(sl(4));                            // fine rows 2J + 4, 2J + 5
+        issue(sl(5));
+        cp_commit();
+        cp_wait<1>();                            // fine rows <= 2J + 3 have landed
+        __syncwarp();
+        int32_t hm[8], hn[8];
+        hrow(sl(1), hm);
+        hrow(sl(2), hn);
+        int32_t H[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { H[k] = hp[k] + 2 * hm[k] + hn[k]; hp[k] = hn[k]; }
+        if (act) {
+          bool redo = !ec.fast;
+          if (ec.fast)
+            redo = emit8<PASS1, V32, FOLD>(ec, fq, H, H, false, nvalid, partial, out, tmp, crow0 + J, c0, ormag,
+                                           vmax, vmin);
+          if (redo) redo_rows |= 1u << i;
+          any = any || nvalid > 0;
+        }
+        b = sl(2);
+      }
+      cp_wait<0>();
+    };
+    if (ec.fold) {
+      if (ec.v32) walk(std::true_type{}, std::true_type{});
+      else walk(std::false_type{}, std::true_type{});
+    } else {
+      if (ec.v32) walk(std::true_type{}, std::false_type{});
+      else walk(std::false_type{}, std::false_type{});
+    }
+    for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
+      const int J = J0 + __ffs(m) - 1;
+      if (act) restrict3_slow<PASS1>(f, p, out, tmp, J, K, c0, red);
+    }
+  }
+  if (PASS1) fold_key(red, ormag, any && ec.fast);
+  else red.nrm = max(red.nrm, packed_norm(vmax, vmin, out.is32 != 0));
+  block_commit(red, q.meta_out, q.stats, PASS1);
+  if (!PASS1) op_epilogue(q, p);
+}
+
+// ---------------------------------------------------------------------------
 // Interpolation: y' = y - P d (CORR) or P d.  A lane owns 8 fine columns c0..
 // (coarse columns C = c0/2 .. C+3 and C-1 from the previous lane); a stage is
 // coarse row P (lane slots of 8 bytes after the west halo pair) and fine rows
-// 2P, 2P+1 of y.
+// 2P, 2P+1 of y.  In 3D the CTAs of fine plane k stage coarse row P of the
+// planes that plane interpolates from: Q for k = 2Q + 1 (weight 2), Q - 1 and Q
+// for k = 2Q (weight 1 each), combined before the horizontal interpolation.
 // ---------------------------------------------------------------------------
 constexpr int kPStages = 4;
 constexpr int kPRowWords = 4 + 64;
+template <int ND>
 struct __align__(16) StageP {
-  uint32_t d[kPStages][kPRowWords];
+  uint32_t d[kPStages][ND == 3 ? 2 : 1][kPRowWords];
   uint4 y[kPStages][2][32];
 };
 
-// H (= P_m d) and L (= y) of fine row j from global memory (general path)
-template <bool CORR>
-__device__ __forceinline__ void prolong_hl_global(const VIn& d, const VIn& y, int64_t j, int64_t c0, int32_t (&H)[8],
-                                                  int32_t (&L)[8]) {
-  auto gx = [&](int64_t J, int64_t i) -> int32_t {   // horizontal interpolation of coarse row J at fine column i
-    return (i & 1) ? 2 * ld1_16(d, J, (i - 1) >> 1) : ld1_16(d, J, (i >> 1) - 1) + ld1_16(d, J, i >> 1);
+// H (= P_m d) and L (= y) of fine row j of plane kf from global memory (general path)
+template <bool CORR, int ND>
+__device__ __forceinline__ void prolong_hl_global(const VIn& d, const VIn& y, int64_t j, int64_t kf, int64_t c0,
+                                                  int32_t (&H)[8], int32_t (&L)[8]) {
+  const int64_t cny = d.ny;
+  auto gx = [&](int64_t Q, int64_t J, int64_t i) -> int32_t {   // coarse row J of plane Q at fine column i
+    if (J < 0 || J >= cny || Q < 0 || Q >= d.nz) return 0;
+    const int64_t row = Q * cny + J;
+    return (i & 1) ? 2 * ld1_16(d, row, (i - 1) >> 1) : ld1_16(d, row, (i >> 1) - 1) + ld1_16(d, row, i >> 1);
   };
+  auto gyx = [&](int64_t Q, int64_t i) -> int32_t {            // interpolation in y, then x, on plane Q
+    return (j & 1) ? 2 * gx(Q, (j - 1) >> 1, i) : gx(Q, (j >> 1) - 1, i) + gx(Q, j >> 1, i);
+  };
+  const int64_t frow = kf * y.ny + j;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int64_t i = c0 + k;
-    const int32_t pd = (j & 1) ? 2 * gx((j - 1) >> 1, i) : gx((j >> 1) - 1, i) + gx(j >> 1, i);
+    int32_t pd;
+    if (ND == 3) pd = (kf & 1) ? 2 * gyx((kf - 1) >> 1, i) : gyx((kf >> 1) - 1, i) + gyx(kf >> 1, i);
+    else pd = gyx(0, i);
     H[k] = CORR ? -pd : pd;
-    L[k] = CORR ? ld1_16(y, j, i) : 0;
+    L[k] = CORR ? ld1_16(y, frow, i) : 0;
   }
 }
 
-template <bool CORR, bool PASS1>
+template <bool CORR, bool PASS1, int ND>
 __device__ __noinline__ void prolong_slow(const VIn& d, const VIn& y, const Plan& p, const VOut& out, int32_t* tmp,
-                                          int64_t j, int64_t c0, Red& red) {
+                                          int64_t j, int64_t kf, int64_t c0, Red& red) {
   int32_t H[8], L[8];
-  prolong_hl_global<CORR>(d, y, j, c0, H, L);
-  slow_hl8<PASS1>(H, L, p, out, tmp, j, c0, red);
+  prolong_hl_global<CORR, ND>(d, y, j, kf, c0, H, L);
+  slow_hl8<PASS1>(H, L, p, out, tmp, kf * out.ny + j, c0, red);
 }
 
-template <bool CORR, bool PASS1>
-__global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y, const QDesc q, const VOut out,
-                                                        const int rs) {
+// grid: (256-column chunks, strips of 4 * rs row pairs, fine planes)
+template <bool CORR, bool PASS1, int ND>
+__global__ void __launch_bounds__(128, 6) k_prolong16(const VIn d, const VIn y, const QDesc q, const VOut out,
+                                                      const int rs) {
   __shared__ Plan sp;
-  __shared__ StageP stg[4];
+  __shared__ StageP<ND> stg[4];
   if (threadIdx.x == 0) {
     build_plan(q, sp);
     if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
@@ -386,7 +579,9 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * 256 + lane * 8;
   const int64_t C = c0 >> 1;                     // first coarse column of this lane (multiple of 4)
-  const int ny = (int)out.ny;                    // fine rows
+  const int ny = (int)out.ny;                    // fine rows (of one plane)
+  const int kf = ND == 3 ? (int)blockIdx.z : 0;  // fine plane
+  const int64_t frow0 = (int64_t)kf * ny;        // global row of the plane's fine row 0
   const int P0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);   // first row pair (fine rows 2P0, 2P0+1)
   const int P1 = min(P0 + rs, (ny + 1) / 2);
   const bool act = c0 < out.ld;
@@ -403,21 +598,34 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
   for (int i = 0; i < 4; ++i)
     ymask[i] = ((2 * i < nvalid) ? 0xffffu : 0u) | ((2 * i + 1 < nvalid) ? 0xffff0000u : 0u);
 
-  StageP& S = stg[warp];
-  const int ncr = (int)(d.ny * d.nz), nyr = CORR ? (int)(y.ny * y.nz) : 1;
+  StageP<ND>& S = stg[warp];
+  const int ncr = (int)d.ny, nyr = CORR ? ny : 1;   // rows per plane
   const int16_t* db = reinterpret_cast<const int16_t*>(d.m);
   const int16_t* yb = CORR ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
   const bool dseg = C < d.nx && C < d.ld;
   const bool hok = lane == 0 && C >= 2 && C - 1 < d.nx;
   const bool yseg = CORR && c0 < y.nx && c0 < y.ld;
+  // coarse planes: qa (and qb = qa + 1 on even fine planes of a 3D grid); a plane outside the grid reads 0
+  const bool odd = ND == 3 && (kf & 1);
+  const int qa = ND == 3 ? (odd ? (kf - 1) >> 1 : (kf >> 1) - 1) : 0;
+  const bool qaok = (unsigned)qa < (unsigned)d.nz, qbok = ND == 3 && !odd && (unsigned)(qa + 1) < (unsigned)d.nz;
+  const int64_t qdelta = (int64_t)ncr * d.ld;    // plane qb - plane qa
   // the next stage: coarse row jc (stage s holds coarse row P0 - 1 + s, y rows 2 jc, 2 jc + 1)
   int jc = P0 - 1;
-  int64_t od = (int64_t)jc * d.ld + C, oy = CORR ? (int64_t)(2 * jc) * y.ld + c0 : 0;
+  int64_t od = ((int64_t)qa * ncr + jc) * d.ld + C, oy = CORR ? (frow0 + 2 * jc) * y.ld + c0 : 0;
   auto issue = [&](int slot, bool with_y) {
     const bool in = (unsigned)jc < (unsigned)ncr;
-    cp8(&S.d[slot][4 + 2 * lane], db + ((in && dseg) ? od : 0), (in && dseg) ? 8u : 0u);
-    const bool hk = hok && in;
-    cp4_if(lane == 0, &S.d[slot][3], db + (hk ? od - 2 : 0), hk ? 4u : 0u);
+    const bool ia = in && qaok;
+    cp8(&S.d[slot][0][4 + 2 * lane], db + ((ia && dseg) ? od : 0), (ia && dseg) ? 8u : 0u);
+    const bool hk = hok && ia;
+    cp4_if(lane == 0, &S.d[slot][0][3], db + (hk ? od - 2 : 0), hk ? 4u : 0u);
+    if (ND == 3 && !odd) {
+      const int pb = ND == 3 ? 1 : 0;
+      const bool ib = in && qbok;
+      cp8(&S.d[slot][pb][4 + 2 * lane], db + ((ib && dseg) ? od + qdelta : 0), (ib && dseg) ? 8u : 0u);
+      const bool hb = hok && ib;
+      cp4_if(lane == 0, &S.d[slot][pb][3], db + (hb ? od + qdelta - 2 : 0), hb ? 4u : 0u);
+    }
     if (CORR && with_y) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -430,14 +638,29 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
     ++jc;
     cp_commit();
   };
-  // g_k: horizontal interpolation of the coarse row in `slot` at fine columns c0 + k
-  auto grow = [&](int slot, int32_t (&g)[8]) {
-    const uint2 u = *reinterpret_cast<const uint2*>(&S.d[slot][4 + 2 * lane]);
+  // coarse columns C - 1 .. C + 3 of the staged row of plane slot pl
+  auto dvals = [&](int slot, int pl, int32_t (&dv)[5]) {
+    const uint2 u = *reinterpret_cast<const uint2*>(&S.d[slot][pl][4 + 2 * lane]);
     const uint32_t u0 = u.x & cm0, u1 = u.y & cm1;
-    int32_t dv[5];
-    dv[0] = reinterpret_cast<const int16_t*>(&S.d[slot][0])[7 + 4 * lane];   // coarse column C - 1
+    dv[0] = reinterpret_cast<const int16_t*>(&S.d[slot][pl][0])[7 + 4 * lane];   // coarse column C - 1
     dv[1] = (int32_t)(int16_t)(u0 & 0xffffu); dv[2] = (int32_t)u0 >> 16;
     dv[3] = (int32_t)(int16_t)(u1 & 0xffffu); dv[4] = (int32_t)u1 >> 16;
+  };
+  // g_k: horizontal interpolation of the (plane-combined) coarse row in `slot` at fine columns c0 + k
+  auto grow = [&](int slot, int32_t (&g)[8]) {
+    int32_t dv[5];
+    dvals(slot, 0, dv);
+    if (ND == 3) {
+      if (odd) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) dv[m] *= 2;
+      } else {
+        int32_t db5[5];
+        dvals(slot, ND == 3 ? 1 : 0, db5);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) dv[m] += db5[m];
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) g[k] = (k & 1) ? 2 * dv[(k + 1) / 2] : dv[k / 2] + dv[k / 2 + 1];
   };
@@ -447,7 +670,7 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
   bool any = false;
   if (!PASS1 && p.narrow) {
     for (int j = 2 * P0; j < 2 * P1 && j < ny; ++j)
-      if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, j, c0, red);
+      if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, frow0 + j, c0, red);
   } else if (P0 < P1) {
     auto walk = [&](auto v32tag, auto foldtag) {
       constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
@@ -484,7 +707,8 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
           if (act) {
             bool redo = !ec.fast;
             if (ec.fast)
-              redo = emit8<PASS1, V32, FOLD>(ec, fq, H, L, CORR, nvalid, partial, out, tmp, j, c0, ormag, vmax, vmin);
+              redo = emit8<PASS1, V32, FOLD>(ec, fq, H, L, CORR, nvalid, partial, out, tmp, frow0 + j, c0, ormag, vmax,
+                                             vmin);
             if (redo) redo_rows |= 1u << (2 * i + h);
             any = any || nvalid > 0;
           }
@@ -503,7 +727,7 @@ __global__ void __launch_bounds__(128, 6) k_prolong2d16(const VIn d, const VIn y
     }
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = 2 * P0 + __ffs(m) - 1;
-      if (act) prolong_slow<CORR, PASS1>(d, y, p, out, tmp, j, c0, red);
+      if (act) prolong_slow<CORR, PASS1, ND>(d, y, p, out, tmp, j, kf, c0, red);
     }
   }
   if (PASS1) fold_key(red, ormag, any && ec.fast);

@@ -197,7 +197,11 @@ def test_jacobi(shape, w, mode, zero_guess):
     check(yo, ref, st, rs)
 
 
-@pytest.mark.parametrize("nc", [(1, 1), (3, 3), (20, 33), (2, 2, 2), (4, 3, 5)])
+# coarse shapes; the 3D ones span several strips of rows and two column chunks of the fine grid
+TRANSFER_SHAPES = [(1, 1), (3, 3), (20, 33), (2, 2, 2), (4, 3, 5), (5, 40, 140), (3, 70, 9), (0, 0), (0, 0, 0)]
+
+
+@pytest.mark.parametrize("nc", TRANSFER_SHAPES)
 @pytest.mark.parametrize("w", [8, 16, 32])
 @pytest.mark.parametrize("mode", MODES)
 def test_restrict(nc, w, mode):
@@ -212,7 +216,7 @@ def test_restrict(nc, w, mode):
     check(c, ref, st, rs)
 
 
-@pytest.mark.parametrize("nc", [(1, 1), (3, 3), (20, 33), (2, 2, 2), (4, 3, 5)])
+@pytest.mark.parametrize("nc", TRANSFER_SHAPES)
 @pytest.mark.parametrize("w", [8, 16, 32])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("correct", [True, False])
