@@ -34,6 +34,8 @@ struct CoarseOp {
   int32_t a, b, out;     // buffer ids (-1: none)
   int32_t solo;          // run by warp 0 alone
   int32_t sync_before;   // first full-block op after a run of solo ops
+  int32_t run;           // on the op at CoarseArgs::run_k: the number of identical solo sweeps (on a
+                         // level of <= 32 points, alternating between buffers a and out) it starts
   int64_t c, nb, mw;     // stencil / smoother coefficients
   QDesc q;               // static description (meta pointers unused)
 };
@@ -47,6 +49,7 @@ struct CoarseArgs {
   const CoarseOp* ops;
   const CoarseBuf* bufs;
   int32_t nops, nbufs;
+  int32_t run_k;         // first op of the coarsest level's sweep run (nops: none)
   int32_t meta_off;      // byte offsets in dynamic shared memory: meta blocks,
   int32_t ops_off;       // the op list (copied in at start),
   int32_t bufs_off;      // the buffer table
@@ -393,6 +396,91 @@ struct CoarseCounts {
   }
 };
 
+// A run of damped-Jacobi sweeps on a level of n x n <= 32 points, on warp 0
+// with the grid in registers (lane l holds point (l mod n, l / n); neighbours
+// by shuffles).  Every sweep plans and quantises exactly as the general loop's
+// int16 register path (lean plan, Z = k0 y + k1 (W + E + S + N) + k2 r, one
+// shift, the nnqcomp range test, qcomp's block-maximum key); the meta block is
+// written once, for the run's last output.  A sweep whose plan leaves that
+// path stops the run: its input goes to shared memory and the general loop
+// takes over from it.  Out of line (and with results returned by value): the
+// main loop keeps its own register allocation.
+struct CoarseRun {
+  int32_t done;          // sweeps done
+  int32_t prev;          // buffer holding their result (the next op's input), meta in (pe, pn)
+  int64_t pe, pn;
+  int32_t sat;           // this lane's saturated elements
+  CoarseCounts cnt;      // thread 0: the sweeps' counters
+};
+
+__device__ __noinline__ CoarseRun coarse_sweep_run(unsigned char* sm, const CoarseOp* op0, const CoarseBuf* bufs,
+                                                   int64_t* metas, int64_t ea, int64_t na, int64_t eb, int64_t nb) {
+  CoarseRun res;
+  res.done = 0; res.prev = -1; res.pe = 0; res.pn = 0; res.sat = 0;
+  res.cnt = CoarseCounts{0, 0, 0, 0};
+  CoarseCounts& cnt = res.cnt;
+  int sat = 0;
+  const CoarseOp op = *op0;                      // register copy: every sweep has the same descriptor
+  const int lane = threadIdx.x & 31;
+  const int n = bufs[op.out].n;
+  const bool act = lane < n * n;
+  const int i = act ? lane % n : 0, j = act ? lane / n : 0;
+  const bool hw = act && i > 0, he = act && i + 1 < n, hs = act && j > 0, hn = act && j + 1 < n;
+  const int32_t bv = act ? (int32_t)cview<int16_t>(sm, bufs[op.b])(i, j) : 0;
+  int32_t y = act ? (int32_t)cview<int16_t>(sm, bufs[op.a])(i, j) : 0;
+  const bool qc = op.q.mode == kQcomp;
+  int bin = op.a, bout = op.out;
+  int r = 0;
+  for (; r < op.run; ++r) {
+    CoarseLean L;
+    CoarseExec ex;
+    if (!lean_first(op, ea, na, eb, nb, L, ex) || !ex.m.ok) break;
+    const int32_t wv = __shfl_sync(0xffffffffu, y, hw ? lane - 1 : lane);
+    const int32_t ev = __shfl_sync(0xffffffffu, y, he ? lane + 1 : lane);
+    const int32_t sv = __shfl_sync(0xffffffffu, y, hs ? lane - n : lane);
+    const int32_t nv = __shfl_sync(0xffffffffu, y, hn ? lane + n : lane);
+    const int32_t ns = ((hw ? wv : 0) + (he ? ev : 0)) + ((hs ? sv : 0) + (hn ? nv : 0));
+    if (qc) {
+      const int64_t z1 = (int64_t)ex.m.k0 * y + (int64_t)ex.m.k1 * ns + (int64_t)ex.m.k2 * bv;
+      const uint64_t om = (uint64_t)(z1 ^ (z1 >> 63));
+      const unsigned key = act ? (unsigned)(256 + (64 - __clzll((long long)om)) + 1) : 0u;
+      const unsigned kk = __reduce_max_sync(0xffffffffu, key);
+      if (!lean_second(op, (int32_t)kk, L, ex) || !ex.m.ok) break;
+    }
+    const CoarseMul& m = ex.m;
+    const int64_t z = (int64_t)m.k0 * y + (int64_t)m.k1 * ns + (int64_t)m.k2 * bv;
+    const uint32_t zl = (uint32_t)z, zh = (uint32_t)((uint64_t)z >> 32);
+    int32_t v = m.t < 32 ? (int32_t)__funnelshift_r(zl, zh, m.t) : ((int32_t)zh >> (m.t - 32));
+    const bool out = m.clamp && (uint64_t)(z - m.zmin) >= m.zrange;
+    v = out ? (z < 0 ? m.vlo : m.vhi) : v;
+    sat += (out && act) ? 1 : 0;
+    v = act ? v : 0;
+    const unsigned nn = __reduce_max_sync(0xffffffffu, (unsigned)(v < 0 ? -v : v));
+    y = v;
+    cnt.add(L.ov != 0, L.un != 0, qc);           // every lane (thread 0's copy is the one kept)
+    ea = L.e_out;
+    na = (int64_t)nn;
+    const int t = bin;
+    bin = bout;
+    bout = t;
+  }
+  // y is the input of sweep r (the output of sweep r - 1, or the run's input when r == 0)
+  if (r > 0) {
+    if (act) cview<int16_t>(sm, bufs[bin]).put(i, j, y);
+    if (threadIdx.x == 0) {
+      metas[bin * BFP_META_WORDS] = ea;
+      metas[bin * BFP_META_WORDS + 1] = na;
+    }
+    __syncwarp();
+  }
+  res.done = r;
+  res.prev = bin;
+  res.pe = ea;
+  res.pn = na;
+  res.sat = sat;
+  return res;
+}
+
 // Every thread that runs an op plans it in registers; a full-block op then
 // costs one barrier (qcomp two) for its block maximum, a solo op (warp 0
 // alone) only warp reductions.  Thread 0 writes every meta block; the output
@@ -437,7 +525,9 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const Coars
   int sat = 0;
   CoarseCounts cnt = {0, 0, 0, 0};
   Plan* pp = &s_plan[warp];
-  for (int k = 0; k < a.nops; ++k) {
+  // the op list in two ranges around the sweep run (the run's call stays out of the loop body)
+  auto exec_ops = [&](int k_begin, int k_end) {
+  for (int k = k_begin; k < k_end; ++k) {
     const CoarseOp& op = ops[k];
     const bool solo = op.solo != 0;
     if (solo && warp != 0) continue;
@@ -522,6 +612,31 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const Coars
       cnt.add(lean ? L.ov != 0 : pp->overflow != 0, lean ? L.un != 0 : pp->underflow != 0, qc);
     }
   }
+  };
+  const int kr = a.run_k < a.nops ? a.run_k : a.nops;
+  exec_ops(0, kr);
+  int k_next = kr;
+  if (sizeof(T) == 2 && kr < a.nops && warp == 0) {
+    // the sweep run (warp 0; the other warps pass its solo ops and wait at the next full-block op)
+    const CoarseOp& op = ops[kr];
+    const int64_t ea = op.a == prev ? pe : metas[op.a * BFP_META_WORDS];
+    const int64_t na = op.a == prev ? pn : metas[op.a * BFP_META_WORDS + 1];
+    const int64_t eb = op.b == prev ? pe : metas[op.b * BFP_META_WORDS];
+    const int64_t nb = op.b == prev ? pn : metas[op.b * BFP_META_WORDS + 1];
+    const CoarseRun run = coarse_sweep_run(sm, &op, bufs, metas, ea, na, eb, nb);
+    if (run.done > 0) {
+      prev = run.prev;
+      pe = run.pe;
+      pn = run.pn;
+      sat += run.sat;
+      cnt.calls += run.cnt.calls;
+      cnt.recomputed += run.cnt.recomputed;
+      cnt.overflow += run.cnt.overflow;
+      cnt.underflow += run.cnt.underflow;
+    }
+    k_next = kr + run.done;      // the general loop resumes at the first sweep not done
+  }
+  exec_ops(k_next, a.nops);
   {
     const long long s = warp_sum((long long)sat);
     if (lane == 0 && s) atomicAdd(&s_sat, (unsigned long long)s);

@@ -332,7 +332,7 @@ struct bfp_hierarchy {
   int smem_bytes = 0;
   int meta_off = 0, ops_off = 0, bufs_off = 0, data_off = 0;
   std::vector<CoarseOp*> d_ops;          // per start level k >= kc
-  std::vector<int> nops, rbuf, ybuf;
+  std::vector<int> nops, rbuf, ybuf, runk;
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
   flt_vec fy0{};                         // its float counterpart (float hierarchies)
   // captured IR step
@@ -466,6 +466,28 @@ int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vecto
   return BFP_OK;
 }
 
+// Marks the first run of identical solo damped-Jacobi sweeps on a level of <= 32 points that
+// alternate between two buffers (the coarsest level's sweeps), which the kernel runs with the grid
+// in registers; returns its first op (ops.size(): none).
+int mark_sweep_run(std::vector<CoarseOp>& ops, const std::vector<CoarseBuf>& bufs) {
+  auto same = [&](const CoarseOp& x, const CoarseOp& p) {
+    return x.kind == cJac && x.solo && !x.sync_before && x.a == p.out && x.out == p.a && x.b == p.b &&
+           x.c == p.c && x.nb == p.nb && x.mw == p.mw && std::memcmp(&x.q, &p.q, sizeof(QDesc)) == 0;
+  };
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const CoarseOp& o = ops[i];
+    if (!(o.kind == cJac && o.solo && o.a >= 0 && o.a != o.out && (int64_t)bufs[o.out].n * bufs[o.out].n <= 32))
+      continue;
+    size_t e = i + 1;
+    while (e < ops.size() && same(ops[e], ops[e - 1])) ++e;
+    if (e - i > 1) {
+      ops[i].run = (int32_t)(e - i);
+      return (int)i;
+    }
+  }
+  return (int)ops.size();
+}
+
 bool allow_coarse_smem(bool is32, int optin) {
   cudaFuncAttributes fa;
   const cudaError_t e0 = is32 ? cudaFuncGetAttributes(&fa, k_coarse_vcycle<int32_t>)
@@ -529,6 +551,7 @@ int32_t coarse_setup(bfp_hierarchy* h) {
     int res = -1;
     TRY(coarse_flatten(h, k, lb[k - h->kc].r, lb, ops, &res));
     for (size_t i = 1; i < ops.size(); ++i) ops[i].sync_before = (ops[i - 1].solo && !ops[i].solo) ? 1 : 0;
+    const int rk = mark_sweep_run(ops, bufs);
     if ((int)ops.size() > max_ops) return BFP_ERR_ARG;
     CoarseOp* d = (CoarseOp*)dalloc(h, ops.size() * sizeof(CoarseOp));
     if (!d) return BFP_ERR_CUDA;
@@ -537,6 +560,7 @@ int32_t coarse_setup(bfp_hierarchy* h) {
     h->nops.push_back((int)ops.size());
     h->rbuf.push_back(lb[k - h->kc].r);
     h->ybuf.push_back(res);
+    h->runk.push_back(rk);
   }
   // the attribute is per kernel, shared by every hierarchy: allow the device maximum once rather than
   // this hierarchy's size (a later hierarchy with a smaller on-chip part must not shrink it)
@@ -549,6 +573,7 @@ int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* 
   std::memset(&a, 0, sizeof(a));
   a.ops = h->d_ops[i];
   a.nops = h->nops[i];
+  a.run_k = h->runk[i];
   a.bufs = h->d_bufs;
   a.nbufs = h->nbufs;
   a.meta_off = h->meta_off;
