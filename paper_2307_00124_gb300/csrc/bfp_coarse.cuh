@@ -481,6 +481,139 @@ __device__ __noinline__ CoarseRun coarse_sweep_run(unsigned char* sm, const Coar
   return res;
 }
 
+// The smoothing of a coarsest level with n^d <= 32 points (int16 mantissas)
+// when it runs from global memory (3D, or 2D without the on-chip cycle): the
+// level's first sweep from y = 0 and its remaining sweeps in one launch of one
+// warp, the grid in registers (lane l holds point (l mod n, (l / n) mod n,
+// l / n^2)).  Each sweep follows the on-chip schedule's ops exactly: the lean
+// plan and folded multipliers when they apply, else the full plan and the
+// general per-element quantiser; qcomp's second pass recomputes.  Only the last
+// result, its meta block (e, max |m|) and the counters are written.
+struct SweepRunArgs {
+  CoarseOp op0, op1;     // damped Jacobi from y = 0, and from y
+  int32_t sweeps, n, nd;
+  VIn r;                 // right-hand side of the level
+  const int64_t* r_meta;
+  VOut y;                // result (padding columns written as 0)
+  int64_t* y_meta;
+  uint64_t* stats;
+};
+
+__global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
+  const int lane = threadIdx.x;
+  const int n = a.n, nn = n * n, np = a.nd == 3 ? nn * n : nn;
+  const bool act = lane < np;
+  const int i = act ? lane % n : 0, j = act ? (lane / n) % n : 0, k = act ? lane / nn : 0;
+  const bool hw = act && i > 0, he = act && i + 1 < n, hs = act && j > 0, hn = act && j + 1 < n;
+  const bool hb = act && a.nd == 3 && k > 0, ht = act && a.nd == 3 && k + 1 < n;
+  const int64_t row = (int64_t)j + (int64_t)n * k;
+  const int32_t bv = act ? (int32_t)reinterpret_cast<const int16_t*>(a.r.m)[row * a.r.ld + i] : 0;
+  const int64_t eb = a.r_meta[0], nb = a.r_meta[1];
+  int64_t ea = 0, na = 0;
+  int32_t y = 0;
+  int sat = 0;
+  CoarseCounts cnt = {0, 0, 0, 0};
+  for (int sw = 0; sw < a.sweeps; ++sw) {
+    const CoarseOp& op = sw == 0 ? a.op0 : a.op1;
+    const bool qc = op.q.mode == kQcomp;
+    // neighbour sum of y (the first sweep has no y)
+    const int32_t wv = __shfl_sync(0xffffffffu, y, hw ? lane - 1 : lane);
+    const int32_t ev = __shfl_sync(0xffffffffu, y, he ? lane + 1 : lane);
+    const int32_t sv = __shfl_sync(0xffffffffu, y, hs ? lane - n : lane);
+    const int32_t nv = __shfl_sync(0xffffffffu, y, hn ? lane + n : lane);
+    const int32_t bz = __shfl_sync(0xffffffffu, y, hb ? lane - nn : lane);
+    const int32_t tz = __shfl_sync(0xffffffffu, y, ht ? lane + nn : lane);
+    const int32_t ns = (((hw ? wv : 0) + (he ? ev : 0)) + ((hs ? sv : 0) + (hn ? nv : 0))) +
+                       ((hb ? bz : 0) + (ht ? tz : 0));
+    const int64_t H = sw == 0 ? op.mw * (int64_t)bv : op.c * (int64_t)y + op.nb * (int64_t)ns;
+    const int64_t Lg = sw == 0 ? 0 : op.mw * (int64_t)bv;
+    CoarseLean L;
+    CoarseExec ex;
+    Plan P;
+    const bool lean0 = lean_first(op, ea, na, eb, nb, L, ex);
+    bool lean = lean0;
+    if (!lean) {
+      build_plan_v(op.q, ea, na, eb, nb, P);
+      ex.f = make_fast(P, qc);
+      ex.m = make_mul(op.kind, ex.f, op);
+    }
+    // Z on the register path (folded multipliers: the same value as (H << dh) + (L << dl))
+    auto zreg = [&](const CoarseMul& m) -> int64_t {
+      return sw == 0 ? (int64_t)m.k0 * bv : (int64_t)m.k0 * y + (int64_t)m.k1 * ns + (int64_t)m.k2 * bv;
+    };
+    if (qc) {
+      long long key = 0;
+      if (act) {
+        if (ex.m.ok) {
+          const int64_t z = zreg(ex.m);
+          key = 256 + (64 - __clzll((long long)(uint64_t)(z ^ (z >> 63)))) + 1;
+        } else if (ex.f.ok) {
+          const int64_t Z = (int64_t)((uint64_t)H << ex.f.dh) + (int64_t)((uint64_t)Lg << ex.f.dl);
+          key = 256 + msb64(Z);
+        } else {
+          key = coarse_key_general(H, Lg, &P);
+        }
+      }
+      const unsigned kk = __reduce_max_sync(0xffffffffu, (unsigned)key);
+      if (lean) lean = lean_second(op, (int32_t)kk, L, ex);
+      if (!lean) {
+        if (lean0) build_plan_v(op.q, ea, na, eb, nb, P);
+        plan_from_mu(P, (int64_t)kk);
+        ex.f = make_fast(P, false);
+        ex.m = make_mul(op.kind, ex.f, op);
+      }
+    }
+    int32_t v = 0;
+    if (act) {
+      if (ex.m.ok) {
+        const CoarseMul& m = ex.m;
+        const int64_t z = zreg(m);
+        const uint32_t zl = (uint32_t)z, zh = (uint32_t)((uint64_t)z >> 32);
+        v = m.t < 32 ? (int32_t)__funnelshift_r(zl, zh, m.t) : ((int32_t)zh >> (m.t - 32));
+        if (m.clamp && (uint64_t)(z - m.zmin) >= m.zrange) {
+          v = z < 0 ? m.vlo : m.vhi;
+          ++sat;
+        }
+      } else if (ex.f.ok) {
+        const int64_t Z = (int64_t)((uint64_t)H << ex.f.dh) + (int64_t)((uint64_t)Lg << ex.f.dl);
+        const int64_t hi = (1ll << (ex.f.w - 1)) - 1, lo = -(1ll << (ex.f.w - 1));
+        int64_t t = Z >> ex.f.t;
+        if (ex.f.clamp) {
+          if (t > hi) { t = hi; ++sat; } else if (t < lo) { t = lo; ++sat; }
+        }
+        v = (int32_t)t;
+      } else {
+        const int64_t rr = coarse_val_general(H, Lg, &P);
+        v = (int32_t)(uint32_t)rr;
+        sat += (int)(rr >> 32);
+      }
+    }
+    const unsigned nrm = __reduce_max_sync(0xffffffffu, (unsigned)(v < 0 ? -v : v));
+    cnt.add(lean ? L.ov != 0 : P.overflow != 0, lean ? L.un != 0 : P.underflow != 0, qc);
+    ea = lean ? (int64_t)L.e_out : P.e_out;
+    na = (int64_t)nrm;
+    y = v;
+  }
+  // the result with its padding columns, the meta block, the counters
+  const int rows = a.nd == 3 ? nn : n;
+  const int64_t ld = a.y.ld, total = (int64_t)rows * ld;
+  for (int64_t base = 0; base < total; base += 32) {
+    const int64_t idx = base + lane;
+    const int64_t rr = idx / ld, cc = idx - rr * ld;
+    const int src = (int)(rr * n + (cc < n ? cc : 0));
+    const int32_t val = __shfl_sync(0xffffffffu, y, src < 32 ? src : 0);
+    if (idx < total) reinterpret_cast<int16_t*>(a.y.m)[idx] = (int16_t)(cc < n ? val : 0);
+  }
+  const long long sats = warp_sum((long long)sat);
+  if (lane < BFP_META_WORDS) a.y_meta[lane] = lane == 0 ? ea : (lane == 1 ? na : 0);
+  if (lane == 0 && a.stats) {
+    const unsigned long long cc[5] = {cnt.calls, cnt.recomputed, cnt.overflow, cnt.underflow,
+                                      (unsigned long long)sats};
+    for (int t = 0; t < 5; ++t)
+      if (cc[t]) atomicAdd((unsigned long long*)&a.stats[t], cc[t]);
+  }
+}
+
 // Every thread that runs an op plans it in registers; a full-block op then
 // costs one barrier (qcomp two) for its block maximum, a solo op (warp 0
 // alone) only warp reductions.  Thread 0 writes every meta block; the output

@@ -11,7 +11,8 @@
 // Layout: FP64 vectors are dense (row stride n), so a lane owns the
 // interleaved columns cb + 32 k + lane (k < kIrV): every warp access is a
 // contiguous 256-byte line whatever the row alignment.  A warp walks a strip
-// of rows keeping x rows j-1, j, j+1 (and j+2, prefetched) in registers.
+// of rows keeping x rows j-1, j, j+1 (and j+2, prefetched) in registers; the
+// f row and the edge values are also loaded one row ahead.
 #pragma once
 
 #include "bfp_host.h"
@@ -186,16 +187,25 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
     ldrow(j0 - 1, xm);
     ldrow(j0, xc);
     ldrow(j0 + 1, xp);
+    // f row j and the x edge values of row j (lanes 0, 31), loaded one row ahead
+    auto ldb = [&](int64_t j, double (&v)[kIrV], double& we, double& ee) {
+#pragma unroll
+      for (int k = 0; k < kIrV; ++k) {
+        const int64_t i = cb + 32 * k + lane;
+        v[k] = (j < j1 && i < nx) ? __ldg(a.b + j * nx + i) : 0.0;
+      }
+      we = (j < j1 && lane == 0 && cb > 0) ? __ldg(a.x + j * nx + cb - 1) : 0.0;
+      ee = (j < j1 && lane == 31 && cb + kIrCols < nx) ? __ldg(a.x + j * nx + cb + kIrCols) : 0.0;
+    };
+    double bn[kIrV], wn, en;
+    ldb(j0, bn, wn, en);
     for (int64_t j = j0; j < j1; ++j) {
       ldrow(j + 2, xpp);
       double bv[kIrV];
 #pragma unroll
-      for (int k = 0; k < kIrV; ++k) {
-        const int64_t i = cb + 32 * k + lane;
-        bv[k] = i < nx ? __ldg(a.b + j * nx + i) : 0.0;
-      }
-      const double wedge = (lane == 0 && cb > 0) ? __ldg(a.x + j * nx + cb - 1) : 0.0;
-      const double eedge = (lane == 31 && cb + kIrCols < nx) ? __ldg(a.x + j * nx + cb + kIrCols) : 0.0;
+      for (int k = 0; k < kIrV; ++k) bv[k] = bn[k];
+      const double wedge = wn, eedge = en;
+      ldb(j + 1, bn, wn, en);
 #pragma unroll
       for (int k = 0; k < kIrV; ++k) {
         const int64_t i = cb + 32 * k + lane;

@@ -412,6 +412,41 @@ struct CoarseLevelBufs {
   int r, y0, y1;
 };
 
+// One op of the on-chip schedule on level l: the QDesc the C ABI op would build (meta pointers
+// unused; qcomp without the window buffer) and the op's coefficients.
+int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, int out, CoarseOp* res) {
+  const int w = h->o.w, nd = h->o.ndim;
+  CoarseOp op;
+  std::memset(&op, 0, sizeof(op));
+  op.kind = kind; op.a = a; op.b = b; op.out = out;
+  QDesc& d = op.q;
+  int rule = 0;
+  int32_t rc = BFP_OK;
+  switch (kind) {
+    case cJac0: rc = desc_jacobi(&h->A, 0, w, d, &rule); op.mw = h->A.omega.m; break;
+    case cJac: {
+      int64_t Sc, Sn, eS;
+      rc = desc_jacobi(&h->A, w, w, d, &rule);
+      if (!rc) rc = jacobi_operator(&h->A, &Sc, &Sn, &eS);
+      op.c = Sc; op.nb = Sn; op.mw = h->A.omega.m;
+      break;
+    }
+    case cRes: rc = desc_residual(&h->A, w, w, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
+    case cRestrict: rc = desc_restrict(nd, w, d, &rule); break;
+    default: rc = desc_prolong(nd, w, w, d, &rule); break;
+  }
+  if (rc) return rc;
+  if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;
+  if (op.c != (int32_t)op.c || op.nb != (int32_t)op.nb || op.mw != (int32_t)op.mw) return BFP_ERR_WIDTH;
+  d.mode = h->o.mode;
+  d.w_out = w;
+  d.w_tmp = w + rule;
+  d.use_tmp = 0;
+  op.solo = h->lv[l + (kind == cRestrict ? 1 : 0)].n <= 15 ? 1 : 0;   // output level size
+  *res = op;
+  return BFP_OK;
+}
+
 // Flattens the V-cycle schedule of levels l.. (the same op order as vcycle_rec)
 int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vector<CoarseLevelBufs>& lb,
                        std::vector<CoarseOp>& ops, int* res) {
@@ -419,35 +454,9 @@ int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vecto
   const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
   const CoarseLevelBufs& B = lb[l - h->kc];
   int cur = B.y0, oth = B.y1;
-  const int w = h->o.w, nd = h->o.ndim;
   auto push = [&](int kind, int a, int b, int out) -> int32_t {
     CoarseOp op;
-    std::memset(&op, 0, sizeof(op));
-    op.kind = kind; op.a = a; op.b = b; op.out = out;
-    QDesc& d = op.q;
-    int rule = 0;
-    int32_t rc = BFP_OK;
-    switch (kind) {
-      case cJac0: rc = desc_jacobi(&h->A, 0, w, d, &rule); op.mw = h->A.omega.m; break;
-      case cJac: {
-        int64_t Sc, Sn, eS;
-        rc = desc_jacobi(&h->A, w, w, d, &rule);
-        if (!rc) rc = jacobi_operator(&h->A, &Sc, &Sn, &eS);
-        op.c = Sc; op.nb = Sn; op.mw = h->A.omega.m;
-        break;
-      }
-      case cRes: rc = desc_residual(&h->A, w, w, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
-      case cRestrict: rc = desc_restrict(nd, w, d, &rule); break;
-      default: rc = desc_prolong(nd, w, w, d, &rule); break;
-    }
-    if (rc) return rc;
-    if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;
-    if (op.c != (int32_t)op.c || op.nb != (int32_t)op.nb || op.mw != (int32_t)op.mw) return BFP_ERR_WIDTH;
-    d.mode = h->o.mode;
-    d.w_out = w;
-    d.w_tmp = w + rule;
-    d.use_tmp = 0;
-    op.solo = h->lv[l + (kind == cRestrict ? 1 : 0)].n <= 15 ? 1 : 0;   // output level size
+    TRY(make_coarse_op(h, l, kind, a, b, out, &op));
     ops.push_back(op);
     return BFP_OK;
   };
@@ -486,6 +495,32 @@ int mark_sweep_run(std::vector<CoarseOp>& ops, const std::vector<CoarseBuf>& buf
     }
   }
   return (int)ops.size();
+}
+
+// The coarsest level's sweeps in one launch (k_sweep_run) when the level has at most 32 points
+// and int16 mantissas.
+bool sweep_run_fits(const bfp_hierarchy* h, int k) {
+  const int64_t n = h->lv[k].n;
+  const int64_t np = h->o.ndim == 3 ? n * n * n : n * n;
+  return h->o.w <= 16 && np >= 1 && np <= 32 && k + 1 == (int)h->lv.size();
+}
+
+int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, cudaStream_t s) {
+  SweepRunArgs a;
+  std::memset(&a, 0, sizeof(a));
+  TRY(make_coarse_op(h, k, cJac0, -1, 0, 0, &a.op0));
+  TRY(make_coarse_op(h, k, cJac, 0, 0, 0, &a.op1));
+  a.sweeps = h->o.coarse_sweeps;
+  a.n = (int32_t)h->lv[k].n;
+  a.nd = h->o.ndim;
+  a.r = vin(r);
+  a.r_meta = r->meta;
+  a.y = vout(y);
+  a.y_meta = y->meta;
+  a.stats = h->stats;
+  k_sweep_run<<<1, 32, 0, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
 bool allow_coarse_smem(bool is32, int optin) {
@@ -615,6 +650,12 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
     return BFP_OK;
   }
   const bool coarsest = (k + 1 == (int)h->lv.size());
+  if (coarsest && sweep_run_fits(h, k)) {   // the coarsest level's sweeps in one launch
+    bfp_vec y = at_slot(bufA);
+    TRY(sweep_run(h, k, r, &y, s));
+    *res = y;
+    return BFP_OK;
+  }
   const int nu1 = coarsest ? h->o.coarse_sweeps : h->o.nu1;
   // writes per level: 1 (omega r) + (nu1 - 1) sweeps [+ correction + nu2 sweeps]
   const int writes = coarsest ? nu1 : (nu1 + 1 + h->o.nu2);

@@ -246,18 +246,24 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
     zmdst = smem_u32(&S.zm[0][lane]);
     zpdst = smem_u32(&S.zp[0][lane]);
   }
-  auto issue = [&](int slot) {
+  // INT: an interior strip (every row it stages inside the grid, every lane's 8 columns inside
+  // the row), so the copies need no bounds; with_r: stage s >= 2 (the r rows of stages 0, 1 are
+  // never read)
+  auto issue = [&](int slot, auto inttag, bool with_r) {
+    constexpr bool INT = decltype(inttag)::value;
     if (kUseY) {
-      const bool in = (unsigned)jy < (unsigned)nyin;
-      const bool ok = in && ycol;
+      const bool in = INT || (unsigned)jy < (unsigned)nyin;
+      const bool ok = INT || (in && ycol);
       cp16u(ydst + (uint32_t)slot * kYRowBytes, yb + (ok ? oy : 0), ok ? ybytes : 0u);
       const bool ek = eok && in;
       cp4u_if(edge_lane, edst + (uint32_t)slot * kYRowBytes, yb + (ek ? oy + edelta : 0), ek ? 4u : 0u);
       oy += ystride;
     }
     if (kUseR) {
-      const bool ok = rcol && (unsigned)(jy - 1) < (unsigned)nrin;
-      cp16u(rdst + (uint32_t)slot * kRRowBytes, rb + (ok ? orr : 0), ok ? rbytes : 0u);
+      if (with_r) {
+        const bool ok = INT || (rcol && (unsigned)(jy - 1) < (unsigned)nrin);
+        cp16u(rdst + (uint32_t)slot * kRRowBytes, rb + (ok ? orr : 0), ok ? rbytes : 0u);
+      }
       orr += rstride;
     }
     if (ND == 3 && kUseY) {
@@ -284,15 +290,23 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
       if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, rowoff + j, c0, red);
   } else if (j0 < j1) {
     // the row walk, instantiated for both saturation tests (a uniform choice per CTA)
-    auto walk = [&](auto v32tag, auto foldtag) {
+    auto walk = [&](auto v32tag, auto foldtag, auto inttag) {
       constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
+      constexpr bool INT = decltype(inttag)::value;
+      // stages with a row that is read: y rows j0 - 1 .. j1 (stage s = y row j0 - 1 + s); the
+      // ring's later stages are committed empty so that the group count stays the same
+      const int nst = j1 - j0 + 2;
   #pragma unroll
-      for (int s = 0; s < NS - 1; ++s) issue(s);
+      for (int s = 0; s < NS - 1; ++s) {
+        if (s < nst) issue(s, inttag, s >= 2);
+        else cp_commit();
+      }
       // ring slots of stages i, i + 1, i + 2 and i + NS - 1 (= i - 1 mod NS)
       int s0 = 0, s1 = 1, s2 = 2, sn = NS - 1;
       for (int j = j0; j < j1; ++j) {
         const int i = j - j0;
-        issue(sn);                                // stage i + NS - 1, into the slot of row j - 2
+        if (i + NS - 1 < nst) issue(sn, inttag, true);   // stage i + NS - 1, into the slot of row j - 2
+        else cp_commit();
         cp_wait<NS - 3>();                        // stages <= i + 2 have landed (own copies)
         __syncwarp();                             // ... and the other lanes' (neighbours, halo)
         Pk8 ym, yc, yp, rc, zm, zp;
@@ -303,7 +317,7 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
           yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
   #pragma unroll
           for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
-          if (partial) {   // padding columns may hold anything: the east neighbour of the last column is 0
+          if (!INT && partial) {   // padding columns may hold anything: the east neighbour of the last column is 0
 #pragma unroll
             for (int k = 0; k < 8; ++k)
               if (k >= nvalid) yv[k] = 0;
@@ -321,7 +335,7 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
         s0 = s1;
         s1 = s2;
         s2 = s2 + 1 == NS ? 0 : s2 + 1;
-        if (act) {
+        if (INT || act) {
           bool redo = !fast;
           int32_t o[8];
           bool ovf = false;
@@ -349,14 +363,14 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
               const int32_t v = FOLD ? (int32_t)__funnelshift_r((uint32_t)(uint64_t)Z, (uint32_t)((uint64_t)Z >> 32), t)
                                    : (int32_t)(Z >> t);
               if (PASS1) {
-                if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
+                if (INT || k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
                 o[k] = (int32_t)((uint32_t)v << sh) >> sh;
               } else {
                 o[k] = v;
-                if (!V32 && fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)zmin > zrange) && (k < nvalid);
+                if (!V32 && fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)zmin > zrange) && (INT || k < nvalid);
               }
             }
-            if (partial) {
+            if (!INT && partial) {
   #pragma unroll
               for (int k = 0; k < 8; ++k)
                 if (k >= nvalid) o[k] = 0;
@@ -395,12 +409,17 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
       }
       cp_wait<0>();
     };
-    if (fold) {
-      if (v32) walk(std::true_type{}, std::true_type{});
-      else walk(std::false_type{}, std::true_type{});
+    // interior strip: y rows j0 - 1 .. j1 inside the plane, the chunk's 256 columns inside the row
+    const bool xfull = (int64_t)blockIdx.x * kS16Cols + kS16Cols <= out.nx;
+    const bool interior = xfull && (!kUseY || (j0 >= 1 && j1 < ny));
+    const std::false_type no;
+    if (fold && v32 && interior) walk(std::true_type{}, std::true_type{}, std::true_type{});
+    else if (fold) {
+      if (v32) walk(std::true_type{}, std::true_type{}, no);
+      else walk(std::false_type{}, std::true_type{}, no);
     } else {
-      if (v32) walk(std::true_type{}, std::false_type{});
-      else walk(std::false_type{}, std::false_type{});
+      if (v32) walk(std::true_type{}, std::false_type{}, no);
+      else walk(std::false_type{}, std::false_type{}, no);
     }
     // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
