@@ -73,3 +73,28 @@ def smoothed_random_rhs(n: int, seed: int, sweeps: int = 4) -> np.ndarray:
         p = np.pad(f, 1)
         f = 0.5 * f + 0.125 * (p[1:-1, :-2] + p[1:-1, 2:] + p[:-2, 1:-1] + p[2:, 1:-1])
     return f
+
+
+def grf_nodes(n: int, seed: int = 1, modes: int = 64, kmax: int = 8, sigma: float = 1.0) -> np.ndarray:
+    """Coefficient field k = exp(g) at the (n+2) x (n+2) grid nodes, boundary included
+    (numpy order [y, x], node (i, j) at (i h, j h), h = 1/(n+1)).
+
+    g is a seeded smooth Gaussian random field: sigma sqrt(2/modes) times the sum of
+    `modes` terms cos(pi (kx x + ky y) + phi) with integer wave numbers kx, ky uniform in
+    [-kmax, kmax] (not both zero) and phases uniform in [0, 2 pi).  The same (kx, ky, phi)
+    for every n, so the coarse grids of a hierarchy sample the same field.
+    """
+    rng = np.random.default_rng(seed)
+    kx, ky = [], []
+    while len(kx) < modes:
+        a, b = (int(v) for v in rng.integers(-kmax, kmax + 1, size=2))
+        if a == 0 and b == 0:
+            continue
+        kx.append(a)
+        ky.append(b)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=modes)
+    t = np.arange(n + 2) / (n + 1)
+    g = np.zeros((n + 2, n + 2))
+    for m in range(modes):
+        g += np.cos(np.pi * (kx[m] * t[None, :] + ky[m] * t[:, None]) + phi[m])
+    return np.exp(sigma * math.sqrt(2.0 / modes) * g)
