@@ -199,6 +199,49 @@ int32_t bfp_restrict(const bfp_vec* r_f, const bfp_vec* r_c, const bfp_q* q,
 int32_t bfp_prolong(const bfp_vec* d, const bfp_vec* y, const bfp_vec* y_out,
                     const bfp_q* q, const bfp_stats* st, bfp_stream stream);
 
+/* ---- variable coefficients (2D; the configs' -div(k grad u), not in the paper) ---- */
+
+/* The 5-point operator of -div(k grad u) with harmonic-mean face coefficients,
+ * scaled by h^2 (A' = h^2 A_h): row i has c_i = k_W + k_E + k_S + k_N on the
+ * diagonal and -k_f for its faces W, E, S, N.  The four face arrays are one
+ * BFP block (int16 mantissas, exponent e_k); the centre is their exact
+ * integer sum.  Damped Jacobi uses per-point weights q_i 2^e_q ~ omega / c_i.
+ *   n     : interior points (x, y); every array is n[1] rows of pitch ld
+ *           (ld >= n[0], ld % 8 == 0), device memory, 16-byte aligned;
+ *   k     : face mantissas W, E, S, N (k[f][j ld + i]);   e_k : their exponent;
+ *   q, e_q: smoother weights;
+ *   a_norm: max_i 2 c_i (||A'||_inf = a_norm 2^e_k);  q_norm: max_i q_i;
+ *   omega : the damping, used by the residual's gamma rule.
+ * The arrays are owned by the caller, or by a hierarchy
+ * (bfp_hierarchy_var_level). */
+typedef struct {
+  int64_t n[2];
+  int64_t ld;
+  const int16_t* k[4];
+  int64_t e_k;
+  const int16_t* q;
+  int64_t e_q;
+  int64_t a_norm;
+  int64_t q_norm;
+  bfp_scalar omega;
+} bfp_varstencil;
+
+/* z = A' x (exact, then q).  gamma rule ||A'||_inf ||x||_inf, w_add 2. */
+int32_t bfp_var_apply(const bfp_varstencil* A, const bfp_vec* x, const bfp_vec* z, const bfp_q* q,
+                      const bfp_stats* st, bfp_stream stream);
+/* rv = A' y - r (the paper's residual sign).  gamma (omega + 1/4) ||r||_inf
+ * (Table tab:estimates, V residual row), w_add 4. */
+int32_t bfp_var_residual(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* rv,
+                         const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+/* y_out = y + Q (r - A' y), Q = diag(q 2^e_q); y == NULL: y_out = Q r.  gamma
+ * ||y|| + ||q|| ||r|| (||I - Q A'||_inf = 1 when q_i c_i 2^(e_q+e_k) <= 1),
+ * w_add 2.  Requires -40 <= e_q + e_k <= 0. */
+int32_t bfp_var_jacobi(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* y_out,
+                       const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+/* All three: 2D vectors of shape n, 1 <= w <= 24; BFP_ERR_SHAPE on a shape
+ * mismatch, BFP_ERR_WIDTH when the exact width would pass 62 bits, BFP_ERR_ARG
+ * for null arrays or aliasing. */
+
 /* ---- no-allocation variant ---------------------------------------------------- */
 
 /* bfp_jacobi for callers that cannot allocate device memory at the call site
@@ -312,6 +355,23 @@ typedef struct {
  * read the residual norm.  Returns BFP_ERR_NOCONV when max_iter is reached. */
 int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts* o,
                  bfp_ir_report* rep, bfp_stream stream);
+
+/* Hierarchy of the variable-coefficient problem -div(k grad u) = f (2D):
+ * k_nodes are k at the (n+2) x (n+2) grid nodes, boundary included, host
+ * doubles row-major [y][x].  Each level's operator comes from the node values
+ * injected to that level (coarse node c = fine node 2c), set up on the host:
+ * harmonic-mean faces ((2 a) b) / (a + b) in FP64, floor-quantised to 16-bit
+ * mantissas with one exponent (the largest face gets 15 significant bits), and
+ * weights q_i = floor(omega_m 2^s / c_i) with the largest s that keeps q in 16
+ * bits.  opts: ndim 2, arith BFP, w <= 24 (coarse_onchip is ignored).  The
+ * solver calls (bfp_vcycle, bfp_fmg, bfp_ir_iterate, ir_solve,
+ * bfp_ir_residual) then use these operators, b' = h^2 f, and the FP64 IR
+ * residual b' - (c x - (((k_W x_W + k_E x_E) + k_S x_S) + k_N x_N)) with the
+ * unquantised FP64 faces, c = ((k_W + k_E) + k_S) + k_N. */
+int32_t bfp_hierarchy_create_var(const bfp_solver_opts* o, const double* k_nodes, bfp_hierarchy** h);
+/* Level l's operator (device arrays owned by the hierarchy; 0 = finest).
+ * BFP_ERR_ARG for a constant-coefficient hierarchy or a bad level. */
+int32_t bfp_hierarchy_var_level(const bfp_hierarchy* h, int32_t level, bfp_varstencil* out);
 
 /* ---- batched solves (many independent instances, one graph launch) ------------ */
 /* count independent hierarchies (opts[i]: size, width, mode, schedule of

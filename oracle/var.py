@@ -85,10 +85,10 @@ def smoother_weights(c: np.ndarray, e_k: int, om: B.Scalar, w: int = W_K):
     while fits(s + 1):
         s += 1
 
-    def qi(ci: int) -> int:
-        return (wm << s) // ci if s >= 0 else wm // (ci << -s)
-    q = np.array([qi(int(ci)) for ci in c.ravel()], dtype=np.int64).reshape(c.shape)
-    return q, int(om.e) - e_k - s
+    # exact integer floor division (omega_m 2^s < 2^15 c_min < 2^33: int64 is exact)
+    c64 = np.asarray(c, dtype=np.int64)
+    q = (np.int64(wm << s) // c64) if s >= 0 else (np.int64(wm) // (c64 << np.int64(-s)))
+    return q.astype(np.int64), int(om.e) - e_k - s
 
 
 @dataclass

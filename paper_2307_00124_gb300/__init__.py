@@ -61,6 +61,12 @@ class bfp_stencil(C.Structure):
                 ("e", C.c_int64), ("omega", bfp_scalar)]
 
 
+class bfp_varstencil(C.Structure):
+    _fields_ = [("n", C.c_int64 * 2), ("ld", C.c_int64), ("k", C.c_void_p * 4), ("e_k", C.c_int64),
+                ("q", C.c_void_p), ("e_q", C.c_int64), ("a_norm", C.c_int64), ("q_norm", C.c_int64),
+                ("omega", bfp_scalar)]
+
+
 class bfp_solver_opts(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("w", C.c_int32), ("n", C.c_int64), ("mode", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
@@ -110,6 +116,13 @@ _sig = {
                                        P(bfp_stats), C.c_void_p]),
     "bfp_solver_opts_default": (C.c_int32, [C.c_int32, C.c_int64, C.c_int32, P(bfp_solver_opts)]),
     "bfp_hierarchy_create": (C.c_int32, [P(bfp_solver_opts), P(C.c_void_p)]),
+    "bfp_hierarchy_create_var": (C.c_int32, [P(bfp_solver_opts), C.c_void_p, P(C.c_void_p)]),
+    "bfp_hierarchy_var_level": (C.c_int32, [C.c_void_p, C.c_int32, P(bfp_varstencil)]),
+    "bfp_var_apply": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
+    "bfp_var_residual": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q),
+                                     P(bfp_stats), C.c_void_p]),
+    "bfp_var_jacobi": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q),
+                                   P(bfp_stats), C.c_void_p]),
     "bfp_hierarchy_destroy": (None, [C.c_void_p]),
     "bfp_hierarchy_read_stats": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "bfp_hierarchy_reset_stats": (C.c_int32, [C.c_void_p, C.c_void_p]),
@@ -367,6 +380,22 @@ def bfp_jacobi(A, y, r, y_out, qq, stats=None, stream=None):
                            _st(stats), _stream(stream)), "bfp_jacobi")
 
 
+def bfp_var_apply(A, x, z, qq, stats=None, stream=None):
+    _check(_lib.bfp_var_apply(C.byref(A), C.byref(x.struct()), C.byref(z.struct()), C.byref(qq), _st(stats),
+                              _stream(stream)), "bfp_var_apply")
+
+
+def bfp_var_residual(A, y, r, rv, qq, stats=None, stream=None):
+    _check(_lib.bfp_var_residual(C.byref(A), C.byref(y.struct()), C.byref(r.struct()), C.byref(rv.struct()),
+                                 C.byref(qq), _st(stats), _stream(stream)), "bfp_var_residual")
+
+
+def bfp_var_jacobi(A, y, r, y_out, qq, stats=None, stream=None):
+    yp = None if y is None else C.byref(y.struct())
+    _check(_lib.bfp_var_jacobi(C.byref(A), yp, C.byref(r.struct()), C.byref(y_out.struct()), C.byref(qq),
+                               _st(stats), _stream(stream)), "bfp_var_jacobi")
+
+
 def bfp_jacobi_noalloc(A, y, r, y_out, qq, stats=None, stream=None):
     """bfp_jacobi whose qcomp window lives in the library's static device array (no allocation)."""
     yp = None if y is None else C.byref(y.struct())
@@ -422,11 +451,26 @@ def bfp_solver_opts_default(ndim: int, n: int, w: int) -> bfp_solver_opts:
 class Hierarchy:
     """Owns a bfp_hierarchy (level buffers, captured graphs) on the current device."""
 
-    def __init__(self, opts: bfp_solver_opts):
+    def __init__(self, opts: bfp_solver_opts, k_nodes=None):
+        """k_nodes: None (the constant-coefficient model problem) or the (n+2) x (n+2) node
+        values of k for -div(k grad u) = f (2D, host float64, [y, x], boundary included)."""
         self.opts = opts
         h = C.c_void_p()
-        _check(_lib.bfp_hierarchy_create(C.byref(opts), C.byref(h)), "bfp_hierarchy_create")
+        if k_nodes is None:
+            _check(_lib.bfp_hierarchy_create(C.byref(opts), C.byref(h)), "bfp_hierarchy_create")
+        else:
+            k = np.ascontiguousarray(k_nodes, dtype=np.float64)
+            if k.shape != (opts.n + 2, opts.n + 2):
+                raise ValueError("k_nodes must have shape (n+2, n+2)")
+            _check(_lib.bfp_hierarchy_create_var(C.byref(opts), k.ctypes.data_as(C.c_void_p), C.byref(h)),
+                   "bfp_hierarchy_create_var")
         self.h = h
+
+    def var_level(self, level: int = 0) -> bfp_varstencil:
+        """The variable-coefficient operator of a level (arrays owned by the hierarchy)."""
+        out = bfp_varstencil()
+        _check(_lib.bfp_hierarchy_var_level(self.h, level, C.byref(out)), "bfp_hierarchy_var_level")
+        return out
 
     def close(self):
         if self.h:

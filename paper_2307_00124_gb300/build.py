@@ -22,6 +22,7 @@ LIB = os.path.join(LIBDIR, "libbfpmg.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 
 

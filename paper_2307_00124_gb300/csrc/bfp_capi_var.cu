@@ -1,0 +1,199 @@
+// bfp_capi_var.cu -- C ABI: the variable-coefficient 5-point operator of
+// -div(k grad u) (2D; the configs' variable-coefficient workload, not in the
+// paper): bfp_var_apply, bfp_var_residual, bfp_var_jacobi.
+//
+// Each op forms its exact result per element in int64 and quantises it
+// through the generic two-group quantiser (qcomp / nnqcomp, Alg. qcomp and
+// Alg. nnqcomp):
+//   apply    : H = A'x = c x - (k_W x_W + k_E x_E + k_S x_S + k_N x_N)  at e_k + e_x
+//   residual : H = A'y at e_k + e_y,  L = -r at e_r
+//   jacobi   : H = y 2^s - q A'y at e_q + e_k + e_y (s = -(e_q + e_k)),  L = q r at e_q + e_r
+//   jacobi0  : H = q r at e_q + e_r
+// with c = k_W + k_E + k_S + k_N exact.  The face arrays share e_k (one BFP
+// block); q is the per-point smoother weight block.
+#include "bfp_desc.h"
+
+using namespace bfp;
+
+namespace {
+
+struct VarView {
+  VIn k[4];   // W, E, S, N
+  VIn q;
+};
+
+VIn kview(const int16_t* p, const bfp_varstencil* A) {
+  VIn v;
+  v.m = p;
+  v.ld = A->ld;
+  v.nx = A->n[0];
+  v.ny = A->n[1];
+  v.nz = 1;
+  return v;
+}
+
+template <class T, int KIND>
+struct OpVar {
+  VIn y, r;
+  VarView A;
+  int32_t s;   // jacobi: left shift of y into the H group
+  __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
+    if (KIND == kJacobi0) {
+      int32_t rv[8], qv[8];
+      ld8<T>(r, row, c0, rv);
+      ldv<int16_t, 8>(A.q, row, c0, qv);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) { H[k] = (int64_t)qv[k] * rv[k]; L[k] = 0; }
+      return;
+    }
+    const int64_t ny = y.ny;
+    int32_t ctr[8], up[8], dn[8], kw[8], ke[8], ks[8], kn[8], rv[8], qv[8];
+    ld8<T>(y, row, c0, ctr);
+    ld8<T>(y, row - 1, c0, dn);                  // rows outside the grid read 0
+    ld8<T>(y, row + 1 < ny ? row + 1 : -1, c0, up);
+    const int64_t wv = ld1<T>(y, row, c0 - 1), ev = ld1<T>(y, row, c0 + 8);
+    ldv<int16_t, 8>(A.k[0], row, c0, kw);
+    ldv<int16_t, 8>(A.k[1], row, c0, ke);
+    ldv<int16_t, 8>(A.k[2], row, c0, ks);
+    ldv<int16_t, 8>(A.k[3], row, c0, kn);
+    if (KIND != kApply) ld8<T>(r, row, c0, rv);
+    if (KIND == kJacobi) ldv<int16_t, 8>(A.q, row, c0, qv);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t W = k == 0 ? wv : ctr[k - 1];
+      const int64_t E = k == 7 ? ev : ctr[k + 1];
+      const int64_t c = (int64_t)kw[k] + ke[k] + ks[k] + kn[k];
+      const int64_t ay = c * ctr[k] - ((int64_t)kw[k] * W + (int64_t)ke[k] * E + (int64_t)ks[k] * dn[k] +
+                                       (int64_t)kn[k] * up[k]);
+      if (KIND == kApply) {
+        H[k] = ay;
+        L[k] = 0;
+      } else if (KIND == kResidual) {
+        H[k] = ay;
+        L[k] = -(int64_t)rv[k];
+      } else {
+        H[k] = (int64_t)((uint64_t)(int64_t)ctr[k] << s) - (int64_t)qv[k] * ay;
+        L[k] = (int64_t)qv[k] * rv[k];
+      }
+    }
+  }
+};
+
+int32_t check_var(const bfp_varstencil* A, bool need_q) {
+  if (!A || A->n[0] < 0 || A->n[1] < 0 || A->ld < A->n[0] || A->ld % 8 != 0 || A->ld <= 0) return BFP_ERR_ARG;
+  for (int f = 0; f < 4; ++f)
+    if (!A->k[f] || reinterpret_cast<uintptr_t>(A->k[f]) % 16 != 0) return BFP_ERR_ARG;
+  if (need_q && (!A->q || reinterpret_cast<uintptr_t>(A->q) % 16 != 0)) return BFP_ERR_ARG;
+  if (A->a_norm < 0 || A->a_norm >= (1ll << 20) || A->q_norm < 0 || A->q_norm >= (1ll << 15)) return BFP_ERR_ARG;
+  return BFP_OK;
+}
+
+bool var_shape(const bfp_varstencil* A, const bfp_vec* v) {
+  return v->ndim == 2 && v->n[0] == A->n[0] && v->n[1] == A->n[1];
+}
+
+VarView view(const bfp_varstencil* A) {
+  VarView v;
+  for (int f = 0; f < 4; ++f) v.k[f] = kview(A->k[f], A);
+  v.q = kview(A->q ? A->q : A->k[0], A);
+  return v;
+}
+
+template <int KIND>
+int32_t var_launch(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, const QDesc& d, const bfp_vec* out,
+                   int32_t s, cudaStream_t st) {
+  const bfp_vec* in = y ? y : r;
+  const VIn yv = vin(y ? y : r), rv = vin(r ? r : in);
+  if (is32(in)) return launch_quant(OpVar<int32_t, KIND>{yv, rv, view(A), s}, d, out, st);
+  return launch_quant(OpVar<int16_t, KIND>{yv, rv, view(A), s}, d, out, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t bfp_var_apply(const bfp_varstencil* A, const bfp_vec* x, const bfp_vec* z, const bfp_q* q,
+                      const bfp_stats* st, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_var(A, false)) || (rc = check_vec(x)) || (rc = check_vec(z))) return rc;
+  if (!var_shape(A, x) || !same_shape(x, z)) return BFP_ERR_SHAPE;
+  if (x->w > 24) return BFP_ERR_WIDTH;
+  if (overlaps(x, z)) return BFP_ERR_ARG;
+  QDesc d = blank_desc();
+  d.ch = A->e_k; d.ha = 1; d.two = 0;
+  d.hbits = hmsb(A->a_norm) + x->w + 1;
+  d.ng = 1; d.gv[0] = 0; d.gm[0] = (uint64_t)A->a_norm; d.ge[0] = A->e_k;   // ||A'|| ||x||
+  if ((rc = fill_q(d, q, z, 2))) return rc;
+  d.meta_a = x->meta; d.meta_out = z->meta; d.stats = st ? st->counters : nullptr;
+  return var_launch<kApply>(A, x, nullptr, d, z, 0, as_stream(stream));
+}
+
+int32_t bfp_var_residual(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* rv,
+                         const bfp_q* q, const bfp_stats* st, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_var(A, false)) || (rc = check_vec(y)) || (rc = check_vec(r)) || (rc = check_vec(rv))) return rc;
+  if (!var_shape(A, y) || !same_shape(y, r) || !same_shape(y, rv)) return BFP_ERR_SHAPE;
+  if (y->w > 24 || r->w > 24) return BFP_ERR_WIDTH;
+  if (is32(y) != is32(r)) return BFP_ERR_ARG;
+  if (overlaps(y, rv) || overlaps(r, rv)) return BFP_ERR_ARG;
+  QDesc d = blank_desc();
+  d.ch = A->e_k; d.ha = 1;
+  d.cl = 0; d.lb = 1;
+  d.two = 1;
+  d.hbits = hmsb(A->a_norm) + y->w + 1;
+  d.lbits = r->w + 1;
+  // gamma = (omega + 1/4) ||r|| (the V residual row, as for constant coefficients)
+  const int64_t om = iabs64(A->omega.m), oe = A->omega.e;
+  uint64_t cm;
+  int64_t ce;
+  if (oe <= -2) { cm = (uint64_t)om + (1ull << (-2 - oe)); ce = oe; }
+  else {
+    if (oe + 2 > 30) return BFP_ERR_ARG;
+    cm = ((uint64_t)om << (oe + 2)) + 1ull; ce = -2;
+  }
+  if (cm >= (1ull << 32)) return BFP_ERR_ARG;
+  d.ng = 1; d.gv[0] = 1; d.gm[0] = cm; d.ge[0] = ce;
+  if ((rc = fill_q(d, q, rv, 4))) return rc;
+  d.meta_a = y->meta; d.meta_b = r->meta; d.meta_out = rv->meta; d.stats = st ? st->counters : nullptr;
+  return var_launch<kResidual>(A, y, r, d, rv, 0, as_stream(stream));
+}
+
+int32_t bfp_var_jacobi(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* y_out,
+                       const bfp_q* q, const bfp_stats* st, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_var(A, true)) || (rc = check_vec(r)) || (rc = check_vec(y_out))) return rc;
+  if (!var_shape(A, r) || !same_shape(r, y_out)) return BFP_ERR_SHAPE;
+  if (r->w > 24) return BFP_ERR_WIDTH;
+  if (overlaps(r, y_out)) return BFP_ERR_ARG;
+  QDesc d = blank_desc();
+  const int qb = hmsb(A->q_norm);
+  if (!y) {
+    d.ch = A->e_q; d.hb = 1; d.two = 0;            // Q r at e_q + e_r
+    d.hbits = qb + r->w + 1;
+    d.ng = 1; d.gv[0] = 1; d.gm[0] = (uint64_t)A->q_norm; d.ge[0] = A->e_q;   // ||q|| ||r||
+    if ((rc = fill_q(d, q, y_out, 2))) return rc;
+    d.meta_b = r->meta; d.meta_out = y_out->meta; d.stats = st ? st->counters : nullptr;
+    return var_launch<kJacobi0>(A, nullptr, r, d, y_out, 0, as_stream(stream));
+  }
+  if ((rc = check_vec(y))) return rc;
+  if (!same_shape(y, r)) return BFP_ERR_SHAPE;
+  if (y->w > 24) return BFP_ERR_WIDTH;
+  if (is32(y) != is32(r)) return BFP_ERR_ARG;
+  if (overlaps(y, y_out)) return BFP_ERR_ARG;
+  const int64_t s = -(A->e_q + A->e_k);
+  if (s < 0 || s > 40) return BFP_ERR_ARG;
+  d.ch = A->e_q + A->e_k; d.ha = 1;                 // y 2^s - q A'y at e_q + e_k + e_y
+  d.cl = A->e_q; d.lb = 1;                          // q r at e_q + e_r
+  d.two = 1;
+  const int hb1 = y->w + (int)s, hb2 = qb + hmsb(A->a_norm) + y->w;
+  d.hbits = (hb1 > hb2 ? hb1 : hb2) + 2;
+  d.lbits = qb + r->w + 1;
+  d.ng = 2;                                         // gamma = ||y|| + ||q|| ||r||
+  d.gv[0] = 0; d.gm[0] = 1; d.ge[0] = 0;
+  d.gv[1] = 1; d.gm[1] = (uint64_t)A->q_norm; d.ge[1] = A->e_q;
+  if ((rc = fill_q(d, q, y_out, 2))) return rc;
+  d.meta_a = y->meta; d.meta_b = r->meta; d.meta_out = y_out->meta; d.stats = st ? st->counters : nullptr;
+  return var_launch<kJacobi>(A, y, r, d, y_out, (int32_t)s, as_stream(stream));
+}
+
+}  // extern "C"

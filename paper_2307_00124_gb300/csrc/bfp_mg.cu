@@ -190,6 +190,47 @@ __global__ void __launch_bounds__(256) k_ir_resnorm(const double* __restrict__ b
   }
 }
 
+// FP64 IR residual of the variable-coefficient operator (2D, dense n x n):
+// r = b' - (c x - (((k_W x_W + k_E x_E) + k_S x_S) + k_N x_N)), every product and sum
+// correctly rounded in this order, zero outside the grid.
+__global__ void __launch_bounds__(256) k_var_res64(const double* __restrict__ b, double bscale,
+                                                   const double* __restrict__ x, const double* __restrict__ kw,
+                                                   const double* __restrict__ ke, const double* __restrict__ ks,
+                                                   const double* __restrict__ kn, const double* __restrict__ c64,
+                                                   int64_t n, double* __restrict__ r) {
+  const int64_t total = n * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    const double W = i > 0 ? x[idx - 1] : 0.0, E = i + 1 < n ? x[idx + 1] : 0.0;
+    const double S = j > 0 ? x[idx - n] : 0.0, N = j + 1 < n ? x[idx + n] : 0.0;
+    double s = __dadd_rn(__dmul_rn(kw[idx], W), __dmul_rn(ke[idx], E));
+    s = __dadd_rn(s, __dmul_rn(ks[idx], S));
+    s = __dadd_rn(s, __dmul_rn(kn[idx], N));
+    const double ax = __dsub_rn(__dmul_rn(c64[idx], x[idx]), s);
+    r[idx] = __dsub_rn(__dmul_rn(b[idx], bscale), ax);
+  }
+}
+
+// max |r| and max |b' scale| (ir_solve's stopping test)
+__global__ void __launch_bounds__(256) k_absmax2(const double* __restrict__ r, const double* __restrict__ b,
+                                                 double bscale, int64_t total, unsigned long long* out) {
+  double mx = 0.0, mb = 0.0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    mx = fmax(mx, fabs(r[idx]));
+    mb = fmax(mb, fabs(__dmul_rn(b[idx], bscale)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(mx));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(mb));
+  }
+}
+
 // ---- float baselines: FP64 IR residual rounded to FP32 (then BF16), update, conversions ----
 
 template <class S>
@@ -311,6 +352,12 @@ struct Level {
   double* b = nullptr;            // FP64 right-hand side (levels >= 1)
   double* x = nullptr;            // FP64 iterate (levels >= 1)
   flt_vec fr{}, fya{}, fyb{}, frv{};   // float baselines: the same buffers as float vectors
+  // variable coefficients: the level's operator, its unquantised FP64 faces and centre
+  // (dense n x n) and the FP64 IR residual before quantisation
+  bfp_varstencil vs{};
+  double* kf64[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* c64 = nullptr;
+  double* r64 = nullptr;
 };
 
 }  // namespace
@@ -333,6 +380,7 @@ struct bfp_hierarchy {
   int meta_off = 0, ops_off = 0, bufs_off = 0, data_off = 0;
   std::vector<CoarseOp*> d_ops;          // per start level k >= kc
   std::vector<int> nops, rbuf, ybuf, runk;
+  int var = 0;                           // variable-coefficient operator (bfp_hierarchy_create_var)
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
   flt_vec fy0{};                         // its float counterpart (float hierarchies)
   // captured IR step
@@ -650,7 +698,10 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
     return BFP_OK;
   }
   const bool coarsest = (k + 1 == (int)h->lv.size());
-  if (coarsest && sweep_run_fits(h, k)) {   // the coarsest level's sweeps in one launch
+  auto jacobi = [&](const bfp_vec* y, const bfp_vec* out) -> int32_t {
+    return h->var ? bfp_var_jacobi(&L.vs, y, r, out, &q.q, &q.st, s) : bfp_jacobi(&h->A, y, r, out, &q.q, &q.st, s);
+  };
+  if (coarsest && !h->var && sweep_run_fits(h, k)) {   // the coarsest level's sweeps in one launch
     bfp_vec y = at_slot(bufA);
     TRY(sweep_run(h, k, r, &y, s));
     *res = y;
@@ -663,17 +714,18 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
   const bfp_vec* curb = (writes % 2 == 1) ? bufA : bufB;
   const bfp_vec* othb = (curb == bufA) ? bufB : bufA;
   bfp_vec cur = at_slot(curb);
-  TRY(bfp_jacobi(&h->A, nullptr, r, &cur, &q.q, &q.st, s));            // relaxation from y = 0
+  TRY(jacobi(nullptr, &cur));                                          // relaxation from y = 0
   for (int i = 1; i < nu1; ++i) {
     bfp_vec nx = at_slot(othb);
-    TRY(bfp_jacobi(&h->A, &cur, r, &nx, &q.q, &q.st, s));
+    TRY(jacobi(&cur, &nx));
     cur = nx;
     std::swap(curb, othb);
   }
   if (!coarsest) {
     Level& C = h->lv[k + 1];
     bfp_vec rv = at_slot(&L.rv);
-    TRY(bfp_residual(&h->A, &cur, r, &rv, &q.q, &q.st, s));            // r_v = A y - r
+    if (h->var) TRY(bfp_var_residual(&L.vs, &cur, r, &rv, &q.q, &q.st, s));   // r_v = A y - r
+    else TRY(bfp_residual(&h->A, &cur, r, &rv, &q.q, &q.st, s));
     bfp_vec rc = at_slot(&C.r);
     TRY(bfp_restrict(&rv, &rc, &q.q, &q.st, s));                       // r_c = R~ r_v
     bfp_vec d;
@@ -684,7 +736,7 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
     std::swap(curb, othb);
     for (int i = 0; i < h->o.nu2; ++i) {
       bfp_vec nx2 = at_slot(othb);
-      TRY(bfp_jacobi(&h->A, &cur, r, &nx2, &q.q, &q.st, s));
+      TRY(jacobi(&cur, &nx2));
       cur = nx2;
       std::swap(curb, othb);
     }
@@ -707,6 +759,14 @@ Grid grid_of(int nd, int64_t n) { return Grid{n, n, nd == 3 ? n : 1}; }
 // r (BFP, width w, normalised) = quant(b' - A' x) on level k (Alg. ir residual line)
 int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, const double* x, const bfp_vec* r,
                       cudaStream_t s) {
+  if (h->var) {   // variable coefficients: the FP64 residual, then quant() (bfp_from_f64)
+    const Level& L = h->lv[k];
+    k_var_res64<<<grid_for(L.n * L.n, 256), 256, 0, s>>>(b, bscale, x, L.kf64[0], L.kf64[1], L.kf64[2], L.kf64[3],
+                                                         L.c64, L.n, L.r64);
+    note_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return BFP_ERR_CUDA;
+    return bfp_from_f64(L.r64, r, s);
+  }
   const int nd = h->o.ndim;
   const Grid g = grid_of(nd, h->lv[k].n);
   const double cdiag = (2.0 * nd) / pscale(nd), cnb = -1.0 / pscale(nd);
@@ -830,9 +890,121 @@ int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double*
   return ir_update(x, &y, s);
 }
 
-double bscale_of(int nd, int64_t n) {
-  const double hh = 1.0 / (double)(n + 1);
-  return hh * hh / pscale(nd);   // an exact power of two for n + 1 = 2^J
+// ---- variable coefficients: host setup of every level's operator ----
+
+double harmonic(double a, double b) { return ((2.0 * a) * b) / (a + b); }
+
+// Level l's operator from the node values K ((n+2)^2, [y][x], boundary included): faces,
+// one-exponent int16 face block, integer smoother weights, FP64 faces for the IR residual.
+int32_t var_level_setup(bfp_hierarchy* h, Level& L, const std::vector<double>& K) {
+  const int64_t n = L.n, m = n + 2, ld = bfp_pitch(n), pts = n * n;
+  std::vector<double> F[4];
+  for (auto& f : F) f.assign((size_t)pts, 0.0);
+  double M = 0.0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      const double c = K[(j + 1) * m + i + 1];
+      const int64_t p = j * n + i;
+      F[0][p] = harmonic(K[(j + 1) * m + i], c);
+      F[1][p] = harmonic(c, K[(j + 1) * m + i + 2]);
+      F[2][p] = harmonic(K[j * m + i + 1], c);
+      F[3][p] = harmonic(c, K[(j + 2) * m + i + 1]);
+      for (auto& f : F) {
+        if (!(f[p] > 0.0) || !std::isfinite(f[p])) return BFP_ERR_ARG;
+        M = f[p] > M ? f[p] : M;
+      }
+    }
+  int fe = 0;
+  std::frexp(M, &fe);
+  const int64_t e_k = fe - 15;                      // the largest face: 15 significant bits
+  std::vector<int16_t> km[4];
+  for (auto& v : km) v.assign((size_t)(n * ld), 0);
+  std::vector<int64_t> c((size_t)pts, 0);
+  int64_t cmin = INT64_MAX, cmax = 0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t p = j * n + i;
+      int64_t sum = 0;
+      for (int f = 0; f < 4; ++f) {
+        const double v = std::floor(std::ldexp(F[f][p], (int)-e_k));
+        if (v < 0.0 || v >= 32768.0) return BFP_ERR_ARG;
+        km[f][j * ld + i] = (int16_t)v;
+        sum += (int64_t)v;
+      }
+      c[p] = sum;
+      cmin = sum < cmin ? sum : cmin;
+      cmax = sum > cmax ? sum : cmax;
+    }
+  if (cmin <= 0) return BFP_ERR_ARG;
+  // q_i = floor(omega_m 2^s / c_i), the largest s with max q < 2^15
+  const int64_t wm = h->A.omega.m;
+  if (wm <= 0 || wm >= (1ll << 16)) return BFP_ERR_ARG;
+  const int64_t lim = cmin << 15;                   // omega_m 2^s < lim
+  auto bitlen = [](int64_t v) { int b = 0; while (v) { ++b; v >>= 1; } return b; };
+  auto fits = [&](int sv) { return sv >= 0 ? (wm << sv) < lim : wm < (lim << -sv); };
+  int sh = bitlen(lim) - bitlen(wm);
+  while (!fits(sh)) --sh;
+  while (sh < 40 && fits(sh + 1)) ++sh;
+  std::vector<int16_t> qm((size_t)(n * ld), 0);
+  int64_t qmax = 0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t ci = c[j * n + i];
+      const int64_t qv = sh >= 0 ? (wm << sh) / ci : wm / (ci << -sh);
+      qm[j * ld + i] = (int16_t)qv;
+      qmax = qv > qmax ? qv : qmax;
+    }
+  std::vector<double> c64((size_t)pts);
+  for (int64_t p = 0; p < pts; ++p) c64[p] = ((F[0][p] + F[1][p]) + F[2][p]) + F[3][p];
+  // device copies
+  const size_t kb = (size_t)(n * ld) * sizeof(int16_t), fb = (size_t)pts * sizeof(double);
+  int16_t* dk[4];
+  for (int f = 0; f < 4; ++f) {
+    dk[f] = (int16_t*)dalloc(h, kb ? kb : 16);
+    L.kf64[f] = (double*)dalloc(h, fb ? fb : 16);
+    if (!dk[f] || !L.kf64[f]) return BFP_ERR_CUDA;
+    if (kb && cudaMemcpy(dk[f], km[f].data(), kb, cudaMemcpyHostToDevice) != cudaSuccess) return BFP_ERR_CUDA;
+    if (fb && cudaMemcpy(L.kf64[f], F[f].data(), fb, cudaMemcpyHostToDevice) != cudaSuccess) return BFP_ERR_CUDA;
+  }
+  int16_t* dq = (int16_t*)dalloc(h, kb ? kb : 16);
+  L.c64 = (double*)dalloc(h, fb ? fb : 16);
+  L.r64 = (double*)dalloc(h, fb ? fb : 16);
+  if (!dq || !L.c64 || !L.r64) return BFP_ERR_CUDA;
+  if (kb && cudaMemcpy(dq, qm.data(), kb, cudaMemcpyHostToDevice) != cudaSuccess) return BFP_ERR_CUDA;
+  if (fb && cudaMemcpy(L.c64, c64.data(), fb, cudaMemcpyHostToDevice) != cudaSuccess) return BFP_ERR_CUDA;
+  bfp_varstencil& V = L.vs;
+  V.n[0] = n; V.n[1] = n; V.ld = ld;
+  for (int f = 0; f < 4; ++f) V.k[f] = dk[f];
+  V.e_k = e_k;
+  V.q = dq;
+  V.e_q = h->A.omega.e - e_k - sh;
+  V.a_norm = 2 * cmax;
+  V.q_norm = qmax;
+  V.omega = h->A.omega;
+  return BFP_OK;
+}
+
+int32_t var_setup(bfp_hierarchy* h, const double* k_nodes) {
+  int64_t mprev = h->o.n + 2;
+  std::vector<double> K(k_nodes, k_nodes + mprev * mprev);
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    Level& L = h->lv[l];
+    if (l > 0) {   // injection: coarse node c sits on fine node 2c
+      const int64_t m = L.n + 2;
+      std::vector<double> Kc((size_t)(m * m));
+      for (int64_t j = 0; j < m; ++j)
+        for (int64_t i = 0; i < m; ++i) Kc[j * m + i] = K[(2 * j) * mprev + 2 * i];
+      K.swap(Kc);
+      mprev = m;
+    }
+    TRY(var_level_setup(h, L, K));
+  }
+  return BFP_OK;
+}
+
+double bscale_of(const bfp_hierarchy* h) {
+  const double hh = 1.0 / (double)(h->o.n + 1);
+  return h->var ? hh * hh : hh * hh / pscale(h->o.ndim);   // an exact power of two for n + 1 = 2^J
 }
 
 }  // namespace
@@ -950,6 +1122,32 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   return BFP_OK;
 }
 
+int32_t bfp_hierarchy_create_var(const bfp_solver_opts* o, const double* k_nodes, bfp_hierarchy** out) {
+  if (!o || !k_nodes || !out) return BFP_ERR_ARG;
+  *out = nullptr;
+  if (o->ndim != 2 || o->arith != BFP_ARITH_BFP || o->w > 24) return BFP_ERR_ARG;
+  bfp_solver_opts oo = *o;
+  oo.coarse_onchip = 0;                              // the on-chip cycle has the constant operator only
+  bfp_hierarchy* h = nullptr;
+  int32_t rc = bfp_hierarchy_create(&oo, &h);
+  if (rc) return rc;
+  h->var = 1;
+  rc = var_setup(h, k_nodes);
+  if (rc == BFP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = BFP_ERR_CUDA;
+  if (rc) {
+    bfp_hierarchy_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return BFP_OK;
+}
+
+int32_t bfp_hierarchy_var_level(const bfp_hierarchy* h, int32_t level, bfp_varstencil* out) {
+  if (!h || !out || !h->var || level < 0 || level >= (int32_t)h->lv.size()) return BFP_ERR_ARG;
+  *out = h->lv[level].vs;
+  return BFP_OK;
+}
+
 int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream) {
   if (!h || !host8) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
@@ -986,7 +1184,7 @@ int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_str
 
 static int32_t ir_iterate_direct(bfp_hierarchy* h, const double* f, double* x, int32_t k, cudaStream_t s) {
   TileScope ts(h->o.tile_rows);
-  const double bs = bscale_of(h->o.ndim, h->o.n);
+  const double bs = bscale_of(h);
   for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));
   return BFP_OK;
 }
@@ -1022,7 +1220,7 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
   const int nd = h->o.ndim;
   const int nl = (int)h->lv.size();
   const double rscale = nd == 2 ? 0.25 : 0.0625;   // R~ = P^T (2D), P^T/2 (3D): weights prod(2-|d|) * 2^e_R
-  const double bs0 = bscale_of(nd, h->o.n);
+  const double bs0 = bscale_of(h);
   // right-hand sides b_k = R~ b_{k-1}, b_0 = s f
   for (int k = 1; k < nl; ++k) {
     const Level& F = h->lv[k - 1];
@@ -1076,7 +1274,7 @@ int32_t bfp_ir_residual(bfp_hierarchy* h, const double* f, const double* x, cons
   int32_t rc;
   if ((rc = check_vec(r))) return rc;
   if (!same_shape(r, &h->lv[0].r)) return BFP_ERR_SHAPE;
-  return ir_residual_q(h, 0, f, bscale_of(h->o.ndim, h->o.n), x, r, as_stream(stream));
+  return ir_residual_q(h, 0, f, bscale_of(h), x, r, as_stream(stream));
 }
 
 int32_t flt_vcycle(bfp_hierarchy* h, const flt_vec* r, const flt_vec* y, bfp_stream stream) {
@@ -1110,13 +1308,21 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
   const int nd = h->o.ndim;
   const Grid g = grid_of(nd, h->o.n);
   const double cdiag = (2.0 * nd) / pscale(nd), cnb = -1.0 / pscale(nd);
-  const double bs = bscale_of(nd, h->o.n);
+  const double bs = bscale_of(h);
   const int64_t tot = g.nx * g.ny * g.nz;
   for (int it = 0;; ++it) {
     if (cudaMemsetAsync(h->norms, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return BFP_ERR_CUDA;
-    if (nd == 2) k_ir_resnorm<2><<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, g, cdiag, cnb, h->norms);
-    else k_ir_resnorm<3><<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, g, cdiag, cnb, h->norms);
-    note_launches(1);
+    if (h->var) {
+      const Level& L = h->lv[0];
+      k_var_res64<<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, L.kf64[0], L.kf64[1], L.kf64[2], L.kf64[3], L.c64,
+                                                     L.n, L.r64);
+      k_absmax2<<<grid_for(tot, 256), 256, 0, s>>>(L.r64, f, bs, tot, h->norms);
+      note_launches(2);
+    } else {
+      if (nd == 2) k_ir_resnorm<2><<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, g, cdiag, cnb, h->norms);
+      else k_ir_resnorm<3><<<grid_for(tot, 256), 256, 0, s>>>(f, bs, x, g, cdiag, cnb, h->norms);
+      note_launches(1);
+    }
     unsigned long long hn[2] = {0, 0};
     if (cudaMemcpyAsync(hn, h->norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BFP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return BFP_ERR_CUDA;
@@ -1164,7 +1370,7 @@ namespace {
 int32_t instance_solve(bfp_hierarchy* h, const double* f, double* x, int32_t k, int32_t fmg, cudaStream_t s) {
   TileScope ts(h->o.tile_rows);
   if (fmg) TRY(bfp_fmg(h, f, x, s));
-  const double bs = bscale_of(h->o.ndim, h->o.n);
+  const double bs = bscale_of(h);
   for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));
   return BFP_OK;
 }
