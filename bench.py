@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BFP V-cycle GDOF/s (IR-V steps, 2D Poisson 4095^2, w=16)"
-JACOBI_TRAFFIC = 97467904   # bytes per launch of the 4095^2 Jacobi sweep (ncu dram__bytes read + write)
+JACOBI_TRAFFIC = 92429056       # dram bytes read + written per finest-level Jacobi launch (ncu, 67.7 + 24.7 MB)
 UNIT = "GDOF/s"
 
 
@@ -184,6 +184,106 @@ def accuracy_ratio_gpu(torch, x, n):
         ae = 4.0 * e - p[1:-1, :-2] - p[1:-1, 2:] - p[:-2, 1:-1] - p[2:, 1:-1]
         return float((e * ae).sum()) / h ** 2
     return math.sqrt(energy(u - x) / energy(u - uh))
+
+
+def var_compare(bfp, torch, stream, n=2047, steps=10):
+    """The variable-coefficient workload (-div(k grad u) = f on 2047^2, k = exp(GRF seed 1), RHS seed 2
+    smoothed): IR-V step throughput, and time to discretisation accuracy at w = 16 and w = 24 (FMG + K IR-V
+    steps, K the smallest with ||u_h - x||_A <= 0.5 ||u_h - P u_2h||_A; u_h, u_2h from FMG + 100 IR-V steps at
+    w = 24, qcomp).  The energy norms are measurement only, outside every timed region."""
+    import math
+    import numpy as np
+    from bfp_inputs import grf_nodes, smoothed_random_rhs
+    K = grf_nodes(n, seed=1)
+    f_host = smoothed_random_rhs(n, 2)
+    f = torch.from_numpy(f_host).cuda()
+    Kt = torch.from_numpy(K).cuda()
+
+    def faces(Kn):
+        def hm(a, b):
+            return ((2.0 * a) * b) / (a + b)
+        c = Kn[1:-1, 1:-1]
+        return hm(Kn[1:-1, :-2], c), hm(c, Kn[1:-1, 2:]), hm(Kn[:-2, 1:-1], c), hm(c, Kn[2:, 1:-1])
+    fw, fe, fs, fn = faces(Kt)
+
+    def energy(e):
+        p = torch.nn.functional.pad(e, (1, 1, 1, 1))
+        ae = (fw + fe + fs + fn) * e - (fw * p[1:-1, :-2] + fe * p[1:-1, 2:] + fs * p[:-2, 1:-1] + fn * p[2:, 1:-1])
+        return math.sqrt(max(float((e * ae).sum()), 0.0))
+
+    def hier(nn, w, mode, Kn):
+        o = bfp.bfp_solver_opts_default(2, nn, w)
+        o.mode = mode
+        return bfp.Hierarchy(o, k_nodes=Kn)
+
+    # reference discrete solutions on the grid and on the next coarser one
+    nc = (n - 1) // 2
+    bprime = torch.from_numpy(f_host * (1.0 / (n + 1)) ** 2).cuda()
+    bc = torch.zeros((nc, nc), dtype=torch.float64, device="cuda")
+    for dj in (-1, 0, 1):                                   # b'_2h = R~ b'_h (full weighting, P^T)
+        for di in (-1, 0, 1):
+            wgt = (2 - abs(dj)) * (2 - abs(di)) * 0.25
+            bc += wgt * bprime[1 + dj:1 + dj + 2 * nc:2, 1 + di:1 + di + 2 * nc:2]
+    fc = bc / (1.0 / (nc + 1)) ** 2
+    href, hc = hier(n, 24, bfp.QCOMP, K), hier(nc, 24, bfp.QCOMP, K[::2, ::2])
+    uh, uc = torch.zeros_like(f), torch.zeros_like(fc)
+    with torch.cuda.stream(stream):
+        href.fmg(f, uh)
+        href.ir_iterate(f, uh, 100)
+        hc.fmg(fc, uc)
+        hc.ir_iterate(fc, uc, 100)
+    stream.synchronize()
+    href.close()
+    hc.close()
+    # bilinear P u_2h: fine index 2I+1 on coarse I, fine 2I halfway between I-1 and I (zero outside)
+    pc = torch.nn.functional.pad(uc, (1, 1, 1, 1))
+    tx = torch.zeros((nc + 2, n), dtype=torch.float64, device="cuda")
+    tx[:, 1::2] = pc[:, 1:-1]
+    tx[:, 0::2] = 0.5 * (pc[:, :-1] + pc[:, 1:])
+    pu = torch.zeros_like(f)
+    pu[1::2, :] = tx[1:-1, :]
+    pu[0::2, :] = 0.5 * (tx[:-1, :] + tx[1:, :])
+    disc = energy(uh - pu)
+    out = {"workload": "-div(k grad u) = f, 2047^2, k = exp(GRF, 64 modes, |k_x|,|k_y| <= 8, sigma 1, seed 1), "
+                       "RHS uniform seed 2 smoothed, nnqcomp, FMG + IR-V"}
+    for w in (16, 24):
+        h = hier(n, w, bfp.NNQCOMP, K)
+        x = torch.zeros_like(f)
+        with torch.cuda.stream(stream):
+            h.ir_iterate(f, x, 3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.ir_iterate(f, x, steps)
+            b.record(stream)
+        stream.synchronize()
+        ms = a.elapsed_time(b) / steps
+        x.zero_()
+        with torch.cuda.stream(stream):
+            h.fmg(f, x)
+        stream.synchronize()
+        k, ratio = 0, energy(uh - x) / disc
+        while ratio > 0.5 and k < 40:
+            with torch.cuda.stream(stream):
+                h.ir_iterate(f, x, 1)
+            stream.synchronize()
+            k += 1
+            ratio = energy(uh - x) / disc
+        times = []
+        for _ in range(3):
+            x.zero_()
+            with torch.cuda.stream(stream):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                h.fmg(f, x)
+                if k:
+                    h.ir_iterate(f, x, k)
+                b.record(stream)
+            stream.synchronize()
+            times.append(a.elapsed_time(b))
+        out["w%d" % w] = {"ir_step_ms": ms, "GDOF/s": n * n / ms / 1e6, "ir_steps_after_fmg": k,
+                          "error_ratio": ratio, "reached": bool(ratio <= 0.5), "time_to_accuracy_ms": min(times)}
+        h.close()
+    return out
 
 
 def solver_compare(bfp, torch, args, f, stream, hbfp):
@@ -362,9 +462,10 @@ def run_ours(args):
         e2e = {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
                "d2h_bytes_per_step": 8 * dof}
 
-    floats, tta = None, None
+    floats, tta, var = None, None, None
     if rank == 0 and not args.no_compare:
         floats, tta = solver_compare(bfp, torch, args, f, stream, h)
+        var = var_compare(bfp, torch, stream) if nd == 2 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -388,7 +489,7 @@ def run_ours(args):
             "roofline": roof, "kernels": kern_out, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches_per_step * args.steps),
             "op_stats_2_steps": op_stats,
-            "float_baselines": floats, "time_to_accuracy": tta,
+            "float_baselines": floats, "time_to_accuracy": tta, "variable_coefficients": var,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
