@@ -38,6 +38,7 @@ def parse():
     p.add_argument("--mode", default="nnqcomp", choices=["nnqcomp", "qcomp"])
     p.add_argument("--n", type=int, default=4095)
     p.add_argument("--nd", type=int, default=2, choices=[2, 3], help="dimension of the --op problem")
+    p.add_argument("--var", action="store_true", help="--op on the variable-coefficient 2D problem")
     p.add_argument("--w", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -609,7 +610,11 @@ def run_op(args):
     mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
-    h = bfp.Hierarchy(o)
+    if args.var:
+        from bfp_inputs import grf_nodes
+        h = bfp.Hierarchy(o, k_nodes=grf_nodes(n, seed=1))
+    else:
+        h = bfp.Hierarchy(o)
     f = torch.from_numpy(manufactured_rhs(nd, n)).cuda()
     x = torch.zeros_like(f)
     A = bfp.bfp_laplace_stencil(nd, o.omega, o.w_omega)

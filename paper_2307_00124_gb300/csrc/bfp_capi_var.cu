@@ -120,10 +120,8 @@ int32_t bfp_var_apply(const bfp_varstencil* A, const bfp_vec* x, const bfp_vec* 
   if (x->w > 24) return BFP_ERR_WIDTH;
   if (overlaps(x, z)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
-  d.ch = A->e_k; d.ha = 1; d.two = 0;
-  d.hbits = hmsb(A->a_norm) + x->w + 1;
-  d.ng = 1; d.gv[0] = 0; d.gm[0] = (uint64_t)A->a_norm; d.ge[0] = A->e_k;   // ||A'|| ||x||
-  if ((rc = fill_q(d, q, z, 2))) return rc;
+  int rule = 0;
+  if ((rc = desc_var_apply(A, x->w, d, &rule)) || (rc = fill_q(d, q, z, rule))) return rc;
   d.meta_a = x->meta; d.meta_out = z->meta; d.stats = st ? st->counters : nullptr;
   return var_launch<kApply>(A, x, nullptr, d, z, 0, as_stream(stream));
 }
@@ -137,23 +135,8 @@ int32_t bfp_var_residual(const bfp_varstencil* A, const bfp_vec* y, const bfp_ve
   if (is32(y) != is32(r)) return BFP_ERR_ARG;
   if (overlaps(y, rv) || overlaps(r, rv)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
-  d.ch = A->e_k; d.ha = 1;
-  d.cl = 0; d.lb = 1;
-  d.two = 1;
-  d.hbits = hmsb(A->a_norm) + y->w + 1;
-  d.lbits = r->w + 1;
-  // gamma = (omega + 1/4) ||r|| (the V residual row, as for constant coefficients)
-  const int64_t om = iabs64(A->omega.m), oe = A->omega.e;
-  uint64_t cm;
-  int64_t ce;
-  if (oe <= -2) { cm = (uint64_t)om + (1ull << (-2 - oe)); ce = oe; }
-  else {
-    if (oe + 2 > 30) return BFP_ERR_ARG;
-    cm = ((uint64_t)om << (oe + 2)) + 1ull; ce = -2;
-  }
-  if (cm >= (1ull << 32)) return BFP_ERR_ARG;
-  d.ng = 1; d.gv[0] = 1; d.gm[0] = cm; d.ge[0] = ce;
-  if ((rc = fill_q(d, q, rv, 4))) return rc;
+  int rule = 0;
+  if ((rc = desc_var_residual(A, y->w, r->w, d, &rule)) || (rc = fill_q(d, q, rv, rule))) return rc;
   d.meta_a = y->meta; d.meta_b = r->meta; d.meta_out = rv->meta; d.stats = st ? st->counters : nullptr;
   return var_launch<kResidual>(A, y, r, d, rv, 0, as_stream(stream));
 }
@@ -166,12 +149,10 @@ int32_t bfp_var_jacobi(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec*
   if (r->w > 24) return BFP_ERR_WIDTH;
   if (overlaps(r, y_out)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
-  const int qb = hmsb(A->q_norm);
+  int rule = 0;
+  int32_t s = 0;
   if (!y) {
-    d.ch = A->e_q; d.hb = 1; d.two = 0;            // Q r at e_q + e_r
-    d.hbits = qb + r->w + 1;
-    d.ng = 1; d.gv[0] = 1; d.gm[0] = (uint64_t)A->q_norm; d.ge[0] = A->e_q;   // ||q|| ||r||
-    if ((rc = fill_q(d, q, y_out, 2))) return rc;
+    if ((rc = desc_var_jacobi(A, 0, r->w, d, &rule, &s)) || (rc = fill_q(d, q, y_out, rule))) return rc;
     d.meta_b = r->meta; d.meta_out = y_out->meta; d.stats = st ? st->counters : nullptr;
     return var_launch<kJacobi0>(A, nullptr, r, d, y_out, 0, as_stream(stream));
   }
@@ -180,20 +161,9 @@ int32_t bfp_var_jacobi(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec*
   if (y->w > 24) return BFP_ERR_WIDTH;
   if (is32(y) != is32(r)) return BFP_ERR_ARG;
   if (overlaps(y, y_out)) return BFP_ERR_ARG;
-  const int64_t s = -(A->e_q + A->e_k);
-  if (s < 0 || s > 40) return BFP_ERR_ARG;
-  d.ch = A->e_q + A->e_k; d.ha = 1;                 // y 2^s - q A'y at e_q + e_k + e_y
-  d.cl = A->e_q; d.lb = 1;                          // q r at e_q + e_r
-  d.two = 1;
-  const int hb1 = y->w + (int)s, hb2 = qb + hmsb(A->a_norm) + y->w;
-  d.hbits = (hb1 > hb2 ? hb1 : hb2) + 2;
-  d.lbits = qb + r->w + 1;
-  d.ng = 2;                                         // gamma = ||y|| + ||q|| ||r||
-  d.gv[0] = 0; d.gm[0] = 1; d.ge[0] = 0;
-  d.gv[1] = 1; d.gm[1] = (uint64_t)A->q_norm; d.ge[1] = A->e_q;
-  if ((rc = fill_q(d, q, y_out, 2))) return rc;
+  if ((rc = desc_var_jacobi(A, y->w, r->w, d, &rule, &s)) || (rc = fill_q(d, q, y_out, rule))) return rc;
   d.meta_a = y->meta; d.meta_b = r->meta; d.meta_out = y_out->meta; d.stats = st ? st->counters : nullptr;
-  return var_launch<kJacobi>(A, y, r, d, y_out, (int32_t)s, as_stream(stream));
+  return var_launch<kJacobi>(A, y, r, d, y_out, s, as_stream(stream));
 }
 
 }  // extern "C"

@@ -27,7 +27,8 @@
 
 namespace bfp {
 
-enum CoarseKind : int32_t { cJac0 = 0, cJac = 1, cRes = 2, cRestrict = 3, cProlong = 4 };
+enum CoarseKind : int32_t { cJac0 = 0, cJac = 1, cRes = 2, cRestrict = 3, cProlong = 4,
+                            cVarJac0 = 5, cVarJac = 6 };   // the last two: the coarsest-level run only
 
 struct CoarseOp {
   int32_t kind;
@@ -492,6 +493,9 @@ __device__ __noinline__ CoarseRun coarse_sweep_run(unsigned char* sm, const Coar
 struct SweepRunArgs {
   CoarseOp op0, op1;     // damped Jacobi from y = 0, and from y
   int32_t sweeps, n, nd;
+  int32_t var;           // variable coefficients (2D): per-point faces kf and weights kq, H = y 2^s - q A'y
+  int32_t s;
+  VIn kf[4], kq;
   VIn r;                 // right-hand side of the level
   const int64_t* r_meta;
   VOut y;                // result (padding columns written as 0)
@@ -508,6 +512,10 @@ __global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
   const bool hb = act && a.nd == 3 && k > 0, ht = act && a.nd == 3 && k + 1 < n;
   const int64_t row = (int64_t)j + (int64_t)n * k;
   const int32_t bv = act ? (int32_t)reinterpret_cast<const int16_t*>(a.r.m)[row * a.r.ld + i] : 0;
+  auto kld = [&](const VIn& v) -> int32_t {
+    return (a.var && act) ? (int32_t)reinterpret_cast<const int16_t*>(v.m)[row * v.ld + i] : 0;
+  };
+  const int32_t fw = kld(a.kf[0]), fe = kld(a.kf[1]), fs = kld(a.kf[2]), fn = kld(a.kf[3]), qv = kld(a.kq);
   const int64_t eb = a.r_meta[0], nb = a.r_meta[1];
   int64_t ea = 0, na = 0;
   int32_t y = 0;
@@ -525,8 +533,17 @@ __global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
     const int32_t tz = __shfl_sync(0xffffffffu, y, ht ? lane + nn : lane);
     const int32_t ns = (((hw ? wv : 0) + (he ? ev : 0)) + ((hs ? sv : 0) + (hn ? nv : 0))) +
                        ((hb ? bz : 0) + (ht ? tz : 0));
-    const int64_t H = sw == 0 ? op.mw * (int64_t)bv : op.c * (int64_t)y + op.nb * (int64_t)ns;
-    const int64_t Lg = sw == 0 ? 0 : op.mw * (int64_t)bv;
+    int64_t H, Lg;
+    if (a.var) {       // y 2^s - q (c y - sum k_f y_f) and q r (q r alone on the first sweep)
+      const int64_t ay = ((int64_t)fw + fe + fs + fn) * y -
+                         ((int64_t)fw * (hw ? wv : 0) + (int64_t)fe * (he ? ev : 0) + (int64_t)fs * (hs ? sv : 0) +
+                          (int64_t)fn * (hn ? nv : 0));
+      H = sw == 0 ? (int64_t)qv * bv : (int64_t)((uint64_t)(int64_t)y << a.s) - (int64_t)qv * ay;
+      Lg = sw == 0 ? 0 : (int64_t)qv * bv;
+    } else {
+      H = sw == 0 ? op.mw * (int64_t)bv : op.c * (int64_t)y + op.nb * (int64_t)ns;
+      Lg = sw == 0 ? 0 : op.mw * (int64_t)bv;
+    }
     CoarseLean L;
     CoarseExec ex;
     Plan P;
@@ -537,6 +554,7 @@ __global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
       ex.f = make_fast(P, qc);
       ex.m = make_mul(op.kind, ex.f, op);
     }
+    if (a.var) ex.m.ok = 0;   // folded multipliers need constant coefficients
     // Z on the register path (folded multipliers: the same value as (H << dh) + (L << dl))
     auto zreg = [&](const CoarseMul& m) -> int64_t {
       return sw == 0 ? (int64_t)m.k0 * bv : (int64_t)m.k0 * y + (int64_t)m.k1 * ns + (int64_t)m.k2 * bv;
@@ -562,6 +580,7 @@ __global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
         ex.f = make_fast(P, false);
         ex.m = make_mul(op.kind, ex.f, op);
       }
+      if (a.var) ex.m.ok = 0;
     }
     int32_t v = 0;
     if (act) {

@@ -121,4 +121,64 @@ inline int32_t desc_prolong(int nd, int wd, int wy, QDesc& d, int* w_add_rule) {
   return BFP_OK;
 }
 
+// ---- variable coefficients (bfp_varstencil): the exponent groups, width bounds and gamma rules
+// of bfp_var_apply / bfp_var_residual / bfp_var_jacobi (shared with the coarsest-level run) ----
+
+// A'x: H = A'x at e_k + e_x; gamma ||A'|| ||x||
+inline int32_t desc_var_apply(const bfp_varstencil* A, int wx, QDesc& d, int* w_add_rule) {
+  d.ch = A->e_k; d.ha = 1; d.two = 0;
+  d.hbits = hmsb(A->a_norm) + wx + 1;
+  d.ng = 1; d.gv[0] = 0; d.gm[0] = (uint64_t)A->a_norm; d.ge[0] = A->e_k;
+  *w_add_rule = 2;
+  return BFP_OK;
+}
+
+// r_v = A'y - r: H = A'y at e_k + e_y, L = -r at e_r; gamma (omega + 1/4) ||r|| (V residual row)
+inline int32_t desc_var_residual(const bfp_varstencil* A, int wy, int wr, QDesc& d, int* w_add_rule) {
+  d.ch = A->e_k; d.ha = 1;
+  d.cl = 0; d.lb = 1;
+  d.two = 1;
+  d.hbits = hmsb(A->a_norm) + wy + 1;
+  d.lbits = wr + 1;
+  const int64_t om = iabs64(A->omega.m), oe = A->omega.e;
+  uint64_t cm;
+  int64_t ce;
+  if (oe <= -2) { cm = (uint64_t)om + (1ull << (-2 - oe)); ce = oe; }
+  else {
+    if (oe + 2 > 30) return BFP_ERR_ARG;
+    cm = ((uint64_t)om << (oe + 2)) + 1ull; ce = -2;
+  }
+  if (cm >= (1ull << 32)) return BFP_ERR_ARG;
+  d.ng = 1; d.gv[0] = 1; d.gm[0] = cm; d.ge[0] = ce;
+  *w_add_rule = 4;
+  return BFP_OK;
+}
+
+// y' = y + Q (r - A'y): H = y 2^s - q A'y at e_q + e_k + e_y (s = -(e_q + e_k)), L = q r at e_q + e_r;
+// gamma ||y|| + ||q|| ||r||.  wy == 0: y' = Q r (H = q r at e_q + e_r; gamma ||q|| ||r||).
+inline int32_t desc_var_jacobi(const bfp_varstencil* A, int wy, int wr, QDesc& d, int* w_add_rule, int32_t* s_out) {
+  const int qb = hmsb(A->q_norm);
+  *w_add_rule = 2;
+  *s_out = 0;
+  if (wy == 0) {
+    d.ch = A->e_q; d.hb = 1; d.two = 0;
+    d.hbits = qb + wr + 1;
+    d.ng = 1; d.gv[0] = 1; d.gm[0] = (uint64_t)A->q_norm; d.ge[0] = A->e_q;
+    return BFP_OK;
+  }
+  const int64_t s = -(A->e_q + A->e_k);
+  if (s < 0 || s > 40) return BFP_ERR_ARG;
+  d.ch = A->e_q + A->e_k; d.ha = 1;
+  d.cl = A->e_q; d.lb = 1;
+  d.two = 1;
+  const int hb1 = wy + (int)s, hb2 = qb + hmsb(A->a_norm) + wy;
+  d.hbits = (hb1 > hb2 ? hb1 : hb2) + 2;
+  d.lbits = qb + wr + 1;
+  d.ng = 2;
+  d.gv[0] = 0; d.gm[0] = 1; d.ge[0] = 0;
+  d.gv[1] = 1; d.gm[1] = (uint64_t)A->q_norm; d.ge[1] = A->e_q;
+  *s_out = (int32_t)s;
+  return BFP_OK;
+}
+
 }  // namespace bfp

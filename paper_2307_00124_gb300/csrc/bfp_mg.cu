@@ -556,8 +556,36 @@ bool sweep_run_fits(const bfp_hierarchy* h, int k) {
 int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, cudaStream_t s) {
   SweepRunArgs a;
   std::memset(&a, 0, sizeof(a));
-  TRY(make_coarse_op(h, k, cJac0, -1, 0, 0, &a.op0));
-  TRY(make_coarse_op(h, k, cJac, 0, 0, 0, &a.op1));
+  if (h->var) {   // the level's bfp_var_jacobi descriptors
+    const bfp_varstencil& V = h->lv[k].vs;
+    const int w = h->o.w;
+    for (int t = 0; t < 2; ++t) {
+      CoarseOp& op = t == 0 ? a.op0 : a.op1;
+      op.kind = t == 0 ? cVarJac0 : cVarJac;
+      op.a = t == 0 ? -1 : 0;
+      op.solo = 1;
+      int rule = 0;
+      int32_t sh = 0;
+      TRY(desc_var_jacobi(&V, t == 0 ? 0 : w, w, op.q, &rule, &sh));
+      if (op.q.hbits > 62 || (op.q.two && op.q.lbits > 62)) return BFP_ERR_WIDTH;
+      op.q.mode = h->o.mode;
+      op.q.w_out = w;
+      op.q.w_tmp = w + rule;
+      op.q.use_tmp = 0;
+      if (t == 1) a.s = sh;
+    }
+    a.var = 1;
+    auto view = [&](const int16_t* p) {
+      VIn v;
+      v.m = p; v.ld = V.ld; v.nx = V.n[0]; v.ny = V.n[1]; v.nz = 1;
+      return v;
+    };
+    for (int f = 0; f < 4; ++f) a.kf[f] = view(V.k[f]);
+    a.kq = view(V.q);
+  } else {
+    TRY(make_coarse_op(h, k, cJac0, -1, 0, 0, &a.op0));
+    TRY(make_coarse_op(h, k, cJac, 0, 0, 0, &a.op1));
+  }
   a.sweeps = h->o.coarse_sweeps;
   a.n = (int32_t)h->lv[k].n;
   a.nd = h->o.ndim;
@@ -701,7 +729,7 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
   auto jacobi = [&](const bfp_vec* y, const bfp_vec* out) -> int32_t {
     return h->var ? bfp_var_jacobi(&L.vs, y, r, out, &q.q, &q.st, s) : bfp_jacobi(&h->A, y, r, out, &q.q, &q.st, s);
   };
-  if (coarsest && !h->var && sweep_run_fits(h, k)) {   // the coarsest level's sweeps in one launch
+  if (coarsest && sweep_run_fits(h, k)) {   // the coarsest level's sweeps in one launch
     bfp_vec y = at_slot(bufA);
     TRY(sweep_run(h, k, r, &y, s));
     *res = y;
