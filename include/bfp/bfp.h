@@ -287,6 +287,11 @@ typedef struct {
   int32_t arith;         /* bfp_arith: the V-cycle's vectors and arithmetic (default BFP) */
   int32_t tile_rows;     /* rows per warp strip of the row-walking kernels for this solver's
                             ops (0: the launchers' size heuristic); set by an autotuner */
+  int32_t w_step;        /* progressive precision (Sec. 4, eq. width-bounds: the inner width grows
+                            by m = 1 bit per refinement): level k (0 = finest) gives its ops'
+                            results, the restriction to level k+1 and the IR residual on level k
+                            included, w_k = max(w - k w_step, 2) bits; 0: w on every level
+                            (default).  w_step > 0 needs w <= 16 and arith BFP */
 } bfp_solver_opts;
 
 /* BFP_ARITH_BFP is the paper's method; FP32 and BF16 (storage, with FP32

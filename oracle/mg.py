@@ -189,6 +189,7 @@ class BFPSolver:
     omega: float = 0.8               # damped-Jacobi weight for A_h's diagonal
     w_omega: int = 16                # storage width of the weight (w_check)
     n_fmg: int = 2                   # N of Alg. fmg
+    w_step: int = 0                  # progressive precision: bits fewer per coarser level
     stats: B.Stats = field(default_factory=B.Stats)
 
     def __post_init__(self):
@@ -203,12 +204,22 @@ class BFPSolver:
             m = (m - 1) // 2
         self.sizes = sizes
 
+    def width(self, k: int) -> int:
+        """Inner width of level k (0 finest): w - k w_step, at least 2.  Progressive precision
+        (Sec. 4, eq. width-bounds): w_check_j = j m + q grows by m = 1 bit per finer level (never
+        below 2 bits unless w is); every
+        op of Alg. v-cycle on level j, the restriction to level j-1 included, outputs w_check_j."""
+        return max(self.w - k * self.w_step, min(self.w, 2))
+
     @property
     def q(self) -> B.Quant:
         return B.Quant(self.w, self.mode)
 
+    def ql(self, k: int) -> B.Quant:
+        return B.Quant(self.width(k), self.mode)
+
     def vcycle(self, k: int, r: B.BFP) -> B.BFP:
-        A, om, q, st = self.A, self.om, self.q, self.stats
+        A, om, q, st = self.A, self.om, self.ql(k), self.stats
         if k == len(self.sizes) - 1:
             y = B.jacobi(A, om, None, r, q, st)
             for _ in range(self.coarse_sweeps - 1):
@@ -226,9 +237,9 @@ class BFPSolver:
         return y
 
     def ir_step(self, k: int, b: np.ndarray, x: np.ndarray, trace: Optional[list] = None):
-        """One IR-V step (Alg. ir): FP64 residual, quantise, V-cycle, FP64 update."""
+        """One IR-V step (Alg. ir): FP64 residual, quantise (to the level's width), V-cycle, FP64 update."""
         r64 = residual_f64(b, x)
-        r = B.from_f64(r64, self.w)
+        r = B.from_f64(r64, self.width(k))
         y = self.vcycle(k, r)
         if trace is not None:
             trace.append((r, y))
@@ -248,8 +259,8 @@ class BFPSolver:
             if x is None:
                 x = np.zeros(bs[k].shape)
             else:
-                xq = B.from_f64(x, self.w)
-                xp = B.prolong(xq, None, bs[k].shape, self.q, self.stats)
+                xq = B.from_f64(x, self.width(k + 1))
+                xp = B.prolong(xq, None, bs[k].shape, self.ql(k), self.stats)
                 x = B.to_f64(xp)
             for _ in range(self.n_fmg):
                 x = self.ir_step(k, bs[k], x, trace)

@@ -220,6 +220,7 @@ class VarSolver:
     omega: float = 0.8
     w_omega: int = 16
     n_fmg: int = 2
+    w_step: int = 0                  # progressive precision (as mg.BFPSolver)
     stats: B.Stats = field(default_factory=B.Stats)
 
     def __post_init__(self):
@@ -234,12 +235,18 @@ class VarSolver:
                 break
             K, m = coarse_nodes(K), (m - 1) // 2
 
+    def width(self, k: int) -> int:
+        return max(self.w - k * self.w_step, min(self.w, 2))
+
     @property
     def q(self) -> B.Quant:
         return B.Quant(self.w, self.mode)
 
+    def ql(self, k: int) -> B.Quant:
+        return B.Quant(self.width(k), self.mode)
+
     def vcycle(self, k: int, r: B.BFP) -> B.BFP:
-        op, q, st = self.ops[k], self.q, self.stats
+        op, q, st = self.ops[k], self.ql(k), self.stats
         coarsest = k == len(self.sizes) - 1
         y = jacobi(op, None, r, q, st)
         for _ in range((self.coarse_sweeps if coarsest else self.nu1) - 1):
@@ -255,7 +262,7 @@ class VarSolver:
         return y
 
     def ir_step(self, k: int, b: np.ndarray, x: np.ndarray) -> np.ndarray:
-        r = B.from_f64(residual_f64(self.ops[k], b, x), self.w)
+        r = B.from_f64(residual_f64(self.ops[k], b, x), self.width(k))
         return x + B.to_f64(self.vcycle(k, r))
 
     def rhs_hierarchy(self, f: np.ndarray):
@@ -271,7 +278,7 @@ class VarSolver:
             if x is None:
                 x = np.zeros(bs[k].shape)
             else:
-                xp = B.prolong(B.from_f64(x, self.w), None, bs[k].shape, self.q, self.stats)
+                xp = B.prolong(B.from_f64(x, self.width(k + 1)), None, bs[k].shape, self.ql(k), self.stats)
                 x = B.to_f64(xp)
             for _ in range(self.n_fmg):
                 x = self.ir_step(k, bs[k], x)

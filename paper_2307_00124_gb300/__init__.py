@@ -72,7 +72,7 @@ class bfp_solver_opts(C.Structure):
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
                 ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
                 ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32), ("arith", C.c_int32),
-                ("tile_rows", C.c_int32)]
+                ("tile_rows", C.c_int32), ("w_step", C.c_int32)]
 
 
 class flt_vec(C.Structure):

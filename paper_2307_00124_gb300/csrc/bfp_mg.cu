@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(256) k_restrict_f64(const double* __restrict__
 
 struct Level {
   int64_t n = 0;
+  int w = 0;                      // width of this level's op results (progressive precision)
   int64_t* slots = nullptr;       // meta blocks of this level's op call sites (zeroed once per step)
   int nslots = 0;
   bfp_vec r{}, ya{}, yb{}, rv{};  // BFP buffers (mantissa + meta)
@@ -440,7 +441,7 @@ struct Q {
 Q make_q(const bfp_hierarchy* h, const Level& L) {
   Q r;
   std::memset(&r, 0, sizeof(r));
-  r.q.w_out = h->o.w;
+  r.q.w_out = L.w;
   r.q.w_add = -1;
   r.q.mode = h->o.mode;
   r.q.tmp = (h->o.mode == BFP_QCOMP && h->o.use_tmp) ? L.tmp : nullptr;
@@ -463,7 +464,12 @@ struct CoarseLevelBufs {
 // One op of the on-chip schedule on level l: the QDesc the C ABI op would build (meta pointers
 // unused; qcomp without the window buffer) and the op's coefficients.
 int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, int out, CoarseOp* res) {
-  const int w = h->o.w, nd = h->o.ndim;
+  const int nd = h->o.ndim;
+  // result width: level l's; input widths for the exact-width bounds: y, r_v on level l at w_l, the
+  // right-hand side at most w_(l-1) (the finer level's restriction), d from level l+1 at w_(l+1)
+  const int w = h->lv[l].w;
+  const int wr = l > 0 ? h->lv[l - 1].w : w;
+  const int wc = l + 1 < (int)h->lv.size() ? h->lv[l + 1].w : w;
   CoarseOp op;
   std::memset(&op, 0, sizeof(op));
   op.kind = kind; op.a = a; op.b = b; op.out = out;
@@ -471,17 +477,17 @@ int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, in
   int rule = 0;
   int32_t rc = BFP_OK;
   switch (kind) {
-    case cJac0: rc = desc_jacobi(&h->A, 0, w, d, &rule); op.mw = h->A.omega.m; break;
+    case cJac0: rc = desc_jacobi(&h->A, 0, wr, d, &rule); op.mw = h->A.omega.m; break;
     case cJac: {
       int64_t Sc, Sn, eS;
-      rc = desc_jacobi(&h->A, w, w, d, &rule);
+      rc = desc_jacobi(&h->A, w, wr, d, &rule);
       if (!rc) rc = jacobi_operator(&h->A, &Sc, &Sn, &eS);
       op.c = Sc; op.nb = Sn; op.mw = h->A.omega.m;
       break;
     }
-    case cRes: rc = desc_residual(&h->A, w, w, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
+    case cRes: rc = desc_residual(&h->A, w, wr, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
     case cRestrict: rc = desc_restrict(nd, w, d, &rule); break;
-    default: rc = desc_prolong(nd, w, w, d, &rule); break;
+    default: rc = desc_prolong(nd, wc, w, d, &rule); break;
   }
   if (rc) return rc;
   if (d.hbits > 62 || (d.two && d.lbits > 62)) return BFP_ERR_WIDTH;
@@ -558,7 +564,7 @@ int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, c
   std::memset(&a, 0, sizeof(a));
   if (h->var) {   // the level's bfp_var_jacobi descriptors
     const bfp_varstencil& V = h->lv[k].vs;
-    const int w = h->o.w;
+    const int w = h->lv[k].w, wr = k > 0 ? h->lv[k - 1].w : w;
     for (int t = 0; t < 2; ++t) {
       CoarseOp& op = t == 0 ? a.op0 : a.op1;
       op.kind = t == 0 ? cVarJac0 : cVarJac;
@@ -566,7 +572,7 @@ int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, c
       op.solo = 1;
       int rule = 0;
       int32_t sh = 0;
-      TRY(desc_var_jacobi(&V, t == 0 ? 0 : w, w, op.q, &rule, &sh));
+      TRY(desc_var_jacobi(&V, t == 0 ? 0 : w, wr, op.q, &rule, &sh));
       if (op.q.hbits > 62 || (op.q.two && op.q.lbits > 62)) return BFP_ERR_WIDTH;
       op.q.mode = h->o.mode;
       op.q.w_out = w;
@@ -755,6 +761,7 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
     if (h->var) TRY(bfp_var_residual(&L.vs, &cur, r, &rv, &q.q, &q.st, s));   // r_v = A y - r
     else TRY(bfp_residual(&h->A, &cur, r, &rv, &q.q, &q.st, s));
     bfp_vec rc = at_slot(&C.r);
+    rc.w = L.w;                                                        // restricted at this level's width
     TRY(bfp_restrict(&rv, &rc, &q.q, &q.st, s));                       // r_c = R~ r_v
     bfp_vec d;
     TRY(vcycle_rec(h, k + 1, &rc, &C.ya, &C.yb, &d, s));               // d = V(r_c)
@@ -909,6 +916,7 @@ int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double*
   if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;   // every call-site meta of this step
   PrezeroedScope pz;
   bfp_vec r = L.r;
+  r.w = L.w;                                                  // quantised to this level's width
   r.meta = L.slots + BFP_META_WORDS * (L.nslots - 1);         // the IR residual's own slot
   TRY(ir_residual_q(h, k, b, bscale, x, &r, s));
   const bfp_vec* A = (k == 0) ? &h->y0 : &L.ya;
@@ -1075,6 +1083,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if (o->mode != BFP_QCOMP && o->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
   if (o->arith != BFP_ARITH_BFP && o->arith != BFP_ARITH_FP32 && o->arith != BFP_ARITH_BF16) return BFP_ERR_ARG;
   if (o->tile_rows < 0 || o->tile_rows > 64) return BFP_ERR_ARG;
+  if (o->w_step < 0 || (o->w_step > 0 && (o->w > 16 || o->arith != BFP_ARITH_BFP))) return BFP_ERR_ARG;
   // n = 2^J - 1 with J >= 2
   if (o->n < 3 || ((o->n + 1) & o->n) != 0) return BFP_ERR_SHAPE;
   bfp_hierarchy* h = new (std::nothrow) bfp_hierarchy();
@@ -1085,6 +1094,8 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   for (int64_t n = o->n; n >= 3; n = (n - 1) / 2) {
     Level L;
     L.n = n;
+    const int64_t wk = (int64_t)o->w - (int64_t)h->lv.size() * o->w_step, wmin = o->w < 2 ? o->w : 2;
+    L.w = (int)(wk > wmin ? wk : wmin);         // w_k = max(w - k w_step, min(w, 2))
     h->lv.push_back(L);
     if (n == 3) break;
   }
@@ -1098,8 +1109,9 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
       ok = make_fvec(h, L.fr, nd, L.n, dt) && make_fvec(h, L.fya, nd, L.n, dt) && make_fvec(h, L.fyb, nd, L.n, dt) &&
            make_fvec(h, L.frv, nd, L.n, dt);
     } else {
-      ok = make_vec(h, L.r, nd, L.n, o->w) && make_vec(h, L.ya, nd, L.n, o->w) &&
-           make_vec(h, L.yb, nd, L.n, o->w) && make_vec(h, L.rv, nd, L.n, o->w);
+      // storage follows w (int16 for every level when w_step > 0: all widths <= 16)
+      ok = make_vec(h, L.r, nd, L.n, L.w) && make_vec(h, L.ya, nd, L.n, L.w) &&
+           make_vec(h, L.yb, nd, L.n, L.w) && make_vec(h, L.rv, nd, L.n, L.w);
     }
     const int64_t pts = L.n * L.n * (nd == 3 ? L.n : 1);
     if (ok && o->use_tmp && !flt) {

@@ -11,15 +11,16 @@ from oracle import mg  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def make(nd, n, w, mode, use_tmp=1, use_graph=1, coarse_onchip=1):
+def make(nd, n, w, mode, use_tmp=1, use_graph=1, coarse_onchip=1, w_step=0):
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
     o.use_tmp = use_tmp
     o.use_graph = use_graph
     o.coarse_onchip = coarse_onchip
+    o.w_step = w_step
     h = bfp.Hierarchy(o)
     s = mg.BFPSolver(nd, n, w=w, mode="qcomp" if mode == bfp.QCOMP else "nnqcomp",
-                     omega=o.omega, w_omega=o.w_omega)
+                     omega=o.omega, w_omega=o.w_omega, w_step=w_step)
     return h, s
 
 
@@ -122,3 +123,43 @@ def test_ir_residual_window_and_padding(nd, n):
     st = h.stats()
     assert st["ir_residuals"] == 4
     assert st["ir_recomputed"] == 2       # the first call (no gamma yet) and the overflowing one
+
+
+@pytest.mark.parametrize("nd,n,w,onchip", [(2, 63, 16, 63), (2, 63, 16, 0), (2, 127, 12, 63), (2, 255, 14, 15),
+                                           (3, 15, 16, 0)])
+@pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
+def test_progressive_precision_bit_exact(nd, n, w, onchip, mode):
+    """w_step = 1: every level's ops at w - k bits (the restriction at the finer level's width);
+    V-cycle, FMG and IR steps against the oracle bit for bit, counters included."""
+    h, s = make(nd, n, w, mode, coarse_onchip=onchip, w_step=1)
+    rm = random_mantissas((n,) * nd, w, 5, "smooth")
+    r = bfp.BFPVector.from_mantissas(rm, -18, w)
+    y = bfp.BFPVector((n,) * nd, w)
+    h.reset_stats()
+    h.vcycle(r, y)
+    torch.cuda.synchronize()
+    ref = s.vcycle(0, B.BFP(rm, -18, w))
+    assert y.exponent == ref.e and np.array_equal(y.mantissas(), ref.m)
+    st = h.stats()
+    assert (st["calls"], st["saturated"]) == (s.stats.calls, s.stats.saturated)
+    f = manufactured_rhs(nd, n)
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.fmg(ft, xt)
+        h.ir_iterate(ft, xt, 2)
+    stream.synchronize()
+    xr = s.fmg(f)
+    b = s.rhs_hierarchy(f)[0]
+    for _ in range(2):
+        xr = s.ir_step(0, b, xr)
+    assert np.array_equal(xt.cpu().numpy(), xr)
+
+
+def test_progressive_precision_rejects_wide_or_float():
+    for w, arith in ((24, bfp.ARITH_BFP), (16, bfp.ARITH_FP32)):
+        o = bfp.bfp_solver_opts_default(2, 63, w)
+        o.w_step, o.arith = 1, arith
+        with pytest.raises(bfp.BFPError):
+            bfp.Hierarchy(o)

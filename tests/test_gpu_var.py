@@ -242,3 +242,27 @@ def test_2047_reaches_discretisation_accuracy():
     print("IR-V steps after FMG to accuracy:", steps)
     for hh in (href, hc):
         hh.close()
+
+
+@pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
+def test_progressive_precision_bit_exact(mode):
+    n, w = 63, 16
+    o = bfp.bfp_solver_opts_default(2, n, w)
+    o.mode, o.w_step = mode, 1
+    K = grf_nodes(n, seed=2)
+    h = bfp.Hierarchy(o, k_nodes=K)
+    s = V.VarSolver(K, w=w, mode="qcomp" if mode == bfp.QCOMP else "nnqcomp", w_step=1)
+    f = smoothed_random_rhs(n, 2)
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.fmg(ft, xt)
+        h.ir_iterate(ft, xt, 2)
+    stream.synchronize()
+    xr = s.fmg(f)
+    b = s.rhs_hierarchy(f)[0]
+    for _ in range(2):
+        xr = s.ir_step(0, b, xr)
+    assert np.array_equal(xt.cpu().numpy(), xr)
+    h.close()

@@ -162,3 +162,28 @@ def test_bfp_ir_converges_to_discrete_solution():
     facs = [b_ / a_ for a_, b_ in zip(errs, errs[1:])]
     assert max(facs[:6]) < 0.3
     assert errs[-1] < 1e-8 * math.sqrt(mg.energy_sq(uh))
+
+
+def test_progressive_precision_widths():
+    """Progressive precision (w_check_j = j + q: one bit fewer per coarser level, Sec. 4 eq.
+    width-bounds): level widths follow w - k, never below 2; the smallest finest width with which
+    FMG + 1 IR-V step reaches the accuracy test is within one bit of the uniform-width one, and it
+    grows by 1 to 3 bits per halving of h (second-order accuracy: about 2 bits)."""
+    s = mg.BFPSolver(2, 255, w=9, w_step=1)
+    assert [s.width(k) for k in range(len(s.sizes))] == [9, 8, 7, 6, 5, 4, 3]
+    assert mg.BFPSolver(2, 63, w=1).width(4) == 1
+    prog, uni = [], []
+    for n in (63, 127, 255):
+        f = manufactured_rhs(2, n)
+        for step, out in ((1, prog), (0, uni)):
+            for w in range(6, 20):
+                sv = mg.BFPSolver(2, n, w=w, mode="nnqcomp", w_step=step)
+                x = sv.ir_step(0, sv.rhs_hierarchy(f)[0], sv.fmg(f))
+                if mg.accuracy_ratio(2, x) <= 1.5:
+                    out.append(w)
+                    break
+    assert len(prog) == len(uni) == 3, (prog, uni)
+    for p, u in zip(prog, uni):
+        assert p <= u + 1
+    for a, b in zip(prog, prog[1:]):
+        assert 1 <= b - a <= 3
