@@ -287,6 +287,44 @@ def var_compare(bfp, torch, stream, n=2047, steps=10):
     return out
 
 
+def width_sweep(bfp, torch, args, f, stream, steps=10):
+    """The 4095^2 workload at mantissa widths 4 ... 32 (int16 storage up to 16, int32 above): IR-V step
+    throughput, and the accuracy ratio after FMG and after one more IR-V step, for nnqcomp (FMG's saturation /
+    truncation heuristic) and qcomp (renormalising ops); plus progressive precision (w = 16 on the finest level,
+    one bit fewer per coarser level)."""
+    n = args.n
+    dof = n * n
+    out = []
+    cases = [(w, m, 0) for w in (4, 8, 12, 16, 24, 32) for m in ("nnqcomp", "qcomp")] + [(16, "nnqcomp", 1)]
+    for w, m, step in cases:
+        o = bfp.bfp_solver_opts_default(2, n, w)
+        o.mode = bfp.NNQCOMP if m == "nnqcomp" else bfp.QCOMP
+        o.w_step = step
+        h = bfp.Hierarchy(o)
+        x = torch.zeros_like(f)
+        with torch.cuda.stream(stream):
+            h.ir_iterate(f, x, 3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.ir_iterate(f, x, steps)
+            b.record(stream)
+        stream.synchronize()
+        ms = a.elapsed_time(b) / steps
+        x.zero_()
+        with torch.cuda.stream(stream):
+            h.fmg(f, x)
+        stream.synchronize()
+        r0 = accuracy_ratio_gpu(torch, x, n)
+        with torch.cuda.stream(stream):
+            h.ir_iterate(f, x, 1)
+        stream.synchronize()
+        r1 = accuracy_ratio_gpu(torch, x, n)
+        out.append({"w": w, "mode": m, "w_step": step, "ir_step_ms": ms, "GDOF/s": dof / ms / 1e6,
+                    "ratio_after_fmg": r0, "ratio_after_fmg_plus_1": r1})
+        h.close()
+    return out
+
+
 def solver_compare(bfp, torch, args, f, stream, hbfp):
     """Float baselines beside the BFP solver on the same workload: GDOF/s of IR-V steps, and time to
     discretisation accuracy (FMG + K IR-V steps, K the smallest with accuracy ratio <= 1.5)."""
@@ -463,9 +501,10 @@ def run_ours(args):
         e2e = {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
                "d2h_bytes_per_step": 8 * dof}
 
-    floats, tta, var = None, None, None
+    floats, tta, var, sweep = None, None, None, None
     if rank == 0 and not args.no_compare:
         floats, tta = solver_compare(bfp, torch, args, f, stream, h)
+        sweep = width_sweep(bfp, torch, args, f, stream) if nd == 2 else None
         var = var_compare(bfp, torch, stream) if nd == 2 else None
 
     cpu = None
@@ -490,7 +529,8 @@ def run_ours(args):
             "roofline": roof, "kernels": kern_out, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches_per_step * args.steps),
             "op_stats_2_steps": op_stats,
-            "float_baselines": floats, "time_to_accuracy": tta, "variable_coefficients": var,
+            "float_baselines": floats, "time_to_accuracy": tta, "width_sweep": sweep,
+            "variable_coefficients": var,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
