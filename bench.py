@@ -325,6 +325,70 @@ def width_sweep(bfp, torch, args, f, stream, steps=10):
     return out
 
 
+def bfp_ir_compare(bfp, torch, args, f, stream, steps=10):
+    """IR with BFP x and b' (bfp_ir_iterate_bfp: qgemv residual at the inner width, V-cycle, qsub at x's
+    width 32; b' quantised to 32 bits) beside the FP64-residual IR on the same hierarchy: ms per IR-V step,
+    and IR-V steps and ms from x = 0 to the accuracy ratio <= 1.5 (at most 30 steps)."""
+    n = args.n
+    o = bfp.bfp_solver_opts_default(2, n, args.w)
+    o.mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
+    h = bfp.Hierarchy(o)
+    b = bfp.BFPVector((n, n), 32)
+    bp = f * h.rhs_scale()
+    x = bfp.BFPVector((n, n), 32)
+    xd = torch.zeros_like(f)
+    out = {"w_inner": args.w, "w_x": 32, "w_b": 32, "mode": args.mode}
+
+    def zero_x():
+        x.mant.zero_()
+        x.meta.zero_()
+        xd.zero_()
+
+    with torch.cuda.stream(stream):
+        bfp.bfp_from_f64(bp, b, stream)
+        h.ir_iterate_bfp(b, x, 4)
+        h.ir_iterate(f, xd, 4)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        h.ir_iterate_bfp(b, x, steps)
+        ev[1].record(stream)
+        h.ir_iterate(f, xd, steps)
+        ev[2].record(stream)
+    stream.synchronize()
+    out["bfp_ir_step_ms"] = ev[0].elapsed_time(ev[1]) / steps
+    out["fp64_ir_step_ms"] = ev[1].elapsed_time(ev[2]) / steps
+    for name in ("bfp", "fp64"):
+        zero_x()
+        k, ratio = 0, float("inf")
+        while ratio > 1.5 and k < 30:
+            with torch.cuda.stream(stream):
+                if name == "bfp":
+                    h.ir_iterate_bfp(b, x, 1)
+                    bfp.bfp_to_f64(x, xd, stream)
+                else:
+                    h.ir_iterate(f, xd, 1)
+            stream.synchronize()
+            k += 1
+            ratio = accuracy_ratio_gpu(torch, xd, n)
+        times = []
+        for _ in range(3):
+            zero_x()
+            with torch.cuda.stream(stream):
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                if name == "bfp":
+                    h.ir_iterate_bfp(b, x, k)
+                else:
+                    h.ir_iterate(f, xd, k)
+                c.record(stream)
+            stream.synchronize()
+            times.append(a.elapsed_time(c))
+        out[name + "_from_zero"] = {"ir_steps": k, "ms": min(times), "accuracy_ratio": ratio,
+                                    "reached": bool(ratio <= 1.5)}
+    h.close()
+    return out
+
+
 def solver_compare(bfp, torch, args, f, stream, hbfp):
     """Float baselines beside the BFP solver on the same workload: GDOF/s of IR-V steps, and time to
     discretisation accuracy (FMG + K IR-V steps, K the smallest with accuracy ratio <= 1.5)."""
@@ -501,11 +565,12 @@ def run_ours(args):
         e2e = {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
                "d2h_bytes_per_step": 8 * dof}
 
-    floats, tta, var, sweep = None, None, None, None
+    floats, tta, var, sweep, irb = None, None, None, None, None
     if rank == 0 and not args.no_compare:
         floats, tta = solver_compare(bfp, torch, args, f, stream, h)
         sweep = width_sweep(bfp, torch, args, f, stream) if nd == 2 else None
         var = var_compare(bfp, torch, stream) if nd == 2 else None
+        irb = bfp_ir_compare(bfp, torch, args, f, stream) if nd == 2 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -530,7 +595,7 @@ def run_ours(args):
             "gpu_launches": int(launches_per_step * args.steps),
             "op_stats_2_steps": op_stats,
             "float_baselines": floats, "time_to_accuracy": tta, "width_sweep": sweep,
-            "variable_coefficients": var,
+            "variable_coefficients": var, "bfp_ir": irb,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

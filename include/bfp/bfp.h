@@ -160,7 +160,8 @@ int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream);
 /* out (device, dense doubles) = m * 2^e, exact when representable (w <= 32). */
 int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream);
 
-/* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp). */
+/* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp); x and y may
+ * differ in width and storage (int16 / int32). */
 int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
                  const bfp_vec* z, const bfp_q* q, const bfp_stats* st, bfp_stream stream);
 
@@ -204,26 +205,32 @@ int32_t bfp_prolong(const bfp_vec* d, const bfp_vec* y, const bfp_vec* y_out,
 /* The 5-point operator of -div(k grad u) with harmonic-mean face coefficients,
  * scaled by h^2 (A' = h^2 A_h): row i has c_i = k_W + k_E + k_S + k_N on the
  * diagonal and -k_f for its faces W, E, S, N.  The four face arrays are one
- * BFP block (int16 mantissas, exponent e_k); the centre is their exact
- * integer sum.  Damped Jacobi uses per-point weights q_i 2^e_q ~ omega / c_i.
+ * BFP block (int16 mantissas, or int32 for a high-precision copy used only
+ * by apply / residual; one exponent e_k); the centre is their exact integer
+ * sum.  Damped Jacobi uses per-point weights q_i 2^e_q ~ omega / c_i.
  *   n     : interior points (x, y); every array is n[1] rows of pitch ld
  *           (ld >= n[0], ld % 8 == 0), device memory, 16-byte aligned;
  *   k     : face mantissas W, E, S, N (k[f][j ld + i]);   e_k : their exponent;
- *   q, e_q: smoother weights;
- *   a_norm: max_i 2 c_i (||A'||_inf = a_norm 2^e_k);  q_norm: max_i q_i;
- *   omega : the damping, used by the residual's gamma rule.
+ *   q, e_q: smoother weights (int16; may be NULL for apply / residual);
+ *   a_norm: max_i 2 c_i (||A'||_inf = a_norm 2^e_k), < 2^20 for int16 faces,
+ *           < 2^34 for int32 faces;  q_norm: max_i q_i;
+ *   omega : the damping, used by the residual's gamma rule;
+ *   k_storage : 16 (or 0) = int16 faces, 32 = int32 faces (bfp_var_jacobi
+ *           needs 16).
  * The arrays are owned by the caller, or by a hierarchy
  * (bfp_hierarchy_var_level). */
 typedef struct {
   int64_t n[2];
   int64_t ld;
-  const int16_t* k[4];
+  const void* k[4];
   int64_t e_k;
   const int16_t* q;
   int64_t e_q;
   int64_t a_norm;
   int64_t q_norm;
   bfp_scalar omega;
+  int32_t k_storage;
+  int32_t reserved;
 } bfp_varstencil;
 
 /* z = A' x (exact, then q).  gamma rule ||A'||_inf ||x||_inf, w_add 2. */
@@ -238,7 +245,8 @@ int32_t bfp_var_residual(const bfp_varstencil* A, const bfp_vec* y, const bfp_ve
  * w_add 2.  Requires -40 <= e_q + e_k <= 0. */
 int32_t bfp_var_jacobi(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* y_out,
                        const bfp_q* q, const bfp_stats* st, bfp_stream stream);
-/* All three: 2D vectors of shape n, 1 <= w <= 24; BFP_ERR_SHAPE on a shape
+/* All three: 2D vectors of shape n, 1 <= w <= 32 for apply / residual and
+ * w <= 24 for jacobi (y and r of one storage class); BFP_ERR_SHAPE on a shape
  * mismatch, BFP_ERR_WIDTH when the exact width would pass 62 bits, BFP_ERR_ARG
  * for null arrays or aliasing. */
 
@@ -337,6 +345,29 @@ int32_t bfp_ir_update(double* x, const bfp_vec* y, bfp_stream stream);
 int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k,
                        bfp_stream stream);
 
+/* IR with x and b held as BFP blocks (Alg. ir as printed, no FP64 pass):
+ * k steps of
+ *   r = qgemv(A', x, b, 1, -1)  quantised by Alg. qcomp to the finest level's
+ *                               width (qcomp on every IR residual),
+ *   y = V(r)                    (the hierarchy's V-cycle, as bfp_vcycle),
+ *   x = qsub(x, y)              quantised by Alg. qcomp to x->w bits.
+ * b: the scaled right-hand side b' = s f (s from bfp_hierarchy_rhs_scale),
+ * quantised by the caller (e.g. bfp_from_f64) to b->w bits.  x: the iterate,
+ * updated in place; x->w is the working width (1..32).  x and b have the
+ * finest shape, the same storage (int16 for w <= 16, else int32; b->w <= 32)
+ * and do not overlap.  Variable-coefficient hierarchies use their finest
+ * operator with 27-bit faces (bfp_hierarchy_var_ir_operator: Alg. ir
+ * quantises A to the input width, finer than the inner solver's 16-bit
+ * faces).  A scratch copy of x is allocated on the first call (and again
+ * when x's storage changes).  With opts.use_graph and a
+ * non-default stream two steps are captured once per (b, x, stream) and
+ * replayed.  Float hierarchies: BFP_ERR_ARG.  No host sync. */
+int32_t bfp_ir_iterate_bfp(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x, int32_t k,
+                           bfp_stream stream);
+/* s with b' = s f for this hierarchy's finest level: h^2 for variable
+ * coefficients, h^2 / 2^p for the model problem (p = 2 in 2D, 3 in 3D). */
+int32_t bfp_hierarchy_rhs_scale(const bfp_hierarchy* h, double* out);
+
 /* Full multigrid (Alg. fmg) from x = 0: on each level from the coarsest,
  * interpolate the coarser solution at width w (bfp_prolong) and run n_fmg
  * IR-V steps; the coarse right-hand sides are full-weighting restrictions of
@@ -377,6 +408,11 @@ int32_t bfp_hierarchy_create_var(const bfp_solver_opts* o, const double* k_nodes
 /* Level l's operator (device arrays owned by the hierarchy; 0 = finest).
  * BFP_ERR_ARG for a constant-coefficient hierarchy or a bad level. */
 int32_t bfp_hierarchy_var_level(const bfp_hierarchy* h, int32_t level, bfp_varstencil* out);
+/* The finest operator of the IR residual in bfp_ir_iterate_bfp: the same
+ * faces floor-quantised to 27-bit int32 mantissas (the largest face gets 26
+ * significant bits, so A'x is exact in 62 bits for x up to 32 bits); q NULL,
+ * k_storage 32.  BFP_ERR_ARG for a constant-coefficient hierarchy. */
+int32_t bfp_hierarchy_var_ir_operator(const bfp_hierarchy* h, bfp_varstencil* out);
 
 /* ---- batched solves (many independent instances, one graph launch) ------------ */
 /* count independent hierarchies (opts[i]: size, width, mode, schedule of

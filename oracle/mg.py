@@ -245,6 +245,16 @@ class BFPSolver:
             trace.append((r, y))
         return x + B.to_f64(y)
 
+    def ir_step_bfp(self, b: B.BFP, x: B.BFP) -> B.BFP:
+        """One step of Alg. ir as printed, with x and b' held as BFP blocks (no FP64 pass):
+        r = qgemv(A', x, b', 1, -1) at the inner width, y = V(r), x - y (qsub) at x's width
+        (the working width).  Both results by Alg. qcomp: the IR residual always (the remark on
+        skipping normalisation in IR-V, applied to every step), the update because x is the
+        normalised working-precision iterate."""
+        r = B.residual(self.A, x, b, B.Quant(self.width(0), "qcomp"), self.om, self.stats)
+        y = self.vcycle(0, r)
+        return B.axpy(B.ONE, x, B.MINUS_ONE, y, B.Quant(x.w, "qcomp"), self.stats)
+
     def rhs_hierarchy(self, f: np.ndarray):
         bs = [scaled_rhs(f)]
         for _ in self.sizes[1:]:

@@ -45,6 +45,8 @@ from . import bfp as B
 from . import mg
 
 W_K = 16          # face-coefficient mantissa width (the configs' w_check)
+W_IR = 27         # face width of the finest operator in the BFP IR residual (Alg. ir quantises A to
+                  # the input width): A'x exact in 62 bits for x up to 32 bits
 
 
 def harmonic(a, b):
@@ -127,6 +129,16 @@ def make_level(K: np.ndarray, om: B.Scalar) -> VarOp:
     fw, fe, fs, fn = faces
     c64 = ((fw + fe) + fs) + fn
     return VarOp(kw, ke, ks, kn, e_k, q, e_q, faces, c64)
+
+
+def make_ir_level(K: np.ndarray, om: B.Scalar, w: int = W_IR) -> VarOp:
+    """The finest operator for the IR residual with BFP x and b: the same faces floor-quantised
+    to w bits as one block (no smoother weights: apply / residual only)."""
+    faces = face_arrays(K)
+    (kw, ke, ks, kn), e_k = quantize_faces(faces, w)
+    fw, fe, fs, fn = faces
+    zero = np.zeros_like(kw)
+    return VarOp(kw, ke, ks, kn, e_k, zero, 0, faces, ((fw + fe) + fs) + fn)
 
 
 def coarse_nodes(K: np.ndarray) -> np.ndarray:
@@ -221,6 +233,7 @@ class VarSolver:
     w_omega: int = 16
     n_fmg: int = 2
     w_step: int = 0                  # progressive precision (as mg.BFPSolver)
+    w_ir: int = W_IR                 # face width of the BFP IR residual's operator
     stats: B.Stats = field(default_factory=B.Stats)
 
     def __post_init__(self):
@@ -264,6 +277,15 @@ class VarSolver:
     def ir_step(self, k: int, b: np.ndarray, x: np.ndarray) -> np.ndarray:
         r = B.from_f64(residual_f64(self.ops[k], b, x), self.width(k))
         return x + B.to_f64(self.vcycle(k, r))
+
+    def ir_step_bfp(self, b: B.BFP, x: B.BFP) -> B.BFP:
+        """mg.BFPSolver.ir_step_bfp with the finest variable operator; the residual's operator
+        has W_IR-bit faces (Alg. ir: A quantised to the input width), the V-cycle's W_K-bit."""
+        if not hasattr(self, "op_ir"):
+            self.op_ir = make_ir_level(self.K, self.om, self.w_ir)
+        r = residual(self.op_ir, x, b, B.Quant(self.width(0), "qcomp"), self.om, self.stats)
+        y = self.vcycle(0, r)
+        return B.axpy(B.ONE, x, B.MINUS_ONE, y, B.Quant(x.w, "qcomp"), self.stats)
 
     def rhs_hierarchy(self, f: np.ndarray):
         bs = [scaled_rhs(f)]

@@ -64,7 +64,7 @@ class bfp_stencil(C.Structure):
 class bfp_varstencil(C.Structure):
     _fields_ = [("n", C.c_int64 * 2), ("ld", C.c_int64), ("k", C.c_void_p * 4), ("e_k", C.c_int64),
                 ("q", C.c_void_p), ("e_q", C.c_int64), ("a_norm", C.c_int64), ("q_norm", C.c_int64),
-                ("omega", bfp_scalar)]
+                ("omega", bfp_scalar), ("k_storage", C.c_int32), ("reserved", C.c_int32)]
 
 
 class bfp_solver_opts(C.Structure):
@@ -118,6 +118,7 @@ _sig = {
     "bfp_hierarchy_create": (C.c_int32, [P(bfp_solver_opts), P(C.c_void_p)]),
     "bfp_hierarchy_create_var": (C.c_int32, [P(bfp_solver_opts), C.c_void_p, P(C.c_void_p)]),
     "bfp_hierarchy_var_level": (C.c_int32, [C.c_void_p, C.c_int32, P(bfp_varstencil)]),
+    "bfp_hierarchy_var_ir_operator": (C.c_int32, [C.c_void_p, P(bfp_varstencil)]),
     "bfp_var_apply": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
     "bfp_var_residual": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q),
                                      P(bfp_stats), C.c_void_p]),
@@ -128,6 +129,8 @@ _sig = {
     "bfp_hierarchy_reset_stats": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "bfp_vcycle": (C.c_int32, [C.c_void_p, P(bfp_vec), P(bfp_vec), C.c_void_p]),
     "bfp_ir_iterate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "bfp_ir_iterate_bfp": (C.c_int32, [C.c_void_p, P(bfp_vec), P(bfp_vec), C.c_int32, C.c_void_p]),
+    "bfp_hierarchy_rhs_scale": (C.c_int32, [C.c_void_p, P(C.c_double)]),
     "bfp_fmg": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bfp_ir_residual": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, P(bfp_vec), C.c_void_p]),
     "bfp_ir_update": (C.c_int32, [C.c_void_p, P(bfp_vec), C.c_void_p]),
@@ -472,6 +475,12 @@ class Hierarchy:
         _check(_lib.bfp_hierarchy_var_level(self.h, level, C.byref(out)), "bfp_hierarchy_var_level")
         return out
 
+    def var_ir_operator(self) -> bfp_varstencil:
+        """The finest operator with 27-bit faces used by ir_iterate_bfp (variable coefficients)."""
+        out = bfp_varstencil()
+        _check(_lib.bfp_hierarchy_var_ir_operator(self.h, C.byref(out)), "bfp_hierarchy_var_ir_operator")
+        return out
+
     def close(self):
         if self.h:
             _lib.bfp_hierarchy_destroy(self.h)
@@ -502,6 +511,17 @@ class Hierarchy:
     def ir_iterate(self, f, x, k: int, stream=None):
         _check(_lib.bfp_ir_iterate(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()), int(k),
                                    _stream(stream)), "bfp_ir_iterate")
+
+    def ir_iterate_bfp(self, b, x, k: int, stream=None):
+        """k IR steps with BFP x (updated in place) and BFP b' (bfp_ir_iterate_bfp)."""
+        _check(_lib.bfp_ir_iterate_bfp(self.h, C.byref(b.struct()), C.byref(x.struct()), int(k), _stream(stream)),
+               "bfp_ir_iterate_bfp")
+
+    def rhs_scale(self) -> float:
+        """s with b' = s f on the finest level."""
+        out = C.c_double()
+        _check(_lib.bfp_hierarchy_rhs_scale(self.h, C.byref(out)), "bfp_hierarchy_rhs_scale")
+        return out.value
 
     def ir_residual(self, f, x, r, stream=None):
         _check(_lib.bfp_ir_residual(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()),

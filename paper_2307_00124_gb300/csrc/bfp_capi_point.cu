@@ -224,7 +224,6 @@ int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
   int32_t rc;
   if ((rc = check_vec(x)) || (rc = check_vec(y)) || (rc = check_vec(z))) return rc;
   if (!same_shape(x, y) || !same_shape(x, z)) return BFP_ERR_SHAPE;
-  if (is32(x) != is32(y)) return BFP_ERR_ARG;
   if (overlaps(x, z) || overlaps(y, z)) return BFP_ERR_ARG;
   if (a.m >= (1ll << 31) || a.m < -(1ll << 31) || b.m >= (1ll << 31) || b.m < -(1ll << 31)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
@@ -240,8 +239,12 @@ int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
   d.gv[0] = 0; d.gm[0] = (uint64_t)(a.m < 0 ? -a.m : a.m); d.ge[0] = a.e;
   d.gv[1] = 1; d.gm[1] = (uint64_t)(b.m < 0 ? -b.m : b.m); d.ge[1] = b.e;
   cudaStream_t s = as_stream(stream);
-  if (is32(x)) return launch_quant(OpAxpy<int32_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
-  return launch_quant(OpAxpy<int16_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
+  if (is32(x)) {
+    if (is32(y)) return launch_quant(OpAxpy<int32_t, int32_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
+    return launch_quant(OpAxpy<int32_t, int16_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
+  }
+  if (is32(y)) return launch_quant(OpAxpy<int16_t, int32_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
+  return launch_quant(OpAxpy<int16_t, int16_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
 }
 
 int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream) {

@@ -10,7 +10,8 @@
 //   jacobi   : H = y 2^s - q A'y at e_q + e_k + e_y (s = -(e_q + e_k)),  L = q r at e_q + e_r
 //   jacobi0  : H = q r at e_q + e_r
 // with c = k_W + k_E + k_S + k_N exact.  The face arrays share e_k (one BFP
-// block); q is the per-point smoother weight block.
+// block, int16 or, for apply / residual, int32 mantissas); q is the per-point
+// smoother weight block.
 #include "bfp_desc.h"
 
 using namespace bfp;
@@ -22,7 +23,7 @@ struct VarView {
   VIn q;
 };
 
-VIn kview(const int16_t* p, const bfp_varstencil* A) {
+VIn kview(const void* p, const bfp_varstencil* A) {
   VIn v;
   v.m = p;
   v.ld = A->ld;
@@ -32,7 +33,7 @@ VIn kview(const int16_t* p, const bfp_varstencil* A) {
   return v;
 }
 
-template <class T, int KIND>
+template <class T, int KIND, class TK = int16_t>
 struct OpVar {
   VIn y, r;
   VarView A;
@@ -52,10 +53,10 @@ struct OpVar {
     ld8<T>(y, row - 1, c0, dn);                  // rows outside the grid read 0
     ld8<T>(y, row + 1 < ny ? row + 1 : -1, c0, up);
     const int64_t wv = ld1<T>(y, row, c0 - 1), ev = ld1<T>(y, row, c0 + 8);
-    ldv<int16_t, 8>(A.k[0], row, c0, kw);
-    ldv<int16_t, 8>(A.k[1], row, c0, ke);
-    ldv<int16_t, 8>(A.k[2], row, c0, ks);
-    ldv<int16_t, 8>(A.k[3], row, c0, kn);
+    ldv<TK, 8>(A.k[0], row, c0, kw);
+    ldv<TK, 8>(A.k[1], row, c0, ke);
+    ldv<TK, 8>(A.k[2], row, c0, ks);
+    ldv<TK, 8>(A.k[3], row, c0, kn);
     if (KIND != kApply) ld8<T>(r, row, c0, rv);
     if (KIND == kJacobi) ldv<int16_t, 8>(A.q, row, c0, qv);
 #pragma unroll
@@ -79,12 +80,17 @@ struct OpVar {
   }
 };
 
+bool wide_k(const bfp_varstencil* A) { return A->k_storage == 32; }
+
 int32_t check_var(const bfp_varstencil* A, bool need_q) {
   if (!A || A->n[0] < 0 || A->n[1] < 0 || A->ld < A->n[0] || A->ld % 8 != 0 || A->ld <= 0) return BFP_ERR_ARG;
+  if (A->k_storage != 0 && A->k_storage != 16 && A->k_storage != 32) return BFP_ERR_ARG;
+  if (need_q && wide_k(A)) return BFP_ERR_ARG;
   for (int f = 0; f < 4; ++f)
     if (!A->k[f] || reinterpret_cast<uintptr_t>(A->k[f]) % 16 != 0) return BFP_ERR_ARG;
   if (need_q && (!A->q || reinterpret_cast<uintptr_t>(A->q) % 16 != 0)) return BFP_ERR_ARG;
-  if (A->a_norm < 0 || A->a_norm >= (1ll << 20) || A->q_norm < 0 || A->q_norm >= (1ll << 15)) return BFP_ERR_ARG;
+  if (A->a_norm < 0 || A->a_norm >= (1ll << (wide_k(A) ? 34 : 20))) return BFP_ERR_ARG;
+  if (A->q_norm < 0 || A->q_norm >= (1ll << 15)) return BFP_ERR_ARG;
   return BFP_OK;
 }
 
@@ -104,6 +110,10 @@ int32_t var_launch(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, 
                    int32_t s, cudaStream_t st) {
   const bfp_vec* in = y ? y : r;
   const VIn yv = vin(y ? y : r), rv = vin(r ? r : in);
+  if (KIND != kJacobi && KIND != kJacobi0 && wide_k(A)) {   // int32 faces: apply / residual only
+    if (is32(in)) return launch_quant(OpVar<int32_t, KIND, int32_t>{yv, rv, view(A), s}, d, out, st);
+    return launch_quant(OpVar<int16_t, KIND, int32_t>{yv, rv, view(A), s}, d, out, st);
+  }
   if (is32(in)) return launch_quant(OpVar<int32_t, KIND>{yv, rv, view(A), s}, d, out, st);
   return launch_quant(OpVar<int16_t, KIND>{yv, rv, view(A), s}, d, out, st);
 }
@@ -117,7 +127,7 @@ int32_t bfp_var_apply(const bfp_varstencil* A, const bfp_vec* x, const bfp_vec* 
   int32_t rc;
   if ((rc = check_var(A, false)) || (rc = check_vec(x)) || (rc = check_vec(z))) return rc;
   if (!var_shape(A, x) || !same_shape(x, z)) return BFP_ERR_SHAPE;
-  if (x->w > 24) return BFP_ERR_WIDTH;
+  if (x->w > 32) return BFP_ERR_WIDTH;
   if (overlaps(x, z)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
   int rule = 0;
@@ -131,7 +141,7 @@ int32_t bfp_var_residual(const bfp_varstencil* A, const bfp_vec* y, const bfp_ve
   int32_t rc;
   if ((rc = check_var(A, false)) || (rc = check_vec(y)) || (rc = check_vec(r)) || (rc = check_vec(rv))) return rc;
   if (!var_shape(A, y) || !same_shape(y, r) || !same_shape(y, rv)) return BFP_ERR_SHAPE;
-  if (y->w > 24 || r->w > 24) return BFP_ERR_WIDTH;
+  if (y->w > 32 || r->w > 32) return BFP_ERR_WIDTH;
   if (is32(y) != is32(r)) return BFP_ERR_ARG;
   if (overlaps(y, rv) || overlaps(r, rv)) return BFP_ERR_ARG;
   QDesc d = blank_desc();

@@ -343,6 +343,11 @@ __global__ void __launch_bounds__(256) k_restrict_f64(const double* __restrict__
 
 // ---- hierarchy ---------------------------------------------------------------------
 
+// Face width of the finest operator in the IR residual with BFP x and b: the largest face gets
+// 26 significant bits, so A'x stays exact in 62 bits for x up to 32 bits
+// (msb(||A'||_inf) <= 29).
+constexpr int kIrFaceBits = 27;
+
 struct Level {
   int64_t n = 0;
   int w = 0;                      // width of this level's op results (progressive precision)
@@ -356,6 +361,7 @@ struct Level {
   // variable coefficients: the level's operator, its unquantised FP64 faces and centre
   // (dense n x n) and the FP64 IR residual before quantisation
   bfp_varstencil vs{};
+  bfp_varstencil vs_ir{};         // finest level only: the faces at kIrFaceBits (int32) for the BFP IR
   double* kf64[4] = {nullptr, nullptr, nullptr, nullptr};
   double* c64 = nullptr;
   double* r64 = nullptr;
@@ -389,6 +395,12 @@ struct bfp_hierarchy {
   const double* graph_f = nullptr;
   double* graph_x = nullptr;
   cudaStream_t graph_stream = nullptr;
+  // IR with a BFP iterate: scratch copy of x, and two captured steps x -> xt -> x
+  bfp_vec xt{};
+  size_t xt_bytes = 0;
+  cudaGraphExec_t graph2 = nullptr;
+  bfp_vec graph2_b{}, graph2_x{};
+  cudaStream_t graph2_stream = nullptr;
 };
 
 namespace {
@@ -581,7 +593,7 @@ int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, c
       if (t == 1) a.s = sh;
     }
     a.var = 1;
-    auto view = [&](const int16_t* p) {
+    auto view = [&](const void* p) {
       VIn v;
       v.m = p; v.ld = V.ld; v.nx = V.n[0]; v.ny = V.n[1]; v.nz = 1;
       return v;
@@ -926,6 +938,42 @@ int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double*
   return ir_update(x, &y, s);
 }
 
+// One step of Alg. ir with BFP x and b on the finest level:
+//   r = A'x - b (qcomp, level width), y = V(r), x_out = x - y (qcomp, x_out->w bits).
+// x_out must not overlap x (the two qcomp passes read x twice).
+int32_t ir_step_bfp(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x, const bfp_vec* x_out, cudaStream_t s) {
+  Level& L = h->lv[0];
+  if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;
+  bfp_vec y;
+  {
+    PrezeroedScope pz;
+    Q q = make_q(h, L);
+    q.q.mode = BFP_QCOMP;
+    q.q.tmp = h->o.use_tmp ? L.tmp : nullptr;
+    bfp_vec r = L.r;
+    r.w = L.w;
+    r.meta = L.slots + BFP_META_WORDS * (L.nslots - 1);   // the IR residual's own slot
+    if (h->var) TRY(bfp_var_residual(&L.vs_ir, x, b, &r, &q.q, &q.st, s));
+    else TRY(bfp_residual(&h->A, x, b, &r, &q.q, &q.st, s));
+    TRY(vcycle_rec(h, 0, &r, &h->y0, &L.yb, &y, s));
+  }
+  // x_out's meta is not an arena slot: the op zeroes it itself
+  Q q = make_q(h, L);
+  q.q.w_out = x_out->w;
+  q.q.mode = BFP_QCOMP;
+  q.q.tmp = nullptr;
+  const bfp_scalar one{1, 0}, minus_one{-1, 0};
+  return bfp_axpy(one, x, minus_one, &y, x_out, &q.q, &q.st, s);
+}
+
+int32_t ir_bfp_direct(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x, int32_t k, cudaStream_t s) {
+  for (int32_t i = 0; i < k; ++i) {
+    const bool even = (i % 2) == 0;
+    TRY(ir_step_bfp(h, b, even ? x : &h->xt, even ? &h->xt : x, s));
+  }
+  return BFP_OK;
+}
+
 // ---- variable coefficients: host setup of every level's operator ----
 
 double harmonic(double a, double b) { return ((2.0 * a) * b) / (a + b); }
@@ -1017,6 +1065,38 @@ int32_t var_level_setup(bfp_hierarchy* h, Level& L, const std::vector<double>& K
   V.a_norm = 2 * cmax;
   V.q_norm = qmax;
   V.omega = h->A.omega;
+  V.k_storage = 16;
+  if (&L != &h->lv[0]) return BFP_OK;
+  // the finest level's faces again at kIrFaceBits (int32): the IR residual's operator when x and
+  // b are BFP blocks (bfp_ir_iterate_bfp)
+  const int64_t e_w = fe - (kIrFaceBits - 1);
+  const size_t wb = (size_t)(n * ld) * sizeof(int32_t);
+  std::vector<int32_t> kw((size_t)(n * ld), 0);
+  int64_t wmax = 0;
+  std::vector<int64_t> cw((size_t)pts, 0);
+  for (int f = 0; f < 4; ++f) {
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t i = 0; i < n; ++i) {
+        const double v = std::floor(std::ldexp(F[f][j * n + i], (int)-e_w));
+        if (v < 0.0 || v >= 2147483648.0) return BFP_ERR_ARG;
+        kw[j * ld + i] = (int32_t)v;
+        cw[j * n + i] += (int64_t)v;
+      }
+    int32_t* d = (int32_t*)dalloc(h, wb ? wb : 16);
+    if (!d) return BFP_ERR_CUDA;
+    if (wb && cudaMemcpy(d, kw.data(), wb, cudaMemcpyHostToDevice) != cudaSuccess) return BFP_ERR_CUDA;
+    L.vs_ir.k[f] = d;
+  }
+  for (int64_t v : cw) wmax = v > wmax ? v : wmax;
+  bfp_varstencil& W = L.vs_ir;
+  W.n[0] = n; W.n[1] = n; W.ld = ld;
+  W.e_k = e_w;
+  W.q = nullptr;
+  W.e_q = 0;
+  W.a_norm = 2 * wmax;
+  W.q_norm = 0;
+  W.omega = h->A.omega;
+  W.k_storage = 32;
   return BFP_OK;
 }
 
@@ -1071,6 +1151,7 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
 void bfp_hierarchy_destroy(bfp_hierarchy* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->graph2) cudaGraphExecDestroy(h->graph2);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -1188,6 +1269,12 @@ int32_t bfp_hierarchy_var_level(const bfp_hierarchy* h, int32_t level, bfp_varst
   return BFP_OK;
 }
 
+int32_t bfp_hierarchy_var_ir_operator(const bfp_hierarchy* h, bfp_varstencil* out) {
+  if (!h || !out || !h->var) return BFP_ERR_ARG;
+  *out = h->lv[0].vs_ir;
+  return BFP_OK;
+}
+
 int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream) {
   if (!h || !host8) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
@@ -1250,6 +1337,70 @@ int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k, 
   }
   for (int i = 0; i < k; ++i)
     if (cudaGraphLaunch(h->graph, s) != cudaSuccess) return BFP_ERR_CUDA;
+  return BFP_OK;
+}
+
+static bool same_vec(const bfp_vec& a, const bfp_vec& b) { return std::memcmp(&a, &b, sizeof(bfp_vec)) == 0; }
+
+int32_t bfp_ir_iterate_bfp(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x, int32_t k, bfp_stream stream) {
+  if (!h || !b || !x || k < 0 || is_float(h)) return BFP_ERR_ARG;
+  int32_t rc;
+  if ((rc = check_vec(b)) || (rc = check_vec(x))) return rc;
+  const Level& L = h->lv[0];
+  if (!same_shape(b, &L.r) || !same_shape(x, &L.r)) return BFP_ERR_SHAPE;
+  if (is32(b) != is32(x)) return BFP_ERR_ARG;
+  if (overlaps(b, x)) return BFP_ERR_ARG;
+  if (x->ld != L.r.ld) return BFP_ERR_SHAPE;
+  if (k == 0) return BFP_OK;
+  cudaStream_t s = as_stream(stream);
+  // scratch iterate with x's storage (pitch and rows of the finest level)
+  const size_t bytes = (size_t)(L.r.n[1] * L.r.n[2] * L.r.ld) * (is32(x) ? 4 : 2);
+  if (!h->xt.mant || h->xt_bytes != bytes) {
+    void* m = dalloc(h, bytes);
+    int64_t* meta = (int64_t*)dalloc(h, BFP_META_WORDS * sizeof(int64_t));
+    if (!m || !meta) return BFP_ERR_CUDA;
+    h->xt_bytes = bytes;
+    h->xt.mant = m;
+    h->xt.meta = meta;
+  }
+  h->xt.w = x->w; h->xt.ndim = x->ndim; h->xt.ld = x->ld;
+  for (int d = 0; d < 3; ++d) h->xt.n[d] = x->n[d];
+  if (overlaps(b, &h->xt) || overlaps(x, &h->xt)) return BFP_ERR_ARG;
+  TileScope ts(h->o.tile_rows);
+  const int32_t pairs = k / 2;
+  if (pairs > 0 && h->o.use_graph && s != nullptr) {
+    // two steps (x -> xt -> x) captured once per (b, x, stream) and replayed
+    if (!h->graph2 || !same_vec(h->graph2_b, *b) || !same_vec(h->graph2_x, *x) || h->graph2_stream != s) {
+      if (h->graph2) { cudaGraphExecDestroy(h->graph2); h->graph2 = nullptr; }
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BFP_ERR_CUDA;
+      rc = ir_bfp_direct(h, b, x, 2, s);
+      cudaError_t ce = cudaStreamEndCapture(s, &g);
+      if (rc != BFP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+      if (ce != cudaSuccess) return BFP_ERR_CUDA;
+      ce = cudaGraphInstantiate(&h->graph2, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) { h->graph2 = nullptr; return BFP_ERR_CUDA; }
+      h->graph2_b = *b; h->graph2_x = *x; h->graph2_stream = s;
+    }
+    for (int32_t i = 0; i < pairs; ++i)
+      if (cudaGraphLaunch(h->graph2, s) != cudaSuccess) return BFP_ERR_CUDA;
+  } else if (pairs > 0) {
+    TRY(ir_bfp_direct(h, b, x, 2 * pairs, s));
+  }
+  if (k % 2 == 1) {   // the last step lands in the scratch copy: move it back
+    TRY(ir_bfp_direct(h, b, x, 1, s));
+    if (cudaMemcpyAsync(x->mant, h->xt.mant, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(x->meta, h->xt.meta, BFP_META_WORDS * sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+      return BFP_ERR_CUDA;
+  }
+  return BFP_OK;
+}
+
+int32_t bfp_hierarchy_rhs_scale(const bfp_hierarchy* h, double* out) {
+  if (!h || !out) return BFP_ERR_ARG;
+  *out = bscale_of(h);
   return BFP_OK;
 }
 

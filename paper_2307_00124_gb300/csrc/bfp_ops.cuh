@@ -110,15 +110,15 @@ struct OpCopy {
   }
 };
 
-// axpby (Alg. eaxpby-row):  H = m_alpha x, L = m_beta y
-template <class T>
+// axpby (Alg. eaxpby-row):  H = m_alpha x, L = m_beta y (x, y stored as TX, TY)
+template <class TX, class TY>
 struct OpAxpy {
   VIn x, y;
   int64_t am, bm;
   __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
     int32_t a[8], b[8];
-    ld8<T>(x, row, c0, a);
-    ld8<T>(y, row, c0, b);
+    ld8<TX>(x, row, c0, a);
+    ld8<TY>(y, row, c0, b);
 #pragma unroll
     for (int k = 0; k < 8; ++k) { H[k] = am * a[k]; L[k] = bm * b[k]; }
   }

@@ -187,3 +187,59 @@ def test_progressive_precision_widths():
         assert p <= u + 1
     for a, b in zip(prog, prog[1:]):
         assert 1 <= b - a <= 3
+
+
+def _exact_rhs(A, x):
+    """b = A' x exactly, as a BFP block (the IR residual of x is then exactly 0)."""
+    ex = B.espmv_stencil(A, x)
+    z = np.asarray(ex.z, dtype=np.int64)
+    return B.BFP(z, ex.e, 32)
+
+
+@pytest.mark.parametrize("mode", ["qcomp", "nnqcomp"])
+def test_bfp_ir_fixed_point(mode):
+    """Alg. ir with BFP x and b: when b = A' x exactly the residual is 0, V(0) = 0 and the
+    update returns x itself (a dropped b term or a wrong scale moves x)."""
+    s = mg.BFPSolver(2, 31, w=16, mode=mode)
+    x = B.normalize(B.BFP(np.asarray(np.random.default_rng(3).integers(-2**23, 2**23, (31, 31))), -40, 24),
+                    B.Quant(24, "qcomp"))
+    xn = s.ir_step_bfp(_exact_rhs(s.A, x), x)
+    assert xn.e == x.e and np.array_equal(xn.m, x.m)
+    # b lowered at one point by 2^12 of its units (above x's ulp after A'^-1): x moves down
+    # there, most at that point (A'^-1 has positive entries, largest on the diagonal)
+    b = _exact_rhs(s.A, x)
+    b.m[7, 9] -= 1 << 12
+    d = s.ir_step_bfp(b, x).m - x.m
+    assert d.max() <= 0 and d.min() < 0 and d[7, 9] == d.min()
+
+
+def _bfp_ir_errors(s, b, x, uh, steps):
+    eu = math.sqrt(mg.energy_sq(uh))
+    out = []
+    for _ in range(steps):
+        x = s.ir_step_bfp(b, x)
+        out.append(math.sqrt(mg.energy_sq(B.to_f64(x) - uh)) / eu)
+    return x, out
+
+
+def test_bfp_ir_converges_to_the_width_floor():
+    """From x = 0, Alg. ir with BFP x, b (w_x = w_b = 32, inner w = 16) contracts like the
+    FP64-residual IR (V-cycle factor ~0.11 here) down to a floor set by x's width: the
+    floor at w_x = 28 is 2^4 times the one at 32 (within a factor 2), and both limits agree
+    with the FP64-residual IR's discrete solution to that floor."""
+    n = 63
+    f = manufactured_rhs(2, n)
+    uh = mg.discrete_solution(2, n)
+    floors = {}
+    for wx in (32, 28):
+        s = mg.BFPSolver(2, n, w=16, mode="qcomp")
+        b = B.from_f64(s.rhs_hierarchy(f)[0], 32)
+        x0 = B.BFP(np.zeros((n, n), dtype=np.int64), 0, wx)
+        x, errs = _bfp_ir_errors(s, b, x0, uh, 12)
+        assert x.w == wx
+        facs = [e1 / e0 for e0, e1 in zip(errs, errs[1:6])]
+        assert max(facs) < 0.15, facs
+        floors[wx] = errs[-1]
+        assert errs[-1] <= 1.1 * min(errs[-4:])           # settled
+    assert floors[32] < 3e-8
+    assert 8 <= floors[28] / floors[32] <= 32, floors

@@ -154,3 +154,40 @@ def test_fmg_ir_reaches_accuracy(w):
     for _ in range(6):
         x = s.ir_step(0, bs[0], x)
     assert V.energy(s.ops[0], uh - x) <= 0.6 ** 6 * e0
+
+
+def test_bfp_ir_fixed_point_and_convergence():
+    """Alg. ir with BFP x and b on the variable operator: b = A'x exactly leaves x unchanged;
+    from x = 0 the iteration follows the FP64-residual IR (same V-cycle) towards the discrete
+    solution of A'u = b' (sparse direct solve) until a floor set by the width of the residual's
+    operator (Alg. ir quantises A to the input width): 11 more face bits (27 vs 16) lower the
+    floor by about 2^11."""
+    n = 31
+    K = grf_nodes(n, seed=4)
+    s = V.VarSolver(K, w=16, mode="nnqcomp")
+    x = B.normalize(B.BFP(random_mantissas((n, n), 12, 8), -20, 12), B.Quant(12, "qcomp"))
+    ex = V.apply_exact(V.make_ir_level(K, s.om), x)
+    b = B.BFP(np.asarray(ex.z, dtype=np.int64), ex.e, 40)
+    xn = s.ir_step_bfp(b, x)
+    assert xn.e == x.e and np.array_equal(xn.m, x.m)
+    f = smoothed_random_rhs(n, 5)
+    op = s.ops[0]
+    bp = s.rhs_hierarchy(f)[0]
+    uh = V.discrete_solution(op, bp)
+    eu = V.energy(op, uh)
+    floors = {}
+    for w_ir in (27, 16):
+        sv = V.VarSolver(K, w=16, mode="nnqcomp", w_ir=w_ir)
+        bq = B.from_f64(bp, 32)
+        x, xf = B.BFP(np.zeros((n, n), dtype=np.int64), 0, 32), np.zeros((n, n))
+        errs, errf = [], []
+        for _ in range(30):
+            x, xf = sv.ir_step_bfp(bq, x), sv.ir_step(0, bp, xf)
+            errs.append(V.energy(op, B.to_f64(x) - uh) / eu)
+            errf.append(V.energy(op, xf - uh) / eu)
+        floors[w_ir] = errs[-1]
+        assert errs[-1] <= 1.1 * min(errs[-5:])                      # settled
+        for e, g in zip(errs, errf):
+            assert e <= 1.05 * g + 2 * errs[-1]
+    assert floors[27] < 3e-6
+    assert 2 ** 9 <= floors[16] / floors[27] <= 2 ** 13, floors
