@@ -356,7 +356,7 @@ int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k,
  * updated in place; x->w is the working width (1..32).  x and b have the
  * finest shape, the same storage (int16 for w <= 16, else int32; b->w <= 32)
  * and do not overlap.  Variable-coefficient hierarchies use their finest
- * operator with 27-bit faces (bfp_hierarchy_var_ir_operator: Alg. ir
+ * operator with 26-bit faces (bfp_hierarchy_var_ir_operator: Alg. ir
  * quantises A to the input width, finer than the inner solver's 16-bit
  * faces).  A scratch copy of x is allocated on the first call (and again
  * when x's storage changes).  With opts.use_graph and a
@@ -409,8 +409,8 @@ int32_t bfp_hierarchy_create_var(const bfp_solver_opts* o, const double* k_nodes
  * BFP_ERR_ARG for a constant-coefficient hierarchy or a bad level. */
 int32_t bfp_hierarchy_var_level(const bfp_hierarchy* h, int32_t level, bfp_varstencil* out);
 /* The finest operator of the IR residual in bfp_ir_iterate_bfp: the same
- * faces floor-quantised to 27-bit int32 mantissas (the largest face gets 26
- * significant bits, so A'x is exact in 62 bits for x up to 32 bits); q NULL,
+ * faces floor-quantised to 26-bit int32 mantissas (the largest face gets 25
+ * significant bits, so A'x stays within 62 bits for x up to 32 bits); q NULL,
  * k_storage 32.  BFP_ERR_ARG for a constant-coefficient hierarchy. */
 int32_t bfp_hierarchy_var_ir_operator(const bfp_hierarchy* h, bfp_varstencil* out);
 

@@ -181,13 +181,13 @@ class BFPSolver:
     """Schedule of the BFP solver: widths, mode, sweeps and the quantised weight."""
     ndim: int
     n: int
-    w: int = 16                      # one width for w_check = w = w_hat (configs)
+    w: int = 16                      # one width for the input, working and inner widths (w_check = w = w_dot)
     mode: str = "qcomp"
     nu1: int = 2
     nu2: int = 2
     coarse_sweeps: int = 32
     omega: float = 0.8               # damped-Jacobi weight for A_h's diagonal
-    w_omega: int = 16                # storage width of the weight (w_check)
+    w_omega: int = 16                # storage width of the weight (an input, w_check)
     n_fmg: int = 2                   # N of Alg. fmg
     w_step: int = 0                  # progressive precision: bits fewer per coarser level
     stats: B.Stats = field(default_factory=B.Stats)
@@ -206,9 +206,9 @@ class BFPSolver:
 
     def width(self, k: int) -> int:
         """Inner width of level k (0 finest): w - k w_step, at least 2.  Progressive precision
-        (Sec. 4, eq. width-bounds): w_check_j = j m + q grows by m = 1 bit per finer level (never
-        below 2 bits unless w is); every
-        op of Alg. v-cycle on level j, the restriction to level j-1 included, outputs w_check_j."""
+        (Sec. 4, eq. width-bounds): the inner width w_dot_j = j m + q grows by m = 1 bit per finer
+        level (never below 2 bits unless w is); every op of Alg. v-cycle on level j, the
+        restriction to level j-1 included, outputs w_dot_j."""
         return max(self.w - k * self.w_step, min(self.w, 2))
 
     @property

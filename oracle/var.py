@@ -44,9 +44,9 @@ import numpy as np
 from . import bfp as B
 from . import mg
 
-W_K = 16          # face-coefficient mantissa width (the configs' w_check)
-W_IR = 27         # face width of the finest operator in the BFP IR residual (Alg. ir quantises A to
-                  # the input width): A'x exact in 62 bits for x up to 32 bits
+W_K = 16          # face-coefficient mantissa width of the V-cycle's operator (int16)
+W_IR = 26         # face width of the finest operator in the BFP IR residual (Alg. ir quantises A to
+                  # the input width): A'x within the 62-bit group bound for x up to 32 bits
 
 
 def harmonic(a, b):

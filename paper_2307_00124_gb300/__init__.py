@@ -476,7 +476,7 @@ class Hierarchy:
         return out
 
     def var_ir_operator(self) -> bfp_varstencil:
-        """The finest operator with 27-bit faces used by ir_iterate_bfp (variable coefficients)."""
+        """The finest operator with 26-bit faces used by ir_iterate_bfp (variable coefficients)."""
         out = bfp_varstencil()
         _check(_lib.bfp_hierarchy_var_ir_operator(self.h, C.byref(out)), "bfp_hierarchy_var_ir_operator")
         return out

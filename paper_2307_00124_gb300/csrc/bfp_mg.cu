@@ -344,9 +344,9 @@ __global__ void __launch_bounds__(256) k_restrict_f64(const double* __restrict__
 // ---- hierarchy ---------------------------------------------------------------------
 
 // Face width of the finest operator in the IR residual with BFP x and b: the largest face gets
-// 26 significant bits, so A'x stays exact in 62 bits for x up to 32 bits
-// (msb(||A'||_inf) <= 29).
-constexpr int kIrFaceBits = 27;
+// 25 significant bits, so ||A'||_inf < 2^28 and A'x fits the quantiser's 62-bit group bound
+// (msb(||A'||_inf) + w_x + 1 <= 62) for x up to 32 bits.
+constexpr int kIrFaceBits = 26;
 
 struct Level {
   int64_t n = 0;

@@ -165,7 +165,7 @@ def test_bfp_ir_converges_to_discrete_solution():
 
 
 def test_progressive_precision_widths():
-    """Progressive precision (w_check_j = j + q: one bit fewer per coarser level, Sec. 4 eq.
+    """Progressive precision (inner width w_dot_j = j + q: one bit fewer per coarser level, Sec. 4 eq.
     width-bounds): level widths follow w - k, never below 2; the smallest finest width with which
     FMG + 1 IR-V step reaches the accuracy test is within one bit of the uniform-width one, and it
     grows by 1 to 3 bits per halving of h (second-order accuracy: about 2 bits)."""
