@@ -325,67 +325,74 @@ def width_sweep(bfp, torch, args, f, stream, steps=10):
     return out
 
 
-def bfp_ir_compare(bfp, torch, args, f, stream, steps=10):
+def bfp_ir_compare(bfp, torch, args, stream, sizes=(1023, 2047, 4095), steps=10):
     """IR with BFP x and b' (bfp_ir_iterate_bfp: qgemv residual at the inner width, V-cycle, qsub at x's
-    width 32; b' quantised to 32 bits) beside the FP64-residual IR on the same hierarchy: ms per IR-V step,
-    and IR-V steps and ms from x = 0 to the accuracy ratio <= 1.5 (at most 30 steps)."""
-    n = args.n
-    o = bfp.bfp_solver_opts_default(2, n, args.w)
-    o.mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
-    h = bfp.Hierarchy(o)
-    b = bfp.BFPVector((n, n), 32)
-    bp = f * h.rhs_scale()
-    x = bfp.BFPVector((n, n), 32)
-    xd = torch.zeros_like(f)
-    out = {"w_inner": args.w, "w_x": 32, "w_b": 32, "mode": args.mode}
+    width 32; b' quantised to 32 bits) beside the FP64-residual IR on the same hierarchy, per grid size:
+    ms per IR-V step, and IR-V steps and ms from x = 0 to the accuracy ratio <= 1.5 (at most 30 steps).
+    With 32-bit x the floor quantisation of the iterate leaves an energy-norm error of about 0.26 ulp / h,
+    above the discretisation error at h = 1/4096."""
+    from bfp_inputs import manufactured_rhs
+    out = []
+    for n in sizes:
+        f = torch.from_numpy(manufactured_rhs(2, n)).cuda()
+        o = bfp.bfp_solver_opts_default(2, n, args.w)
+        o.mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
+        h = bfp.Hierarchy(o)
+        b = bfp.BFPVector((n, n), 32)
+        bp = f * h.rhs_scale()
+        x = bfp.BFPVector((n, n), 32)
+        xd = torch.zeros_like(f)
+        row = {"n": n, "w_inner": args.w, "w_x": 32, "w_b": 32, "mode": args.mode}
 
-    def zero_x():
-        x.mant.zero_()
-        x.meta.zero_()
-        xd.zero_()
+        def zero_x():
+            x.mant.zero_()
+            x.meta.zero_()
+            xd.zero_()
 
-    with torch.cuda.stream(stream):
-        bfp.bfp_from_f64(bp, b, stream)
-        h.ir_iterate_bfp(b, x, 4)
-        h.ir_iterate(f, xd, 4)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(stream)
-        h.ir_iterate_bfp(b, x, steps)
-        ev[1].record(stream)
-        h.ir_iterate(f, xd, steps)
-        ev[2].record(stream)
-    stream.synchronize()
-    out["bfp_ir_step_ms"] = ev[0].elapsed_time(ev[1]) / steps
-    out["fp64_ir_step_ms"] = ev[1].elapsed_time(ev[2]) / steps
-    for name in ("bfp", "fp64"):
-        zero_x()
-        k, ratio = 0, float("inf")
-        while ratio > 1.5 and k < 30:
-            with torch.cuda.stream(stream):
-                if name == "bfp":
-                    h.ir_iterate_bfp(b, x, 1)
-                    bfp.bfp_to_f64(x, xd, stream)
-                else:
-                    h.ir_iterate(f, xd, 1)
-            stream.synchronize()
-            k += 1
-            ratio = accuracy_ratio_gpu(torch, xd, n)
-        times = []
-        for _ in range(3):
+        with torch.cuda.stream(stream):
+            bfp.bfp_from_f64(bp, b, stream)
+            h.ir_iterate_bfp(b, x, 4)
+            h.ir_iterate(f, xd, 4)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            h.ir_iterate_bfp(b, x, steps)
+            ev[1].record(stream)
+            h.ir_iterate(f, xd, steps)
+            ev[2].record(stream)
+        stream.synchronize()
+        row["bfp_ir_step_ms"] = ev[0].elapsed_time(ev[1]) / steps
+        row["fp64_ir_step_ms"] = ev[1].elapsed_time(ev[2]) / steps
+        for name in ("bfp", "fp64"):
             zero_x()
-            with torch.cuda.stream(stream):
-                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                if name == "bfp":
-                    h.ir_iterate_bfp(b, x, k)
-                else:
-                    h.ir_iterate(f, xd, k)
-                c.record(stream)
-            stream.synchronize()
-            times.append(a.elapsed_time(c))
-        out[name + "_from_zero"] = {"ir_steps": k, "ms": min(times), "accuracy_ratio": ratio,
-                                    "reached": bool(ratio <= 1.5)}
-    h.close()
+            k, ratio, best = 0, float("inf"), float("inf")
+            while ratio > 1.5 and k < 30:
+                with torch.cuda.stream(stream):
+                    if name == "bfp":
+                        h.ir_iterate_bfp(b, x, 1)
+                        bfp.bfp_to_f64(x, xd, stream)
+                    else:
+                        h.ir_iterate(f, xd, 1)
+                stream.synchronize()
+                k += 1
+                ratio = accuracy_ratio_gpu(torch, xd, n)
+                best = min(best, ratio)
+            times = []
+            for _ in range(3):
+                zero_x()
+                with torch.cuda.stream(stream):
+                    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    if name == "bfp":
+                        h.ir_iterate_bfp(b, x, k)
+                    else:
+                        h.ir_iterate(f, xd, k)
+                    c.record(stream)
+                stream.synchronize()
+                times.append(a.elapsed_time(c))
+            row[name + "_from_zero"] = {"ir_steps": k, "ms": min(times), "accuracy_ratio": ratio,
+                                        "best_ratio": best, "reached": bool(ratio <= 1.5)}
+        h.close()
+        out.append(row)
     return out
 
 
@@ -570,7 +577,7 @@ def run_ours(args):
         floats, tta = solver_compare(bfp, torch, args, f, stream, h)
         sweep = width_sweep(bfp, torch, args, f, stream) if nd == 2 else None
         var = var_compare(bfp, torch, stream) if nd == 2 else None
-        irb = bfp_ir_compare(bfp, torch, args, f, stream) if nd == 2 else None
+        irb = bfp_ir_compare(bfp, torch, args, stream) if nd == 2 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

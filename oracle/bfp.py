@@ -523,6 +523,7 @@ def espmv_prolong(d: BFP, fine_shape) -> Exact:
 
 W_ADD = {
     "jacobi": 2,       # Table tab:estimates, V relaxation row
+    "cheby": 2,        # V relaxation row (the paper's Chebyshev step)
     "residual": 4,     # V residual row
     "restrict": 6,     # V restriction row
     "correct": 1,      # V correction row
@@ -643,6 +644,12 @@ def jacobi(A: Stencil, omega: Scalar, y: Optional[BFP], r: BFP, q: Quant, stats=
         S = jacobi_operator(A, omega)
         ex = egemv(S, y, r, ONE, omega)
     return quantize(ex, q, "jacobi", gamma_jacobi(A, omega, y, r), stats)
+
+
+def cheby(A: Stencil, c1: Scalar, c2: Scalar, r: BFP, q: Quant, stats=None) -> BFP:
+    """Alg. v-cycle relaxation line from y = 0: y = qgemv(A, r, r, c2, c1) = c2 A r + c1 r
+    (two Chebyshev steps in one qgemv); gamma = c1 ||r|| (Table tab:estimates relaxation row)."""
+    return quantize(egemv(A, r, r, c2, c1), q, "cheby", dy_mul(sabs(c1), norm(r)), stats)
 
 
 def restrict(rv: BFP, q: Quant, stats=None) -> BFP:

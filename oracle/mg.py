@@ -173,6 +173,73 @@ def vcycle_f64(r: np.ndarray, om: float, nu1=2, nu2=2, coarse_sweeps=32) -> np.n
 
 
 # ---------------------------------------------------------------------------
+# Chebyshev relaxation (Alg. cheby-nodes, Alg. v-cycle relaxation line)
+# ---------------------------------------------------------------------------
+
+L_EST = 5          # level on which the Chebyshev nodes are estimated (Sec. 4)
+
+
+def cheby_nodes(rho: float, eta: float) -> tuple[float, float]:
+    """Alg. cheby-nodes: (c1, c2) of two Chebyshev steps targeting [eta rho, rho]."""
+    alpha = 0.5 * (1.0 + eta) * rho
+    c = 0.5 * (1.0 - eta) * rho
+    beta = alpha - (c * c) / (2.0 * alpha)
+    return 2.0 / beta, -1.0 / (alpha * beta)
+
+
+def rho_gen(ndim: int, level: int = L_EST) -> float:
+    """Largest eigenvalue of A x = lambda D x for the finite-difference Laplacian on level j
+    (h = 2^-j): 1 + cos(pi h), the mode of highest frequency in every direction (the upper
+    bound Alg. solver-setup asks for, taken exactly)."""
+    del ndim
+    return 1.0 + math.cos(math.pi * 2.0 ** -level)
+
+
+def cheby_scaled(ndim: int, c1: float, c2: float) -> tuple[float, float]:
+    """Coefficients for A' with diagonal d (1 in 2D, 3/4 in 3D): relaxing D^-1 A y = D^-1 r
+    with (c1 I + c2 D^-1 A) is y = (c1 / d) r + (c2 / d^2) A' r."""
+    d = diag_coef(ndim)
+    return c1 / d, (c2 / d) / d
+
+
+def cheby_f64(r: np.ndarray, c1: float, c2: float) -> np.ndarray:
+    return c2 * apply_f64(r) + c1 * r
+
+
+def vcycle10_f64(r: np.ndarray, c1: float, c2: float) -> np.ndarray:
+    """FP64 V(1,0) of Alg. v-cycle with the Chebyshev relaxation (coarsest level: the
+    relaxation alone); c1, c2 already scaled for A'."""
+    y = cheby_f64(r, c1, c2)
+    if r.shape[0] <= 3:
+        return y
+    d = vcycle10_f64(restrict_f64(apply_f64(y) - r), c1, c2)
+    return y - prolong_f64(d, r.shape)
+
+
+def vcycle10_rate(ndim: int, n: int, eta: float, iters: int = 40, seed: int = 0) -> float:
+    """Asymptotic convergence factor of V(1,0) as a stationary iteration (power iteration on
+    the error e <- e - V(A' e), unquantised coefficients)."""
+    c1, c2 = cheby_scaled(ndim, *cheby_nodes(rho_gen(ndim), eta))
+    e = np.random.default_rng(seed).standard_normal((n,) * ndim)
+    e /= np.linalg.norm(e)
+    rate = 0.0
+    for i in range(iters):
+        e = e - vcycle10_f64(apply_f64(e), c1, c2)
+        nrm = float(np.linalg.norm(e))
+        if i >= iters - 10:
+            rate += math.log(nrm) / 10
+        e /= nrm
+    return math.exp(rate)
+
+
+def eta_search(ndim: int, n: int = 31) -> float:
+    """eta = i/100 (0 < i < 100) minimising the V(1,0) convergence factor on n^d points
+    (Sec. 4: the targeted part of the spectrum is found empirically)."""
+    rates = [(vcycle10_rate(ndim, n, i / 100.0), i) for i in range(1, 100)]
+    return min(rates)[1] / 100.0
+
+
+# ---------------------------------------------------------------------------
 # BFP multigrid schedule
 # ---------------------------------------------------------------------------
 
@@ -250,10 +317,11 @@ class BFPSolver:
         r = qgemv(A', x, b', 1, -1) at the inner width, y = V(r), x - y (qsub) at x's width
         (the working width).  Both results by Alg. qcomp: the IR residual always (the remark on
         skipping normalisation in IR-V, applied to every step), the update because x is the
-        normalised working-precision iterate."""
+        normalised working-precision iterate; the update's w_add is Table tab:estimates' IR
+        correction row (0)."""
         r = B.residual(self.A, x, b, B.Quant(self.width(0), "qcomp"), self.om, self.stats)
         y = self.vcycle(0, r)
-        return B.axpy(B.ONE, x, B.MINUS_ONE, y, B.Quant(x.w, "qcomp"), self.stats)
+        return B.axpy(B.ONE, x, B.MINUS_ONE, y, B.Quant(x.w, "qcomp", 0), self.stats)
 
     def rhs_hierarchy(self, f: np.ndarray):
         bs = [scaled_rhs(f)]

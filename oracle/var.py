@@ -285,7 +285,7 @@ class VarSolver:
             self.op_ir = make_ir_level(self.K, self.om, self.w_ir)
         r = residual(self.op_ir, x, b, B.Quant(self.width(0), "qcomp"), self.om, self.stats)
         y = self.vcycle(0, r)
-        return B.axpy(B.ONE, x, B.MINUS_ONE, y, B.Quant(x.w, "qcomp"), self.stats)
+        return B.axpy(B.ONE, x, B.MINUS_ONE, y, B.Quant(x.w, "qcomp", 0), self.stats)
 
     def rhs_hierarchy(self, f: np.ndarray):
         bs = [scaled_rhs(f)]

@@ -1,5 +1,6 @@
 // bfp_capi_star.cu -- C ABI: star-stencil ops (Alg. espmv / egemv on the
-// 5- and 7-point Laplacian): bfp_stencil_apply, bfp_residual, bfp_jacobi.
+// 5- and 7-point Laplacian): bfp_stencil_apply, bfp_residual, bfp_jacobi,
+// bfp_cheby.
 #include "bfp_desc.h"
 #include "bfp_star2d.cuh"
 
@@ -67,6 +68,21 @@ int32_t bfp_residual(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r, c
   if ((rc = desc_residual(A, y->w, r->w, d, &rule)) || (rc = fill_q(d, q, rv, rule))) return rc;
   d.meta_a = y->meta; d.meta_b = r->meta; d.meta_out = rv->meta; d.stats = st ? st->counters : nullptr;
   return star_dispatch<kResidual>(A->ndim, y, r, d, rv, A->center, A->nbr, 0, is32(y), as_stream(stream));
+}
+
+int32_t bfp_cheby(const bfp_stencil* A, bfp_scalar c1, bfp_scalar c2, const bfp_vec* r, const bfp_vec* y_out,
+                  const bfp_q* q, const bfp_stats* st, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_vec(r)) || (rc = check_vec(y_out)) || (rc = check_stencil(A, r))) return rc;
+  if (!same_shape(r, y_out)) return BFP_ERR_SHAPE;
+  if (overlaps(r, y_out)) return BFP_ERR_ARG;
+  QDesc d = blank_desc();
+  int rule = 0;
+  int64_t Tc = 0, Tn = 0;
+  if ((rc = desc_cheby(A, c1, c2, r->w, d, &rule, &Tc, &Tn)) || (rc = fill_q(d, q, y_out, rule))) return rc;
+  d.meta_a = r->meta; d.meta_out = y_out->meta; d.stats = st ? st->counters : nullptr;
+  // T r is a stencil apply with T's coefficients
+  return star_dispatch<kApply>(A->ndim, r, nullptr, d, y_out, Tc, Tn, 0, is32(r), as_stream(stream));
 }
 
 int32_t bfp_jacobi(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* y_out,

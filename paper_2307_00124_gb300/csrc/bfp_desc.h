@@ -87,6 +87,44 @@ inline int32_t desc_jacobi(const bfp_stencil* A, int wy, int wr, QDesc& d, int* 
   return BFP_OK;
 }
 
+// Two Chebyshev steps from y = 0 as one stencil (Alg. v-cycle relaxation line,
+// qgemv(A, r, r, c2, c1) = c2 A r + c1 r): T = c1 I + c2 A exactly, one block at
+// e_T = min(e_c1, e_c2 + e_A); BFP_ERR_WIDTH when a coefficient passes 31 bits.
+inline int32_t cheby_operator(const bfp_stencil* A, bfp_scalar c1, bfp_scalar c2, int64_t* Tc, int64_t* Tn,
+                              int64_t* eT) {
+  if (c1.m >= (1ll << 31) || c1.m < -(1ll << 31) || c2.m >= (1ll << 31) || c2.m < -(1ll << 31)) return BFP_ERR_ARG;
+  const int64_t e2 = c2.e + A->e;
+  *eT = c1.e < e2 ? c1.e : e2;
+  auto shl = [](int64_t v, int64_t s, int64_t* o) {
+    if (v == 0) { *o = 0; return true; }
+    if (s < 0 || hmsb(v) + s > 40) return false;
+    *o = (int64_t)((uint64_t)v << s);
+    return true;
+  };
+  int64_t a, b, n;
+  if (!shl(c1.m, c1.e - *eT, &a) || !shl(c2.m * A->center, e2 - *eT, &b) || !shl(c2.m * A->nbr, e2 - *eT, &n))
+    return BFP_ERR_WIDTH;
+  *Tc = a + b;
+  *Tn = n;
+  if (*Tc >= (1ll << 31) || *Tc < -(1ll << 31) || *Tn >= (1ll << 31) || *Tn < -(1ll << 31)) return BFP_ERR_WIDTH;
+  return BFP_OK;
+}
+
+// y = T r: H = T r at e_T + e_r; gamma c1 ||r|| (relaxation row, w_add 2)
+inline int32_t desc_cheby(const bfp_stencil* A, bfp_scalar c1, bfp_scalar c2, int wr, QDesc& d, int* w_add_rule,
+                          int64_t* Tc, int64_t* Tn) {
+  int64_t eT;
+  const int32_t rc = cheby_operator(A, c1, c2, Tc, Tn, &eT);
+  if (rc) return rc;
+  const int mA = 2 * A->ndim + 1;
+  const int wT = hmsb(*Tc) > hmsb(*Tn) ? hmsb(*Tc) : hmsb(*Tn);
+  d.ch = eT; d.ha = 1; d.two = 0;
+  d.hbits = wT + wr + clog2(mA);
+  d.ng = 1; d.gv[0] = 0; d.gm[0] = (uint64_t)iabs64(c1.m); d.ge[0] = c1.e;
+  *w_add_rule = 2;
+  return BFP_OK;
+}
+
 // r_c = R~ r_f (full weighting, m_R = 3^d; R~ = P^T in 2D, P^T/2 in 3D)
 inline int32_t desc_restrict(int nd, int wf, QDesc& d, int* w_add_rule) {
   const int64_t eR = nd == 2 ? -2 : -4;

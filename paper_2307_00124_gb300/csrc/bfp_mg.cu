@@ -960,6 +960,7 @@ int32_t ir_step_bfp(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x, const 
   // x_out's meta is not an arena slot: the op zeroes it itself
   Q q = make_q(h, L);
   q.q.w_out = x_out->w;
+  q.q.w_add = 0;                 // Table tab:estimates, IR correction row (gamma ||x|| + ||y||)
   q.q.mode = BFP_QCOMP;
   q.q.tmp = nullptr;
   const bfp_scalar one{1, 0}, minus_one{-1, 0};
