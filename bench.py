@@ -402,15 +402,19 @@ def solver_compare(bfp, torch, args, f, stream, hbfp):
     n, nd = args.n, 2
     dof = n ** nd
     out, tta = {}, {}
-    for name, arith in (("bfp", bfp.ARITH_BFP), ("fp32", bfp.ARITH_FP32), ("bf16", bfp.ARITH_BF16)):
-        if arith == bfp.ARITH_BFP:
+    for name, arith in (("bfp", bfp.ARITH_BFP), ("fp32", bfp.ARITH_FP32), ("bf16", bfp.ARITH_BF16),
+                        ("bfp_cheby_v10", bfp.ARITH_BFP)):
+        if name == "bfp":
             h = hbfp
         else:
             o = bfp.bfp_solver_opts_default(nd, n, args.w)
             o.arith = arith
+            if name == "bfp_cheby_v10":      # the paper's V(1,0) with two Chebyshev steps per relaxation
+                o.smoother = bfp.SMOOTH_CHEBY
+                o.mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
             h = bfp.Hierarchy(o)
         x = torch.zeros_like(f)
-        if arith != bfp.ARITH_BFP:
+        if name != "bfp":
             with torch.cuda.stream(stream):
                 h.ir_iterate(f, x, 3)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -420,13 +424,13 @@ def solver_compare(bfp, torch, args, f, stream, hbfp):
             stream.synchronize()
             t = a.elapsed_time(b) / 1e3
             out[name] = {"value": dof * args.steps / t / 1e9, "unit": "GDOF/s", "ms_per_step": 1e3 * t / args.steps}
-        # K: IR-V steps after FMG until the accuracy ratio is <= 1.5 (at most 20)
+        # K: IR-V steps after FMG until the accuracy ratio is <= 1.5 (at most 20; 40 for V(1,0))
         x.zero_()
         with torch.cuda.stream(stream):
             h.fmg(f, x)
         stream.synchronize()
         k, ratio = 0, accuracy_ratio_gpu(torch, x, n)
-        while ratio > 1.5 and k < 20:
+        while ratio > 1.5 and k < (40 if name == "bfp_cheby_v10" else 20):
             with torch.cuda.stream(stream):
                 h.ir_iterate(f, x, 1)
             stream.synchronize()

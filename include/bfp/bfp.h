@@ -181,6 +181,15 @@ int32_t bfp_residual(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r,
                      const bfp_vec* rv, const bfp_q* q, const bfp_stats* st,
                      bfp_stream stream);
 
+/* Two Chebyshev steps from y = 0 in one call (Alg. v-cycle relaxation line,
+ * qgemv(A, r, r, c2, c1)): y_out = c2 A r + c1 r, computed exactly as the
+ * stencil T = c1 I + c2 A (one block at e_T = min(e_c1, e_c2 + e_A)) applied
+ * to r, then quantised.  gamma = |c1| ||r||_inf (Table tab:estimates
+ * relaxation row), w_add 2.  BFP_ERR_WIDTH when a coefficient of T passes
+ * 31 bits. */
+int32_t bfp_cheby(const bfp_stencil* A, bfp_scalar c1, bfp_scalar c2, const bfp_vec* r,
+                  const bfp_vec* y_out, const bfp_q* q, const bfp_stats* st, bfp_stream stream);
+
 /* y_out = y + omega (r - A y) = S y + omega r with S = I - omega A (damped
  * Jacobi in the relaxation slot of Alg. v-cycle; egemv(S, y, r, 1, omega)).
  * y == NULL means a zero initial guess: y_out = omega r. */
@@ -300,7 +309,25 @@ typedef struct {
                             results, the restriction to level k+1 and the IR residual on level k
                             included, w_k = max(w - k w_step, 2) bits; 0: w on every level
                             (default).  w_step > 0 needs w <= 16 and arith BFP */
+  int32_t smoother;      /* bfp_smoother (default BFP_SMOOTH_JACOBI) */
+  double cheby_eta;      /* BFP_SMOOTH_CHEBY: the part [eta rho, rho] of the spectrum the two
+                            Chebyshev steps target, 0 < eta < 1 (default 0.15: the i/100 that
+                            minimises the FP64 V(1,0) convergence factor on level 5, 2D and 3D) */
 } bfp_solver_opts;
+
+/* Relaxation of the V-cycle.
+ *   BFP_SMOOTH_JACOBI: V(nu1, nu2) with damped Jacobi (omega), coarse_sweeps
+ *     sweeps on the coarsest level (the configs' smoother).
+ *   BFP_SMOOTH_CHEBY: the paper's V(1,0) (Alg. v-cycle): one bfp_cheby
+ *     relaxation from y = 0, then residual, restriction, coarse correction; no
+ *     post-smoothing; the coarsest level gets the relaxation alone.  c1, c2
+ *     come from Alg. cheby-nodes with rho = 1 + cos(pi/32) (the largest
+ *     eigenvalue of D^-1 A on level 5, Alg. solver-setup's bound taken exactly)
+ *     and cheby_eta, scaled for A's diagonal d (c1/d, c2/d^2) and
+ *     floor-quantised to w_omega bits; the V residual's gamma uses c1
+ *     ((2 c1 + 1)/4 ||r||).  nu1, nu2, coarse_sweeps and omega are unused.
+ *     Constant coefficients and arith BFP only. */
+typedef enum { BFP_SMOOTH_JACOBI = 0, BFP_SMOOTH_CHEBY = 1 } bfp_smoother;
 
 /* BFP_ARITH_BFP is the paper's method; FP32 and BF16 (storage, with FP32
  * arithmetic) are float baselines of the same schedule for comparison. */

@@ -177,6 +177,7 @@ def vcycle_f64(r: np.ndarray, om: float, nu1=2, nu2=2, coarse_sweeps=32) -> np.n
 # ---------------------------------------------------------------------------
 
 L_EST = 5          # level on which the Chebyshev nodes are estimated (Sec. 4)
+RHO_L5 = 1.995184726672197   # 1 + cos(pi/32) correctly rounded: rho_gen on level 5 without libm
 
 
 def cheby_nodes(rho: float, eta: float) -> tuple[float, float]:
@@ -257,11 +258,18 @@ class BFPSolver:
     w_omega: int = 16                # storage width of the weight (an input, w_check)
     n_fmg: int = 2                   # N of Alg. fmg
     w_step: int = 0                  # progressive precision: bits fewer per coarser level
+    smoother: str = "jacobi"         # "jacobi": V(nu1, nu2) damped Jacobi; "cheby": the paper's V(1,0)
+    eta: float = 0.15                # Chebyshev: targeted part [eta rho, rho] of the spectrum
     stats: B.Stats = field(default_factory=B.Stats)
 
     def __post_init__(self):
         self.A = B.laplace_stencil(self.ndim)
         self.om = B.scalar_floor(omega_scaled(self.ndim, self.omega), self.w_omega)
+        if self.smoother == "cheby":
+            c1, c2 = cheby_scaled(self.ndim, *cheby_nodes(RHO_L5, self.eta))
+            self.c1 = B.scalar_floor(c1, self.w_omega)
+            self.c2 = B.scalar_floor(c2, self.w_omega)
+            self.om_res = B.Scalar(self.c1.m, self.c1.e - 1)   # (2 c1 + 1)/4 = c1/2 + 1/4
         sizes = []
         m = self.n
         while True:
@@ -285,7 +293,21 @@ class BFPSolver:
     def ql(self, k: int) -> B.Quant:
         return B.Quant(self.width(k), self.mode)
 
+    def vcycle10(self, k: int, r: B.BFP) -> B.BFP:
+        """Alg. v-cycle, V(1,0): y = qgemv(A, r, r, c2, c1); on levels above the coarsest the
+        residual, restriction, coarse correction and interpolation follow (no post-smoothing)."""
+        A, q, st = self.A, self.ql(k), self.stats
+        y = B.cheby(A, self.c1, self.c2, r, q, st)
+        if k == len(self.sizes) - 1:
+            return y
+        rv = B.residual(A, y, r, q, self.om_res, st)
+        rc = B.restrict(rv, q, st)
+        d = self.vcycle(k + 1, rc)
+        return B.prolong(d, y, r.m.shape, q, st)
+
     def vcycle(self, k: int, r: B.BFP) -> B.BFP:
+        if self.smoother == "cheby":
+            return self.vcycle10(k, r)
         A, om, q, st = self.A, self.om, self.ql(k), self.stats
         if k == len(self.sizes) - 1:
             y = B.jacobi(A, om, None, r, q, st)

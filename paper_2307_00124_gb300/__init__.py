@@ -23,6 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 META_WORDS = 8
 QCOMP, NNQCOMP = 0, 1
 ARITH_BFP, ARITH_FP32, ARITH_BF16 = 0, 1, 2
+SMOOTH_JACOBI, SMOOTH_CHEBY = 0, 1
 F32, BF16 = 0, 1
 
 STATUS = {0: "BFP_OK", -1: "BFP_ERR_ARG", -2: "BFP_ERR_SHAPE", -3: "BFP_ERR_WIDTH", -4: "BFP_ERR_CUDA",
@@ -72,7 +73,8 @@ class bfp_solver_opts(C.Structure):
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("coarse_sweeps", C.c_int32), ("n_fmg", C.c_int32),
                 ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
                 ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32), ("arith", C.c_int32),
-                ("tile_rows", C.c_int32), ("w_step", C.c_int32)]
+                ("tile_rows", C.c_int32), ("w_step", C.c_int32), ("smoother", C.c_int32),
+                ("cheby_eta", C.c_double)]
 
 
 class flt_vec(C.Structure):
@@ -119,6 +121,8 @@ _sig = {
     "bfp_hierarchy_create_var": (C.c_int32, [P(bfp_solver_opts), C.c_void_p, P(C.c_void_p)]),
     "bfp_hierarchy_var_level": (C.c_int32, [C.c_void_p, C.c_int32, P(bfp_varstencil)]),
     "bfp_hierarchy_var_ir_operator": (C.c_int32, [C.c_void_p, P(bfp_varstencil)]),
+    "bfp_cheby": (C.c_int32, [P(bfp_stencil), bfp_scalar, bfp_scalar, P(bfp_vec), P(bfp_vec), P(bfp_q),
+                              P(bfp_stats), C.c_void_p]),
     "bfp_var_apply": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
     "bfp_var_residual": (C.c_int32, [P(bfp_varstencil), P(bfp_vec), P(bfp_vec), P(bfp_vec), P(bfp_q),
                                      P(bfp_stats), C.c_void_p]),
@@ -375,6 +379,11 @@ def bfp_stencil_apply(A, x, z, qq, stats=None, stream=None):
 def bfp_residual(A, y, r, rv, qq, stats=None, stream=None):
     _check(_lib.bfp_residual(C.byref(A), C.byref(y.struct()), C.byref(r.struct()), C.byref(rv.struct()),
                              C.byref(qq), _st(stats), _stream(stream)), "bfp_residual")
+
+
+def bfp_cheby(A, c1, c2, r, y_out, qq, stats=None, stream=None):
+    _check(_lib.bfp_cheby(C.byref(A), c1, c2, C.byref(r.struct()), C.byref(y_out.struct()), C.byref(qq),
+                          _st(stats), _stream(stream)), "bfp_cheby")
 
 
 def bfp_jacobi(A, y, r, y_out, qq, stats=None, stream=None):

@@ -28,7 +28,8 @@
 namespace bfp {
 
 enum CoarseKind : int32_t { cJac0 = 0, cJac = 1, cRes = 2, cRestrict = 3, cProlong = 4,
-                            cVarJac0 = 5, cVarJac = 6 };   // the last two: the coarsest-level run only
+                            cVarJac0 = 5, cVarJac = 6,   // these two: the coarsest-level run only
+                            cCheb = 7 };   // host side only: built as a cJac op (T r, reading r for y)
 
 struct CoarseOp {
   int32_t kind;

@@ -388,6 +388,9 @@ struct bfp_hierarchy {
   std::vector<CoarseOp*> d_ops;          // per start level k >= kc
   std::vector<int> nops, rbuf, ybuf, runk;
   int var = 0;                           // variable-coefficient operator (bfp_hierarchy_create_var)
+  int cheby = 0;                         // V(1,0) with the Chebyshev relaxation (opts.smoother)
+  bfp_scalar c1{}, c2{};                 // its quantised coefficients (Alg. cheby-nodes, scaled for A')
+  bfp_stencil Ares{};                    // A with omega = c1 / 2: the V residual's gamma (2 c1 + 1)/4 ||r||
   bfp_vec y0{};                          // spare finest-level buffer for ir steps
   flt_vec fy0{};                         // its float counterpart (float hierarchies)
   // captured IR step
@@ -445,6 +448,28 @@ inline int fdtype(const bfp_hierarchy* h) { return h->o.arith == BFP_ARITH_BF16 
 
 inline double pscale(int nd) { return nd == 2 ? 4.0 : 8.0; }
 
+// Chebyshev relaxation (Alg. cheby-nodes, Alg. solver-setup).  rho: the largest eigenvalue of
+// A x = lambda D x on level 5 (h = 1/32), 1 + cos(pi/32), as a literal (the correctly rounded
+// double) so that no libm call enters the coefficients.
+constexpr double kChebRho = 1.995184726672197;
+constexpr double kChebEta = 0.15;
+
+// c1, c2 of two Chebyshev steps on [eta rho, rho] for D^-1 A, scaled for A' (diagonal d: c1 / d,
+// c2 / d^2) and floor-quantised to w_omega bits.
+int32_t cheby_setup(const bfp_solver_opts* o, const bfp_stencil& A, bfp_scalar* c1q, bfp_scalar* c2q) {
+  const double eta = o->cheby_eta, rho = kChebRho;
+  const double alpha = 0.5 * (1.0 + eta) * rho;
+  const double c = 0.5 * (1.0 - eta) * rho;
+  const double beta = alpha - (c * c) / (2.0 * alpha);
+  const double c1 = 2.0 / beta, c2 = -1.0 / (alpha * beta);
+  const double d = (2.0 * o->ndim) / pscale(o->ndim);
+  int32_t rc = bfp_scalar_from_double(c1 / d, o->w_omega, c1q);
+  if (!rc) rc = bfp_scalar_from_double((c2 / d) / d, o->w_omega, c2q);
+  if (rc) return rc;
+  int64_t Tc, Tn, eT;
+  return cheby_operator(&A, *c1q, *c2q, &Tc, &Tn, &eT);
+}
+
 struct Q {
   bfp_q q;
   bfp_stats st;
@@ -475,6 +500,10 @@ struct CoarseLevelBufs {
 
 // One op of the on-chip schedule on level l: the QDesc the C ABI op would build (meta pointers
 // unused; qcomp without the window buffer) and the op's coefficients.
+// The operator whose omega feeds the V residual's gamma rule: with the Chebyshev relaxation the
+// rule (2 c1 + 1)/4 ||r|| is (omega + 1/4) ||r|| at omega = c1 / 2.
+const bfp_stencil* res_op(const bfp_hierarchy* h) { return h->cheby ? &h->Ares : &h->A; }
+
 int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, int out, CoarseOp* res) {
   const int nd = h->o.ndim;
   // result width: level l's; input widths for the exact-width bounds: y, r_v on level l at w_l, the
@@ -497,7 +526,13 @@ int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, in
       op.c = Sc; op.nb = Sn; op.mw = h->A.omega.m;
       break;
     }
-    case cRes: rc = desc_residual(&h->A, w, wr, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
+    case cRes: rc = desc_residual(res_op(h), w, wr, d, &rule); op.c = h->A.center; op.nb = h->A.nbr; break;
+    case cCheb: {   // T r as a damped-Jacobi op reading r for y, with no omega r term
+      int64_t Tc = 0, Tn = 0;
+      rc = desc_cheby(&h->A, h->c1, h->c2, wr, d, &rule, &Tc, &Tn);
+      op.kind = cJac; op.a = b; op.c = Tc; op.nb = Tn; op.mw = 0;
+      break;
+    }
     case cRestrict: rc = desc_restrict(nd, w, d, &rule); break;
     default: rc = desc_prolong(nd, wc, w, d, &rule); break;
   }
@@ -526,6 +561,19 @@ int32_t coarse_flatten(const bfp_hierarchy* h, int l, int rbuf, const std::vecto
     ops.push_back(op);
     return BFP_OK;
   };
+  if (h->cheby) {   // V(1,0): relaxation; residual, restriction, coarse correction
+    TRY(push(cCheb, -1, rbuf, cur));
+    if (!coarsest) {
+      const int rnext = lb[l + 1 - h->kc].r;
+      TRY(push(cRes, cur, rbuf, oth));
+      TRY(push(cRestrict, oth, -1, rnext));
+      int d = -1;
+      TRY(coarse_flatten(h, l + 1, rnext, lb, ops, &d));
+      TRY(push(cProlong, d, cur, oth)); std::swap(cur, oth);
+    }
+    *res = cur;
+    return BFP_OK;
+  }
   TRY(push(cJac0, -1, rbuf, cur));
   for (int i = 1; i < nu1; ++i) { TRY(push(cJac, cur, rbuf, oth)); std::swap(cur, oth); }
   if (!coarsest) {
@@ -568,7 +616,7 @@ int mark_sweep_run(std::vector<CoarseOp>& ops, const std::vector<CoarseBuf>& buf
 bool sweep_run_fits(const bfp_hierarchy* h, int k) {
   const int64_t n = h->lv[k].n;
   const int64_t np = h->o.ndim == 3 ? n * n * n : n * n;
-  return h->o.w <= 16 && np >= 1 && np <= 32 && k + 1 == (int)h->lv.size();
+  return !h->cheby && h->o.w <= 16 && np >= 1 && np <= 32 && k + 1 == (int)h->lv.size();
 }
 
 int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, cudaStream_t s) {
@@ -744,6 +792,25 @@ int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* buf
     return BFP_OK;
   }
   const bool coarsest = (k + 1 == (int)h->lv.size());
+  if (h->cheby) {   // V(1,0) of Alg. v-cycle: relax from 0, then the coarse correction
+    bfp_vec cur = at_slot(coarsest ? bufA : bufB);
+    TRY(bfp_cheby(&h->A, h->c1, h->c2, r, &cur, &q.q, &q.st, s));
+    if (!coarsest) {
+      Level& C = h->lv[k + 1];
+      bfp_vec rv = at_slot(&L.rv);
+      TRY(bfp_residual(&h->Ares, &cur, r, &rv, &q.q, &q.st, s));        // r_v = A y - r
+      bfp_vec rc = at_slot(&C.r);
+      rc.w = L.w;
+      TRY(bfp_restrict(&rv, &rc, &q.q, &q.st, s));
+      bfp_vec d;
+      TRY(vcycle_rec(h, k + 1, &rc, &C.ya, &C.yb, &d, s));
+      bfp_vec nx = at_slot(bufA);
+      TRY(bfp_prolong(&d, &cur, &nx, &q.q, &q.st, s));                 // y = y - P d
+      cur = nx;
+    }
+    *res = cur;
+    return BFP_OK;
+  }
   auto jacobi = [&](const bfp_vec* y, const bfp_vec* out) -> int32_t {
     return h->var ? bfp_var_jacobi(&L.vs, y, r, out, &q.q, &q.st, s) : bfp_jacobi(&h->A, y, r, out, &q.q, &q.st, s);
   };
@@ -1146,6 +1213,8 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
   o->coarse_onchip = 63;
   o->arith = BFP_ARITH_BFP;
   o->tile_rows = 0;
+  o->smoother = BFP_SMOOTH_JACOBI;
+  o->cheby_eta = kChebEta;
   return BFP_OK;
 }
 
@@ -1166,6 +1235,9 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if (o->arith != BFP_ARITH_BFP && o->arith != BFP_ARITH_FP32 && o->arith != BFP_ARITH_BF16) return BFP_ERR_ARG;
   if (o->tile_rows < 0 || o->tile_rows > 64) return BFP_ERR_ARG;
   if (o->w_step < 0 || (o->w_step > 0 && (o->w > 16 || o->arith != BFP_ARITH_BFP))) return BFP_ERR_ARG;
+  if (o->smoother != BFP_SMOOTH_JACOBI && o->smoother != BFP_SMOOTH_CHEBY) return BFP_ERR_ARG;
+  if (o->smoother == BFP_SMOOTH_CHEBY && (o->arith != BFP_ARITH_BFP || !(o->cheby_eta > 0.0 && o->cheby_eta < 1.0)))
+    return BFP_ERR_ARG;
   // n = 2^J - 1 with J >= 2
   if (o->n < 3 || ((o->n + 1) & o->n) != 0) return BFP_ERR_SHAPE;
   bfp_hierarchy* h = new (std::nothrow) bfp_hierarchy();
@@ -1173,6 +1245,14 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   h->o = *o;
   int32_t rc = bfp_laplace_stencil(o->ndim, o->omega, o->w_omega, &h->A);
   if (rc) { delete h; return rc; }
+  h->Ares = h->A;
+  if (o->smoother == BFP_SMOOTH_CHEBY) {
+    h->cheby = 1;
+    rc = cheby_setup(o, h->A, &h->c1, &h->c2);
+    if (rc) { delete h; return rc; }
+    h->Ares.omega.m = h->c1.m;
+    h->Ares.omega.e = h->c1.e - 1;
+  }
   for (int64_t n = o->n; n >= 3; n = (n - 1) / 2) {
     Level L;
     L.n = n;
@@ -1247,7 +1327,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
 int32_t bfp_hierarchy_create_var(const bfp_solver_opts* o, const double* k_nodes, bfp_hierarchy** out) {
   if (!o || !k_nodes || !out) return BFP_ERR_ARG;
   *out = nullptr;
-  if (o->ndim != 2 || o->arith != BFP_ARITH_BFP || o->w > 24) return BFP_ERR_ARG;
+  if (o->ndim != 2 || o->arith != BFP_ARITH_BFP || o->w > 24 || o->smoother != BFP_SMOOTH_JACOBI) return BFP_ERR_ARG;
   bfp_solver_opts oo = *o;
   oo.coarse_onchip = 0;                              // the on-chip cycle has the constant operator only
   bfp_hierarchy* h = nullptr;
