@@ -396,6 +396,37 @@ def bfp_ir_compare(bfp, torch, args, stream, sizes=(1023, 2047, 4095), steps=10)
     return out
 
 
+def recompute_table(bfp, torch, args, f, stream):
+    """The analogue of Table tab:recomputation on this workload: qcomp calls that recomputed (the
+    w_tmp window from gamma overflowed or underflowed) during one BFP-FMG (N = 2) on the finest level,
+    with w_tmp = w_out + min(w_add*, w_add_max), for w_add_max in {inf, 4, 2, 0}; the damped-Jacobi
+    V(2,2) and the paper's Chebyshev V(1,0).  Counts cover the V-cycle ops, the FMG interpolation and
+    the IR residual (FP64, quantised by qcomp with the previous residual as gamma)."""
+    n = args.n
+    rows = []
+    for smoother in ("jacobi", "cheby"):
+        for cap in (-1, 4, 2, 0):
+            o = bfp.bfp_solver_opts_default(2, n, args.w)
+            o.mode = bfp.QCOMP
+            o.w_add_max = cap
+            o.smoother = bfp.SMOOTH_CHEBY if smoother == "cheby" else bfp.SMOOTH_JACOBI
+            h = bfp.Hierarchy(o)
+            x = torch.zeros_like(f)
+            h.reset_stats(stream)
+            with torch.cuda.stream(stream):
+                h.fmg(f, x)
+            stream.synchronize()
+            fin, tot = h.finest_stats(stream), h.stats(stream)
+            rows.append({"smoother": smoother, "w_add_max": None if cap < 0 else cap,
+                         "finest": {"recomputed": fin["recomputed"] + fin["ir_recomputed"],
+                                    "qcomp_calls": fin["calls"] + fin["ir_residuals"],
+                                    "ir_residual_recomputed": fin["ir_recomputed"]},
+                         "all_levels": {"recomputed": tot["recomputed"] + tot["ir_recomputed"],
+                                        "qcomp_calls": tot["calls"] + tot["ir_residuals"]}})
+            h.close()
+    return rows
+
+
 def solver_compare(bfp, torch, args, f, stream, hbfp):
     """Float baselines beside the BFP solver on the same workload: GDOF/s of IR-V steps, and time to
     discretisation accuracy (FMG + K IR-V steps, K the smallest with accuracy ratio <= 1.5)."""
@@ -576,12 +607,13 @@ def run_ours(args):
         e2e = {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
                "d2h_bytes_per_step": 8 * dof}
 
-    floats, tta, var, sweep, irb = None, None, None, None, None
+    floats, tta, var, sweep, irb, rtab = None, None, None, None, None, None
     if rank == 0 and not args.no_compare:
         floats, tta = solver_compare(bfp, torch, args, f, stream, h)
         sweep = width_sweep(bfp, torch, args, f, stream) if nd == 2 else None
         var = var_compare(bfp, torch, stream) if nd == 2 else None
         irb = bfp_ir_compare(bfp, torch, args, stream) if nd == 2 else None
+        rtab = recompute_table(bfp, torch, args, f, stream) if nd == 2 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -606,7 +638,7 @@ def run_ours(args):
             "gpu_launches": int(launches_per_step * args.steps),
             "op_stats_2_steps": op_stats,
             "float_baselines": floats, "time_to_accuracy": tta, "width_sweep": sweep,
-            "variable_coefficients": var, "bfp_ir": irb,
+            "variable_coefficients": var, "bfp_ir": irb, "recomputations": rtab,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -313,6 +313,9 @@ typedef struct {
   double cheby_eta;      /* BFP_SMOOTH_CHEBY: the part [eta rho, rho] of the spectrum the two
                             Chebyshev steps target, 0 < eta < 1 (default 0.15: the i/100 that
                             minimises the FP64 V(1,0) convergence factor on level 5, 2D and 3D) */
+  int32_t w_add_max;     /* cap on the Table tab:estimates w_add of every op the solver enqueues:
+                            w_tmp = w_out + min(w_add*, w_add_max) (Table tab:recomputation's
+                            experiment); < 0: no cap (default -1) */
 } bfp_solver_opts;
 
 /* Relaxation of the V-cycle.
@@ -343,10 +346,17 @@ void bfp_hierarchy_destroy(bfp_hierarchy* h);
 
 /* Copies the hierarchy's device counters (bfp_stats layout, uint64[8], plus
  * [5] FP64 IR residual quantisations and [6] of those that recomputed the
- * residual because the Alg. qcomp window missed) to host memory;
- * synchronises the stream.  bfp_hierarchy_reset_stats zeroes
- * them (asynchronously). */
+ * residual because the Alg. qcomp window missed; the window's gamma is the
+ * previous IR residual's norm with w_add 4, or on an FMG level's first step
+ * the coarser level's last one with w_add 5, Table tab:estimates) to host
+ * memory; synchronises the stream.  bfp_hierarchy_reset_stats zeroes them
+ * (asynchronously). */
 int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream);
+/* The same counters for the finest level's separately launched ops alone
+ * (its V-cycle ops, FMG interpolation, IR residual and, for
+ * bfp_ir_iterate_bfp, the IR residual and update; not the on-chip coarse
+ * cycle). */
+int32_t bfp_hierarchy_read_finest_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream);
 int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream);
 
 /* y = V(nu1,nu2)(r) on the finest level: approximate solution of A' y = r

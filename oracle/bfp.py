@@ -582,6 +582,7 @@ class Quant:
     mode: str = "qcomp"           # "qcomp" | "nnqcomp"
     w_add: Optional[int] = None   # None -> Table tab:estimates value of the op
     gamma: Optional[tuple[int, int]] = None   # None -> rule of the op
+    w_add_max: Optional[int] = None   # cap on the table value (Table tab:recomputation's experiment)
 
 
 @dataclass
@@ -602,6 +603,8 @@ def quantize(ex: Exact, q: Quant, op: str, gamma_rule, stats: Optional[Stats] = 
     st = Stats(calls=1)
     if q.mode == "qcomp":
         w_add = W_ADD[op] if q.w_add is None else q.w_add
+        if q.w_add is None and q.w_add_max is not None:
+            w_add = min(w_add, q.w_add_max)
         out, ovf, unf = qcomp_alg(ex, q.w_out, q.w_out + max(w_add, 0), g)
         ref = qcomp_def(ex, q.w_out)
         assert out.e == ref.e and np.array_equal(to_object(out.m), to_object(ref.m))

@@ -260,6 +260,7 @@ class BFPSolver:
     w_step: int = 0                  # progressive precision: bits fewer per coarser level
     smoother: str = "jacobi"         # "jacobi": V(nu1, nu2) damped Jacobi; "cheby": the paper's V(1,0)
     eta: float = 0.15                # Chebyshev: targeted part [eta rho, rho] of the spectrum
+    w_add_max: Optional[int] = None  # cap on every op's table w_add (Table tab:recomputation)
     stats: B.Stats = field(default_factory=B.Stats)
 
     def __post_init__(self):
@@ -288,10 +289,10 @@ class BFPSolver:
 
     @property
     def q(self) -> B.Quant:
-        return B.Quant(self.w, self.mode)
+        return B.Quant(self.w, self.mode, w_add_max=self.w_add_max)
 
     def ql(self, k: int) -> B.Quant:
-        return B.Quant(self.width(k), self.mode)
+        return B.Quant(self.width(k), self.mode, w_add_max=self.w_add_max)
 
     def vcycle10(self, k: int, r: B.BFP) -> B.BFP:
         """Alg. v-cycle, V(1,0): y = qgemv(A, r, r, c2, c1); on levels above the coarsest the

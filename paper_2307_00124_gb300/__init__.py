@@ -74,7 +74,7 @@ class bfp_solver_opts(C.Structure):
                 ("omega", C.c_double), ("w_omega", C.c_int32), ("use_tmp", C.c_int32),
                 ("use_graph", C.c_int32), ("coarse_onchip", C.c_int32), ("arith", C.c_int32),
                 ("tile_rows", C.c_int32), ("w_step", C.c_int32), ("smoother", C.c_int32),
-                ("cheby_eta", C.c_double)]
+                ("cheby_eta", C.c_double), ("w_add_max", C.c_int32)]
 
 
 class flt_vec(C.Structure):
@@ -131,6 +131,7 @@ _sig = {
     "bfp_hierarchy_destroy": (None, [C.c_void_p]),
     "bfp_hierarchy_read_stats": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "bfp_hierarchy_reset_stats": (C.c_int32, [C.c_void_p, C.c_void_p]),
+    "bfp_hierarchy_read_finest_stats": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "bfp_vcycle": (C.c_int32, [C.c_void_p, P(bfp_vec), P(bfp_vec), C.c_void_p]),
     "bfp_ir_iterate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "bfp_ir_iterate_bfp": (C.c_int32, [C.c_void_p, P(bfp_vec), P(bfp_vec), C.c_int32, C.c_void_p]),
@@ -504,6 +505,14 @@ class Hierarchy:
     def stats(self, stream=None) -> dict:
         host = (C.c_uint64 * 8)()
         _check(_lib.bfp_hierarchy_read_stats(self.h, host, _stream(stream)), "bfp_hierarchy_read_stats")
+        keys = ("calls", "recomputed", "overflow", "underflow", "saturated", "ir_residuals", "ir_recomputed")
+        return {k: int(host[i]) for i, k in enumerate(keys)}
+
+    def finest_stats(self, stream=None) -> dict:
+        """The finest level's counters (bfp_hierarchy_read_finest_stats)."""
+        host = (C.c_uint64 * 8)()
+        _check(_lib.bfp_hierarchy_read_finest_stats(self.h, host, _stream(stream)),
+               "bfp_hierarchy_read_finest_stats")
         keys = ("calls", "recomputed", "overflow", "underflow", "saturated", "ir_residuals", "ir_recomputed")
         return {k: int(host[i]) for i, k in enumerate(keys)}
 

@@ -18,6 +18,10 @@ int& tile_rows_override() {
   static thread_local int rows = 0;
   return rows;
 }
+int& wadd_cap() {
+  static thread_local int cap = -1;
+  return cap;
+}
 }  // namespace bfp
 
 namespace {

@@ -34,6 +34,15 @@ struct TileScope {
   explicit TileScope(int rows) : saved(tile_rows_override()) { if (rows > 0) tile_rows_override() = rows; }
   ~TileScope() { tile_rows_override() = saved; }
 };
+// Cap on the ops' default w_add (Table tab:estimates values): w_tmp = w_out + min(w_add*, cap)
+// for ops enqueued inside the scope (negative: no cap; thread-local).
+int& wadd_cap();
+struct WaddScope {
+  int saved;
+  explicit WaddScope(int cap) : saved(wadd_cap()) { wadd_cap() = cap; }
+  ~WaddScope() { wadd_cap() = saved; }
+};
+inline int capped_wadd(int rule, int cap) { return cap >= 0 && cap < rule ? cap : rule; }
 inline int pick_rows(int heuristic, int cap) {
   const int v = tile_rows_override();
   return v > 0 ? (v < cap ? v : cap) : heuristic;
@@ -138,7 +147,7 @@ inline unsigned grid_for(int64_t work_items, int threads) {
 inline int32_t fill_q(QDesc& d, const bfp_q* q, const bfp_vec* out, int w_add_rule) {
   if (!q || q->w_out < 1 || q->w_out > 32 || q->w_out != out->w) return BFP_ERR_ARG;
   if (q->mode != BFP_QCOMP && q->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
-  int w_add = q->w_add < 0 ? w_add_rule : q->w_add;
+  int w_add = q->w_add < 0 ? capped_wadd(w_add_rule, wadd_cap()) : q->w_add;
   d.mode = q->mode;
   d.w_out = q->w_out;
   d.w_tmp = q->w_out + w_add;

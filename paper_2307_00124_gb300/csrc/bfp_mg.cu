@@ -374,7 +374,9 @@ struct bfp_hierarchy {
   bfp_stencil A;
   std::vector<Level> lv;
   std::vector<void*> allocs;
-  uint64_t* stats = nullptr;
+  uint64_t* stats = nullptr;             // counters of levels >= 1 and the on-chip coarse cycle
+  uint64_t* stats0 = nullptr;            // counters of the finest level's separately launched ops
+  int ir_first = 0;                      // the IR step being enqueued is an FMG level's first
   unsigned long long* norms = nullptr;   // 2 words for the residual norm
   int64_t* ir_gam = nullptr;             // per level: previous IR residual mu* (+2^40), 0 = unknown
   int64_t* arena = nullptr;              // all call-site meta blocks, contiguous
@@ -482,7 +484,7 @@ Q make_q(const bfp_hierarchy* h, const Level& L) {
   r.q.w_add = -1;
   r.q.mode = h->o.mode;
   r.q.tmp = (h->o.mode == BFP_QCOMP && h->o.use_tmp) ? L.tmp : nullptr;
-  r.st.counters = h->stats;
+  r.st.counters = &L == &h->lv[0] ? h->stats0 : h->stats;   // the finest level counts apart
   return r;
 }
 
@@ -541,7 +543,7 @@ int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, in
   if (op.c != (int32_t)op.c || op.nb != (int32_t)op.nb || op.mw != (int32_t)op.mw) return BFP_ERR_WIDTH;
   d.mode = h->o.mode;
   d.w_out = w;
-  d.w_tmp = w + rule;
+  d.w_tmp = w + capped_wadd(rule, h->o.w_add_max);
   d.use_tmp = 0;
   op.solo = h->lv[l + (kind == cRestrict ? 1 : 0)].n <= 15 ? 1 : 0;   // output level size
   *res = op;
@@ -636,7 +638,7 @@ int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, c
       if (op.q.hbits > 62 || (op.q.two && op.q.lbits > 62)) return BFP_ERR_WIDTH;
       op.q.mode = h->o.mode;
       op.q.w_out = w;
-      op.q.w_tmp = w + rule;
+      op.q.w_tmp = w + capped_wadd(rule, h->o.w_add_max);
       op.q.use_tmp = 0;
       if (t == 1) a.s = sh;
     }
@@ -897,10 +899,12 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
   a.nbshift = nd == 2 ? 2 : 3;                   // nb = -2^-nbshift
   a.out = o; a.meta = r->meta;
   a.w = r->w;
-  a.w_tmp = r->w + 4;                            // Table tab:estimates, IR residual (i > 1): w_add = 4
+  // Table tab:estimates, IR residual: w_add = 4 (i > 1), 5 for the first step on an FMG level
+  // (gamma from the coarser level's last residual)
+  a.w_tmp = r->w + capped_wadd(h->ir_first ? 5 : 4, h->o.w_add_max);
   a.tmp = (h->lv[k].tmp && a.w_tmp <= 32) ? (int32_t*)h->lv[k].tmp : nullptr;
   a.gamma_mu = h->ir_gam + k;
-  a.stats = h->stats;
+  a.stats = k == 0 ? h->stats0 : h->stats;
   if (nd == 2) {
     if (cdiag != 1.0) return BFP_ERR_ARG;
     const int rs = pick_rows(g.ny >= 2048 ? 16 : (g.ny >= 1024 ? 8 : (g.ny >= 256 ? 4 : 2)), 64);
@@ -1215,6 +1219,7 @@ int32_t bfp_solver_opts_default(int32_t ndim, int64_t n, int32_t w, bfp_solver_o
   o->tile_rows = 0;
   o->smoother = BFP_SMOOTH_JACOBI;
   o->cheby_eta = kChebEta;
+  o->w_add_max = -1;
   return BFP_OK;
 }
 
@@ -1236,6 +1241,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if (o->tile_rows < 0 || o->tile_rows > 64) return BFP_ERR_ARG;
   if (o->w_step < 0 || (o->w_step > 0 && (o->w > 16 || o->arith != BFP_ARITH_BFP))) return BFP_ERR_ARG;
   if (o->smoother != BFP_SMOOTH_JACOBI && o->smoother != BFP_SMOOTH_CHEBY) return BFP_ERR_ARG;
+  if (o->w_add_max > 32) return BFP_ERR_ARG;
   if (o->smoother == BFP_SMOOTH_CHEBY && (o->arith != BFP_ARITH_BFP || !(o->cheby_eta > 0.0 && o->cheby_eta < 1.0)))
     return BFP_ERR_ARG;
   // n = 2^J - 1 with J >= 2
@@ -1309,11 +1315,12 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
     if (crc) { bfp_hierarchy_destroy(h); return crc; }
   }
   if (ok) {
-    h->stats = (uint64_t*)dalloc(h, 8 * sizeof(uint64_t));
+    h->stats = (uint64_t*)dalloc(h, 16 * sizeof(uint64_t));
+    h->stats0 = h->stats ? h->stats + 8 : nullptr;
     h->norms = (unsigned long long*)dalloc(h, 2 * sizeof(unsigned long long));
     h->ir_gam = (int64_t*)dalloc(h, h->lv.size() * sizeof(int64_t));
     ok = h->stats && h->norms && h->ir_gam;
-    if (ok) cudaMemset(h->stats, 0, 8 * sizeof(uint64_t));
+    if (ok) cudaMemset(h->stats, 0, 16 * sizeof(uint64_t));
     if (ok) cudaMemset(h->ir_gam, 0, h->lv.size() * sizeof(int64_t));
   }
   if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
@@ -1356,18 +1363,29 @@ int32_t bfp_hierarchy_var_ir_operator(const bfp_hierarchy* h, bfp_varstencil* ou
   return BFP_OK;
 }
 
-int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream) {
+static int32_t read_counters(bfp_hierarchy* h, uint64_t* host8, bool finest_only, bfp_stream stream) {
   if (!h || !host8) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
-  if (cudaMemcpyAsync(host8, h->stats, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  uint64_t both[16];
+  if (cudaMemcpyAsync(both, h->stats, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return BFP_ERR_CUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BFP_ERR_CUDA;
+  for (int i = 0; i < 8; ++i) host8[i] = both[8 + i] + (finest_only ? 0 : both[i]);
+  return BFP_OK;
+}
+
+int32_t bfp_hierarchy_read_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream) {
+  return read_counters(h, host8, false, stream);
+}
+
+int32_t bfp_hierarchy_read_finest_stats(bfp_hierarchy* h, uint64_t* host8, bfp_stream stream) {
+  return read_counters(h, host8, true, stream);
 }
 
 int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream) {
   if (!h) return BFP_ERR_ARG;
-  return cudaMemsetAsync(h->stats, 0, 8 * sizeof(uint64_t), as_stream(stream)) == cudaSuccess ? BFP_OK
-                                                                                               : BFP_ERR_CUDA;
+  return cudaMemsetAsync(h->stats, 0, 16 * sizeof(uint64_t), as_stream(stream)) == cudaSuccess ? BFP_OK
+                                                                                                : BFP_ERR_CUDA;
 }
 
 int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_stream stream) {
@@ -1382,6 +1400,7 @@ int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_str
   if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;
   PrezeroedScope pz;
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   bfp_vec res;
   TRY(vcycle_rec(h, 0, r, y, &h->y0, &res, s));
   // the result's mantissas are in y; its exponent and norm are in a call-site slot
@@ -1392,6 +1411,7 @@ int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_str
 
 static int32_t ir_iterate_direct(bfp_hierarchy* h, const double* f, double* x, int32_t k, cudaStream_t s) {
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   const double bs = bscale_of(h);
   for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));
   return BFP_OK;
@@ -1448,6 +1468,7 @@ int32_t bfp_ir_iterate_bfp(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x,
   for (int d = 0; d < 3; ++d) h->xt.n[d] = x->n[d];
   if (overlaps(b, &h->xt) || overlaps(x, &h->xt)) return BFP_ERR_ARG;
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   const int32_t pairs = k / 2;
   if (pairs > 0 && h->o.use_graph && s != nullptr) {
     // two steps (x -> xt -> x) captured once per (b, x, stream) and replayed
@@ -1489,6 +1510,7 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
   if (!h || !f || !x) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   const int nd = h->o.ndim;
   const int nl = (int)h->lv.size();
   const double rscale = nd == 2 ? 0.25 : 0.0625;   // R~ = P^T (2D), P^T/2 (3D): weights prod(2-|d|) * 2^e_R
@@ -1536,7 +1558,17 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
     }
     const double* bk = (k == 0) ? f : L.b;
     const double sc = (k == 0) ? bs0 : 1.0;
-    for (int i = 0; i < h->o.n_fmg; ++i) TRY(ir_step(h, k, bk, sc, xk, s));
+    if (k < nl - 1) {   // first step: gamma from the coarser level's last IR residual (i = 1 row)
+      if (cudaMemcpyAsync(h->ir_gam + k, h->ir_gam + k + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+        return BFP_ERR_CUDA;
+    }
+    for (int i = 0; i < h->o.n_fmg; ++i) {
+      h->ir_first = (i == 0 && k < nl - 1) ? 1 : 0;
+      const int32_t rc = ir_step(h, k, bk, sc, xk, s);
+      h->ir_first = 0;
+      TRY(rc);
+    }
   }
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -1559,6 +1591,7 @@ int32_t flt_vcycle(bfp_hierarchy* h, const flt_vec* r, const flt_vec* y, bfp_str
   if (foverlaps(r, y)) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   flt_vec res;
   return flt_vcycle_rec(h, 0, r, y, &h->fy0, &res, s);   // the result lands in y (bufA)
 }
@@ -1575,6 +1608,7 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
   if (!h || !f || !x || !o || !rep) return BFP_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   std::memset(rep, 0, sizeof(*rep));
   if (o->fmg_start) TRY(bfp_fmg(h, f, x, s));
   const int nd = h->o.ndim;
@@ -1641,6 +1675,7 @@ namespace {
 // FMG (optional) then k IR-V steps of one instance on stream s (direct launches)
 int32_t instance_solve(bfp_hierarchy* h, const double* f, double* x, int32_t k, int32_t fmg, cudaStream_t s) {
   TileScope ts(h->o.tile_rows);
+  WaddScope wz(h->o.w_add_max);
   if (fmg) TRY(bfp_fmg(h, f, x, s));
   const double bs = bscale_of(h);
   for (int i = 0; i < k; ++i) TRY(ir_step(h, 0, f, bs, x, s));

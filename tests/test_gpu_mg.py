@@ -163,3 +163,35 @@ def test_progressive_precision_rejects_wide_or_float():
         o.w_step, o.arith = 1, arith
         with pytest.raises(bfp.BFPError):
             bfp.Hierarchy(o)
+
+
+@pytest.mark.parametrize("cap", [0, 2, 4])
+@pytest.mark.parametrize("smoother", ["jacobi", "cheby"])
+@pytest.mark.parametrize("onchip", [63, 0])
+def test_w_add_cap_matches_oracle_counts(cap, smoother, onchip):
+    """opts.w_add_max (Table tab:recomputation's experiment): results stay bit-exact (qcomp), and
+    the recomputation counters equal the oracle's with the same cap; the finest level's counters
+    hold its own ops only."""
+    n, w = 127, 16
+    o = bfp.bfp_solver_opts_default(2, n, w)
+    o.mode = bfp.QCOMP
+    o.w_add_max = cap
+    o.coarse_onchip = onchip
+    o.smoother = bfp.SMOOTH_CHEBY if smoother == "cheby" else bfp.SMOOTH_JACOBI
+    h = bfp.Hierarchy(o)
+    s = mg.BFPSolver(2, n, w=w, mode="qcomp", omega=o.omega, w_omega=o.w_omega, smoother=smoother,
+                     w_add_max=cap)
+    rm = random_mantissas((n, n), w, 9, "smooth")
+    r = bfp.BFPVector.from_mantissas(rm, -25, w)
+    y = bfp.BFPVector((n, n), w)
+    h.reset_stats()
+    h.vcycle(r, y)
+    ref = s.vcycle(0, B.BFP(rm, -25, w))
+    torch.cuda.synchronize()
+    assert y.exponent == ref.e and np.array_equal(y.mantissas(), np.asarray(ref.m).astype(np.int64))
+    st, fin = h.stats(), h.finest_stats()
+    assert (st["calls"], st["recomputed"], st["overflow"], st["underflow"]) == (
+        s.stats.calls, s.stats.recomputed, s.stats.overflow, s.stats.underflow)
+    assert fin["calls"] == (4 if smoother == "cheby" else 7)      # the finest level's own ops
+    assert fin["recomputed"] <= st["recomputed"]
+    h.close()
