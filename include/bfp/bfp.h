@@ -53,7 +53,10 @@ typedef enum {
 
 /* One BFP block (Sec. 2: tuple (e, m, w, d)).
  *   mant : device, int16_t when 1 <= w <= 16, int32_t when 17 <= w <= 32;
- *          16-byte aligned.
+ *          16-byte aligned.  int64_t when 33 <= w <= 62 is accepted by
+ *          bfp_normalize, bfp_from_f64, bfp_to_f64, bfp_axpy, bfp_residual
+ *          (y and r) and bfp_ir_iterate_bfp; every other op returns
+ *          BFP_ERR_ARG for it.
  *   meta : device, BFP_META_WORDS int64 (see above), 8-byte aligned.
  *   n    : points per dimension, x fastest; unused dimensions are 1.
  *   ld   : elements between consecutive x-lines (rows); ld >= n[0] and
@@ -157,7 +160,8 @@ int32_t bfp_normalize(const bfp_vec* x, const bfp_vec* out, const bfp_q* q,
  * unspecified. */
 int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream);
 
-/* out (device, dense doubles) = m * 2^e, exact when representable (w <= 32). */
+/* out (device, dense doubles) = m * 2^e, exact when representable (|m| < 2^53;
+ * wider mantissas are rounded to nearest). */
 int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream);
 
 /* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp); x and y may
@@ -176,7 +180,8 @@ int32_t bfp_stencil_apply(const bfp_stencil* A, const bfp_vec* x, const bfp_vec*
                           const bfp_q* q, const bfp_stats* st, bfp_stream stream);
 
 /* rv = A y - r (Alg. egemv with alpha = 1, beta = -1; the V-cycle residual
- * line of Alg. v-cycle, with the paper's sign). */
+ * line of Alg. v-cycle, with the paper's sign).  y and r may differ in
+ * storage, int64 included (rv: w <= 32). */
 int32_t bfp_residual(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r,
                      const bfp_vec* rv, const bfp_q* q, const bfp_stats* st,
                      bfp_stream stream);
@@ -390,9 +395,11 @@ int32_t bfp_ir_iterate(bfp_hierarchy* h, const double* f, double* x, int32_t k,
  *   x = qsub(x, y)              quantised by Alg. qcomp to x->w bits.
  * b: the scaled right-hand side b' = s f (s from bfp_hierarchy_rhs_scale),
  * quantised by the caller (e.g. bfp_from_f64) to b->w bits.  x: the iterate,
- * updated in place; x->w is the working width (1..32).  x and b have the
- * finest shape, the same storage (int16 for w <= 16, else int32; b->w <= 32)
- * and do not overlap.  Variable-coefficient hierarchies use their finest
+ * updated in place; x->w is the working width (1..62; int64 storage above
+ * 32 bits, BFP_ERR_WIDTH when A'x would pass the 62-bit group bound).  x and
+ * b have the finest shape, any storage (b->w <= 62) and do not overlap.
+ * Variable-coefficient hierarchies (x and b of one storage class, at most
+ * 32 bits) use their finest
  * operator with 26-bit faces (bfp_hierarchy_var_ir_operator: Alg. ir
  * quantises A to the input width, finer than the inner solver's 16-bit
  * faces).  A scratch copy of x is allocated on the first call (and again

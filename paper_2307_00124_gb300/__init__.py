@@ -185,7 +185,8 @@ def pitch(n0: int) -> int:
 # ---- BFP vectors backed by torch device memory --------------------------------
 
 class BFPVector:
-    """A BFP block in device memory: mantissas (rows x ld, int16 or int32) + meta (int64[8]).
+    """A BFP block in device memory: mantissas (rows x ld, int16 / int32 / int64 for w <= 16 / 32 / 62)
+    + meta (int64[8]).
 
     ``shape`` is the numpy-order logical shape ((n,), (ny, nx) or (nz, ny, nx)).
     """
@@ -197,7 +198,7 @@ class BFPVector:
         nx = self.shape[-1]
         self.ld = pitch(nx)
         self.rows = int(np.prod(self.shape[:-1])) if len(self.shape) > 1 else 1
-        dt = torch.int16 if self.w <= 16 else torch.int32
+        dt = torch.int16 if self.w <= 16 else (torch.int32 if self.w <= 32 else torch.int64)
         # at least one row of storage: the C ABI wants a non-null mantissa pointer, also for an empty grid
         self.mant = mant if mant is not None else torch.zeros((max(self.rows, 1), self.ld), dtype=dt, device=device)
         self.meta = meta if meta is not None else torch.zeros(META_WORDS, dtype=torch.int64, device=device)
@@ -223,7 +224,7 @@ class BFPVector:
         import torch
         m = np.asarray(m, dtype=np.int64)
         v = cls(m.shape, w, device)
-        host = np.zeros(tuple(v.mant.shape), dtype=np.int16 if w <= 16 else np.int32)
+        host = np.zeros(tuple(v.mant.shape), dtype=np.int16 if w <= 16 else (np.int32 if w <= 32 else np.int64))
         host[: v.rows, : m.shape[-1]] = m.reshape(v.rows, m.shape[-1])
         v.mant.copy_(torch.from_numpy(host))
         meta = np.zeros(META_WORDS, dtype=np.int64)

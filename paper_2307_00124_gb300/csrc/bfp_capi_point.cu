@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ x, 
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = idx / nvec, c0 = (idx - row * nvec) << 3;
-    int32_t o[8];
+    int64_t o[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       o[k] = 0;
@@ -71,11 +71,20 @@ __global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ x, 
       } else {
         const int64_t sh = E - e_out;
         const int64_t v = sh >= 0 ? (int64_t)((uint64_t)M << (sh > 63 ? 63 : sh)) : (M >> (-sh > 63 ? 63 : -sh));
-        o[k] = (int32_t)v;
+        o[k] = v;
         red.nrm = max(red.nrm, (long long)(v < 0 ? -v : v));
       }
     }
-    if (!pass1) st8(out, row, c0, o);
+    if (!pass1) {
+      if (out.is64) {
+        stw8(out, row, c0, o);
+      } else {
+        int32_t o32[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o32[k] = (int32_t)o[k];
+        st8(out, row, c0, o32);
+      }
+    }
   }
   if (bad) atomicOr((unsigned long long*)&meta_out[BFP_META_FLAGS], 1ull);
   block_commit(red, meta_out, nullptr, pass1);
@@ -208,17 +217,21 @@ int32_t bfp_laplace_stencil(int32_t ndim, double omega, int32_t w_omega, bfp_ste
 int32_t bfp_normalize(const bfp_vec* x, const bfp_vec* out, const bfp_q* q, const bfp_stats* st,
                       bfp_stream stream) {
   int32_t rc;
-  if ((rc = check_vec(x)) || (rc = check_vec(out))) return rc;
+  if ((rc = check_vec_wide(x)) || (rc = check_vec_wide(out))) return rc;
   if (!same_shape(x, out)) return BFP_ERR_SHAPE;
   if (overlaps(x, out)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
-  if ((rc = fill_q(d, q, out, 2))) return rc;
+  if ((rc = fill_q(d, q, out, 2, true))) return rc;
   d.meta_a = x->meta;
   d.meta_out = out->meta;
   d.stats = st ? st->counters : nullptr;
   d.ch = 0; d.ha = 1; d.two = 0; d.hbits = x->w;
   d.ng = 1; d.gv[0] = 0; d.gm[0] = 1; d.ge[0] = 0;   // gamma = ||x||
   cudaStream_t s = as_stream(stream);
+  if (is64(x) || is64(out)) {
+    const OpCopyW op{vin(x), esize(x)};
+    return is64(out) ? launch_quant_wide(op, d, out, s) : launch_quant(op, d, out, s);
+  }
   if (is32(x)) return launch_quant(OpCopy<int32_t>{vin(x)}, d, out, s);
   return launch_quant(OpCopy<int16_t>{vin(x)}, d, out, s);
 }
@@ -226,12 +239,12 @@ int32_t bfp_normalize(const bfp_vec* x, const bfp_vec* out, const bfp_q* q, cons
 int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y, const bfp_vec* z,
                  const bfp_q* q, const bfp_stats* st, bfp_stream stream) {
   int32_t rc;
-  if ((rc = check_vec(x)) || (rc = check_vec(y)) || (rc = check_vec(z))) return rc;
+  if ((rc = check_vec_wide(x)) || (rc = check_vec_wide(y)) || (rc = check_vec_wide(z))) return rc;
   if (!same_shape(x, y) || !same_shape(x, z)) return BFP_ERR_SHAPE;
   if (overlaps(x, z) || overlaps(y, z)) return BFP_ERR_ARG;
   if (a.m >= (1ll << 31) || a.m < -(1ll << 31) || b.m >= (1ll << 31) || b.m < -(1ll << 31)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
-  if ((rc = fill_q(d, q, z, 2))) return rc;
+  if ((rc = fill_q(d, q, z, 2, true))) return rc;
   d.meta_a = x->meta; d.meta_b = y->meta; d.meta_out = z->meta;
   d.stats = st ? st->counters : nullptr;
   d.ch = a.e; d.ha = 1;                 // alpha x at e_alpha + e_x (Alg. eaxpby-setup)
@@ -243,6 +256,10 @@ int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
   d.gv[0] = 0; d.gm[0] = (uint64_t)(a.m < 0 ? -a.m : a.m); d.ge[0] = a.e;
   d.gv[1] = 1; d.gm[1] = (uint64_t)(b.m < 0 ? -b.m : b.m); d.ge[1] = b.e;
   cudaStream_t s = as_stream(stream);
+  if (is64(x) || is64(y) || is64(z)) {
+    const OpAxpyW op{vin(x), vin(y), esize(x), esize(y), a.m, b.m};
+    return is64(z) ? launch_quant_wide(op, d, z, s) : launch_quant(op, d, z, s);
+  }
   if (is32(x)) {
     if (is32(y)) return launch_quant(OpAxpy<int32_t, int32_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
     return launch_quant(OpAxpy<int32_t, int16_t>{vin(x), vin(y), a.m, b.m}, d, z, s);
@@ -254,7 +271,7 @@ int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
 int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream) {
   int32_t rc;
   if (!x) return BFP_ERR_ARG;
-  if ((rc = check_vec(out))) return rc;
+  if ((rc = check_vec_wide(out))) return rc;
   cudaStream_t s = as_stream(stream);
   VOut o = vout(out);
   const int64_t items = rows_of(out) * (out->ld / 8);
@@ -270,12 +287,13 @@ int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream) {
 int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream) {
   int32_t rc;
   if (!out) return BFP_ERR_ARG;
-  if ((rc = check_vec(x))) return rc;
+  if ((rc = check_vec_wide(x))) return rc;
   cudaStream_t s = as_stream(stream);
   const int64_t total = rows_of(x) * x->n[0];
   if (total == 0) return BFP_OK;
   unsigned g = grid_for(total, 256);
-  if (is32(x)) k_to_f64<int32_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
+  if (is64(x)) k_to_f64<long long><<<g, 256, 0, s>>>(vin(x), x->meta, out);
+  else if (is32(x)) k_to_f64<int32_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
   else k_to_f64<int16_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;

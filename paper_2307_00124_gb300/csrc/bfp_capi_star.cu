@@ -59,14 +59,20 @@ int32_t bfp_stencil_apply(const bfp_stencil* A, const bfp_vec* x, const bfp_vec*
 int32_t bfp_residual(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r, const bfp_vec* rv,
                      const bfp_q* q, const bfp_stats* st, bfp_stream stream) {
   int32_t rc;
-  if ((rc = check_vec(y)) || (rc = check_vec(r)) || (rc = check_vec(rv)) || (rc = check_stencil(A, y))) return rc;
+  if ((rc = check_vec_wide(y)) || (rc = check_vec_wide(r)) || (rc = check_vec(rv)) || (rc = check_stencil(A, y)))
+    return rc;
   if (!same_shape(y, r) || !same_shape(y, rv)) return BFP_ERR_SHAPE;
-  if (is32(y) != is32(r)) return BFP_ERR_ARG;
+  const bool wide = is64(y) || is64(r) || is32(y) != is32(r);   // int64 or mixed storage
   if (overlaps(y, rv) || overlaps(r, rv)) return BFP_ERR_ARG;
   QDesc d = blank_desc();
   int rule = 0;
   if ((rc = desc_residual(A, y->w, r->w, d, &rule)) || (rc = fill_q(d, q, rv, rule))) return rc;
   d.meta_a = y->meta; d.meta_b = r->meta; d.meta_out = rv->meta; d.stats = st ? st->counters : nullptr;
+  if (wide) {   // int64 operands or mixed storage: the generic row kernel
+    if (A->ndim == 2)
+      return launch_quant(OpResW<2>{vin(y), vin(r), esize(y), esize(r), A->center, A->nbr}, d, rv, as_stream(stream));
+    return launch_quant(OpResW<3>{vin(y), vin(r), esize(y), esize(r), A->center, A->nbr}, d, rv, as_stream(stream));
+  }
   return star_dispatch<kResidual>(A->ndim, y, r, d, rv, A->center, A->nbr, 0, is32(y), as_stream(stream));
 }
 

@@ -262,32 +262,33 @@ __device__ __forceinline__ int mu_key(Acc Z, int64_t H, int64_t L, const Plan& p
 }
 
 // floor(Z * 2^-t) narrowed to X_w (saturating); sat set when clamped.
-template <class Acc>
-__device__ __forceinline__ int32_t narrow_sat(Acc Z, int64_t t, int w, int& sat) {
+// (R: the mantissa type, int32_t, or int64_t for outputs of 33..62 bits.)
+template <class Acc, class R = int32_t>
+__device__ __forceinline__ R narrow_sat(Acc Z, int64_t t, int w, int& sat) {
   const int64_t hi = (1ll << (w - 1)) - 1, lo = -(1ll << (w - 1));
   if (t >= 0) {
     Acc v = shr_floor(Z, t);
-    if (v > (Acc)hi) { ++sat; return (int32_t)hi; }
-    if (v < (Acc)lo) { ++sat; return (int32_t)lo; }
-    return (int32_t)v;
+    if (v > (Acc)hi) { ++sat; return (R)hi; }
+    if (v < (Acc)lo) { ++sat; return (R)lo; }
+    return (R)v;
   }
   if (Z == 0) return 0;
   int64_t k = -t;
-  if (k >= 64 || msb_acc(Z) + k > w) { ++sat; return Z < 0 ? (int32_t)lo : (int32_t)hi; }
-  return (int32_t)((int64_t)Z << k);
+  if (k >= 64 || msb_acc(Z) + k > w) { ++sat; return Z < 0 ? (R)lo : (R)hi; }
+  return (R)((int64_t)Z << k);
 }
 
 // Output mantissa at the plan's e_out (nnqcomp, or qcomp recompute).
-template <class Acc>
-__device__ __forceinline__ int32_t finish(Acc Z, int64_t H, int64_t L, const Plan& p, int& sat) {
+template <class Acc, class R = int32_t>
+__device__ __forceinline__ R finish(Acc Z, int64_t H, int64_t L, const Plan& p, int& sat) {
   int64_t t = p.e_out - p.Ez;
-  if (!p.guarded || t >= 0) return narrow_sat(Z, t, p.w_out, sat);
+  if (!p.guarded || t >= 0) return narrow_sat<Acc, R>(Z, t, p.w_out, sat);
   int64_t T = p.top_is_h ? H : L, B = p.top_is_h ? L : H;
   if (T != 0) {  // |z*| >= 2^(Ez+63) > 2^(e_out + w_out): saturates
     ++sat;
-    return T < 0 ? (int32_t)(-(1ll << (p.w_out - 1))) : (int32_t)((1ll << (p.w_out - 1)) - 1);
+    return T < 0 ? (R)(-(1ll << (p.w_out - 1))) : (R)((1ll << (p.w_out - 1)) - 1);
   }
-  return narrow_sat((int64_t)B, p.e_out - p.Eb, p.w_out, sat);
+  return narrow_sat<int64_t, R>((int64_t)B, p.e_out - p.Eb, p.w_out, sat);
 }
 
 // qcomp window value decr(w* - w_tmp, z* >> lambda_tmp) at exponent e_tmp.

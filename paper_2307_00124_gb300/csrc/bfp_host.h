@@ -70,10 +70,13 @@ inline int clog2(int64_t m) {
 }
 
 inline bool is32(const bfp_vec* v) { return v->w > 16; }
+// int64 mantissas (33 <= w <= 62): accepted only by the ops that check with check_vec_wide
+inline bool is64(const bfp_vec* v) { return v->w > 32; }
+inline int esize(const bfp_vec* v) { return v->w > 32 ? 8 : (v->w > 16 ? 4 : 2); }
 
-inline int32_t check_vec(const bfp_vec* v) {
+inline int32_t check_vec_w(const bfp_vec* v, int wmax) {
   if (!v || !v->mant || !v->meta) return BFP_ERR_ARG;
-  if (v->w < 1 || v->w > 32) return BFP_ERR_ARG;
+  if (v->w < 1 || v->w > wmax) return BFP_ERR_ARG;
   if (v->ndim < 1 || v->ndim > 3) return BFP_ERR_SHAPE;
   for (int i = 0; i < 3; ++i)
     if (v->n[i] < 0) return BFP_ERR_SHAPE;
@@ -84,6 +87,8 @@ inline int32_t check_vec(const bfp_vec* v) {
   if (reinterpret_cast<uintptr_t>(v->meta) % 8 != 0) return BFP_ERR_SHAPE;
   return BFP_OK;
 }
+inline int32_t check_vec(const bfp_vec* v) { return check_vec_w(v, 32); }
+inline int32_t check_vec_wide(const bfp_vec* v) { return check_vec_w(v, 62); }
 
 inline int64_t rows_of(const bfp_vec* v) { return v->n[1] * v->n[2]; }
 
@@ -94,9 +99,9 @@ inline bool same_shape(const bfp_vec* a, const bfp_vec* b) {
 inline bool overlaps(const bfp_vec* a, const bfp_vec* b) {
   if (!a || !b) return false;
   const char* a0 = (const char*)a->mant;
-  const char* a1 = a0 + (rows_of(a) * a->ld) * (is32(a) ? 4 : 2);
+  const char* a1 = a0 + (rows_of(a) * a->ld) * esize(a);
   const char* b0 = (const char*)b->mant;
-  const char* b1 = b0 + (rows_of(b) * b->ld) * (is32(b) ? 4 : 2);
+  const char* b1 = b0 + (rows_of(b) * b->ld) * esize(b);
   bool mant = a0 < b1 && b0 < a1 && rows_of(a) > 0 && rows_of(b) > 0;
   bool meta = (a->meta < b->meta + BFP_META_WORDS) && (b->meta < a->meta + BFP_META_WORDS);
   return mant || meta;
@@ -120,6 +125,7 @@ inline VOut vout(const bfp_vec* v) {
   r.ny = v->n[1];
   r.nz = v->n[2];
   r.is32 = is32(v) ? 1 : 0;
+  r.is64 = is64(v) ? 1 : 0;
   return r;
 }
 
@@ -144,8 +150,8 @@ inline unsigned grid_for(int64_t work_items, int threads) {
 
 // Fills the quantisation fields of a QDesc from a bfp_q; w_add_rule is the
 // op's Table tab:estimates value.
-inline int32_t fill_q(QDesc& d, const bfp_q* q, const bfp_vec* out, int w_add_rule) {
-  if (!q || q->w_out < 1 || q->w_out > 32 || q->w_out != out->w) return BFP_ERR_ARG;
+inline int32_t fill_q(QDesc& d, const bfp_q* q, const bfp_vec* out, int w_add_rule, bool wide_ok = false) {
+  if (!q || q->w_out < 1 || q->w_out > (wide_ok ? 62 : 32) || q->w_out != out->w) return BFP_ERR_ARG;
   if (q->mode != BFP_QCOMP && q->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
   int w_add = q->w_add < 0 ? capped_wadd(w_add_rule, wadd_cap()) : q->w_add;
   d.mode = q->mode;
@@ -178,6 +184,21 @@ inline int32_t launch_quant(const Op& op, const QDesc& q, const bfp_vec* out, cu
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (q.mode == kQcomp) k_quant<Op, true><<<g, threads, 0, s>>>(op, q, o);
   k_quant<Op, false><<<g, threads, 0, s>>>(op, q, o);
+  note_launches(q.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+// The same for an output with int64 mantissas (33 <= w_out <= 62).
+template <class Op>
+inline int32_t launch_quant_wide(const Op& op, const QDesc& q, const bfp_vec* out, cudaStream_t s) {
+  if (q.hbits > 62 || (q.two && q.lbits > 62)) return BFP_ERR_WIDTH;
+  VOut o = vout(out);
+  const int threads = 256;
+  const int64_t items = rows_of(out) * (out->ld / 8);
+  unsigned g = grid_for(items, threads);
+  if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (q.mode == kQcomp) k_quant_wide<Op, true><<<g, threads, 0, s>>>(op, q, o);
+  k_quant_wide<Op, false><<<g, threads, 0, s>>>(op, q, o);
   note_launches(q.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }

@@ -1446,16 +1446,16 @@ static bool same_vec(const bfp_vec& a, const bfp_vec& b) { return std::memcmp(&a
 int32_t bfp_ir_iterate_bfp(bfp_hierarchy* h, const bfp_vec* b, const bfp_vec* x, int32_t k, bfp_stream stream) {
   if (!h || !b || !x || k < 0 || is_float(h)) return BFP_ERR_ARG;
   int32_t rc;
-  if ((rc = check_vec(b)) || (rc = check_vec(x))) return rc;
+  if ((rc = check_vec_wide(b)) || (rc = check_vec_wide(x))) return rc;
   const Level& L = h->lv[0];
   if (!same_shape(b, &L.r) || !same_shape(x, &L.r)) return BFP_ERR_SHAPE;
-  if (is32(b) != is32(x)) return BFP_ERR_ARG;
+  if (h->var && (is64(b) || is64(x))) return BFP_ERR_WIDTH;   // A'x with 26-bit faces: x <= 32 bits
   if (overlaps(b, x)) return BFP_ERR_ARG;
   if (x->ld != L.r.ld) return BFP_ERR_SHAPE;
   if (k == 0) return BFP_OK;
   cudaStream_t s = as_stream(stream);
   // scratch iterate with x's storage (pitch and rows of the finest level)
-  const size_t bytes = (size_t)(L.r.n[1] * L.r.n[2] * L.r.ld) * (is32(x) ? 4 : 2);
+  const size_t bytes = (size_t)(L.r.n[1] * L.r.n[2] * L.r.ld) * esize(x);
   if (!h->xt.mant || h->xt_bytes != bytes) {
     void* m = dalloc(h, bytes);
     int64_t* meta = (int64_t*)dalloc(h, BFP_META_WORDS * sizeof(int64_t));

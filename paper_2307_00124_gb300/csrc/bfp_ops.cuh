@@ -19,6 +19,7 @@ struct VOut {
   void* m;
   int64_t ld, nx, ny, nz;
   int32_t is32;
+  int32_t is64;   // int64 mantissas (33 <= w <= 62; outputs of k_quant_wide only)
 };
 
 template <class T>
@@ -93,6 +94,43 @@ __device__ __forceinline__ void st8(const VOut& v, int64_t row, int64_t c0, cons
   stv<8>(v, row, c0, o);
 }
 
+// 8 mantissas of any storage (int16 / int32 / int64) widened to int64; the zero rules of ldv.
+template <class T>
+__device__ __forceinline__ void ldw8(const VIn& v, int64_t row, int64_t c0, int64_t (&o)[8]) {
+  if constexpr (sizeof(T) != 8) {
+    int32_t t[8];
+    ldv<T, 8>(v, row, c0, t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = t[k];
+    return;
+  } else {
+  if (row < 0 || row >= v.ny * v.nz || c0 >= v.ld || c0 >= v.nx) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = 0;
+    return;
+  }
+  const longlong2* p = reinterpret_cast<const longlong2*>(reinterpret_cast<const long long*>(v.m) + row * v.ld + c0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const longlong2 a = __ldg(p + q);
+    o[2 * q] = a.x;
+    o[2 * q + 1] = a.y;
+  }
+  if (c0 + 8 > v.nx) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (c0 + k >= v.nx) o[k] = 0;
+  }
+  }
+}
+
+// 8 int64 mantissas (outputs of 33..62 bits).
+__device__ __forceinline__ void stw8(const VOut& v, int64_t row, int64_t c0, const int64_t (&o)[8]) {
+  longlong2* p = reinterpret_cast<longlong2*>(reinterpret_cast<long long*>(v.m) + row * v.ld + c0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) p[q] = make_longlong2(o[2 * q], o[2 * q + 1]);
+}
+
 // ---------------------------------------------------------------------------
 // Exact per-element computations.  Each fills H[k], L[k] (the two exponent
 // groups of z*) for the 8 outputs at (row, c0 .. c0+7).
@@ -121,6 +159,71 @@ struct OpAxpy {
     ld8<TY>(y, row, c0, b);
 #pragma unroll
     for (int k = 0; k < 8; ++k) { H[k] = am * a[k]; L[k] = bm * b[k]; }
+  }
+};
+
+// Storage chosen at run time (es = bytes per mantissa: 2, 4 or 8), widened to int64.
+__device__ __forceinline__ void ldw8d(const VIn& v, int es, int64_t row, int64_t c0, int64_t (&o)[8]) {
+  if (es == 8) ldw8<int64_t>(v, row, c0, o);
+  else if (es == 4) ldw8<int32_t>(v, row, c0, o);
+  else ldw8<int16_t>(v, row, c0, o);
+}
+__device__ __forceinline__ int64_t ld1d(const VIn& v, int es, int64_t row, int64_t col) {
+  return es == 8 ? ld1<long long>(v, row, col) : (es == 4 ? ld1<int32_t>(v, row, col) : ld1<int16_t>(v, row, col));
+}
+
+// Ops on operands of any storage (the paths that take int64 mantissas, 33 <= w <= 62):
+//   copy     : H = x                                   (normalise)
+//   axpby    : H = m_alpha x, L = m_beta y             (Alg. eaxpby-row)
+//   residual : H = c y + n sum_nbrs(y), L = -r         (r_v = A y - r on the star stencil)
+struct OpCopyW {
+  VIn x;
+  int ex;
+  __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
+    ldw8d(x, ex, row, c0, H);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) L[k] = 0;
+  }
+};
+
+struct OpAxpyW {
+  VIn x, y;
+  int ex, ey;
+  int64_t am, bm;
+  __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
+    int64_t a[8], b[8];
+    ldw8d(x, ex, row, c0, a);
+    ldw8d(y, ey, row, c0, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { H[k] = am * a[k]; L[k] = bm * b[k]; }
+  }
+};
+
+template <int NDIM>
+struct OpResW {
+  VIn y, r;
+  int ey, er;
+  int64_t c, n;
+  __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
+    const int64_t nyy = y.ny, yy = row % nyy;
+    int64_t ctr[8], nb[8], b[8];
+    ldw8d(y, ey, row, c0, ctr);
+    ldw8d(y, ey, yy > 0 ? row - 1 : -1, c0, nb);                 // rows outside the grid read 0
+    ldw8d(y, ey, yy + 1 < nyy ? row + 1 : -1, c0, b);
+    int64_t ns[8];
+    const int64_t wv = ld1d(y, ey, row, c0 - 1), ev = ld1d(y, ey, row, c0 + 8);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ns[k] = (((k == 0 ? wv : ctr[k - 1]) + (k == 7 ? ev : ctr[k + 1])) + nb[k]) + b[k];
+    if (NDIM == 3) {
+      const int64_t zz = row / nyy;
+      ldw8d(y, ey, zz > 0 ? row - nyy : -1, c0, nb);
+      ldw8d(y, ey, zz + 1 < y.nz ? row + nyy : -1, c0, b);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ns[k] += nb[k] + b[k];
+    }
+    ldw8d(r, er, row, c0, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { H[k] = c * ctr[k] + n * ns[k]; L[k] = -b[k]; }
   }
 };
 
@@ -456,6 +559,60 @@ __global__ void __launch_bounds__(256) k_quant(const Op op, const QDesc q, const
     int64_t H[8], L[8];
     op(row, c0, H, L);
     quant8<PASS1>(H, L, p, out, tmp, row, c0, red);
+  }
+  block_commit(red, q.meta_out, q.stats, PASS1);
+  if (!PASS1) op_epilogue(q, p);
+}
+
+// Quantisation of 8 exact results into int64 mantissas (33 <= w_out <= 62): the per-element
+// general path of quantvf (no w_tmp window: qcomp recomputes in its second pass).
+template <bool PASS1>
+__device__ __forceinline__ void quant8_wide(const int64_t (&H)[8], const int64_t (&L)[8], const Plan& p,
+                                            const VOut& out, int64_t row, int64_t c0, Red& red) {
+  int64_t o[8];
+  int sat = 0;
+  const int64_t nvalid = out.nx - c0;
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    o[k] = 0;
+    if (k >= nvalid) continue;
+    if (p.wide) {
+      const i128 Z = combine<i128>(H[k], L[k], p);
+      if (PASS1) red.key = max(red.key, (long long)mu_key<i128>(Z, H[k], L[k], p));
+      else o[k] = finish<i128, int64_t>(Z, H[k], L[k], p, sat);
+    } else {
+      const int64_t Z = combine<int64_t>(H[k], L[k], p);
+      if (PASS1) red.key = max(red.key, (long long)mu_key<int64_t>(Z, H[k], L[k], p));
+      else o[k] = finish<int64_t, int64_t>(Z, H[k], L[k], p, sat);
+    }
+  }
+  if (!PASS1) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red.nrm = max(red.nrm, (long long)(o[k] < 0 ? -o[k] : o[k]));
+    red.sat += sat;
+    stw8(out, row, c0, o);
+  }
+}
+
+template <class Op, bool PASS1>
+__global__ void __launch_bounds__(256) k_quant_wide(const Op op, const QDesc q, const VOut out) {
+  __shared__ Plan sp;
+  if (threadIdx.x == 0) {
+    build_plan(q, sp);
+    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
+  }
+  __syncthreads();
+  const Plan p = sp;
+  const int64_t nvec = out.ld >> 3;
+  const int64_t total = out.ny * out.nz * nvec;
+  Red red = {0, 0, 0};
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / nvec;
+    const int64_t c0 = (idx - row * nvec) << 3;
+    int64_t H[8], L[8];
+    op(row, c0, H, L);
+    quant8_wide<PASS1>(H, L, p, out, row, c0, red);
   }
   block_commit(red, q.meta_out, q.stats, PASS1);
   if (!PASS1) op_epilogue(q, p);

@@ -1,8 +1,9 @@
 """IR with the iterate x and the right-hand side b' held as BFP blocks (bfp_ir_iterate_bfp:
 Alg. ir with the qgemv residual and the qsub update, no FP64 pass) against
-oracle.mg / oracle.var ir_step_bfp, bit for bit: constant coefficients in 2D and 3D,
-variable coefficients (the 26-bit residual operator included), direct and graph
-launches, odd and even step counts."""
+oracle.mg / oracle.var ir_step_bfp, bit for bit: constant coefficients in 2D and 3D
+(x up to 55 bits in int64 storage, b of any storage), variable coefficients (the
+26-bit residual operator included), direct and graph launches, odd and even step
+counts."""
 import ctypes as C
 
 import numpy as np
@@ -47,7 +48,7 @@ def run_and_compare(h, s, b_ref, x_ref, wx, wb, steps, stream):
 
 
 @pytest.mark.parametrize("nd,n,w", [(2, 63, 16), (2, 127, 12), (2, 31, 24), (3, 15, 16)])
-@pytest.mark.parametrize("wx,wb", [(32, 32), (24, 28), (16, 16)])
+@pytest.mark.parametrize("wx,wb", [(32, 32), (24, 28), (16, 16), (40, 40), (48, 32), (55, 16)])
 @pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
 @pytest.mark.parametrize("graph", [0, 1])
 def test_constant_bit_exact(nd, n, w, wx, wb, mode, graph):
@@ -155,15 +156,14 @@ def test_argument_checks():
     o = bfp.bfp_solver_opts_default(2, n, 16)
     h = bfp.Hierarchy(o)
     b = bfp.BFPVector((n, n), 32)
-    x16 = bfp.BFPVector((n, n), 16)
     xs = bfp.BFPVector((15, 15), 32)
-    with pytest.raises(bfp.BFPError):
-        h.ir_iterate_bfp(b, x16, 1)          # storage classes differ
     with pytest.raises(bfp.BFPError):
         h.ir_iterate_bfp(b, xs, 1)           # not the finest shape
     with pytest.raises(bfp.BFPError):
         h.ir_iterate_bfp(b, b, 1)            # aliasing
     h.ir_iterate_bfp(b, bfp.BFPVector((n, n), 32), 0)   # k = 0: nothing to do
+    with pytest.raises(bfp.BFPError):
+        h.ir_iterate_bfp(b, bfp.BFPVector((n, n), 56), 1)   # A'x past 62 bits
     o.arith = bfp.ARITH_FP32
     hf = bfp.Hierarchy(o)
     with pytest.raises(bfp.BFPError):

@@ -368,3 +368,86 @@ def test_full_size_jacobi_and_residual_4095(mode):
     bfp.bfp_residual(A, y, r, rv, gq(16, mode))
     ref = B.residual(OA, B.BFP(ym, -20, 16), B.BFP(rm, -19, 16), oq(16, mode), om)
     check(rv, ref)
+
+
+# ---- int64 mantissas (33 <= w <= 62): normalise, from / to FP64, axpy, residual ----
+
+WIDE = [(40, 16), (16, 48), (62, 62), (48, 33), (33, 40), (24, 56)]
+
+
+@pytest.mark.parametrize("shape", [(37, 53), (5, 7, 9), (1000,)])
+@pytest.mark.parametrize("w_in,w_out", WIDE)
+@pytest.mark.parametrize("mode", MODES)
+def test_wide_normalize(shape, w_in, w_out, mode):
+    seed = hash((shape, w_in, w_out, mode)) % 1000
+    m = random_mantissas(shape, w_in, seed)
+    x = dev_vec(m, -7, w_in)
+    z = out_vec(shape, w_out)
+    st = stats_tensor()
+    bfp.bfp_normalize(x, z, gq(w_out, mode), st)
+    rs = B.Stats()
+    check(z, B.normalize(B.BFP(m, -7, w_in), oq(w_out, mode), rs), st, rs)
+
+
+@pytest.mark.parametrize("w", [33, 40, 53, 62])
+def test_wide_from_to_f64(w):
+    rng = np.random.default_rng(w)
+    x = rng.standard_normal((19, 45)) * np.exp(rng.uniform(-30, 30, (19, 45)))
+    xt = torch.from_numpy(x).cuda()
+    z = out_vec((19, 45), w)
+    bfp.bfp_from_f64(xt, z)
+    check(z, B.from_f64(x, w))
+    back = torch.empty_like(xt)
+    bfp.bfp_to_f64(z, back)
+    torch.cuda.synchronize()
+    assert np.array_equal(back.cpu().numpy(), B.to_f64(B.from_f64(x, w)))
+
+
+@pytest.mark.parametrize("wx,wy,wz", [(40, 16, 40), (62, 32, 16), (16, 16, 48), (48, 48, 48), (32, 60, 24)])
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("ea,eb", [(0, 0), (-3, 25), (40, -30)])
+def test_wide_axpy(wx, wy, wz, mode, ea, eb):
+    seed = hash((wx, wy, wz, mode, ea, eb)) % 1000
+    xm = random_mantissas((21, 70), wx, seed)
+    ym = random_mantissas((21, 70), wy, seed + 1)
+    a, b = B.Scalar(3, ea), B.Scalar(-1, eb)
+    x, y = dev_vec(xm, -3, wx), dev_vec(ym, 2, wy)
+    z = out_vec((21, 70), wz)
+    st = stats_tensor()
+    rs = B.Stats()
+    ref = B.axpy(a, B.BFP(xm, -3, wx), b, B.BFP(ym, 2, wy), oq(wz, mode), rs)
+    bfp.bfp_axpy(bfp.scalar(a.m, a.e), x, bfp.scalar(b.m, b.e), y, z, gq(wz, mode), st)
+    check(z, ref, st, rs)
+
+
+@pytest.mark.parametrize("shape", [(37, 45), (63, 63), (5, 6, 7), (3, 260, 17)])
+@pytest.mark.parametrize("wy,wr", [(40, 40), (55, 32), (48, 16), (16, 32), (24, 44)])
+@pytest.mark.parametrize("mode", MODES)
+def test_wide_residual(shape, wy, wr, mode):
+    nd = len(shape)
+    A = bfp.bfp_laplace_stencil(nd, 0.8 if nd == 2 else 6 / 7, 16)
+    seed = hash((shape, wy, wr, mode)) % 1000
+    ym = random_mantissas(shape, wy, seed, "smooth")
+    rm = random_mantissas(shape, wr, seed + 1)
+    y, r = dev_vec(ym, -40, wy), dev_vec(rm, -20, wr)
+    z = out_vec(shape, 16)
+    st = stats_tensor()
+    rs = B.Stats()
+    As = B.laplace_stencil(nd)
+    om = B.Scalar(A.omega.m, A.omega.e)
+    ref = B.residual(As, B.BFP(ym, -40, wy), B.BFP(rm, -20, wr), oq(16, mode), om, rs)
+    bfp.bfp_residual(A, y, r, z, gq(16, mode), st)
+    check(z, ref, st, rs)
+
+
+def test_wide_rejected_elsewhere():
+    A = bfp.bfp_laplace_stencil(2, 0.8, 16)
+    x = bfp.BFPVector((15, 15), 40)
+    z = bfp.BFPVector((15, 15), 16)
+    with pytest.raises(bfp.BFPError):
+        bfp.bfp_stencil_apply(A, x, z, gq(16, bfp.QCOMP))
+    with pytest.raises(bfp.BFPError):
+        bfp.bfp_jacobi(A, None, x, z, gq(16, bfp.QCOMP))
+    y = bfp.BFPVector((15, 15), 56)     # A y would pass 62 bits: 4 + 56 + 3
+    with pytest.raises(bfp.BFPError):
+        bfp.bfp_residual(A, y, z, bfp.BFPVector((15, 15), 16), gq(16, bfp.QCOMP))

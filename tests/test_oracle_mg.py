@@ -223,17 +223,17 @@ def _bfp_ir_errors(s, b, x, uh, steps):
 
 
 def test_bfp_ir_converges_to_the_width_floor():
-    """From x = 0, Alg. ir with BFP x, b (w_x = w_b = 32, inner w = 16) contracts like the
+    """From x = 0, Alg. ir with BFP x, b (w_b = max(32, w_x), inner w = 16) contracts like the
     FP64-residual IR (V-cycle factor ~0.11 here) down to a floor set by x's width: the
-    floor at w_x = 28 is 2^4 times the one at 32 (within a factor 2), and both limits agree
-    with the FP64-residual IR's discrete solution to that floor."""
+    floor at w_x = 28 is 2^4 times the one at 32 and the one at 40 is 2^-8 times it (within a
+    factor 2)."""
     n = 63
     f = manufactured_rhs(2, n)
     uh = mg.discrete_solution(2, n)
     floors = {}
-    for wx in (32, 28):
+    for wx in (32, 28, 40):
         s = mg.BFPSolver(2, n, w=16, mode="qcomp")
-        b = B.from_f64(s.rhs_hierarchy(f)[0], 32)
+        b = B.from_f64(s.rhs_hierarchy(f)[0], max(32, wx))   # b finer than x: x sets the floor
         x0 = B.BFP(np.zeros((n, n), dtype=np.int64), 0, wx)
         x, errs = _bfp_ir_errors(s, b, x0, uh, 12)
         assert x.w == wx
@@ -243,3 +243,4 @@ def test_bfp_ir_converges_to_the_width_floor():
         assert errs[-1] <= 1.1 * min(errs[-4:])           # settled
     assert floors[32] < 3e-8
     assert 8 <= floors[28] / floors[32] <= 32, floors
+    assert 2 ** 7 <= floors[32] / floors[40] <= 2 ** 9, floors        # int64 iterate (w > 32)
