@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--n", type=int, default=4095)
     p.add_argument("--nd", type=int, default=2, choices=[2, 3], help="dimension of the --op problem")
     p.add_argument("--var", action="store_true", help="--op on the variable-coefficient 2D problem")
+    p.add_argument("--smoother", default="jacobi", choices=["jacobi", "cheby"],
+                   help="--op: the hierarchy's relaxation (cheby: the paper's V(1,0))")
     p.add_argument("--w", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -325,12 +327,12 @@ def width_sweep(bfp, torch, args, f, stream, steps=10):
     return out
 
 
-def bfp_ir_compare(bfp, torch, args, stream, sizes=(1023, 2047, 4095), steps=10):
+def bfp_ir_compare(bfp, torch, args, stream, sizes=(1023, 2047, 4095), widths=(32, 40), steps=10):
     """IR with BFP x and b' (bfp_ir_iterate_bfp: qgemv residual at the inner width, V-cycle, qsub at x's
-    width 32; b' quantised to 32 bits) beside the FP64-residual IR on the same hierarchy, per grid size:
-    ms per IR-V step, and IR-V steps and ms from x = 0 to the accuracy ratio <= 1.5 (at most 30 steps).
-    With 32-bit x the floor quantisation of the iterate leaves an energy-norm error of about 0.26 ulp / h,
-    above the discretisation error at h = 1/4096."""
+    width w_x; b' quantised to w_x bits, int64 storage above 32) beside the FP64-residual IR on the same
+    hierarchy, per grid size: ms per IR-V step, and IR-V steps and ms from x = 0 to the accuracy ratio <= 1.5
+    (at most 30 steps).  The floor quantisation of the iterate leaves an energy-norm error of about
+    0.26 ulp / h, above the discretisation error at h = 1/4096 for w_x = 32."""
     from bfp_inputs import manufactured_rhs
     out = []
     for n in sizes:
@@ -338,61 +340,65 @@ def bfp_ir_compare(bfp, torch, args, stream, sizes=(1023, 2047, 4095), steps=10)
         o = bfp.bfp_solver_opts_default(2, n, args.w)
         o.mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
         h = bfp.Hierarchy(o)
-        b = bfp.BFPVector((n, n), 32)
         bp = f * h.rhs_scale()
-        x = bfp.BFPVector((n, n), 32)
         xd = torch.zeros_like(f)
-        row = {"n": n, "w_inner": args.w, "w_x": 32, "w_b": 32, "mode": args.mode}
-
-        def zero_x():
-            x.mant.zero_()
-            x.meta.zero_()
-            xd.zero_()
-
         with torch.cuda.stream(stream):
-            bfp.bfp_from_f64(bp, b, stream)
-            h.ir_iterate_bfp(b, x, 4)
             h.ir_iterate(f, xd, 4)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            ev[0].record(stream)
-            h.ir_iterate_bfp(b, x, steps)
-            ev[1].record(stream)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
             h.ir_iterate(f, xd, steps)
-            ev[2].record(stream)
+            c.record(stream)
         stream.synchronize()
-        row["bfp_ir_step_ms"] = ev[0].elapsed_time(ev[1]) / steps
-        row["fp64_ir_step_ms"] = ev[1].elapsed_time(ev[2]) / steps
-        for name in ("bfp", "fp64"):
-            zero_x()
+        fp64_ms = a.elapsed_time(c) / steps
+
+        def to_accuracy(step, reset, read):
             k, ratio, best = 0, float("inf"), float("inf")
+            reset()
             while ratio > 1.5 and k < 30:
                 with torch.cuda.stream(stream):
-                    if name == "bfp":
-                        h.ir_iterate_bfp(b, x, 1)
-                        bfp.bfp_to_f64(x, xd, stream)
-                    else:
-                        h.ir_iterate(f, xd, 1)
+                    step(1)
+                    read()
                 stream.synchronize()
                 k += 1
                 ratio = accuracy_ratio_gpu(torch, xd, n)
                 best = min(best, ratio)
             times = []
             for _ in range(3):
-                zero_x()
+                reset()
                 with torch.cuda.stream(stream):
                     a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record(stream)
-                    if name == "bfp":
-                        h.ir_iterate_bfp(b, x, k)
-                    else:
-                        h.ir_iterate(f, xd, k)
+                    step(k)
                     c.record(stream)
                 stream.synchronize()
                 times.append(a.elapsed_time(c))
-            row[name + "_from_zero"] = {"ir_steps": k, "ms": min(times), "accuracy_ratio": ratio,
-                                        "best_ratio": best, "reached": bool(ratio <= 1.5)}
+            return {"ir_steps": k, "ms": min(times), "accuracy_ratio": ratio, "best_ratio": best,
+                    "reached": bool(ratio <= 1.5)}
+
+        fp64 = to_accuracy(lambda k: h.ir_iterate(f, xd, k), lambda: xd.zero_(), lambda: None)
+        for wx in widths:
+            b = bfp.BFPVector((n, n), wx)
+            x = bfp.BFPVector((n, n), wx)
+            with torch.cuda.stream(stream):
+                bfp.bfp_from_f64(bp, b, stream)
+                h.ir_iterate_bfp(b, x, 4)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                h.ir_iterate_bfp(b, x, steps)
+                c.record(stream)
+            stream.synchronize()
+
+            def reset():
+                x.mant.zero_()
+                x.meta.zero_()
+                xd.zero_()
+            row = {"n": n, "w_inner": args.w, "w_x": wx, "w_b": wx, "mode": args.mode,
+                   "bfp_ir_step_ms": a.elapsed_time(c) / steps, "fp64_ir_step_ms": fp64_ms,
+                   "bfp_from_zero": to_accuracy(lambda k: h.ir_iterate_bfp(b, x, k), reset,
+                                                lambda: bfp.bfp_to_f64(x, xd, stream)),
+                   "fp64_from_zero": fp64}
+            out.append(row)
         h.close()
-        out.append(row)
     return out
 
 
@@ -758,6 +764,8 @@ def run_op(args):
     mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
+    if args.smoother == "cheby":
+        o.smoother = bfp.SMOOTH_CHEBY
     if args.var:
         from bfp_inputs import grf_nodes
         h = bfp.Hierarchy(o, k_nodes=grf_nodes(n, seed=1))

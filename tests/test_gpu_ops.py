@@ -403,14 +403,14 @@ def test_wide_from_to_f64(w):
     assert np.array_equal(back.cpu().numpy(), B.to_f64(B.from_f64(x, w)))
 
 
-@pytest.mark.parametrize("wx,wy,wz", [(40, 16, 40), (62, 32, 16), (16, 16, 48), (48, 48, 48), (32, 60, 24)])
+@pytest.mark.parametrize("wx,wy,wz", [(40, 16, 40), (60, 32, 16), (16, 16, 48), (48, 48, 48), (32, 60, 24)])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("ea,eb", [(0, 0), (-3, 25), (40, -30)])
 def test_wide_axpy(wx, wy, wz, mode, ea, eb):
     seed = hash((wx, wy, wz, mode, ea, eb)) % 1000
     xm = random_mantissas((21, 70), wx, seed)
     ym = random_mantissas((21, 70), wy, seed + 1)
-    a, b = B.Scalar(3, ea), B.Scalar(-1, eb)
+    a, b = B.Scalar(1 if wx > 58 else 3, ea), B.Scalar(-1, eb)   # msb(a) + w_x <= 62
     x, y = dev_vec(xm, -3, wx), dev_vec(ym, 2, wy)
     z = out_vec((21, 70), wz)
     st = stats_tensor()
@@ -451,3 +451,6 @@ def test_wide_rejected_elsewhere():
     y = bfp.BFPVector((15, 15), 56)     # A y would pass 62 bits: 4 + 56 + 3
     with pytest.raises(bfp.BFPError):
         bfp.bfp_residual(A, y, z, bfp.BFPVector((15, 15), 16), gq(16, bfp.QCOMP))
+    x62 = bfp.BFPVector((15, 15), 62)   # 3 x would pass 62 bits
+    with pytest.raises(bfp.BFPError):
+        bfp.bfp_axpy(bfp.scalar(3, 0), x62, bfp.scalar(1, 0), z, bfp.BFPVector((15, 15), 40), gq(40, bfp.QCOMP))
