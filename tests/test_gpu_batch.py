@@ -67,3 +67,32 @@ def test_batch_instances_reach_tolerance():
         r = mg.residual_f64(bb, x.cpu().numpy())
         assert np.abs(r).max() <= 1e-8 * np.abs(bb).max()   # about 7x per IR-V step from ~7e-3 after FMG
     b.close()
+
+
+def test_batch_with_chebyshev_and_progressive_instances():
+    """Instances with the paper's V(1,0) (Chebyshev relaxation), progressive widths and a w_add cap
+    beside damped-Jacobi ones: each equals its single-hierarchy solve, bit for bit."""
+    spec = [(63, 16, bfp.NNQCOMP, 0, 63), (127, 16, bfp.QCOMP, 0, 0), (255, 12, bfp.NNQCOMP, 0, 63)]
+    olist = [opts(*s) for s in spec]
+    olist[0].smoother = bfp.SMOOTH_CHEBY
+    olist[1].smoother = bfp.SMOOTH_CHEBY
+    olist[1].w_add_max = 2
+    olist[2].w_step = 1
+    ks = [3, 2, 1]
+    fs = [torch.from_numpy(smoothed_random_rhs(s[0], 200 + i)).cuda() for i, s in enumerate(spec)]
+    xs = [torch.zeros_like(f) for f in fs]
+    stream = torch.cuda.Stream()
+    b = bfp.Batch(olist)
+    with torch.cuda.stream(stream):
+        b.solve(fs, xs, ks, fmg=True)
+    stream.synchronize()
+    for i, (o, k) in enumerate(zip(olist, ks)):
+        h = bfp.Hierarchy(o)
+        xr = torch.zeros_like(fs[i])
+        with torch.cuda.stream(stream):
+            h.fmg(fs[i], xr)
+            h.ir_iterate(fs[i], xr, k)
+        stream.synchronize()
+        assert torch.equal(xs[i], xr), i
+        h.close()
+    b.close()
