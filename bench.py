@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BFP V-cycle GDOF/s (IR-V steps, 2D Poisson 4095^2, w=16)"
-JACOBI_TRAFFIC = 92429056       # dram bytes read + written per finest-level Jacobi launch (ncu, 67.7 + 24.7 MB)
+JACOBI_TRAFFIC = 93095168   # dram__bytes_read.sum + dram__bytes_write.sum of one k_star16<2, 0, 2> launch at 4095^2 (ncu)
 UNIT = "GDOF/s"
 
 
