@@ -35,10 +35,15 @@ VIn kview(const void* p, const bfp_varstencil* A) {
 
 template <class T, int KIND, class TK = int16_t>
 struct OpVar {
+  static constexpr int kMinBlocks = 3;   // 85 registers: three 256-thread blocks per SM
   VIn y, r;
   VarView A;
   int32_t s;   // jacobi: left shift of y into the H group
+  // A'y = k_W (y - y_W) + k_E (y - y_E) + k_S (y - y_S) + k_N (y - y_N), exactly c y - sum k_f y_f
+  // (c = sum k_f); one face at a time keeps few registers live.  With int16 y and faces each
+  // difference fits 17 bits and each product one 32 x 32 -> 64 multiply.
   __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
+    constexpr bool kNarrow = sizeof(T) == 2 && sizeof(TK) == 2;
     if (KIND == kJacobi0) {
       int32_t rv[8], qv[8];
       ld8<T>(r, row, c0, rv);
@@ -48,34 +53,49 @@ struct OpVar {
       return;
     }
     const int64_t ny = y.ny;
-    int32_t ctr[8], up[8], dn[8], kw[8], ke[8], ks[8], kn[8], rv[8], qv[8];
+    int32_t ctr[8], nb[8], kf[8];
     ld8<T>(y, row, c0, ctr);
-    ld8<T>(y, row - 1, c0, dn);                  // rows outside the grid read 0
-    ld8<T>(y, row + 1 < ny ? row + 1 : -1, c0, up);
-    const int64_t wv = ld1<T>(y, row, c0 - 1), ev = ld1<T>(y, row, c0 + 8);
-    ldv<TK, 8>(A.k[0], row, c0, kw);
-    ldv<TK, 8>(A.k[1], row, c0, ke);
-    ldv<TK, 8>(A.k[2], row, c0, ks);
-    ldv<TK, 8>(A.k[3], row, c0, kn);
-    if (KIND != kApply) ld8<T>(r, row, c0, rv);
-    if (KIND == kJacobi) ldv<int16_t, 8>(A.q, row, c0, qv);
+    auto add_face = [&](int f, bool first) {
+      ldv<TK, 8>(A.k[f], row, c0, kf);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        int64_t term;
+        if (kNarrow) term = (int64_t)kf[k] * (int32_t)(ctr[k] - nb[k]);
+        else term = (int64_t)kf[k] * ((int64_t)ctr[k] - nb[k]);
+        H[k] = first ? term : H[k] + term;
+      }
+    };
+    {   // W and E: the row shifted by one, with the halo words
+      const int32_t wv = (int32_t)ld1<T>(y, row, c0 - 1), ev = (int32_t)ld1<T>(y, row, c0 + 8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) nb[k] = k == 0 ? wv : ctr[k - 1];
+      add_face(0, true);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) nb[k] = k == 7 ? ev : ctr[k + 1];
+      add_face(1, false);
+    }
+    ld8<T>(y, row - 1, c0, nb);                   // rows outside the grid read 0
+    add_face(2, false);
+    ld8<T>(y, row + 1 < ny ? row + 1 : -1, c0, nb);
+    add_face(3, false);
+    if (KIND == kApply) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) L[k] = 0;
+      return;
+    }
+    int32_t rv[8];
+    ld8<T>(r, row, c0, rv);
+    if (KIND == kResidual) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) L[k] = -(int64_t)rv[k];
+      return;
+    }
+    int32_t qv[8];
+    ldv<int16_t, 8>(A.q, row, c0, qv);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int64_t W = k == 0 ? wv : ctr[k - 1];
-      const int64_t E = k == 7 ? ev : ctr[k + 1];
-      const int64_t c = (int64_t)kw[k] + ke[k] + ks[k] + kn[k];
-      const int64_t ay = c * ctr[k] - ((int64_t)kw[k] * W + (int64_t)ke[k] * E + (int64_t)ks[k] * dn[k] +
-                                       (int64_t)kn[k] * up[k]);
-      if (KIND == kApply) {
-        H[k] = ay;
-        L[k] = 0;
-      } else if (KIND == kResidual) {
-        H[k] = ay;
-        L[k] = -(int64_t)rv[k];
-      } else {
-        H[k] = (int64_t)((uint64_t)(int64_t)ctr[k] << s) - (int64_t)qv[k] * ay;
-        L[k] = (int64_t)qv[k] * rv[k];
-      }
+      H[k] = (int64_t)((uint64_t)(int64_t)ctr[k] << s) - (int64_t)qv[k] * H[k];
+      L[k] = (int64_t)qv[k] * rv[k];
     }
   }
 };

@@ -534,8 +534,14 @@ __device__ __forceinline__ void op_epilogue(const QDesc& q, const Plan& p) {
   }
 }
 
+// Resident blocks per SM an op asks the compiler for (Op::kMinBlocks; default 1).
+template <class Op, class = void>
+struct OpMinBlocks { static constexpr int value = 1; };
+template <class Op>
+struct OpMinBlocks<Op, std::void_t<decltype(Op::kMinBlocks)>> { static constexpr int value = Op::kMinBlocks; };
+
 template <class Op, bool PASS1>
-__global__ void __launch_bounds__(256) k_quant(const Op op, const QDesc q, const VOut out) {
+__global__ void __launch_bounds__(256, OpMinBlocks<Op>::value) k_quant(const Op op, const QDesc q, const VOut out) {
   __shared__ Plan sp;
   if (threadIdx.x == 0) {
     build_plan(q, sp);
