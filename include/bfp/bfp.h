@@ -214,7 +214,7 @@ int32_t bfp_restrict(const bfp_vec* r_f, const bfp_vec* r_c, const bfp_q* q,
 int32_t bfp_prolong(const bfp_vec* d, const bfp_vec* y, const bfp_vec* y_out,
                     const bfp_q* q, const bfp_stats* st, bfp_stream stream);
 
-/* ---- variable coefficients (2D; the configs' -div(k grad u), not in the paper) ---- */
+/* ---- variable coefficients (2D -div(k grad u), a workload not in the paper) ---- */
 
 /* The 5-point operator of -div(k grad u) with harmonic-mean face coefficients,
  * scaled by h^2 (A' = h^2 A_h): row i has c_i = k_W + k_E + k_S + k_N on the
@@ -325,7 +325,7 @@ typedef struct {
 
 /* Relaxation of the V-cycle.
  *   BFP_SMOOTH_JACOBI: V(nu1, nu2) with damped Jacobi (omega), coarse_sweeps
- *     sweeps on the coarsest level (the configs' smoother).
+ *     sweeps on the coarsest level (the default).
  *   BFP_SMOOTH_CHEBY: the paper's V(1,0) (Alg. v-cycle): one bfp_cheby
  *     relaxation from y = 0, then residual, restriction, coarse correction; no
  *     post-smoothing; the coarsest level gets the relaxation alone.  c1, c2

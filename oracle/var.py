@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-The configs' variable-coefficient workload (not in the paper, whose
+A variable-coefficient workload beside the model problem (not in the paper, whose
 experiments use constant-coefficient FE problems): 5-point finite differences
 on n = 2^J - 1 interior points per side with zero Dirichlet boundary, face
 coefficients the harmonic means of k at the two nodes they join.  The

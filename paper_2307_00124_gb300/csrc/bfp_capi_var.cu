@@ -1,5 +1,5 @@
 // bfp_capi_var.cu -- C ABI: the variable-coefficient 5-point operator of
-// -div(k grad u) (2D; the configs' variable-coefficient workload, not in the
+// -div(k grad u) (2D; a workload beside the paper's model problem, not in the
 // paper): bfp_var_apply, bfp_var_residual, bfp_var_jacobi.
 //
 // Each op forms its exact result per element in int64 and quantises it
