@@ -13,6 +13,7 @@
 // block, int16 or, for apply / residual, int32 mantissas); q is the per-point
 // smoother weight block.
 #include "bfp_desc.h"
+#include "bfp_star2d.cuh"
 
 using namespace bfp;
 
@@ -130,6 +131,14 @@ int32_t var_launch(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, 
                    int32_t s, cudaStream_t st) {
   const bfp_vec* in = y ? y : r;
   const VIn yv = vin(y ? y : r), rv = vin(r ? r : in);
+  if (!wide_k(A) && !is32(in) && !is32(out) && (!r || !is32(r))) {   // int16 throughout: the staged kernel
+    VarRow va;
+    const VarView v = view(A);
+    for (int f = 0; f < 4; ++f) va.k[f] = v.k[f];
+    va.q = v.q;
+    va.s = s;
+    return launch_star16_var<KIND>(yv, rv, va, d, out, st);
+  }
   if (KIND != kJacobi && KIND != kJacobi0 && wide_k(A)) {   // int32 faces: apply / residual only
     if (is32(in)) return launch_quant(OpVar<int32_t, KIND, int32_t>{yv, rv, view(A), s}, d, out, st);
     return launch_quant(OpVar<int16_t, KIND, int32_t>{yv, rv, view(A), s}, d, out, st);

@@ -255,8 +255,33 @@ inline int32_t launch_star16(const VIn& y, const VIn& r, int32_t c, int32_t nb, 
   const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;
   const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1),
                (unsigned)(ND == 3 ? o.nz : 1));
-  if (q.mode == kQcomp) k_star16<KIND, true, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
-  k_star16<KIND, false, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
+  const VarRow none{};
+  if (q.mode == kQcomp) k_star16<KIND, true, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, none);
+  k_star16<KIND, false, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, none);
+  note_launches(q.mode == kQcomp ? 2 : 1);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+// 2D variable-coefficient op (int16 y, r, faces, weights and result) through the staged kernel
+template <int KIND>
+inline int32_t launch_star16_var(const VIn& y, const VIn& r, const VarRow& va, const QDesc& q, const bfp_vec* out,
+                                 cudaStream_t s) {
+  if (q.hbits > 62 || (q.two && q.lbits > 62)) return BFP_ERR_WIDTH;
+  static bool carved = false;
+  if (!carved) {
+    cudaFuncSetAttribute(k_star16<KIND, true, 2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_star16<KIND, false, 2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    carved = true;
+  }
+  const VOut o = vout(out);
+  const int64_t ny = out->n[1];
+  const int rs = pick_rows(ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2)), 32);   // <= 32: row masks
+  if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
+  const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
+  const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;
+  const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1), 1u);
+  if (q.mode == kQcomp) k_star16<KIND, true, 2, true><<<g, 128, 0, s>>>(y, r, 0, 0, 0, q, o, rs, va);
+  k_star16<KIND, false, 2, true><<<g, 128, 0, s>>>(y, r, 0, 0, 0, q, o, rs, va);
   note_launches(q.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }

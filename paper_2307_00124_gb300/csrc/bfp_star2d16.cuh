@@ -100,6 +100,15 @@ __device__ __forceinline__ uint32_t min_s16x2(uint32_t a, uint32_t b) {
   return d;
 }
 
+// Per-point coefficients of the variable-coefficient operator (2D, int16 faces W, E, S, N and
+// smoother weights q, in the output's layout; s: the left shift of y into the Jacobi H group).
+// A'y = k_W (y - y_W) + k_E (y - y_E) + k_S (y - y_S) + k_N (y - y_N), exactly c y - sum k_f y_f.
+struct VarRow {
+  VIn k[4];
+  VIn q;
+  int32_t s;
+};
+
 // Inputs of one lane's 8 outputs, for the out-of-line general path.
 struct Row8 {
   int32_t y[8], ym[8], yp[8], r[8], zm[8], zp[8];
@@ -108,11 +117,18 @@ struct Row8 {
 
 // The general path for one lane's 8 outputs of row j of plane kz: reloads its
 // inputs from global memory (zero outside the grid) and quantises through quantvf.
-template <bool PASS1, int KIND, int ND>
+template <bool PASS1, int KIND, int ND, bool VAR>
 __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p, const Fast& fq, const VOut& out,
                                        int32_t* tmp, int64_t j, int64_t kz, int64_t c0, Red& red, int32_t c,
-                                       int32_t nb, int32_t mw) {
+                                       int32_t nb, int32_t mw, const VarRow& va) {
   Row8 in;
+  int32_t kf[4][8], qv[8];
+  if (VAR) {
+    const int64_t row = kz * out.ny + j;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) ldv<int16_t, 8>(va.k[f], row, c0, kf[f]);
+    ldv<int16_t, 8>(va.q, row, c0, qv);
+  }
   const int64_t ny = out.ny, row = kz * ny + j;
   if (KIND != kJacobi0) {
     ldv<int16_t, 8>(y, row, c0, in.y);
@@ -125,6 +141,21 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
   }
   if (KIND != kApply) ldv<int16_t, 8>(r, row, c0, in.r);
   auto hl = [&](int k, int64_t& H, int64_t& L) {
+    if (VAR) {
+      if (KIND == kJacobi0) {
+        H = (int64_t)qv[k] * in.r[k];
+        L = 0;
+        return;
+      }
+      const int64_t yk = in.y[k];
+      const int64_t ay = (int64_t)kf[0][k] * (yk - (k == 0 ? in.wv : in.y[k - 1])) +
+                         (int64_t)kf[1][k] * (yk - (k == 7 ? in.ev : in.y[k + 1])) +
+                         (int64_t)kf[2][k] * (yk - in.ym[k]) + (int64_t)kf[3][k] * (yk - in.yp[k]);
+      if (KIND == kApply) { H = ay; L = 0; }
+      else if (KIND == kResidual) { H = ay; L = -(int64_t)in.r[k]; }
+      else { H = (int64_t)((uint64_t)yk << va.s) - (int64_t)qv[k] * ay; L = (int64_t)qv[k] * in.r[k]; }
+      return;
+    }
     if (KIND == kJacobi0) {
       H = (int64_t)mw * (int64_t)in.r[k];
       L = 0;
@@ -160,10 +191,10 @@ struct __align__(16) Stage16<3> {
 };
 
 // grid: (256-column chunks, strips of 4 * rs rows, planes)
-template <int KIND, bool PASS1, int ND>
-__global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, const VIn r, const int32_t c,
+template <int KIND, bool PASS1, int ND, bool VAR = false>
+__global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const VIn y, const VIn r, const int32_t c,
                                                                  const int32_t nb, const int32_t mw, const QDesc q,
-                                                                 const VOut out, const int rs) {
+                                                                 const VOut out, const int rs, const VarRow va) {
   constexpr int NS = Stage16<ND>::N;
   __shared__ Plan sp;
   __shared__ Stage16<ND> stg[4];
@@ -203,7 +234,7 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
   // coefficients and t < 32, so Z is three mad.wide and the result one funnel shift (else
   // Z = (H << dh) + (L << dl) from the plain coefficients and the result Z >> t)
   const bool fast = fq.ok;
-  const bool fold = cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr && fq.t < 32;
+  const bool fold = !VAR && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr && fq.t < 32;
   const uint32_t dh = (uint32_t)fq.dh, dl = (uint32_t)fq.dl;
   // saturation test on the 32-bit results when Z >> t is exact in int32, else on Z
   const bool v32 = zb - (int)fq.t <= 30;
@@ -307,6 +338,14 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
         const int i = j - j0;
         if (i + NS - 1 < nst) issue(sn, inttag, true);   // stage i + NS - 1, into the slot of row j - 2
         else cp_commit();
+        int32_t kf[4][8], qv[8];                  // this row's coefficients, loaded while the ring fills
+        if constexpr (VAR) {
+          if (KIND != kJacobi0) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) ldv<int16_t, 8>(va.k[f], rowoff + j, c0, kf[f]);
+          }
+          if (KIND == kJacobi || KIND == kJacobi0) ldv<int16_t, 8>(va.q, rowoff + j, c0, qv);
+        }
         cp_wait<NS - 3>();                        // stages <= i + 2 have landed (own copies)
         __syncwarp();                             // ... and the other lanes' (neighbours, halo)
         Pk8 ym, yc, yp, rc, zm, zp;
@@ -343,7 +382,24 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
   #pragma unroll
             for (int k = 0; k < 8; ++k) {
               int64_t Z;
-              if (KIND == kJacobi0) {
+              if constexpr (VAR) {
+                if (KIND == kJacobi0) {
+                  Z = (int64_t)((uint64_t)mulw(qv[k], pk_get(rc, k)) << dh);
+                } else {
+                  const int32_t yk = yv[k];
+                  int64_t ay = mulw(kf[0][k], yk - (k == 0 ? wv : yv[k - 1]));
+                  ay = madw(kf[1][k], yk - (k == 7 ? ev : yv[k + 1]), ay);
+                  ay = madw(kf[2][k], yk - pk_get(ym, k), ay);
+                  ay = madw(kf[3][k], yk - pk_get(yp, k), ay);
+                  int64_t H = ay, L = 0;
+                  if (KIND == kResidual) L = -(int64_t)pk_get(rc, k);
+                  if (KIND == kJacobi) {
+                    H = (int64_t)((uint64_t)(int64_t)yk << va.s) - (int64_t)qv[k] * ay;
+                    L = mulw(qv[k], pk_get(rc, k));
+                  }
+                  Z = (int64_t)((uint64_t)H << dh) + (int64_t)((uint64_t)L << dl);
+                }
+              } else if (KIND == kJacobi0) {
                 Z = FOLD ? mulw(cr32, pk_get(rc, k)) : (int64_t)((uint64_t)mulw(mw, pk_get(rc, k)) << dh);
               } else {
                 const int32_t wk = k == 0 ? wv : yv[k - 1];
@@ -413,7 +469,11 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
     const bool xfull = (int64_t)blockIdx.x * kS16Cols + kS16Cols <= out.nx;
     const bool interior = xfull && (!kUseY || (j0 >= 1 && j1 < ny));
     const std::false_type no;
-    if (fold && v32 && interior) walk(std::true_type{}, std::true_type{}, std::true_type{});
+    if constexpr (VAR) {   // per-point coefficients: no folded constants
+      if (v32 && interior) walk(std::true_type{}, no, std::true_type{});
+      else if (v32) walk(std::true_type{}, no, no);
+      else walk(no, no, no);
+    } else if (fold && v32 && interior) walk(std::true_type{}, std::true_type{}, std::true_type{});
     else if (fold) {
       if (v32) walk(std::true_type{}, std::true_type{}, no);
       else walk(std::false_type{}, std::true_type{}, no);
@@ -424,7 +484,7 @@ __global__ void __launch_bounds__(128, ND == 3 ? 5 : 7) k_star16(const VIn y, co
     // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = j0 + __ffs(m) - 1;
-      if (act) slow_row8<PASS1, KIND, ND>(y, r, p, fq, out, tmp, j, kz, c0, red, c, nb, mw);
+      if (act) slow_row8<PASS1, KIND, ND, VAR>(y, r, p, fq, out, tmp, j, kz, c0, red, c, nb, mw, va);
     }
   }
   if (!PASS1) {

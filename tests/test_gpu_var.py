@@ -266,3 +266,43 @@ def test_progressive_precision_bit_exact(mode):
         xr = s.ir_step(0, b, xr)
     assert np.array_equal(xt.cpu().numpy(), xr)
     h.close()
+
+
+@pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
+def test_ops_bit_exact_several_chunks(mode):
+    """511^2 int16: two 256-column chunks (the second partial), interior and edge strips of the
+    staged kernel, junk in the padding columns."""
+    n, w = 511, 16
+    h, K = var_hierarchy(n, 16, mode, seed=8)
+    A = h.var_level(0)
+    op = V.make_level(K, OM)
+    mstr = "qcomp" if mode == bfp.QCOMP else "nnqcomp"
+    ym = random_mantissas((n, n), w, 41, "smooth")
+    rm = random_mantissas((n, n), w, 42)
+    q, qo = bfp.q(w, mode), B.Quant(w, mstr)
+    y, r = dev_vec(ym, -6, w, 5), dev_vec(rm, -4, w, 6)
+    z, st, rs = out_vec((n, n), w), stats_tensor(), B.Stats()
+    bfp.bfp_var_residual(A, y, r, z, q, st)
+    check(z, V.residual(op, B.BFP(ym, -6, w), B.BFP(rm, -4, w), qo, OM, rs), st, rs)
+    for yy, yo in ((y, B.BFP(ym, -6, w)), (None, None)):
+        z, st, rs = out_vec((n, n), w), stats_tensor(), B.Stats()
+        bfp.bfp_var_jacobi(A, yy, r, z, q, st)
+        check(z, V.jacobi(op, yo, B.BFP(rm, -4, w), qo, rs), st, rs)
+    z, st, rs = out_vec((n, n), w), stats_tensor(), B.Stats()
+    bfp.bfp_var_apply(A, y, z, q, st)
+    check(z, V.apply(op, B.BFP(ym, -6, w), qo, rs), st, rs)
+    h.close()
+
+
+def test_vcycle_bit_exact_511():
+    n, w = 511, 16
+    h, K = var_hierarchy(n, w, bfp.NNQCOMP, seed=9)
+    s = V.VarSolver(K, w=w, mode="nnqcomp")
+    rm = random_mantissas((n, n), w, 23, "smooth")
+    r = bfp.BFPVector.from_mantissas(rm, -18, w)
+    y = bfp.BFPVector((n, n), w)
+    h.vcycle(r, y)
+    torch.cuda.synchronize()
+    ref = s.vcycle(0, B.BFP(rm, -18, w))
+    assert y.exponent == ref.e and np.array_equal(y.mantissas(), ref.m)
+    h.close()
