@@ -131,7 +131,8 @@ int32_t var_launch(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec* r, 
                    int32_t s, cudaStream_t st) {
   const bfp_vec* in = y ? y : r;
   const VIn yv = vin(y ? y : r), rv = vin(r ? r : in);
-  if (!wide_k(A) && !is32(in) && !is32(out) && (!r || !is32(r))) {   // int16 throughout: the staged kernel
+  // int16 throughout, on a grid large enough: the staged kernel
+  if (!wide_k(A) && !is32(in) && !is32(out) && (!r || !is32(r)) && star16_var_fills(out)) {
     VarRow va;
     const VarView v = view(A);
     for (int f = 0; f < 4; ++f) va.k[f] = v.k[f];

@@ -262,6 +262,19 @@ inline int32_t launch_star16(const VIn& y, const VIn& r, int32_t c, int32_t nb, 
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
+// Rows per warp strip of the variable-coefficient staged kernel.
+inline int star16_var_rows(int64_t ny) { return pick_rows(ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2)), 32); }
+
+// The staged kernel pays off once its grid (256-column chunks x strips) fills the GPU about
+// twice over (three CTAs per SM): on smaller grids the row walk's per-row latency is exposed and
+// the generic row kernel, with more independent work per SM, is faster (measured per level of the
+// 2047^2 hierarchy: 1.3x faster at 2047^2, slower from 1023^2 down).
+inline bool star16_var_fills(const bfp_vec* out) {
+  const int64_t ny = out->n[1], rs = star16_var_rows(ny);
+  const int64_t ctas = ((out->ld + kS16Cols - 1) / kS16Cols) * ((ny + 4 * rs - 1) / (4 * rs));
+  return ctas >= 3 * (int64_t)sm_count();
+}
+
 // 2D variable-coefficient op (int16 y, r, faces, weights and result) through the staged kernel
 template <int KIND>
 inline int32_t launch_star16_var(const VIn& y, const VIn& r, const VarRow& va, const QDesc& q, const bfp_vec* out,
@@ -274,8 +287,7 @@ inline int32_t launch_star16_var(const VIn& y, const VIn& r, const VarRow& va, c
     carved = true;
   }
   const VOut o = vout(out);
-  const int64_t ny = out->n[1];
-  const int rs = pick_rows(ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2)), 32);   // <= 32: row masks
+  const int rs = star16_var_rows(out->n[1]);   // <= 32: row masks
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
   const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;

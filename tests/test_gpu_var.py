@@ -268,11 +268,11 @@ def test_progressive_precision_bit_exact(mode):
     h.close()
 
 
-@pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
-def test_ops_bit_exact_several_chunks(mode):
-    """511^2 int16: two 256-column chunks (the second partial), interior and edge strips of the
-    staged kernel, junk in the padding columns."""
-    n, w = 511, 16
+@pytest.mark.parametrize("n,mode", [(511, bfp.QCOMP), (511, bfp.NNQCOMP), (2047, bfp.NNQCOMP)])
+def test_ops_bit_exact_several_chunks(n, mode):
+    """Several 256-column chunks (the last partial) and junk in the padding columns: 511^2 runs the
+    generic row kernel, 2047^2 the staged one (interior and edge strips)."""
+    w = 16
     h, K = var_hierarchy(n, 16, mode, seed=8)
     A = h.var_level(0)
     op = V.make_level(K, OM)
