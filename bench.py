@@ -597,15 +597,30 @@ def run_ours(args):
         xd = torch.empty_like(f)
         fd = torch.empty_like(f)
         k2 = max(3, args.steps // 2)
-        with torch.cuda.stream(stream):
-            for i in range(2 + k2):
-                if i == 2:
-                    a = torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
+        # every step copies f and x in and x out; f's copy runs on a second stream while the
+        # previous step's x goes back to the host (the two directions of the link overlap)
+        cstream = torch.cuda.Stream()
+        f_free = torch.cuda.Event()
+        f_free.record(stream)
+        for i in range(2 + k2):
+            if i == 2:
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cstream.wait_event(a)
+            f_ready = torch.cuda.Event()
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(f_free)
                 fd.copy_(fh, non_blocking=True)
+                f_ready.record(cstream)
+            with torch.cuda.stream(stream):
                 xd.copy_(xh, non_blocking=True)
+                stream.wait_event(f_ready)
                 h.ir_iterate(fd, xd, 1)
+                f_free = torch.cuda.Event()
+                f_free.record(stream)
                 xh.copy_(xd, non_blocking=True)
+        with torch.cuda.stream(stream):
+            stream.wait_stream(cstream)
             b = torch.cuda.Event(enable_timing=True)
             b.record(stream)
         stream.synchronize()
