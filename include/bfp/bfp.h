@@ -365,7 +365,8 @@ int32_t bfp_hierarchy_read_finest_stats(bfp_hierarchy* h, uint64_t* host8, bfp_s
 int32_t bfp_hierarchy_reset_stats(bfp_hierarchy* h, bfp_stream stream);
 
 /* y = V(nu1,nu2)(r) on the finest level: approximate solution of A' y = r
- * (Alg. v-cycle correction scheme with damped Jacobi).  r and y use the
+ * (Alg. v-cycle correction scheme with damped Jacobi, or the paper's V(1,0)
+ * with the Chebyshev relaxation when opts.smoother says so).  r and y use the
  * hierarchy's width and finest shape. */
 int32_t bfp_vcycle(bfp_hierarchy* h, const bfp_vec* r, const bfp_vec* y, bfp_stream stream);
 
