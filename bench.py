@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--n", type=int, default=4095)
     p.add_argument("--nd", type=int, default=2, choices=[2, 3], help="dimension of the --op problem")
     p.add_argument("--var", action="store_true", help="--op on the variable-coefficient 2D problem")
+    p.add_argument("--onchip", type=int, default=None,
+                   help="opts.coarse_onchip of the timed hierarchy (default: the library's)")
     p.add_argument("--smoother", default="jacobi", choices=["jacobi", "cheby"],
                    help="--op: the hierarchy's relaxation (cheby: the paper's V(1,0))")
     p.add_argument("--w", type=int, default=16)
@@ -508,6 +510,8 @@ def run_ours(args):
     mode = bfp.NNQCOMP if args.mode == "nnqcomp" else bfp.QCOMP
     o = bfp.bfp_solver_opts_default(nd, n, w)
     o.mode = mode
+    if args.onchip is not None:
+        o.coarse_onchip = args.onchip
     h = bfp.Hierarchy(o)
     f_host = manufactured_rhs(nd, n)
     f = torch.from_numpy(f_host).cuda()
