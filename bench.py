@@ -555,14 +555,19 @@ def run_ours(args):
         t = float(tt.item())
     value = ws * dof * args.steps / t / 1e9
 
+    h_levels = []
+    m = n
+    while m >= 3:
+        h_levels.append(m)
+        m = (m - 1) // 2
     # roofline: the dominant kernels timed alone with CUDA events on their stream
     hbm, peak_kind = peaks()
     A = bfp.bfp_laplace_stencil(nd, o.omega, o.w_omega)
     rng = np.random.default_rng(0)
-    ym = rng.integers(-(1 << 12), 1 << 12, size=(n, n))
+    ym = rng.integers(-(1 << 12), 1 << 12, size=(n,) * nd)
     y = bfp.BFPVector.from_mantissas(ym, -20, w)
     r = bfp.BFPVector.from_mantissas(ym[::-1].copy(), -19, w)
-    yo = bfp.BFPVector((n, n), w)
+    yo = bfp.BFPVector((n,) * nd, w)
     q = bfp.q(w, mode)
     reps = 30
     kern = {}
@@ -591,7 +596,8 @@ def run_ours(args):
     # this kernel version (profiles/jacobi_4095.txt), None when not captured
     dom = "jacobi"
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern_out[dom]["GBps"], "peak": hbm, "unit": "GB/s",
-            "frac": kern_out[dom]["GBps"] / hbm, "peak_kind": peak_kind, "traffic": JACOBI_TRAFFIC}
+            "frac": kern_out[dom]["GBps"] / hbm, "peak_kind": peak_kind,
+            "traffic": JACOBI_TRAFFIC if (nd, n, w) == (2, 4095, 16) else None}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -655,9 +661,12 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int16+f64" if w <= 16 else "int32+f64",
             "data": "synthetic",
-            "config": {"workload": "2D Poisson 5-point, %dx%d interior, FP64 IR with BFP V(2,2) damped Jacobi "
-                                   "omega=4/5, 11 levels, w=%d, %s" % (n, n, w, args.mode),
-                       "l2": "inputs larger than L2 (x, f: 134 MB each)", "parallelism": "replicas" if ws > 1
+            "config": {"workload": ("2D Poisson 5-point, %dx%d interior, FP64 IR with BFP V(2,2) damped Jacobi "
+                                    "omega=4/5, %d levels, w=%d, %s" % (n, n, len(h_levels), w, args.mode)) if nd == 2
+                       else ("3D Poisson 7-point, %dx%dx%d interior, FP64 IR with BFP V(2,2) damped Jacobi "
+                             "omega=6/7, %d levels, w=%d, %s" % (n, n, n, len(h_levels), w, args.mode)),
+                       "l2": "inputs larger than L2 (x, f: %d MB each)" % (8 * dof // 10 ** 6),
+                       "parallelism": "replicas" if ws > 1
                        else "single GPU"},
             "roofline": roof, "kernels": kern_out, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches_per_step * args.steps),
