@@ -124,6 +124,22 @@ def dist_init(args):
     return ws, rank, local
 
 
+def max_over_ranks(t, device):
+    """The slowest rank's time (replicas: the job ends with its last rank); t itself at one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(ws, units_per_rank, steps, t):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time (G/s)."""
+    return ws * units_per_rank * steps / t / 1e9
+
+
 def cpu_oracle_step(n, w, mode, nd=2):
     """Time one oracle IR-V step on an n^2 grid (numpy, exact integers)."""
     import numpy as np
@@ -553,11 +569,8 @@ def run_ours(args):
         h.ir_iterate(f, x, 2)
     stream.synchronize()
     op_stats = h.stats()
-    if ws > 1:
-        tt = torch.tensor([t], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
-    value = ws * dof * args.steps / t / 1e9
+    t = max_over_ranks(t, "cuda")
+    value = replica_value(ws, dof, args.steps, t)
 
     h_levels = []
     m = n
