@@ -423,6 +423,8 @@ typedef struct {
   int32_t max_iter;   /* IR steps at most */
   int32_t fmg_start;  /* 1: start from FMG, 0: from the given x */
   double tol;         /* stop when ||b' - A'x||_inf <= tol * ||b'||_inf (checked on the host) */
+  int32_t stall_fallback; /* 1: the safety mechanism of Sec. 5 (see ir_solve); 0: off */
+  int32_t reserved;
 } bfp_ir_opts;
 
 typedef struct {
@@ -430,10 +432,17 @@ typedef struct {
   int32_t converged;
   double res_inf;     /* final ||b' - A'x||_inf */
   double res0_inf;    /* ||b'||_inf */
+  int32_t fallback_at; /* the IR step from which the V-cycle ran with qcomp, -1: never */
+  int32_t reserved;
 } bfp_ir_report;
 
 /* IR to a tolerance (Alg. ir): synchronises with the host once per step to
- * read the residual norm.  Returns BFP_ERR_NOCONV when max_iter is reached. */
+ * read the residual norm.  Returns BFP_ERR_NOCONV when max_iter is reached.
+ * Safety mechanism (Sec. 5, closing the discussion of skipping
+ * normalisation): with stall_fallback set and an nnqcomp hierarchy, once the
+ * residual norm after step i is above half the norm two steps earlier (the
+ * convergence stalls), every later step runs the separately launched V-cycle
+ * ops with qcomp (the on-chip coarse cycle keeps its mode). */
 int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts* o,
                  bfp_ir_report* rep, bfp_stream stream);
 

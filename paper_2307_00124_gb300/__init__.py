@@ -83,12 +83,13 @@ class flt_vec(C.Structure):
 
 
 class bfp_ir_opts(C.Structure):
-    _fields_ = [("max_iter", C.c_int32), ("fmg_start", C.c_int32), ("tol", C.c_double)]
+    _fields_ = [("max_iter", C.c_int32), ("fmg_start", C.c_int32), ("tol", C.c_double),
+                ("stall_fallback", C.c_int32), ("reserved", C.c_int32)]
 
 
 class bfp_ir_report(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("res_inf", C.c_double),
-                ("res0_inf", C.c_double)]
+                ("res0_inf", C.c_double), ("fallback_at", C.c_int32), ("reserved", C.c_int32)]
 
 
 P = C.POINTER
@@ -550,9 +551,10 @@ class Hierarchy:
         _check(_lib.bfp_fmg(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()), _stream(stream)),
                "bfp_fmg")
 
-    def ir_solve(self, f, x, max_iter=50, tol=1e-10, fmg_start=True, stream=None):
+    def ir_solve(self, f, x, max_iter=50, tol=1e-10, fmg_start=True, stall_fallback=False, stream=None):
         o = bfp_ir_opts()
         o.max_iter, o.tol, o.fmg_start = int(max_iter), float(tol), int(bool(fmg_start))
+        o.stall_fallback = int(bool(stall_fallback))
         rep = bfp_ir_report()
         rc = _lib.ir_solve(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(o), C.byref(rep),
                            _stream(stream))

@@ -1610,7 +1610,9 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
   TileScope ts(h->o.tile_rows);
   WaddScope wz(h->o.w_add_max);
   std::memset(rep, 0, sizeof(*rep));
+  rep->fallback_at = -1;
   if (o->fmg_start) TRY(bfp_fmg(h, f, x, s));
+  double hist[2] = {-1.0, -1.0};   // residual norms one and two steps back
   const int nd = h->o.ndim;
   const Grid g = grid_of(nd, h->o.n);
   const double cdiag = (2.0 * nd) / pscale(nd), cnb = -1.0 / pscale(nd);
@@ -1640,7 +1642,20 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
     rep->res0_inf = bn;
     if (rn <= o->tol * bn) { rep->converged = 1; return BFP_OK; }
     if (it >= o->max_iter) return BFP_ERR_NOCONV;
-    TRY(ir_step(h, 0, f, bs, x, s));
+    if (o->stall_fallback && h->o.mode == BFP_NNQCOMP && rep->fallback_at < 0 && hist[1] >= 0.0 &&
+        rn > 0.5 * hist[1])
+      rep->fallback_at = it;
+    hist[1] = hist[0];
+    hist[0] = rn;
+    if (rep->fallback_at >= 0) {   // the V-cycle ops of this step with qcomp
+      const int32_t mode = h->o.mode;
+      h->o.mode = BFP_QCOMP;
+      const int32_t rc = ir_step(h, 0, f, bs, x, s);
+      h->o.mode = mode;
+      TRY(rc);
+    } else {
+      TRY(ir_step(h, 0, f, bs, x, s));
+    }
   }
 }
 

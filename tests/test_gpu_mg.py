@@ -195,3 +195,42 @@ def test_w_add_cap_matches_oracle_counts(cap, smoother, onchip):
     assert fin["calls"] == (4 if smoother == "cheby" else 7)      # the finest level's own ops
     assert fin["recomputed"] <= st["recomputed"]
     h.close()
+
+
+def _policy_oracle(s, b, x, steps):
+    """The stall fallback of ir_solve restated: before step i, if the residual norm is above half
+    the one two steps back, step i and every later step run the V-cycle with qcomp."""
+    hist, fb = [-1.0, -1.0], -1
+    for it in range(steps):
+        rn = float(np.abs(mg.residual_f64(b, x)).max())
+        if fb < 0 and hist[1] >= 0 and rn > 0.5 * hist[1]:
+            fb = it
+        hist = [rn, hist[0]]
+        mode = s.mode
+        if fb >= 0:
+            s.mode = "qcomp"
+        x = s.ir_step(0, b, x)
+        s.mode = mode
+    return x, fb
+
+
+@pytest.mark.parametrize("w", [8, 6])
+def test_ir_solve_stall_fallback_matches_oracle(w):
+    """IR-V from zero under nnqcomp first raises the residual (the paper's remark on skipping
+    normalisation); the fallback switches the V-cycle to qcomp at the same step as the restated
+    policy, and the iterate matches it bit for bit."""
+    n, steps = 63, 8
+    h, s = make(2, n, w, bfp.NNQCOMP, coarse_onchip=0)
+    f = manufactured_rhs(2, n)
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    rep = h.ir_solve(ft, xt, max_iter=steps, tol=0.0, fmg_start=False, stall_fallback=True)
+    torch.cuda.synchronize()
+    b = s.rhs_hierarchy(f)[0]
+    xr, fb = _policy_oracle(s, b, np.zeros_like(b), steps)
+    assert rep.fallback_at == fb and fb >= 0
+    assert np.array_equal(xt.cpu().numpy(), xr)
+    # without the fallback the solve keeps nnqcomp
+    xt.zero_()
+    rep = h.ir_solve(ft, xt, max_iter=steps, tol=0.0, fmg_start=False)
+    assert rep.fallback_at == -1
