@@ -369,3 +369,35 @@ def test_scalar_floor():
     assert om.value() <= Fraction(4, 5) < om.value() + Fraction(1, 1 << 15)
     s = B.scalar_floor(-1.0 / 6.0, 16)
     assert B.msb(s.m) <= 16 and B.msb(s.m * 2) > 16
+
+
+def test_wide_blocks_brute_force():
+    """Blocks of 33..62 bits (int64 mantissas): from_f64, axpy and the residual at those widths
+    equal the minimal-exponent floor of the exact rational result."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(13) * 10.0 ** rng.integers(-20, 20)
+    for w in (33, 48, 53, 62):
+        out = B.from_f64(x, w)
+        ref = exact_floor_quant([Fraction(float(v)) for v in x], w)
+        assert out.e == ref[0] and list(map(int, out.m)) == ref[1]
+    for wx, wy, wz in ((60, 16, 40), (40, 40, 62), (16, 55, 33)):
+        xm = rng.integers(-(1 << (wx - 1)), 1 << (wx - 1), size=9, dtype=np.int64)
+        ym = rng.integers(-(1 << (wy - 1)), 1 << (wy - 1), size=9, dtype=np.int64)
+        a, b = B.Scalar(1, -3), B.Scalar(-1, 7)
+        z = B.axpy(a, B.BFP(xm, -20, wx), b, B.BFP(ym, 5, wy), B.Quant(wz, "qcomp"))
+        vals = [a.value() * p + b.value() * q for p, q in zip(frac_vals(xm, -20), frac_vals(ym, 5))]
+        ref = exact_floor_quant(vals, wz)
+        assert z.e == ref[0] and list(map(int, z.m)) == ref[1]
+    # residual r_v = A y - r on a 5 x 4 grid with a 55-bit y
+    A = B.laplace_stencil(2)
+    ym = rng.integers(-(1 << 54), 1 << 54, size=(4, 5), dtype=np.int64)
+    rm = rng.integers(-(1 << 31), 1 << 31, size=(4, 5), dtype=np.int64)
+    out = B.residual(A, B.BFP(ym, -60, 55), B.BFP(rm, -30, 32), B.Quant(16, "qcomp"), B.Scalar(13107, -14))
+    Y = lambda i, j: Fraction(int(ym[j, i])) * Fraction(2) ** -60 if 0 <= i < 5 and 0 <= j < 4 else Fraction(0)
+    vals = []
+    for j in range(4):
+        for i in range(5):
+            ay = Y(i, j) - Fraction(1, 4) * (Y(i - 1, j) + Y(i + 1, j) + Y(i, j - 1) + Y(i, j + 1))
+            vals.append(ay - Fraction(int(rm[j, i])) * Fraction(2) ** -30)
+    ref = exact_floor_quant(vals, 16)
+    assert out.e == ref[0] and list(map(int, np.asarray(out.m).ravel())) == ref[1]
