@@ -99,7 +99,6 @@ int32_t bfp_jacobi(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r, con
   if (y) {
     if ((rc = check_vec(y))) return rc;
     if (!same_shape(y, r)) return BFP_ERR_SHAPE;
-    if (is32(y) != is32(r)) return BFP_ERR_ARG;
     if (overlaps(y, y_out)) return BFP_ERR_ARG;
   }
   if (overlaps(r, y_out)) return BFP_ERR_ARG;
@@ -116,6 +115,10 @@ int32_t bfp_jacobi(const bfp_stencil* A, const bfp_vec* y, const bfp_vec* r, con
   int64_t Sc, Sn, eS;
   if ((rc = jacobi_operator(A, &Sc, &Sn, &eS))) return rc;
   d.meta_a = y->meta; d.meta_b = r->meta;
+  if (is32(y) != is32(r)) {   // mixed storage (progressive widths): the generic row kernel
+    if (A->ndim == 2) return launch_quant(OpJacD<2>{vin(y), vin(r), esize(y), esize(r), Sc, Sn, mw}, d, y_out, s);
+    return launch_quant(OpJacD<3>{vin(y), vin(r), esize(y), esize(r), Sc, Sn, mw}, d, y_out, s);
+  }
   return star_dispatch<kJacobi>(A->ndim, y, r, d, y_out, Sc, Sn, mw, is32(y), s);
 }
 

@@ -105,6 +105,10 @@ int32_t restrict_launch(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cu
 
 template <int ND, bool CORR>
 int32_t prolong_launch(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
+  if (CORR && is32(dc) != is32(y)) {   // mixed storage (progressive widths): y's storage at run time
+    if (is32(dc)) return launch_quant(OpProlong<int32_t, ND, true, int64_t>{vin(dc), vin(y), esize(y)}, d, out, s);
+    return launch_quant(OpProlong<int16_t, ND, true, int64_t>{vin(dc), vin(y), esize(y)}, d, out, s);
+  }
   if (!is32(dc)) return prolong16<CORR, ND>(dc, y, out, d, s);
   VIn yv = vin(y ? y : out);   // carries the fine shape; not read when CORR is false
   if (!CORR) yv.m = nullptr;
@@ -140,7 +144,6 @@ int32_t bfp_prolong(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* y_out, c
   if (y) {
     if ((rc = check_vec(y))) return rc;
     if (!same_shape(y, y_out)) return BFP_ERR_SHAPE;
-    if (is32(y) != is32(dc)) return BFP_ERR_ARG;
     if (overlaps(y, y_out)) return BFP_ERR_ARG;
   }
   QDesc d = blank_desc();

@@ -354,6 +354,7 @@ struct Level {
   int64_t* slots = nullptr;       // meta blocks of this level's op call sites (zeroed once per step)
   int nslots = 0;
   bfp_vec r{}, ya{}, yb{}, rv{};  // BFP buffers (mantissa + meta)
+  bfp_vec rir{};                  // the level's IR residual when r's storage is the finer width's
   void* tmp = nullptr;            // qcomp window (int32)
   double* b = nullptr;            // FP64 right-hand side (levels >= 1)
   double* x = nullptr;            // FP64 iterate (levels >= 1)
@@ -383,6 +384,7 @@ struct bfp_hierarchy {
   size_t arena_words = 0;
   // on-chip coarse V-cycle: levels kc.. run in one CTA (kc = nlevels: disabled)
   int kc = 0;
+  int coarse_wide = 0;                   // the on-chip cycle's storage: int32 (1) or int16 (0)
   CoarseBuf* d_bufs = nullptr;
   int nbufs = 0;
   int smem_bytes = 0;
@@ -618,7 +620,8 @@ int mark_sweep_run(std::vector<CoarseOp>& ops, const std::vector<CoarseBuf>& buf
 bool sweep_run_fits(const bfp_hierarchy* h, int k) {
   const int64_t n = h->lv[k].n;
   const int64_t np = h->o.ndim == 3 ? n * n * n : n * n;
-  return !h->cheby && h->o.w <= 16 && np >= 1 && np <= 32 && k + 1 == (int)h->lv.size();
+  const bool narrow = h->lv[k].w <= 16 && (k == 0 || h->lv[k - 1].w <= 16);   // int16 r and y
+  return !h->cheby && narrow && np >= 1 && np <= 32 && k + 1 == (int)h->lv.size();
 }
 
 int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, cudaStream_t s) {
@@ -688,18 +691,25 @@ int32_t coarse_setup(bfp_hierarchy* h) {
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return BFP_OK;
   const int budget = optin - 2048;   // the kernel's static shared memory is a few hundred bytes
-  const int eb = h->o.w > 16 ? 4 : 2;
+  int eb = h->o.w > 16 ? 4 : 2;
   const int nmax = h->o.coarse_onchip == 1 || h->o.coarse_onchip > 127 ? 127 : h->o.coarse_onchip;   // 4 columns per lane
   auto buf_bytes = [&](int64_t n) { return ((n + 2) * (n + 2) * eb + 15) / 16 * 16; };
-  // the largest start level (n <= 127) whose levels, schedule and tables fit in shared memory
+  // the largest start level (n <= 127) whose levels, schedule and tables fit in shared memory; the
+  // kernel keeps one storage type, so with progressive widths the start level, the level above it
+  // (its right-hand side) and every coarser level share the storage class
   for (int k = 0; k < nl; ++k) {
     if (h->lv[k].n > nmax) continue;
+    // (widths fall towards the coarsest level: comparing the level above with the coarsest covers all)
+    if ((h->lv[k > 0 ? k - 1 : 0].w > 16) != (h->lv[nl - 1].w > 16)) continue;
+    eb = h->lv[k].w > 16 ? 4 : 2;
     const int64_t nops = (int64_t)(nl - 1 - k) * (h->o.nu1 + 3 + h->o.nu2) + h->o.coarse_sweeps;
     int64_t bytes = (int64_t)(nl - k) * 3 * (BFP_META_WORDS * 8 + (int64_t)sizeof(CoarseBuf)) + nops * (int64_t)sizeof(CoarseOp) + 64;
     for (int l = k; l < nl; ++l) bytes += 3 * buf_bytes(h->lv[l].n);
     if (bytes <= budget) { h->kc = k; break; }
   }
   if (h->kc == nl) return BFP_OK;
+  eb = h->lv[h->kc].w > 16 ? 4 : 2;
+  h->coarse_wide = eb == 4;
   const int nb = (nl - h->kc) * 3;
   const int max_ops = (nl - 1 - h->kc) * (h->o.nu1 + 3 + h->o.nu2) + h->o.coarse_sweeps;
   // layout: meta blocks | buffer table | op list | mantissa buffers (16-byte aligned)
@@ -743,7 +753,7 @@ int32_t coarse_setup(bfp_hierarchy* h) {
   }
   // the attribute is per kernel, shared by every hierarchy: allow the device maximum once rather than
   // this hierarchy's size (a later hierarchy with a smaller on-chip part must not shrink it)
-  return allow_coarse_smem(h->o.w > 16, optin) ? BFP_OK : BFP_ERR_CUDA;
+  return allow_coarse_smem(h->coarse_wide != 0, optin) ? BFP_OK : BFP_ERR_CUDA;
 }
 
 int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* out, cudaStream_t s) {
@@ -767,7 +777,7 @@ int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* 
   a.yout_meta = out->meta;
   a.yout_buf = h->ybuf[i];
   a.stats = h->stats;
-  if (h->o.w > 16) k_coarse_vcycle<int32_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
+  if (h->coarse_wide) k_coarse_vcycle<int32_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
   else k_coarse_vcycle<int16_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
@@ -998,7 +1008,7 @@ int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double*
   Level& L = h->lv[k];
   if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;   // every call-site meta of this step
   PrezeroedScope pz;
-  bfp_vec r = L.r;
+  bfp_vec r = L.rir.mant ? L.rir : L.r;
   r.w = L.w;                                                  // quantised to this level's width
   r.meta = L.slots + BFP_META_WORDS * (L.nslots - 1);         // the IR residual's own slot
   TRY(ir_residual_q(h, k, b, bscale, x, &r, s));
@@ -1239,7 +1249,7 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
   if (o->mode != BFP_QCOMP && o->mode != BFP_NNQCOMP) return BFP_ERR_ARG;
   if (o->arith != BFP_ARITH_BFP && o->arith != BFP_ARITH_FP32 && o->arith != BFP_ARITH_BF16) return BFP_ERR_ARG;
   if (o->tile_rows < 0 || o->tile_rows > 64) return BFP_ERR_ARG;
-  if (o->w_step < 0 || (o->w_step > 0 && (o->w > 16 || o->arith != BFP_ARITH_BFP))) return BFP_ERR_ARG;
+  if (o->w_step < 0 || (o->w_step > 0 && o->arith != BFP_ARITH_BFP)) return BFP_ERR_ARG;
   if (o->smoother != BFP_SMOOTH_JACOBI && o->smoother != BFP_SMOOTH_CHEBY) return BFP_ERR_ARG;
   if (o->w_add_max > 32) return BFP_ERR_ARG;
   if (o->smoother == BFP_SMOOTH_CHEBY && (o->arith != BFP_ARITH_BFP || !(o->cheby_eta > 0.0 && o->cheby_eta < 1.0)))
@@ -1277,9 +1287,13 @@ int32_t bfp_hierarchy_create(const bfp_solver_opts* o, bfp_hierarchy** out) {
       ok = make_fvec(h, L.fr, nd, L.n, dt) && make_fvec(h, L.fya, nd, L.n, dt) && make_fvec(h, L.fyb, nd, L.n, dt) &&
            make_fvec(h, L.frv, nd, L.n, dt);
     } else {
-      // storage follows w (int16 for every level when w_step > 0: all widths <= 16)
-      ok = make_vec(h, L.r, nd, L.n, L.w) && make_vec(h, L.ya, nd, L.n, L.w) &&
+      // storage follows w; a level's right-hand side r holds the finer level's restriction, so
+      // it takes the finer width's storage (progressive widths), and where that storage differs
+      // from the level's own, the level's FMG IR residual gets a buffer of its own (rir)
+      const int wr = k == 0 ? L.w : h->lv[k - 1].w;
+      ok = make_vec(h, L.r, nd, L.n, wr) && make_vec(h, L.ya, nd, L.n, L.w) &&
            make_vec(h, L.yb, nd, L.n, L.w) && make_vec(h, L.rv, nd, L.n, L.w);
+      if (ok && (wr > 16) != (L.w > 16)) ok = make_vec(h, L.rir, nd, L.n, L.w);
     }
     const int64_t pts = L.n * L.n * (nd == 3 ? L.n : 1);
     if (ok && o->use_tmp && !flt) {
@@ -1335,6 +1349,7 @@ int32_t bfp_hierarchy_create_var(const bfp_solver_opts* o, const double* k_nodes
   if (!o || !k_nodes || !out) return BFP_ERR_ARG;
   *out = nullptr;
   if (o->ndim != 2 || o->arith != BFP_ARITH_BFP || o->w > 24 || o->smoother != BFP_SMOOTH_JACOBI) return BFP_ERR_ARG;
+  if (o->w_step > 0 && o->w > 16) return BFP_ERR_ARG;   // the variable ops take one storage for y and r
   bfp_solver_opts oo = *o;
   oo.coarse_onchip = 0;                              // the on-chip cycle has the constant operator only
   bfp_hierarchy* h = nullptr;

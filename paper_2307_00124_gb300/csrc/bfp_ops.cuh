@@ -227,6 +227,36 @@ struct OpResW {
   }
 };
 
+// Damped Jacobi S y + m_w r with y and r of different storage (progressive widths: the right-hand
+// side comes from the finer level's width):  H = sc y + sn sum_nbrs(y), L = m_w r.
+template <int NDIM>
+struct OpJacD {
+  VIn y, r;
+  int ey, er;
+  int64_t c, n, mw;
+  __device__ __forceinline__ void operator()(int64_t row, int64_t c0, int64_t (&H)[8], int64_t (&L)[8]) const {
+    const int64_t nyy = y.ny, yy = row % nyy;
+    int64_t ctr[8], nb[8], b[8];
+    ldw8d(y, ey, row, c0, ctr);
+    ldw8d(y, ey, yy > 0 ? row - 1 : -1, c0, nb);
+    ldw8d(y, ey, yy + 1 < nyy ? row + 1 : -1, c0, b);
+    int64_t ns[8];
+    const int64_t wv = ld1d(y, ey, row, c0 - 1), ev = ld1d(y, ey, row, c0 + 8);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ns[k] = (((k == 0 ? wv : ctr[k - 1]) + (k == 7 ? ev : ctr[k + 1])) + nb[k]) + b[k];
+    if (NDIM == 3) {
+      const int64_t zz = row / nyy;
+      ldw8d(y, ey, zz > 0 ? row - nyy : -1, c0, nb);
+      ldw8d(y, ey, zz + 1 < y.nz ? row + nyy : -1, c0, b);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ns[k] += nb[k] + b[k];
+    }
+    ldw8d(r, er, row, c0, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { H[k] = c * ctr[k] + n * ns[k]; L[k] = mw * b[k]; }
+  }
+};
+
 enum StarKind : int32_t { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };
 
 // Star stencil ops (Alg. espmv-row / egemv-row on the 2*ndim+1 point stencil).
@@ -341,9 +371,11 @@ struct OpRestrict {
 
 // Interpolation P d (bilinear / trilinear), optionally with the correction
 // y - P d (Alg. v-cycle correction line):  H = -P_m d (or +P_m d), L = y.
-template <class T, int NDIM, bool CORRECT>
+// T: d's storage; TY: y's (int64_t: the storage given at run time by ey).
+template <class T, int NDIM, bool CORRECT, class TY = T>
 struct OpProlong {
   VIn d, y;
+  int ey = 0;
   __device__ __forceinline__ void hinterp(int64_t crow, int64_t c0, int64_t (&g)[8]) const {
     // fine column i: odd -> 2 d[(i-1)/2]; even -> d[i/2 - 1] + d[i/2]
     const int64_t C = c0 >> 1;   // first coarse column (multiple of 4)
@@ -387,8 +419,9 @@ struct OpProlong {
       }
     }
     if (CORRECT) {
-      int32_t yv[8];
-      ld8<T>(y, row, c0, yv);
+      int64_t yv[8];
+      if constexpr (sizeof(TY) == 8) ldw8d(y, ey, row, c0, yv);
+      else ldw8<TY>(y, row, c0, yv);
 #pragma unroll
       for (int k = 0; k < 8; ++k) { H[k] = -acc[k]; L[k] = yv[k]; }
     } else {

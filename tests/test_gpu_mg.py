@@ -125,13 +125,17 @@ def test_ir_residual_window_and_padding(nd, n):
     assert st["ir_recomputed"] == 2       # the first call (no gamma yet) and the overflowing one
 
 
-@pytest.mark.parametrize("nd,n,w,onchip", [(2, 63, 16, 63), (2, 63, 16, 0), (2, 127, 12, 63), (2, 255, 14, 15),
-                                           (3, 15, 16, 0)])
+@pytest.mark.parametrize("nd,n,w,onchip,step", [(2, 63, 16, 63, 1), (2, 63, 16, 0, 1), (2, 127, 12, 63, 1),
+                                                (2, 255, 14, 15, 1), (3, 15, 16, 0, 1),
+                                                # wider than 16 bits: int32 fine levels, int16 coarse ones
+                                                (2, 63, 20, 63, 1), (2, 127, 24, 63, 2), (2, 255, 32, 15, 3),
+                                                (2, 63, 32, 63, 1), (3, 15, 24, 0, 4), (3, 31, 20, 0, 2)])
 @pytest.mark.parametrize("mode", [bfp.QCOMP, bfp.NNQCOMP])
-def test_progressive_precision_bit_exact(nd, n, w, onchip, mode):
-    """w_step = 1: every level's ops at w - k bits (the restriction at the finer level's width);
-    V-cycle, FMG and IR steps against the oracle bit for bit, counters included."""
-    h, s = make(nd, n, w, mode, coarse_onchip=onchip, w_step=1)
+def test_progressive_precision_bit_exact(nd, n, w, onchip, step, mode):
+    """Level k's ops at w - k w_step bits (the restriction at the finer level's width; storage per
+    width, so a level where the width crosses 16 bits mixes int32 and int16 operands); V-cycle,
+    FMG and IR steps against the oracle bit for bit, counters included."""
+    h, s = make(nd, n, w, mode, coarse_onchip=onchip, w_step=step)
     rm = random_mantissas((n,) * nd, w, 5, "smooth")
     r = bfp.BFPVector.from_mantissas(rm, -18, w)
     y = bfp.BFPVector((n,) * nd, w)
@@ -157,12 +161,16 @@ def test_progressive_precision_bit_exact(nd, n, w, onchip, mode):
     assert np.array_equal(xt.cpu().numpy(), xr)
 
 
-def test_progressive_precision_rejects_wide_or_float():
-    for w, arith in ((24, bfp.ARITH_BFP), (16, bfp.ARITH_FP32)):
-        o = bfp.bfp_solver_opts_default(2, 63, w)
-        o.w_step, o.arith = 1, arith
-        with pytest.raises(bfp.BFPError):
-            bfp.Hierarchy(o)
+def test_progressive_precision_rejects_float_and_wide_variable():
+    o = bfp.bfp_solver_opts_default(2, 63, 16)
+    o.w_step, o.arith = 1, bfp.ARITH_FP32
+    with pytest.raises(bfp.BFPError):
+        bfp.Hierarchy(o)
+    o = bfp.bfp_solver_opts_default(2, 63, 24)
+    o.w_step = 1
+    with pytest.raises(bfp.BFPError):
+        bfp.Hierarchy(o, k_nodes=np.ones((65, 65)))
+    bfp.Hierarchy(bfp.bfp_solver_opts_default(2, 63, 24)).close()
 
 
 @pytest.mark.parametrize("cap", [0, 2, 4])

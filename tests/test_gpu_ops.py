@@ -454,3 +454,40 @@ def test_wide_rejected_elsewhere():
     x62 = bfp.BFPVector((15, 15), 62)   # 3 x would pass 62 bits
     with pytest.raises(bfp.BFPError):
         bfp.bfp_axpy(bfp.scalar(3, 0), x62, bfp.scalar(1, 0), z, bfp.BFPVector((15, 15), 40), gq(40, bfp.QCOMP))
+
+
+# ---- mixed int16 / int32 operands (progressive widths across the 16-bit boundary) ----
+
+@pytest.mark.parametrize("shape", [(37, 45), (63, 63), (5, 6, 7), (3, 260, 17)])
+@pytest.mark.parametrize("wy,wr,wo", [(16, 24, 16), (24, 12, 24), (17, 16, 17), (12, 32, 12)])
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_jacobi(shape, wy, wr, wo, mode):
+    nd = len(shape)
+    omega = 0.8 if nd == 2 else 6 / 7
+    A = bfp.bfp_laplace_stencil(nd, omega, 16)
+    om = B.Scalar(A.omega.m, A.omega.e)
+    seed = hash((shape, wy, wr, wo, mode)) % 1000
+    ym = random_mantissas(shape, wy, seed, "smooth")
+    rm = random_mantissas(shape, wr, seed + 1)
+    y, r = dev_vec(ym, -9, wy, seed), dev_vec(rm, -12, wr, seed + 2)
+    z = out_vec(shape, wo)
+    st = stats_tensor()
+    bfp.bfp_jacobi(A, y, r, z, gq(wo, mode), st)
+    rs = B.Stats()
+    check(z, B.jacobi(B.laplace_stencil(nd), om, B.BFP(ym, -9, wy), B.BFP(rm, -12, wr), oq(wo, mode), rs), st, rs)
+
+
+@pytest.mark.parametrize("cshape", [(15, 15), (31, 7), (3, 7, 5)])
+@pytest.mark.parametrize("wd,wy", [(12, 24), (24, 16), (16, 17)])
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_prolong(cshape, wd, wy, mode):
+    fshape = tuple(2 * c + 1 for c in cshape)
+    seed = hash((cshape, wd, wy, mode)) % 1000
+    dm = random_mantissas(cshape, wd, seed, "smooth")
+    ym = random_mantissas(fshape, wy, seed + 1, "smooth")
+    d, y = dev_vec(dm, -14, wd, seed), dev_vec(ym, -13, wy, seed + 3)
+    z = out_vec(fshape, wy)
+    st = stats_tensor()
+    bfp.bfp_prolong(d, y, z, gq(wy, mode), st)
+    rs = B.Stats()
+    check(z, B.prolong(B.BFP(dm, -14, wd), B.BFP(ym, -13, wy), fshape, oq(wy, mode), rs), st, rs)
