@@ -313,7 +313,9 @@ typedef struct {
                             by m = 1 bit per refinement): level k (0 = finest) gives its ops'
                             results, the restriction to level k+1 and the IR residual on level k
                             included, w_k = max(w - k w_step, 2) bits; 0: w on every level
-                            (default).  w_step > 0 needs w <= 16 and arith BFP */
+                            (default).  Each level's vectors take the storage of their width
+                            (int32 fine levels, int16 coarse ones when w > 16).  w_step > 0
+                            needs arith BFP, and w <= 16 for variable coefficients */
   int32_t smoother;      /* bfp_smoother (default BFP_SMOOTH_JACOBI) */
   double cheby_eta;      /* BFP_SMOOTH_CHEBY: the part [eta rho, rho] of the spectrum the two
                             Chebyshev steps target, 0 < eta < 1 (default 0.15: the i/100 that
