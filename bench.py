@@ -310,17 +310,22 @@ def var_compare(bfp, torch, stream, n=2047, steps=10):
 def width_sweep(bfp, torch, args, f, stream, steps=10):
     """The 4095^2 workload at mantissa widths 4 ... 32 (int16 storage up to 16, int32 above): IR-V step
     throughput, and the accuracy ratio after FMG and after one more IR-V step, for nnqcomp (FMG's saturation /
-    truncation heuristic) and qcomp (renormalising ops); plus progressive precision (w = 16 on the finest level,
-    one bit fewer per coarser level)."""
+    truncation heuristic) and qcomp (renormalising ops); plus progressive precision (w = 16, 24, 32 on the finest
+    level, one bit fewer per coarser level; int32 fine levels and int16 coarse ones above 16 bits)."""
     n = args.n
     dof = n * n
     out = []
-    cases = [(w, m, 0) for w in (4, 8, 12, 16, 24, 32) for m in ("nnqcomp", "qcomp")] + [(16, "nnqcomp", 1)]
+    cases = [(w, m, 0) for w in (4, 8, 12, 16, 24, 32) for m in ("nnqcomp", "qcomp")] + \
+        [(16, "nnqcomp", 1), (24, "nnqcomp", 1), (32, "nnqcomp", 1)]
     for w, m, step in cases:
         o = bfp.bfp_solver_opts_default(2, n, w)
         o.mode = bfp.NNQCOMP if m == "nnqcomp" else bfp.QCOMP
         o.w_step = step
-        h = bfp.Hierarchy(o)
+        try:
+            h = bfp.Hierarchy(o)
+        except bfp.BFPError as exc:   # a configuration the library refuses is reported, not fatal
+            out.append({"w": w, "mode": m, "w_step": step, "error": str(exc)})
+            continue
         x = torch.zeros_like(f)
         with torch.cuda.stream(stream):
             h.ir_iterate(f, x, 3)
