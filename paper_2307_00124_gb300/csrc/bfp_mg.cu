@@ -47,63 +47,6 @@ __device__ __forceinline__ double ir_res(const double* __restrict__ b, double bs
   return __dsub_rn(__dmul_rn(b[idx], bscale), ax);
 }
 
-__device__ __forceinline__ bool split_f64(double v, int64_t& M, int64_t& E) {
-  const uint64_t bits = (uint64_t)__double_as_longlong(v);
-  const int ex = (int)((bits >> 52) & 0x7ff);
-  const uint64_t fr = bits & ((1ull << 52) - 1);
-  if (ex == 0x7ff) return false;
-  if (ex == 0) { M = (int64_t)fr; E = -1074; }
-  else { M = (int64_t)(fr | (1ull << 52)); E = ex - 1075; }
-  if (bits >> 63) M = -M;
-  return true;
-}
-
-constexpr int64_t kKeyOff = 4096;
-
-// Pass 1: max over the residual of msb(M) + E (the quant() normalisation);
-// pass 2: recompute the residual and store floor(r / 2^e_out) as BFP.
-template <int ND, bool PASS1>
-__global__ void __launch_bounds__(256) k_ir_residual(const double* __restrict__ b, double bscale,
-                                                     const double* __restrict__ x, Grid g, double cdiag,
-                                                     double cnb, VOut out, int64_t* meta, int w) {
-  const int64_t nvec = out.ld >> 3, rows = g.ny * g.nz, total = rows * nvec;
-  int64_t e_out = 0;
-  if (!PASS1) {
-    const int64_t key = meta[kMetaMu];
-    e_out = (key > 0 ? key - kKeyOff : -1073) - w;
-  }
-  Red red = {0, 0, 0};
-  bool bad = false;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = idx / nvec, c0 = (idx - row * nvec) << 3;
-    const int64_t j = row % g.ny, k = row / g.ny;
-    int32_t o[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      o[q] = 0;
-      const int64_t i = c0 + q;
-      if (i >= g.nx) continue;
-      const double r = ir_res<ND>(b, bscale, x, g, i, j, k, cdiag, cnb);
-      int64_t M = 0, E = -1074;
-      if (!split_f64(r, M, E)) { bad = true; continue; }
-      if (PASS1) {
-        const int64_t mv = M == 0 ? -1073 : msb64(M) + E;
-        red.key = max(red.key, (long long)(mv + kKeyOff));
-      } else {
-        const int64_t sh = E - e_out;
-        const int64_t v = sh >= 0 ? (int64_t)((uint64_t)M << (sh > 63 ? 63 : sh)) : (M >> (-sh > 63 ? 63 : -sh));
-        o[q] = (int32_t)v;
-        red.nrm = max(red.nrm, (long long)(v < 0 ? -v : v));
-      }
-    }
-    if (!PASS1) st8(out, row, c0, o);
-  }
-  if (bad) atomicOr((unsigned long long*)&meta[BFP_META_FLAGS], 1ull);
-  block_commit(red, meta, nullptr, PASS1);
-  if (!PASS1 && blockIdx.x == 0 && threadIdx.x == 0) meta[0] = e_out;
-}
-
 // 3D IR residual with the Alg. qcomp window (as k_ir2d): pass 1 max msb + w_tmp window
 // from the previous residual's gamma, pass 2 narrows the window or recomputes.  The residual is
 // ir_res<3>'s sequence with the power-of-two scalings done on the exponent field (bit-identical).
