@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
         const int i = j - j0;
         if (i + NS - 1 < nst) issue(sn, inttag, true);   // stage i + NS - 1, into the slot of row j - 2
         else cp_commit();
-        int32_t kf[4][8], qv[8];                  // this row's coefficients, loaded while the ring fills
+        [[maybe_unused]] int32_t kf[4][8], qv[8];   // this row's coefficients, loaded while the ring fills
         if constexpr (VAR) {
           if (KIND != kJacobi0) {
 #pragma unroll
