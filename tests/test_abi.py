@@ -70,3 +70,30 @@ def test_argument_errors_return_before_any_device_call():
     assert bfp._lib.bfp_solver_opts_default(2, 63, 16, C.byref(o)) == 0
     o.n = 62                                              # not 2^J - 1
     assert bfp._lib.bfp_hierarchy_create(C.byref(o), C.byref(h)) == -2
+
+
+STRUCTS = ["bfp_vec", "bfp_scalar", "bfp_q", "bfp_stats", "bfp_stencil", "bfp_varstencil", "bfp_solver_opts",
+           "flt_vec", "bfp_ir_opts", "bfp_ir_report"]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (gcc on the header)."""
+    import paper_2307_00124_gb300 as bfp
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bfp/bfp.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(bfp, name)
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for fld, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fld, name, fld))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(ln.rsplit(" ", 1) for ln in out if ln)
+    for name in STRUCTS:
+        cls = getattr(bfp, name)
+        assert int(got[name + " size"]) == C.sizeof(cls), name
+        for fld, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, fld)]) == getattr(cls, fld).offset, (name, fld)
