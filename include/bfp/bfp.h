@@ -149,12 +149,12 @@ int32_t bfp_laplace_stencil(int32_t ndim, double omega, int32_t w_omega, bfp_ste
 /* ---- BFP ops (Sec. 4, App. B) ------------------------------------------------ */
 
 /* out = quantisation of x to q->w_out bits (exact z* = x; Sec. 2 normalised
- * representation).  out has x's shape. */
+ * representation).  out has x's shape; either may hold int64 mantissas. */
 int32_t bfp_normalize(const bfp_vec* x, const bfp_vec* out, const bfp_q* q,
                       const bfp_stats* st, bfp_stream stream);
 
 /* out = floor-quantised normalised BFP of the doubles x (device, dense,
- * n[0]*n[1]*n[2] values, x fastest) at out->w bits.  The doubles are read as
+ * n[0]*n[1]*n[2] values, x fastest) at out->w bits (1..62).  The doubles are read as
  * one exact block with e* = -1074; the result is Alg. qcomp's (quant() of
  * Alg. ir).  A NaN or Inf sets meta[BFP_META_FLAGS] bit 0 and out is
  * unspecified. */
@@ -164,8 +164,9 @@ int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream);
  * wider mantissas are rounded to nearest). */
 int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream);
 
-/* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp); x and y may
- * differ in width and storage (int16 / int32). */
+/* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp); x, y
+ * and z may differ in width and storage (int16 / int32 / int64; z up to 62
+ * bits).  BFP_ERR_WIDTH when msb(a) + w_x or msb(b) + w_y passes 62. */
 int32_t bfp_axpy(bfp_scalar a, const bfp_vec* x, bfp_scalar b, const bfp_vec* y,
                  const bfp_vec* z, const bfp_q* q, const bfp_stats* st, bfp_stream stream);
 
