@@ -32,7 +32,10 @@ def _worker(rank, ws, port, out):
 def test_max_over_ranks_and_value_gloo():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 29500 + os.getpid() % 1000
+    import socket
+    with socket.socket() as sk:                                # a free port on the loopback interface
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
