@@ -55,7 +55,7 @@ def test_pitch_and_status_strings():
 def test_argument_errors_return_before_any_device_call():
     import paper_2307_00124_gb300 as bfp
     v = bfp.bfp_vec()
-    v.mant, v.meta, v.w, v.ndim = 16, 16, 40, 2          # w = 40 is invalid
+    v.mant, v.meta, v.w, v.ndim = 16, 16, 63, 2          # w = 63 is invalid
     v.n[0], v.n[1], v.n[2], v.ld = 8, 8, 1, 8
     q = bfp.q(16)
     assert bfp._lib.bfp_normalize(C.byref(v), C.byref(v), C.byref(q), None, None) == -1
@@ -70,6 +70,32 @@ def test_argument_errors_return_before_any_device_call():
     assert bfp._lib.bfp_solver_opts_default(2, 63, 16, C.byref(o)) == 0
     o.n = 62                                              # not 2^J - 1
     assert bfp._lib.bfp_hierarchy_create(C.byref(o), C.byref(h)) == -2
+    # defaults of the options added with the paper's variants
+    assert bfp._lib.bfp_solver_opts_default(2, 63, 16, C.byref(o)) == 0
+    assert (o.smoother, o.cheby_eta, o.w_add_max, o.w_step) == (0, 0.15, -1, 0)
+    for field, value in (("smoother", 2), ("w_add_max", 40), ("w_step", -1)):
+        oo = bfp.bfp_solver_opts()
+        bfp._lib.bfp_solver_opts_default(2, 63, 16, C.byref(oo))
+        setattr(oo, field, value)
+        assert bfp._lib.bfp_hierarchy_create(C.byref(oo), C.byref(h)) == -1, field
+    oo = bfp.bfp_solver_opts()
+    bfp._lib.bfp_solver_opts_default(2, 63, 16, C.byref(oo))
+    oo.smoother, oo.cheby_eta = 1, 1.0                    # eta outside (0, 1)
+    assert bfp._lib.bfp_hierarchy_create(C.byref(oo), C.byref(h)) == -1
+    oo.cheby_eta, oo.arith = 0.15, 1                      # Chebyshev V(1,0) is BFP only
+    assert bfp._lib.bfp_hierarchy_create(C.byref(oo), C.byref(h)) == -1
+    # null hierarchies and bad vectors of the newer entry points
+    d = C.c_double()
+    st = (C.c_uint64 * 8)()
+    vs = bfp.bfp_varstencil()
+    assert bfp._lib.bfp_hierarchy_rhs_scale(None, C.byref(d)) == -1
+    assert bfp._lib.bfp_hierarchy_read_finest_stats(None, st, None) == -1
+    assert bfp._lib.bfp_hierarchy_var_ir_operator(None, C.byref(vs)) == -1
+    v.w, v.ld = 16, 8
+    assert bfp._lib.bfp_ir_iterate_bfp(None, C.byref(v), C.byref(v), 1, None) == -1
+    v.w = 63
+    assert bfp._lib.bfp_cheby(C.byref(A), bfp.scalar(1, 0), bfp.scalar(-1, -2), C.byref(v), C.byref(v),
+                              C.byref(q), None, None) == -1
 
 
 STRUCTS = ["bfp_vec", "bfp_scalar", "bfp_q", "bfp_stats", "bfp_stencil", "bfp_varstencil", "bfp_solver_opts",
