@@ -261,6 +261,8 @@ class BFPSolver:
     smoother: str = "jacobi"         # "jacobi": V(nu1, nu2) damped Jacobi; "cheby": the paper's V(1,0)
     eta: float = 0.15                # Chebyshev: targeted part [eta rho, rho] of the spectrum
     w_add_max: Optional[int] = None  # cap on every op's table w_add (Table tab:recomputation)
+    ir_window: bool = True           # the IR residual's quantisation keeps Alg. qcomp's w_tmp window
+    ir_window_bits: int = 32         # widest window kept (32-bit storage); a wider w_tmp recomputes
     stats: B.Stats = field(default_factory=B.Stats)
 
     def __post_init__(self):
@@ -279,6 +281,8 @@ class BFPSolver:
                 break
             m = (m - 1) // 2
         self.sizes = sizes
+        self.ir_gamma = {}           # level -> mu* of that level's previous IR residual (its gamma)
+        self.ir_counts = {}          # level -> [IR residual quantisations, of which recomputed]
 
     def width(self, k: int) -> int:
         """Inner width of level k (0 finest): w - k w_step, at least 2.  Progressive precision
@@ -326,10 +330,44 @@ class BFPSolver:
             y = B.jacobi(A, om, y, r, q, st)
         return y
 
-    def ir_step(self, k: int, b: np.ndarray, x: np.ndarray, trace: Optional[list] = None):
+    def ir_quantize(self, k: int, r64: np.ndarray, first: bool = False) -> B.BFP:
+        """quant(r) of Alg. ir on level k: the normalised floor quantisation of the FP64 residual
+        (B.from_f64; Alg. qcomp's result does not depend on its window), plus the decision Alg. qcomp
+        takes with the window of Table tab:estimates' IR residual rows.  gamma is the previous IR
+        residual of the level: its window position msb(gamma_m) + e_gamma is taken as that residual's
+        mu* (its exponent plus its width); w_add = 4 (i > 1), 5 for the first step on an FMG level,
+        where gamma is the coarser level's last residual (the i = 1 row).  With no previous residual,
+        or no window kept, the quantisation recomputes.  Overflow: mu_tmp < mu*; underflow:
+        lambda_out < lambda_tmp (both in absolute exponents)."""
+        w = self.width(k)
+        r = B.from_f64(r64, w)
+        mu = r.e + w
+        w_add = 5 if first else 4
+        if self.w_add_max is not None:
+            w_add = min(w_add, self.w_add_max)
+        w_tmp = w + w_add
+        gam = self.ir_gamma.get(k)
+        recomputed = True
+        if self.ir_window and gam is not None and w_tmp <= self.ir_window_bits:
+            overflow = gam < mu
+            underflow = (mu - w) < (gam - w_tmp)
+            recomputed = overflow or underflow
+        cnt = self.ir_counts.setdefault(k, [0, 0])
+        cnt[0] += 1
+        cnt[1] += int(recomputed)
+        self.ir_gamma[k] = mu
+        return r
+
+    def ir_totals(self, finest_only: bool = False) -> tuple[int, int]:
+        """(IR residual quantisations, of which recomputed), over all levels or the finest."""
+        ks = [0] if finest_only else list(self.ir_counts)
+        return (sum(self.ir_counts.get(k, [0, 0])[0] for k in ks),
+                sum(self.ir_counts.get(k, [0, 0])[1] for k in ks))
+
+    def ir_step(self, k: int, b: np.ndarray, x: np.ndarray, trace: Optional[list] = None, first: bool = False):
         """One IR-V step (Alg. ir): FP64 residual, quantise (to the level's width), V-cycle, FP64 update."""
         r64 = residual_f64(b, x)
-        r = B.from_f64(r64, self.width(k))
+        r = self.ir_quantize(k, r64, first)
         y = self.vcycle(k, r)
         if trace is not None:
             trace.append((r, y))
@@ -356,6 +394,7 @@ class BFPSolver:
         """Alg. fmg: recurse to the coarsest level, interpolate at w (qspmv(P, x)), N IR-V steps."""
         bs = self.rhs_hierarchy(f)
         x = None
+        self.ir_gamma = {}
         for k in range(len(self.sizes) - 1, -1, -1):
             if x is None:
                 x = np.zeros(bs[k].shape)
@@ -363,8 +402,9 @@ class BFPSolver:
                 xq = B.from_f64(x, self.width(k + 1))
                 xp = B.prolong(xq, None, bs[k].shape, self.ql(k), self.stats)
                 x = B.to_f64(xp)
-            for _ in range(self.n_fmg):
-                x = self.ir_step(k, bs[k], x, trace)
+                self.ir_gamma[k] = self.ir_gamma.get(k + 1)     # gamma of the first step: the coarser residual
+            for i in range(self.n_fmg):
+                x = self.ir_step(k, bs[k], x, trace, first=(i == 0 and k < len(self.sizes) - 1))
         return x
 
 

@@ -244,3 +244,60 @@ def test_bfp_ir_converges_to_the_width_floor():
     assert floors[32] < 3e-8
     assert 8 <= floors[28] / floors[32] <= 32, floors
     assert 2 ** 7 <= floors[32] / floors[40] <= 2 ** 9, floors        # int64 iterate (w > 32)
+
+
+def _f64_block(x):
+    """The doubles as one exact BFP block z* 2^-1074 (Python integers; every double is an
+    integer multiple of 2^-1074)."""
+    M, E = B.f64_split(x)
+    z = np.empty(x.shape, dtype=object)
+    z.ravel()[:] = [int(m) << int(e - B.F64_E_STAR) for m, e in zip(M.ravel(), E.ravel())]
+    return B.Exact(z, B.F64_E_STAR, 2100)
+
+
+def test_ir_window_model_matches_alg_qcomp():
+    """The IR residual's quantisation (ir_quantize: from_f64 plus the window decision) against
+    Alg. qcomp run step by step on the exact FP64 block, for windows around the residual's own mu*
+    and both IR residual rows of Table tab:estimates (w_add 4, and 5 for an FMG level's first step):
+    the same result, and a recomputation exactly when Alg. qcomp overflows or underflows."""
+    rng = np.random.default_rng(11)
+    s = mg.BFPSolver(2, 7, w=16, mode="qcomp")
+    seen = set()
+    for trial in range(6):
+        r64 = rng.standard_normal((7, 7)) * 10.0 ** int(rng.integers(-12, 3))
+        if trial == 5:
+            r64[:] = 0.0                                   # all-zero residual: mu* at e* + 1
+        ex = _f64_block(r64)
+        ref = B.from_f64(r64, 16)
+        mu = ref.e + 16
+        for first in (False, True):
+            w_tmp = 16 + (5 if first else 4)
+            for gam in range(mu - 8, mu + 9):
+                s.ir_gamma, s.ir_counts = {0: gam}, {}
+                got = s.ir_quantize(0, r64, first)
+                out, ovf, unf = B.qcomp_alg(ex, 16, w_tmp, (1, gam - 2))   # msb(1) + (gam - 2) = gam
+                assert got.e == out.e == ref.e
+                assert np.array_equal(np.asarray(got.m, dtype=object), np.asarray(out.m, dtype=object))
+                assert s.ir_counts[0] == [1, int(ovf or unf)]
+                assert s.ir_gamma[0] == mu                   # the next residual's gamma
+                seen.add((ovf, unf))
+    assert seen == {(False, False), (True, False), (False, True)}
+
+
+def test_ir_window_model_recomputes_without_a_window():
+    r64 = np.linspace(-1.0, 2.0, 49).reshape(7, 7) * 1e-6
+    mu = B.from_f64(r64, 16).e + 16
+    for kw in ({"ir_window": False}, {"ir_window_bits": 19}, {}):
+        s = mg.BFPSolver(2, 7, w=16, mode="qcomp", **kw)
+        if kw:
+            s.ir_gamma = {0: mu}                            # a perfect gamma, but no window kept
+        s.ir_quantize(0, r64)                               # (no gamma at all in the last case)
+        assert s.ir_counts[0] == [1, 1]
+    s = mg.BFPSolver(2, 7, w=16, mode="qcomp", w_add_max=0)
+    s.ir_gamma = {0: mu + 1}                                 # w_add capped at 0: lambda_out < lambda_tmp
+    s.ir_quantize(0, r64)
+    assert s.ir_counts[0] == [1, 1]
+    s = mg.BFPSolver(2, 7, w=16, mode="qcomp")
+    s.ir_gamma = {0: mu + 1}
+    s.ir_quantize(0, r64)
+    assert s.ir_counts[0] == [1, 0]
