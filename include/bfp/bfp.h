@@ -164,6 +164,13 @@ int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream);
  * wider mantissas are rounded to nearest). */
 int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream);
 
+/* meta[1] of x = max_i |m_i| over the block's n[0]*n[1]*n[2] mantissas
+ * (padding columns ignored): the norm word every gamma rule reads (Table
+ * tab:estimates norms are max |m| * 2^e; the max-|mantissa| reduction of
+ * Alg. qcomp's first loop).  For blocks whose mantissas were written by the
+ * caller; the exponent word is left as it is.  Any storage (w <= 62). */
+int32_t bfp_block_norm(const bfp_vec* x, bfp_stream stream);
+
 /* z = a*x + b*y (Alg. eaxpby-setup / eaxpby-row, then qcomp or nnqcomp); x, y
  * and z may differ in width and storage (int16 / int32 / int64; z up to 62
  * bits).  BFP_ERR_WIDTH when msb(a) + w_x or msb(b) + w_y passes 62. */
@@ -273,12 +280,17 @@ int32_t bfp_var_jacobi(const bfp_varstencil* A, const bfp_vec* y, const bfp_vec*
  * where the implicit device synchronisation of cudaMalloc / cudaFree is not
  * acceptable).  The paper has no counterpart: this is a deployment variant.
  * Same arguments and result as bfp_jacobi; q->tmp is ignored.  In qcomp mode
- * the w_tmp-bit window lives in a static device array of
+ * with w_tmp = w_out + w_add <= 32 (w_add < 0: the relaxation row's 2) the
+ * w_tmp-bit window lives in a static device array of
  * bfp_noalloc_window_capacity() int32 entries (16 MiB on every GPU that
- * loads the library, held until exit); nothing is allocated.
- *  - Outputs with rows * ld larger than the capacity: BFP_ERR_CAPACITY.
- *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ * loads the library, held until exit); nothing is allocated.  nnqcomp, and
+ * qcomp with a wider w_tmp, use no scratch and take any size.
+ *  - qcomp outputs that use the window with rows * ld larger than the
+ *    capacity: BFP_ERR_CAPACITY.
+ *  - Each call looks up the array's device address on the current device
+ *    (so a device reset in the process is harmless); the first lookup on a
+ *    device may load the module, so make the first call before any stream
+ *    capture.
  *  - All calls on a device share the array; calls that overlap on the GPU
  *    (unordered streams) race on it. */
 int64_t bfp_noalloc_window_capacity(void);

@@ -15,8 +15,6 @@
 // overlap on the GPU (different streams without ordering) race on it.  The
 // window never needs clearing: the first pass writes every entry the second
 // pass reads.
-#include <mutex>
-
 #include "bfp_host.h"
 
 using namespace bfp;
@@ -27,23 +25,18 @@ constexpr int64_t kWindowMax = int64_t(1) << 22;   // int32 entries (rows * ld o
 
 __device__ __align__(256) int32_t g_window[kWindowMax];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_window_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_window on the current device (looked up once per device;
-// the host-side symbol g_window is not a device address and must not be passed
-// to a kernel).
+// Device address of g_window on the current device.  The host-side symbol g_window is not a
+// device address and must not be passed to a kernel.  The address is looked up on every call,
+// so it stays right after a device reset or a new primary context in the same process; a failed
+// lookup clears the runtime's last-error state so that it is not reported by a later, unrelated
+// launch check.
 int32_t window_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BFP_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_window_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_window) != cudaSuccess || p == nullptr) return BFP_ERR_CUDA;
-    g_window_addr[dev] = p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_window) != cudaSuccess || p == nullptr) {
+    (void)cudaGetLastError();
+    return BFP_ERR_CUDA;
   }
-  *out = g_window_addr[dev];
+  *out = p;
   return BFP_OK;
 }
 
@@ -58,10 +51,13 @@ int32_t bfp_jacobi_noalloc(const bfp_stencil* A, const bfp_vec* y, const bfp_vec
   int32_t rc;
   if (!q || !y_out) return BFP_ERR_ARG;
   if ((rc = check_vec(y_out))) return rc;
-  if (rows_of(y_out) * y_out->ld > kWindowMax) return BFP_ERR_CAPACITY;
   bfp_q qq = *q;
   qq.tmp = nullptr;
-  if (q->mode == BFP_QCOMP) {
+  // the window is used by qcomp when w_tmp = w_out + w_add fits in 32 bits (the relaxation row's
+  // w_add 2 unless the caller gives one); nnqcomp, and qcomp with a wider w_tmp, need no scratch
+  const int w_add = q->w_add < 0 ? capped_wadd(2, wadd_cap()) : q->w_add;
+  if (q->mode == BFP_QCOMP && q->w_out + w_add <= 32) {
+    if (rows_of(y_out) * y_out->ld > kWindowMax) return BFP_ERR_CAPACITY;
     void* w = nullptr;
     if ((rc = window_address(&w))) return rc;
     qq.tmp = w;

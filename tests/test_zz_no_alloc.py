@@ -6,7 +6,7 @@ callback, under a memory budget owned by another framework, or where an implicit
 device synchronisation is not acceptable) use this entry point.  This file is
 collected last so that a run stopping at the first failure has run every other
 test before it; it also passes on its own in a fresh process, where the first
-call performs the per-device lookup of the static array.
+call performs the first lookup of the static array on the device.
 """
 import numpy as np
 import pytest
@@ -30,8 +30,14 @@ def _same(a, b):
     assert np.array_equal(a.padding(), b.padding())
 
 
+# (mode, w_add): qcomp with the window (w_tmp = w + 2 <= 32), qcomp whose w_tmp passes 32 bits (no
+# window: the second pass recomputes), nnqcomp (no scratch at all)
+MODES = [(bfp.QCOMP, -1), (bfp.QCOMP, 17), (bfp.NNQCOMP, -1)]
+
+
+@pytest.mark.parametrize("mode,w_add", MODES)
 @pytest.mark.parametrize("shape,w", [((1023, 1001), 16), ((63, 64), 24), ((9, 17, 31), 16)])
-def test_noalloc_matches_allocating_entry_point_twice(shape, w):
+def test_noalloc_matches_allocating_entry_point_twice(shape, w, mode, w_add):
     nd = len(shape)
     A = bfp.bfp_laplace_stencil(nd, 0.8 if nd == 2 else 6 / 7)
     for call in range(2):          # two calls in a row share (and overwrite) the static window
@@ -44,20 +50,26 @@ def test_noalloc_matches_allocating_entry_point_twice(shape, w):
         st_ref = torch.zeros(8, dtype=torch.int64, device="cuda")
         st_out = torch.zeros(8, dtype=torch.int64, device="cuda")
         for zero_guess in (False, True):
-            bfp.bfp_jacobi(A, None if zero_guess else y, r, ref, bfp.q(w, bfp.QCOMP, tmp=tmp), st_ref)
-            bfp.bfp_jacobi_noalloc(A, None if zero_guess else y, r, out, bfp.q(w, bfp.QCOMP), st_out)
+            bfp.bfp_jacobi(A, None if zero_guess else y, r, ref, bfp.q(w, mode, w_add=w_add, tmp=tmp), st_ref)
+            bfp.bfp_jacobi_noalloc(A, None if zero_guess else y, r, out, bfp.q(w, mode, w_add=w_add), st_out)
             _same(out, ref)
         assert torch.equal(st_ref, st_out)
 
 
-def test_noalloc_rejects_sizes_beyond_capacity():
+def test_noalloc_capacity_applies_to_the_window_only():
     cap = bfp.bfp_noalloc_window_capacity()
     assert cap == 1 << 22
     n = 2049                                   # 2049 rows x 2056 ld > 2^22
     A = bfp.bfp_laplace_stencil(2, 0.8)
-    y = bfp.BFPVector((n, n), 16)
-    r = bfp.BFPVector((n, n), 16)
+    y = _vec(random_mantissas((n, n), 16, 7), -12, 16)
+    r = _vec(random_mantissas((n, n), 16, 8, "smooth"), -10, 16)
     out = bfp.BFPVector((n, n), 16)
-    with pytest.raises(bfp.BFPError) as ei:
+    with pytest.raises(bfp.BFPError) as ei:    # qcomp with the window: refused, nothing launched
         bfp.bfp_jacobi_noalloc(A, y, r, out, bfp.q(16, bfp.QCOMP))
     assert ei.value.status == -8
+    for mode, w_add in ((bfp.NNQCOMP, -1), (bfp.QCOMP, 17)):   # no window: any size
+        ref = bfp.BFPVector((n, n), 16)
+        tmp = torch.zeros((ref.rows, ref.ld), dtype=torch.int32, device="cuda")
+        bfp.bfp_jacobi(A, y, r, ref, bfp.q(16, mode, w_add=w_add, tmp=tmp))
+        bfp.bfp_jacobi_noalloc(A, y, r, out, bfp.q(16, mode, w_add=w_add))
+        _same(out, ref)
