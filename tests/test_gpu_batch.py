@@ -96,3 +96,30 @@ def test_batch_with_chebyshev_and_progressive_instances():
         assert torch.equal(xs[i], xr), i
         h.close()
     b.close()
+
+
+def test_batch_instances_equal_the_oracle():
+    """Every instance of one batched launch (mixed sides, widths, modes, strip rows and first on-chip
+    levels) equals the oracle's FMG + K IR-V steps for that instance, bit for bit."""
+    from oracle import mg as M
+    spec = [(255, 16, bfp.NNQCOMP, 8, 127), (127, 16, bfp.QCOMP, 4, 31), (63, 8, bfp.NNQCOMP, 2, 0),
+            (31, 16, bfp.QCOMP, 0, 63), (127, 12, bfp.NNQCOMP, 2, 15), (63, 24, bfp.QCOMP, 0, 15)]
+    olist = [opts(*sp) for sp in spec]
+    ks = [2, 1, 3, 2, 1, 0]
+    fh = [smoothed_random_rhs(sp[0], 300 + i) for i, sp in enumerate(spec)]
+    fs = [torch.from_numpy(f).cuda() for f in fh]
+    xs = [torch.zeros_like(f) for f in fs]
+    stream = torch.cuda.Stream()
+    b = bfp.Batch(olist)
+    with torch.cuda.stream(stream):
+        b.solve(fs, xs, ks, fmg=True)
+    stream.synchronize()
+    for i, (sp, o, k) in enumerate(zip(spec, olist, ks)):
+        s = M.BFPSolver(2, sp[0], w=sp[1], mode="qcomp" if sp[2] == bfp.QCOMP else "nnqcomp",
+                        omega=o.omega, w_omega=o.w_omega)
+        xr = s.fmg(fh[i])
+        bb = s.rhs_hierarchy(fh[i])[0]
+        for _ in range(k):
+            xr = s.ir_step(0, bb, xr)
+        assert np.array_equal(xs[i].cpu().numpy(), xr), i
+    b.close()

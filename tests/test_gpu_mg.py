@@ -20,8 +20,16 @@ def make(nd, n, w, mode, use_tmp=1, use_graph=1, coarse_onchip=1, w_step=0):
     o.w_step = w_step
     h = bfp.Hierarchy(o)
     s = mg.BFPSolver(nd, n, w=w, mode="qcomp" if mode == bfp.QCOMP else "nnqcomp",
-                     omega=o.omega, w_omega=o.w_omega, w_step=w_step)
+                     omega=o.omega, w_omega=o.w_omega, w_step=w_step, ir_window=bool(use_tmp))
     return h, s
+
+
+def ir_counters_match(h, s):
+    """The IR residual counters (quantisations, recomputations) equal the oracle's window model,
+    over all levels and on the finest level."""
+    st, fin = h.stats(), h.finest_stats()
+    assert (st["ir_residuals"], st["ir_recomputed"]) == s.ir_totals()
+    assert (fin["ir_residuals"], fin["ir_recomputed"]) == s.ir_totals(finest_only=True)
 
 
 @pytest.mark.parametrize("nd,n", [(2, 63), (2, 31), (2, 255), (3, 15)])
@@ -64,6 +72,7 @@ def test_fmg_and_ir_bit_exact(nd, n, w, mode):
         stream.synchronize()
         xr = s.ir_step(0, b, xr)
         assert np.array_equal(xt.cpu().numpy(), xr), it
+    ir_counters_match(h, s)
     if nd == 2 and w >= 16:
         assert mg.accuracy_ratio(nd, xt.cpu().numpy()) <= 1.5
 
@@ -114,7 +123,7 @@ def test_ir_residual_window_and_padding(nd, n):
         xt = torch.from_numpy(x).cuda()
         r.mant.fill_(-5)
         h.ir_residual(ft, xt, r)
-        ref = B.from_f64(mg.residual_f64(b, x), 16)
+        ref = s.ir_quantize(0, mg.residual_f64(b, x))
         torch.cuda.synchronize()
         assert r.exponent == ref.e
         assert np.array_equal(r.mantissas(), ref.m)
@@ -123,6 +132,7 @@ def test_ir_residual_window_and_padding(nd, n):
     st = h.stats()
     assert st["ir_residuals"] == 4
     assert st["ir_recomputed"] == 2       # the first call (no gamma yet) and the overflowing one
+    ir_counters_match(h, s)
 
 
 @pytest.mark.parametrize("nd,n,w,onchip,step", [(2, 63, 16, 63, 1), (2, 63, 16, 0, 1), (2, 127, 12, 63, 1),
@@ -242,3 +252,45 @@ def test_ir_solve_stall_fallback_matches_oracle(w):
     xt.zero_()
     rep = h.ir_solve(ft, xt, max_iter=steps, tol=0.0, fmg_start=False)
     assert rep.fallback_at == -1
+
+
+@pytest.mark.parametrize("mode", [bfp.NNQCOMP, bfp.QCOMP])
+def test_benchmarked_ir_steps_4095(mode):
+    """The benchmarked workload itself (2D Poisson 4095^2, w = 16, the library's default schedule:
+    graph-replayed IR-V(2,2) steps, on-chip coarse cycle from 63 down): two IR-V steps from x = 0
+    equal the oracle's FP64 iterate bit for bit (FP64 residual and update, every level's ops, the
+    4095 -> 2047 transfers); the next IR residual on its own (the full 4095^2 grid, window from the
+    previous residual) equals the oracle's quantisation; the V-cycle and IR counters equal the
+    oracle's."""
+    n = 4095
+    o = bfp.bfp_solver_opts_default(2, n, 16)
+    o.mode = mode
+    h = bfp.Hierarchy(o)
+    s = mg.BFPSolver(2, n, w=16, mode="qcomp" if mode == bfp.QCOMP else "nnqcomp", omega=o.omega,
+                     w_omega=o.w_omega)
+    f = manufactured_rhs(2, n)
+    b = s.rhs_hierarchy(f)[0]
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    stream = torch.cuda.Stream()
+    xr = np.zeros_like(f)
+    for it in range(2):
+        with torch.cuda.stream(stream):
+            h.ir_iterate(ft, xt, 1)
+        stream.synchronize()
+        xr = s.ir_step(0, b, xr)
+        assert np.array_equal(xt.cpu().numpy(), xr), it
+    st = h.stats()
+    assert (st["calls"], st["recomputed"], st["saturated"]) == (s.stats.calls, s.stats.recomputed,
+                                                                 s.stats.saturated)
+    ir_counters_match(h, s)
+    r = bfp.BFPVector((n, n), 16)
+    r.mant.fill_(-5)
+    h.ir_residual(ft, xt, r)
+    ref = s.ir_quantize(0, mg.residual_f64(b, xr))
+    torch.cuda.synchronize()
+    assert r.exponent == ref.e
+    assert np.array_equal(r.mantissas(), ref.m)
+    assert np.all(r.padding() == 0)
+    ir_counters_match(h, s)
+    h.close()
