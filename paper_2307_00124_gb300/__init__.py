@@ -103,6 +103,7 @@ _sig = {
     "bfp_normalize": (C.c_int32, [P(bfp_vec), P(bfp_vec), P(bfp_q), P(bfp_stats), C.c_void_p]),
     "bfp_from_f64": (C.c_int32, [C.c_void_p, P(bfp_vec), C.c_void_p]),
     "bfp_to_f64": (C.c_int32, [P(bfp_vec), C.c_void_p, C.c_void_p]),
+    "bfp_block_norm": (C.c_int32, [P(bfp_vec), C.c_void_p]),
     "bfp_axpy": (C.c_int32, [bfp_scalar, P(bfp_vec), bfp_scalar, P(bfp_vec), P(bfp_vec), P(bfp_q),
                              P(bfp_stats), C.c_void_p]),
     "bfp_dot": (C.c_int32, [P(bfp_vec), P(bfp_vec), C.c_int32, C.c_void_p, C.c_void_p]),
@@ -230,8 +231,8 @@ class BFPVector:
         v.mant.copy_(torch.from_numpy(host))
         meta = np.zeros(META_WORDS, dtype=np.int64)
         meta[0] = e
-        meta[1] = int(np.abs(m).max()) if m.size else 0
         v.meta.copy_(torch.from_numpy(meta))
+        bfp_block_norm(v)                       # the norm word, by the library
         return v
 
     def mantissas(self) -> np.ndarray:
@@ -362,6 +363,10 @@ def bfp_from_f64(x, out, stream=None):
 def bfp_to_f64(x, out, stream=None):
     assert out.is_cuda and out.is_contiguous()
     _check(_lib.bfp_to_f64(C.byref(x.struct()), C.c_void_p(out.data_ptr()), _stream(stream)), "bfp_to_f64")
+
+
+def bfp_block_norm(x, stream=None):
+    _check(_lib.bfp_block_norm(C.byref(x.struct()), _stream(stream)), "bfp_block_norm")
 
 
 def bfp_axpy(a, x, b, y, z, qq, stats=None, stream=None):

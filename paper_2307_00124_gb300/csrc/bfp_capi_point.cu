@@ -154,6 +154,23 @@ __global__ void k_dot_finish(const int64_t* mx, const int64_t* my, int64_t* out,
   out[1] = e_star + lam;
 }
 
+// ---- max |m| of a block (the norm word of its meta) -------------------------------
+
+template <class T>
+__global__ void __launch_bounds__(256) k_block_norm(const VIn x, int64_t* meta) {
+  const int64_t rows = x.ny * x.nz, total = rows * x.nx;
+  const T* m = reinterpret_cast<const T*>(x.m);
+  long long mx = 0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / x.nx, c = idx - row * x.nx;
+    const long long v = (long long)m[row * x.ld + c];
+    mx = max(mx, v < 0 ? -v : v);
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax((long long*)&meta[1], mx);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -312,6 +329,21 @@ int32_t bfp_dot(const bfp_vec* x, const bfp_vec* y, int32_t w_out, int64_t* out,
   else k_dot<int16_t><<<g, 256, 0, s>>>(vin(x), vin(y), out);
   k_dot_finish<<<1, 1, 0, s>>>(x->meta, y->meta, out, w_out);
   note_launches(2);
+  return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_block_norm(const bfp_vec* x, bfp_stream stream) {
+  int32_t rc;
+  if ((rc = check_vec_wide(x))) return rc;
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(x->meta + 1, 0, sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
+  const int64_t total = rows_of(x) * x->n[0];
+  if (total == 0) return BFP_OK;
+  unsigned g = grid_for(total, 256);
+  if (is64(x)) k_block_norm<long long><<<g, 256, 0, s>>>(vin(x), x->meta);
+  else if (is32(x)) k_block_norm<int32_t><<<g, 256, 0, s>>>(vin(x), x->meta);
+  else k_block_norm<int16_t><<<g, 256, 0, s>>>(vin(x), x->meta);
+  note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
