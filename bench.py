@@ -24,9 +24,48 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "BFP V-cycle GDOF/s (IR-V steps, 2D Poisson 4095^2, w=16)"
-JACOBI_TRAFFIC = 93095168   # dram__bytes_read.sum + dram__bytes_write.sum of one k_star16<2, 0, 2> launch at 4095^2 (ncu)
 UNIT = "GDOF/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed Jacobi kernel version at 4095^2
+# from one ncu capture (None until this kernel version has been captured)
+JACOBI_TRAFFIC = None
+
+
+def metric_name(nd, n, w):
+    """The metric as run: BFP V-cycle GDOF/s of IR-V steps on the configured grid and width."""
+    grid = ("%d^2" % n) if nd == 2 else ("%d^3" % n)
+    return "BFP V-cycle GDOF/s (IR-V steps, %dD Poisson %s, w=%d)" % (nd, grid, w)
+
+
+def levels_of(n):
+    out = []
+    while n >= 3:
+        out.append(n)
+        n = (n - 1) // 2
+    return out
+
+
+# Algorithmic bytes per DOF of each op on int16 mantissas (each operand read once, each result
+# written once; FP64 x, f are 8 bytes): the V(2,2) schedule of one level is the zero-guess sweep
+# (r in, y out), a sweep (y, r in, y out), the residual (y, r in, r_v out), the restriction (fine r_v
+# in, coarse out: 2 + 2/2^d), the correction (coarse d in, y in, y out) and two sweeps.
+OP_BYTES = {"jacobi0": 4.0, "jacobi": 6.0, "residual": 6.0, "ir_residual": 18.0, "ir_update": 18.0}
+
+
+def step_bytes(nd, n, mb=2):
+    """Algorithmic bytes of one IR-V(2,2) step: every level's V(2,2) ops plus the FP64 IR residual
+    (x, f in; BFP r out) and update (x, y in; x out)."""
+    total = 0.0
+    for m in levels_of(n):
+        dof = m ** nd
+        cdof = ((m - 1) // 2) ** nd
+        lvl = (2 * mb) + 3 * (3 * mb) + (3 * mb)            # zero-guess, three sweeps, residual
+        lvl_dof = lvl * dof
+        lvl_dof += mb * dof + mb * cdof                      # restriction
+        lvl_dof += mb * cdof + 2 * mb * dof                  # correction
+        total += lvl_dof
+    dof = n ** nd
+    total += (16 + mb) * dof + (16 + mb) * dof
+    return total
 
 
 def parse():
@@ -140,71 +179,104 @@ def replica_value(ws, units_per_rank, steps, t):
     return ws * units_per_rank * steps / t / 1e9
 
 
-def cpu_oracle_step(n, w, mode, nd=2):
-    """Time one oracle IR-V step on an n^2 grid (numpy, exact integers)."""
-    import numpy as np
-    from bfp_inputs import manufactured_rhs
-    from oracle import mg
-    f = manufactured_rhs(nd, n)
-    s = mg.BFPSolver(nd, n, w=w, mode=mode)
-    b = s.rhs_hierarchy(f)[0]
-    x = np.zeros_like(b)
-    t0 = time.perf_counter()
-    s.ir_step(0, b, x)
-    return time.perf_counter() - t0
+class OracleRun:
+    """The CPU oracle (oracle/mg.py, numpy exact integers and FP64) stepping the same workload: IR-V
+    steps from x = 0, continuing from the previous iterate like the GPU run."""
+
+    def __init__(self, n, w, mode, nd=2):
+        from bfp_inputs import manufactured_rhs
+        from oracle import mg
+        import numpy as np
+        self.s = mg.BFPSolver(nd, n, w=w, mode=mode)
+        self.b = self.s.rhs_hierarchy(manufactured_rhs(nd, n))[0]
+        self.x = np.zeros_like(self.b)
+
+    def step(self):
+        """One IR-V step; returns (wall seconds, process CPU seconds)."""
+        w0, c0 = time.perf_counter(), time.process_time()
+        self.x = self.s.ir_step(0, self.b, self.x)
+        return time.perf_counter() - w0, time.process_time() - c0
 
 
-def cpu_threads():
-    try:
-        import numpy as np  # noqa: F401
-        return 1   # the oracle is plain numpy on one core (no threaded BLAS on this path)
-    except Exception:
-        return 1
+def cores_used(wall, cpu):
+    """Host cores the timed oracle kept busy: process CPU time over wall time (numpy's elementwise
+    kernels run on one thread; no threaded BLAS is on this path)."""
+    return max(1, int(round(cpu / wall))) if wall > 0 else 1
 
 
 def run_reference(args):
     ws, rank, _ = dist_init(args)
     if rank != 0:
         return
-    # the oracle on the host cores: each step is one IR-V step on a bounded sample
-    # of the workload (a 1023^2 grid of the same problem; GDOF/s is per fine DOF)
-    n = 1023
-    times = []
+    # the oracle on the host cores, on the same workload as the GPU arm: each step is one IR-V step
+    # of the 4095^2 (or --n) problem
+    n = args.n
+    o = OracleRun(n, args.w, args.mode)
+    wall, cpu = 0.0, 0.0
     for i in range(args.warmup + args.steps):
-        t = cpu_oracle_step(n, args.w, args.mode)
+        tw, tc = o.step()
         if i >= args.warmup:
-            times.append(t)
-    tot = sum(times)
+            wall += tw
+            cpu += tc
     dof = n * n
-    value = dof * len(times) / tot / 1e9
+    value = dof * args.steps / wall / 1e9
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "impl": "reference", "metric": metric_name(2, n, args.w), "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16+f64",
-        "data": "synthetic", "config": {"workload": "2D Poisson 5-point, IR-V(2,2) damped Jacobi, w=%d, %s" % (
-            args.w, args.mode), "sample": "%dx%d grid per step" % (n, n)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": "one IR-V step on a %d^2 grid per step" % n},
+        "data": "synthetic", "config": {"workload": "2D Poisson 5-point, %dx%d interior, FP64 IR with BFP V(2,2) "
+                                                    "damped Jacobi omega=4/5, w=%d, %s" % (n, n, args.w, args.mode),
+                                        "sample": "the full %d^2 grid: one oracle IR-V step per step" % n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(wall, cpu), "kind": "oracle",
+                         "sample": "%d IR-V steps of the %d^2 workload after %d untimed" % (args.steps, n,
+                                                                                           args.warmup)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def accuracy_ratio_gpu(torch, x, n):
-    """||u - x||_L / ||u - u_h||_L in the discrete energy norm (e^T A_h e)^(1/2), u = sin(pi x) sin(pi y)
-    and u_h its closed-form discrete solution (measurement only, outside every timed region)."""
+def _energy_gpu(torch, e):
+    """e^T A_h e / h^(d-2)-free form: sum over points of e (2d e - sum of neighbours), zero boundary
+    (the discrete energy norm squared up to the common factor h^(d-2))."""
+    nd = e.dim()
+    p = torch.nn.functional.pad(e, (1, 1) * nd)
+    inner = tuple(slice(1, -1) for _ in range(nd))
+    ae = (2.0 * nd) * e
+    for ax in range(nd):
+        for d in (-1, 1):
+            sl = list(inner)
+            sl[ax] = slice(1 + d, p.shape[ax] - 1 + d)
+            ae = ae - p[tuple(sl)]
+    return float((e * ae).sum())
+
+
+def discrete_solution_gpu(torch, nd, n, device):
+    """u = prod sin(pi x_i) and the closed-form discrete solution u_h = (d pi^2 / lambda_h) u
+    (u is an eigenvector of A_h, lambda_h = 4 d sin^2(pi h / 2) / h^2)."""
     import math
     h = 1.0 / (n + 1)
-    s = torch.sin(math.pi * torch.arange(1, n + 1, dtype=torch.float64, device=x.device) * h)
-    u = torch.outer(s, s)
-    lam = 8.0 * math.sin(math.pi * h / 2) ** 2 / h ** 2
-    uh = (2.0 * math.pi ** 2 / lam) * u
+    s = torch.sin(math.pi * torch.arange(1, n + 1, dtype=torch.float64, device=device) * h)
+    u = s
+    for _ in range(nd - 1):
+        u = u.unsqueeze(0) * s.reshape((n,) + (1,) * u.dim())
+    lam = 4.0 * nd * math.sin(math.pi * h / 2) ** 2 / h ** 2
+    return u, (nd * math.pi ** 2 / lam) * u
 
-    def energy(e):
-        p = torch.nn.functional.pad(e, (1, 1, 1, 1))
-        ae = 4.0 * e - p[1:-1, :-2] - p[1:-1, 2:] - p[:-2, 1:-1] - p[2:, 1:-1]
-        return float((e * ae).sum()) / h ** 2
-    return math.sqrt(energy(u - x) / energy(u - uh))
+
+def accuracy_ratio_gpu(torch, x, n):
+    """||u - x||_L / ||u - u_h||_L in the discrete energy norm (e^T A_h e)^(1/2), u = prod sin(pi x_i)
+    and u_h its closed-form discrete solution (measurement only, outside every timed region)."""
+    import math
+    u, uh = discrete_solution_gpu(torch, x.dim(), n, x.device)
+    return math.sqrt(_energy_gpu(torch, u - x) / _energy_gpu(torch, u - uh))
+
+
+def error_vs_discrete(torch, x, n):
+    """||x - u_h||_A / ||u_h||_A: the solver's error against the exact discrete solution (the
+    solution an FP64 multigrid converges to), relative, in the energy norm."""
+    import math
+    _, uh = discrete_solution_gpu(torch, x.dim(), n, x.device)
+    return math.sqrt(_energy_gpu(torch, x - uh) / _energy_gpu(torch, uh))
 
 
 def var_compare(bfp, torch, stream, n=2047, steps=10):
@@ -456,6 +528,53 @@ def recompute_table(bfp, torch, args, f, stream):
     return rows
 
 
+def c1_time_to_accuracy(bfp, torch, stream, w=16, n=63):
+    """The small 2D configuration (63^2, w = 16, V(2,2), 5 levels): FMG + K IR-V steps, K the smallest
+    with accuracy ratio <= 1.5, timed on the GPU (one graph per IR step; best of 20) and by the CPU
+    oracle (same schedule, same result bit for bit; one host thread)."""
+    import numpy as np
+    from bfp_inputs import manufactured_rhs
+    from oracle import mg
+    fh = manufactured_rhs(2, n)
+    f = torch.from_numpy(fh).cuda()
+    o = bfp.bfp_solver_opts_default(2, n, w)
+    h = bfp.Hierarchy(o)
+    x = torch.zeros_like(f)
+    with torch.cuda.stream(stream):
+        h.fmg(f, x)
+    stream.synchronize()
+    k, ratio = 0, accuracy_ratio_gpu(torch, x, n)
+    while ratio > 1.5 and k < 20:
+        with torch.cuda.stream(stream):
+            h.ir_iterate(f, x, 1)
+        stream.synchronize()
+        k += 1
+        ratio = accuracy_ratio_gpu(torch, x, n)
+    times = []
+    for _ in range(20):
+        x.zero_()
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.fmg(f, x)
+            if k:
+                h.ir_iterate(f, x, k)
+            b.record(stream)
+        stream.synchronize()
+        times.append(a.elapsed_time(b))
+    h.close()
+    s = mg.BFPSolver(2, n, w=w, mode="nnqcomp", omega=o.omega, w_omega=o.w_omega)
+    t0 = time.perf_counter()
+    xr = s.fmg(fh)
+    bb = s.rhs_hierarchy(fh)[0]
+    for _ in range(k):
+        xr = s.ir_step(0, bb, xr)
+    t_cpu = time.perf_counter() - t0
+    return {"workload": "2D Poisson 63^2, w=%d, nnqcomp, V(2,2), 5 levels" % w, "ir_steps_after_fmg": k,
+            "accuracy_ratio": ratio, "gpu_ms": min(times), "oracle_ms": 1e3 * t_cpu, "oracle_cores": 1,
+            "bit_exact_with_oracle": bool(np.array_equal(x.cpu().numpy(), xr))}
+
+
 def solver_compare(bfp, torch, args, f, stream, hbfp):
     """Float baselines beside the BFP solver on the same workload: GDOF/s of IR-V steps, and time to
     discretisation accuracy (FMG + K IR-V steps, K the smallest with accuracy ratio <= 1.5)."""
@@ -484,10 +603,6 @@ def solver_compare(bfp, torch, args, f, stream, hbfp):
             stream.synchronize()
             t = a.elapsed_time(b) / 1e3
             out[name] = {"value": dof * args.steps / t / 1e9, "unit": "GDOF/s", "ms_per_step": 1e3 * t / args.steps}
-        if nd == 3:              # the accuracy ratio below is the 2D energy norm
-            if h is not hbfp:
-                h.close()
-            continue
         # K: IR-V steps after FMG until the accuracy ratio is <= 1.5 (at most 20; 40 for V(1,0))
         x.zero_()
         with torch.cuda.stream(stream):
@@ -513,10 +628,63 @@ def solver_compare(bfp, torch, args, f, stream, hbfp):
             stream.synchronize()
             times.append(a.elapsed_time(b))
         tta[name] = {"ms": min(times), "ir_steps_after_fmg": k, "accuracy_ratio": ratio,
-                     "reached": bool(ratio <= 1.5)}
+                     "reached": bool(ratio <= 1.5), "error_vs_discrete_solution": error_vs_discrete(torch, x, n)}
         if h is not hbfp:
             h.close()
     return out, tta
+
+
+def e2e_run(bfp, torch, o, h, f_host, stream, ws, dof, k2):
+    """IR-V steps of two independent problems, alternating, through the public API with pinned host
+    buffers: every step copies its f and x to the device, runs one IR-V step and copies x back.  Each
+    problem has its own hierarchy and stream, so one problem's copies overlap the other's step (both
+    directions of the host link in use).  Also the link's own copy rate, one direction at a time."""
+    h2 = bfp.Hierarchy(o)
+    hs = [h, h2]
+    streams = [stream, torch.cuda.Stream()]
+    fh = [torch.from_numpy(f_host).pin_memory(), torch.from_numpy(f_host * 0.5).pin_memory()]
+    xh = [torch.zeros_like(fh[0]).pin_memory(), torch.zeros_like(fh[0]).pin_memory()]
+    fd = [torch.empty(f_host.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    xd = [torch.empty_like(fd[0]) for _ in range(2)]
+
+    def step(i):
+        p, st = i % 2, streams[i % 2]
+        with torch.cuda.stream(st):
+            fd[p].copy_(fh[p], non_blocking=True)
+            xd[p].copy_(xh[p], non_blocking=True)
+            hs[p].ir_iterate(fd[p], xd[p], 1)
+            xh[p].copy_(xd[p], non_blocking=True)
+
+    for i in range(4):                    # warm-up (the second hierarchy captures its graph)
+        step(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(streams[0])
+    streams[1].wait_event(a)
+    for i in range(k2):
+        step(i)
+    streams[0].wait_stream(streams[1])
+    b.record(streams[0])
+    torch.cuda.synchronize()
+    te = a.elapsed_time(b) / 1e3
+
+    def copy_rate(dst, src):
+        with torch.cuda.stream(stream):
+            dst.copy_(src, non_blocking=True)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            c1.record(stream)
+        stream.synchronize()
+        return 3 * src.numel() * src.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
+
+    link = {"h2d_GBps": copy_rate(fd[0], fh[0]), "d2h_GBps": copy_rate(xh[0], xd[0])}
+    h2.close()
+    return {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
+            "d2h_bytes_per_step": 8 * dof, "ms_per_step": 1e3 * te / k2, "steps": k2,
+            "schedule": "two independent problems alternating on two streams (copies of one overlap the "
+                        "other's IR-V step)", "link": link}
 
 
 def run_ours(args):
@@ -577,109 +745,105 @@ def run_ours(args):
     t = max_over_ranks(t, "cuda")
     value = replica_value(ws, dof, args.steps, t)
 
-    h_levels = []
-    m = n
-    while m >= 3:
-        h_levels.append(m)
-        m = (m - 1) // 2
-    # roofline: the dominant kernels timed alone with CUDA events on their stream
+    h_levels = levels_of(n)
+    # roofline: the finest-level kernels timed alone with CUDA events on their stream; each op rotates
+    # over three buffer sets so that its inputs are not in L2 when it runs (3 x 100 MB at 4095^2)
     hbm, peak_kind = peaks()
     A = bfp.bfp_laplace_stencil(nd, o.omega, o.w_omega)
     rng = np.random.default_rng(0)
     ym = rng.integers(-(1 << 12), 1 << 12, size=(n,) * nd)
-    y = bfp.BFPVector.from_mantissas(ym, -20, w)
-    r = bfp.BFPVector.from_mantissas(ym[::-1].copy(), -19, w)
-    yo = bfp.BFPVector((n,) * nd, w)
+    nsets = 3 if nd == 2 else 1                 # a 3D vector alone exceeds L2
+    sets = []
+    for i in range(nsets):
+        sets.append((bfp.BFPVector.from_mantissas(np.roll(ym, i), -20, w),
+                     bfp.BFPVector.from_mantissas(np.roll(ym[::-1], i).copy(), -19, w),
+                     bfp.BFPVector((n,) * nd, w)))
     q = bfp.q(w, mode)
     reps = 30
     kern = {}
 
-    def timeit(fn):
+    def timeit(fn, bufs=None):
+        bufs = sets if bufs is None else bufs
         with torch.cuda.stream(stream):
-            for _ in range(3):
-                fn()
+            for i in range(3):
+                fn(bufs[i % nsets])
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            for _ in range(reps):
-                fn()
+            for i in range(reps):
+                fn(bufs[i % nsets])
             b.record(stream)
         stream.synchronize()
         return a.elapsed_time(b) / 1e3 / reps
 
     mb = 2 if w <= 16 else 4
-    kern["jacobi"] = (timeit(lambda: bfp.bfp_jacobi(A, y, r, yo, q, stream=stream)), 3 * mb * dof)
-    kern["residual"] = (timeit(lambda: bfp.bfp_residual(A, y, r, yo, q, stream=stream)), 3 * mb * dof)
-    kern["ir_residual"] = (timeit(lambda: h.ir_residual(f, x, yo, stream=stream)), 2 * 16 * dof + mb * dof)
-    kern["ir_update"] = (timeit(lambda: bfp.bfp_ir_update(x, y, stream=stream)), (16 + mb) * dof)
+    scale = mb / 2.0
+    kern["jacobi"] = (timeit(lambda v: bfp.bfp_jacobi(A, v[0], v[1], v[2], q, stream=stream)),
+                      OP_BYTES["jacobi"] * scale * dof)
+    kern["jacobi0"] = (timeit(lambda v: bfp.bfp_jacobi(A, None, v[1], v[2], q, stream=stream)),
+                       OP_BYTES["jacobi0"] * scale * dof)
+    kern["residual"] = (timeit(lambda v: bfp.bfp_residual(A, v[0], v[1], v[2], q, stream=stream)),
+                        OP_BYTES["residual"] * scale * dof)
+    kern["ir_residual"] = (timeit(lambda v: h.ir_residual(f, x, v[2], stream=stream)), (16 + mb) * dof)
+    kern["ir_update"] = (timeit(lambda v: bfp.bfp_ir_update(x, v[0], stream=stream)), (16 + mb) * dof)
+    # context for the sweep's fraction: torch's elementwise int16 add over arrays of the sweep's shape
+    # moves the same bytes (two reads, one write) with no stencil, timed the same way
+    tsets = [tuple(torch.randint(-4096, 4096, (n, sets[0][2].ld), dtype=torch.int16, device="cuda")
+                   for _ in range(3)) for _ in range(nsets)] if nd == 2 else None
+    t_add = timeit(lambda v: torch.add(v[0], v[1], out=v[2]), tsets) if nd == 2 else None
+    sets_ld = sets[0][2].ld
+    del sets, tsets
     kern_out = {k: {"ms": 1e3 * v[0], "algorithmic_bytes": v[1], "GBps": v[1] / v[0] / 1e9,
                     "frac": v[1] / v[0] / 1e9 / hbm} for k, v in kern.items()}
     # the dominant kernel by share of the step's device time (ncu launch list): the finest-level
     # damped-Jacobi sweep; traffic = dram bytes read + written per launch from one ncu capture of
-    # this kernel version (profiles/jacobi_4095.txt), None when not captured
+    # this kernel version, None when not captured
     dom = "jacobi"
+    sb = step_bytes(nd, n, mb)
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern_out[dom]["GBps"], "peak": hbm, "unit": "GB/s",
             "frac": kern_out[dom]["GBps"] / hbm, "peak_kind": peak_kind,
-            "traffic": JACOBI_TRAFFIC if (nd, n, w) == (2, 4095, 16) else None}
+            "traffic": JACOBI_TRAFFIC if (nd, n, w) == (2, 4095, 16) else None,
+            "timing": "CUDA events over %d launches alone on the op's stream, inputs rotated over %d buffer "
+                      "sets (larger than L2)" % (reps, nsets),
+            "context": None if t_add is None else {
+                "what": "torch int16 add (two reads, one write) of arrays of the sweep's shape, timed the same way",
+                "GBps": 3 * 2 * n * sets_ld / t_add / 1e9, "frac": 3 * 2 * n * sets_ld / t_add / 1e9 / hbm},
+            "step": {"algorithmic_bytes": sb, "ms": 1e3 * t / args.steps,
+                     "achieved": sb / (t / args.steps) / 1e9, "frac": sb / (t / args.steps) / 1e9 / hbm}}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        fh = torch.from_numpy(f_host).pin_memory()
-        xh = torch.zeros_like(fh).pin_memory()
-        xd = torch.empty_like(f)
-        fd = torch.empty_like(f)
-        k2 = max(3, args.steps // 2)
-        # every step copies f and x in and x out; f's copy runs on a second stream while the
-        # previous step's x goes back to the host (the two directions of the link overlap)
-        cstream = torch.cuda.Stream()
-        f_free = torch.cuda.Event()
-        f_free.record(stream)
-        for i in range(2 + k2):
-            if i == 2:
-                a = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                cstream.wait_event(a)
-            f_ready = torch.cuda.Event()
-            with torch.cuda.stream(cstream):
-                cstream.wait_event(f_free)
-                fd.copy_(fh, non_blocking=True)
-                f_ready.record(cstream)
-            with torch.cuda.stream(stream):
-                xd.copy_(xh, non_blocking=True)
-                stream.wait_event(f_ready)
-                h.ir_iterate(fd, xd, 1)
-                f_free = torch.cuda.Event()
-                f_free.record(stream)
-                xh.copy_(xd, non_blocking=True)
-        with torch.cuda.stream(stream):
-            stream.wait_stream(cstream)
-            b = torch.cuda.Event(enable_timing=True)
-            b.record(stream)
-        stream.synchronize()
-        te = a.elapsed_time(b) / 1e3
-        e2e = {"value": ws * dof * k2 / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
-               "d2h_bytes_per_step": 8 * dof}
+        e2e = e2e_run(bfp, torch, o, h, f_host, stream, ws, dof, max(4, args.steps // 2))
 
-    floats, tta, var, sweep, irb, rtab = None, None, None, None, None, None
+    floats, tta, var, sweep, irb, rtab, c1 = None, None, None, None, None, None, None
     if rank == 0 and not args.no_compare:
         floats, tta = solver_compare(bfp, torch, args, f, stream, h)
         sweep = width_sweep(bfp, torch, args, f, stream) if nd == 2 else None
         var = var_compare(bfp, torch, stream) if nd == 2 else None
         irb = bfp_ir_compare(bfp, torch, args, stream) if nd == 2 else None
         rtab = recompute_table(bfp, torch, args, f, stream) if nd == 2 else None
+        c1 = c1_time_to_accuracy(bfp, torch, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            tc = cpu_oracle_step(n, w, args.mode)
-            cpu = {"value": dof / tc / 1e9, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                   "sample": "one IR-V step of the same %d^2 workload (numpy exact-integer oracle)" % n}
+            ns = n if nd == 2 else min(n, 127)     # 3D: a 127^3 grid of the same problem (per-DOF rate)
+            orc = OracleRun(ns, w, args.mode, nd)
+            nst, wall, cpu_s = 0, 0.0, 0.0
+            while nst < 3 and wall < 20.0:         # a bounded sample: up to 3 IR-V steps, ~10-20 s
+                tw, tc = orc.step()
+                nst, wall, cpu_s = nst + 1, wall + tw, cpu_s + tc
+            cpu = {"value": ns ** nd * nst / wall / 1e9, "unit": UNIT, "cores": cores_used(wall, cpu_s),
+                   "kind": "oracle", "sample": "%d IR-V steps of the %s problem from x = 0 (numpy "
+                                               "exact-integer oracle, %.1f s)%s" % (
+                                                   nst, "x".join([str(ns)] * nd), wall,
+                                                   "" if ns == n else "; GDOF/s per DOF of that grid")}
         except Exception as exc:  # the oracle is a reported baseline, never the product path
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % exc}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": metric_name(nd, n, w), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int16+f64" if w <= 16 else "int32+f64",
             "data": "synthetic",
@@ -694,7 +858,7 @@ def run_ours(args):
             "gpu_launches": int(launches_per_step * args.steps),
             "op_stats_2_steps": op_stats,
             "float_baselines": floats, "time_to_accuracy": tta, "width_sweep": sweep,
-            "variable_coefficients": var, "bfp_ir": irb, "recomputations": rtab,
+            "variable_coefficients": var, "bfp_ir": irb, "recomputations": rtab, "c1_small": c1,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -3,9 +3,12 @@
 // and full multigrid (Alg. fmg).  Host code enqueues stream-ordered launches
 // of the BFP ops; exponents and norms stay on the device.
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "bfp_coarse.cuh"
 #include "bfp_desc.h"
@@ -15,6 +18,18 @@
 using namespace bfp;
 
 namespace {
+
+// A named NVTX range around the enqueueing of one solver phase (host side: the
+// ranges show the driver's structure per level and op; a replayed graph shows
+// only the ranges of its capture).
+struct Nvtx {
+  Nvtx(const char* what, int level) {
+    char name[64];
+    std::snprintf(name, sizeof(name), "bfp %s level %d", what, level);
+    nvtxRangePushA(name);
+  }
+  ~Nvtx() { nvtxRangePop(); }
+};
 
 // ---- FP64 kernels with a fixed evaluation order --------------------------------
 //
@@ -732,6 +747,7 @@ int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* 
 // skip their per-op memset.
 int32_t vcycle_rec(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* bufA, const bfp_vec* bufB,
                    bfp_vec* res, cudaStream_t s) {
+  Nvtx range("vcycle", k);
   Level& L = h->lv[k];
   Q q = make_q(h, L);
   int slot = 0;
@@ -948,6 +964,7 @@ int32_t flt_ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, dou
 
 int32_t ir_step(bfp_hierarchy* h, int k, const double* b, double bscale, double* x, cudaStream_t s) {
   if (is_float(h)) return flt_ir_step(h, k, b, bscale, x, s);
+  Nvtx range("ir_step", k);
   Level& L = h->lv[k];
   if (zero_arena(h, s) != cudaSuccess) return BFP_ERR_CUDA;   // every call-site meta of this step
   PrezeroedScope pz;
