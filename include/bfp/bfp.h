@@ -485,13 +485,19 @@ int32_t bfp_hierarchy_var_ir_operator(const bfp_hierarchy* h, bfp_varstencil* ou
 
 /* ---- batched solves (many independent instances, one graph launch) ------------ */
 /* count independent hierarchies (opts[i]: size, width, mode, schedule of
- * instance i), solved together: bfp_batch_solve captures, for every instance
- * on a branch of its own, [FMG] + ir_steps[i] IR-V steps into one CUDA graph
- * (re-captured only when the arguments change) and launches it once on
- * stream (which must not be the legacy default stream).  f[i], x[i]: device
- * dense doubles of instance i (x[i] is the initial iterate when fmg == 0).
- * bfp_batch_times waits for the last launch and writes, per instance, the ms
- * from the launch start to the end of that instance's branch. */
+ * instance i), solved together: bfp_batch_solve captures [FMG] +
+ * ir_steps[i] IR-V steps of every instance into one CUDA graph (re-captured
+ * only when the arguments change) and launches it once on stream (which must
+ * not be the legacy default stream).  Instances with equal options form a
+ * group that runs on one graph branch: each op of the shared schedule is ONE
+ * launch over all the group's instances still running at that point (grid z =
+ * instance), with the same per-instance results as a single-instance solve; a
+ * group whose schedule uses an op without a batched form (3D, int32 storage,
+ * variable coefficients, float baselines) runs its instances on branches of
+ * their own.  f[i], x[i]: device dense doubles of instance i (x[i] is the
+ * initial iterate when fmg == 0).  bfp_batch_times waits for the last launch
+ * and writes, per instance, the ms from the launch start to the end of that
+ * instance's last op. */
 typedef struct bfp_batch bfp_batch;
 int32_t bfp_batch_create(const bfp_solver_opts* opts, int32_t count, bfp_batch** out);
 int32_t bfp_batch_solve(bfp_batch* b, const double* const* f, double* const* x, const int32_t* ir_steps,
@@ -501,6 +507,9 @@ int32_t bfp_batch_solve(bfp_batch* b, const double* const* f, double* const* x, 
 int32_t bfp_batch_solve_one(bfp_batch* b, int32_t i, const double* f, double* x, int32_t ir_steps, int32_t fmg,
                             bfp_stream stream);
 int32_t bfp_batch_times(bfp_batch* b, float* ms);
+/* Of the last captured solve: groups run as merged launches, and instances on
+ * branches of their own. */
+int32_t bfp_batch_info(const bfp_batch* b, int32_t* merged_groups, int32_t* separate_instances);
 void bfp_batch_destroy(bfp_batch* b);
 
 /* ---- float baselines (not in the paper) ------------------------------------------ */

@@ -154,6 +154,7 @@ _sig = {
     "bfp_batch_times": (C.c_int32, [C.c_void_p, P(C.c_float)]),
     "bfp_batch_solve_one": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                         C.c_void_p]),
+    "bfp_batch_info": (C.c_int32, [C.c_void_p, P(C.c_int32), P(C.c_int32)]),
     "bfp_batch_destroy": (None, [C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -602,8 +603,14 @@ class Batch:
         _check(_lib.bfp_batch_solve_one(self.b, int(i), C.c_void_p(f.data_ptr()), C.c_void_p(x.data_ptr()),
                                         int(ir_steps), int(bool(fmg)), _stream(stream)), "bfp_batch_solve_one")
 
+    def info(self):
+        """(groups run as merged launches, instances on branches of their own) of the last captured solve."""
+        g, sep = C.c_int32(), C.c_int32()
+        _check(_lib.bfp_batch_info(self.b, C.byref(g), C.byref(sep)), "bfp_batch_info")
+        return int(g.value), int(sep.value)
+
     def times(self):
-        """ms from the launch start to the end of each instance's branch (waits for the launch)."""
+        """ms from the launch start to the end of each instance's last op (waits for the launch)."""
         ms = (C.c_float * self.count)()
         _check(_lib.bfp_batch_times(self.b, ms), "bfp_batch_times")
         return [float(v) for v in ms]

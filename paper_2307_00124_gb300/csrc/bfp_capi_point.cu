@@ -9,7 +9,11 @@ using namespace bfp;
 
 namespace bfp {
 static std::atomic<long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+std::vector<LaunchRec>*& launch_recorder();
+void note_launches(int n) {
+  if (launch_recorder()) return;   // recorded, not launched (a batched replay counts its own launches)
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 bool& prezeroed() {
   static thread_local bool flag = false;
   return flag;
@@ -21,6 +25,10 @@ int& tile_rows_override() {
 int& wadd_cap() {
   static thread_local int cap = -1;
   return cap;
+}
+std::vector<LaunchRec>*& launch_recorder() {
+  static thread_local std::vector<LaunchRec>* rec = nullptr;
+  return rec;
 }
 }  // namespace bfp
 
@@ -43,8 +51,24 @@ __device__ __forceinline__ bool f64_split(double v, int64_t& M, int64_t& E) {
 constexpr int64_t kF64KeyOffset = 4096;   // keeps the msb key positive for atomicMax
 constexpr int64_t kF64EStar = -1074;      // every double is a multiple of 2^-1074
 
-__global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ x, const VOut out,
-                                                  int64_t* meta_out, int w, bool pass1) {
+struct FromF64P {
+  const double* x;
+  VOut out;
+  int64_t* meta_out;
+  int32_t w, pass1;
+};
+
+// B: a batched launch, grid z the instance, parameters Pb[z]
+template <bool B = false>
+__global__ void __launch_bounds__(256) k_from_f64(const __grid_constant__ FromF64P P1,
+                                                  const FromF64P* __restrict__ Pb) {
+  pdl_wait();
+  const FromF64P& P = B ? Pb[blockIdx.z] : P1;
+  const double* __restrict__ x = P.x;
+  const VOut& out = P.out;
+  int64_t* meta_out = P.meta_out;
+  const int w = P.w;
+  const bool pass1 = P.pass1 != 0;
   const int64_t nvec = out.ld >> 3, rows = out.ny * out.nz, total = rows * nvec;
   int64_t e_out = 0;
   if (!pass1) {
@@ -91,8 +115,19 @@ __global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ x, 
   if (!pass1 && blockIdx.x == 0 && threadIdx.x == 0) meta_out[0] = e_out;
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_to_f64(const VIn x, const int64_t* meta, double* __restrict__ out) {
+struct ToF64P {
+  VIn x;
+  const int64_t* meta;
+  double* out;
+};
+
+template <class T, bool B = false>
+__global__ void __launch_bounds__(256) k_to_f64(const __grid_constant__ ToF64P P1, const ToF64P* __restrict__ Pb) {
+  pdl_wait();
+  const ToF64P& P = B ? Pb[blockIdx.z] : P1;
+  const VIn& x = P.x;
+  const int64_t* meta = P.meta;
+  double* __restrict__ out = P.out;
   const int64_t rows = x.ny * x.nz, total = rows * x.nx;
   int64_t e = meta[0];
   const int ei = (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e));
@@ -293,10 +328,9 @@ int32_t bfp_from_f64(const double* x, const bfp_vec* out, bfp_stream stream) {
   VOut o = vout(out);
   const int64_t items = rows_of(out) * (out->ld / 8);
   unsigned g = grid_for(items, 256);
-  if (cudaMemsetAsync(out->meta + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess)
-    return BFP_ERR_CUDA;
-  k_from_f64<<<g, 256, 0, s>>>(x, o, out->meta, out->w, true);
-  k_from_f64<<<g, 256, 0, s>>>(x, o, out->meta, out->w, false);
+  if (mem_zero(out->meta + 1, (BFP_META_WORDS - 1) * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
+  launch_rec<FromF64P, &k_from_f64<>, &k_from_f64<true>>(g, 256, 0, s, FromF64P{x, o, out->meta, out->w, 1});
+  launch_rec<FromF64P, &k_from_f64<>, &k_from_f64<true>>(g, 256, 0, s, FromF64P{x, o, out->meta, out->w, 0});
   note_launches(2);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -309,9 +343,10 @@ int32_t bfp_to_f64(const bfp_vec* x, double* out, bfp_stream stream) {
   const int64_t total = rows_of(x) * x->n[0];
   if (total == 0) return BFP_OK;
   unsigned g = grid_for(total, 256);
-  if (is64(x)) k_to_f64<long long><<<g, 256, 0, s>>>(vin(x), x->meta, out);
-  else if (is32(x)) k_to_f64<int32_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
-  else k_to_f64<int16_t><<<g, 256, 0, s>>>(vin(x), x->meta, out);
+  const ToF64P P{vin(x), x->meta, out};
+  if (is64(x)) launch_rec<ToF64P, &k_to_f64<long long>, &k_to_f64<long long, true>>(g, 256, 0, s, P);
+  else if (is32(x)) launch_rec<ToF64P, &k_to_f64<int32_t>, &k_to_f64<int32_t, true>>(g, 256, 0, s, P);
+  else launch_rec<ToF64P, &k_to_f64<int16_t>, &k_to_f64<int16_t, true>>(g, 256, 0, s, P);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }

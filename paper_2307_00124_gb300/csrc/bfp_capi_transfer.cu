@@ -36,11 +36,15 @@ int32_t restrict2d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaS
   if (!carved) {
     cudaFuncSetAttribute(k_restrict2d16<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_restrict2d16<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     carved = true;
   }
   if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
-  if (d.mode == kQcomp) k_restrict2d16<true><<<grid, 128, 0, s>>>(vin(rf), d, o, rs);
-  k_restrict2d16<false><<<grid, 128, 0, s>>>(vin(rf), d, o, rs);
+  const TransferP P{vin(rf), vin(rf), d, o, rs};
+  if (d.mode == kQcomp)
+    launch_rec<TransferP, &k_restrict2d16<true>, &k_restrict2d16<true, true>>(grid, 128, 0, s, P);
+  launch_rec<TransferP, &k_restrict2d16<false>, &k_restrict2d16<false, true>>(grid, 128, 0, s, P);
   note_launches(d.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -86,11 +90,22 @@ int32_t prolong16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const
   if (!carved) {
     cudaFuncSetAttribute(k_prolong16<CORR, true, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_prolong16<CORR, false, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if constexpr (ND == 2) {
+      cudaFuncSetAttribute(k_prolong16<CORR, true, 2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_prolong16<CORR, false, 2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     carved = true;
   }
   if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
-  if (d.mode == kQcomp) k_prolong16<CORR, true, ND><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
-  k_prolong16<CORR, false, ND><<<grid, 128, 0, s>>>(vin(dc), yv, d, o, rs);
+  const TransferP P{vin(dc), yv, d, o, rs};
+  if constexpr (ND == 2) {   // recordable for batched solves
+    if (d.mode == kQcomp)
+      launch_rec<TransferP, &k_prolong16<CORR, true, 2>, &k_prolong16<CORR, true, 2, true>>(grid, 128, 0, s, P);
+    launch_rec<TransferP, &k_prolong16<CORR, false, 2>, &k_prolong16<CORR, false, 2, true>>(grid, 128, 0, s, P);
+  } else {
+    if (d.mode == kQcomp) k_prolong16<CORR, true, ND><<<grid, 128, 0, s>>>(P, nullptr);
+    k_prolong16<CORR, false, ND><<<grid, 128, 0, s>>>(P, nullptr);
+  }
   note_launches(d.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }

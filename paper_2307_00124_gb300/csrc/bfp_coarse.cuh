@@ -504,7 +504,11 @@ struct SweepRunArgs {
   uint64_t* stats;
 };
 
-__global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
+template <bool B>
+__global__ void __launch_bounds__(32) k_sweep_run(const __grid_constant__ SweepRunArgs A1,
+                                                  const SweepRunArgs* __restrict__ Ab) {
+  pdl_wait();
+  const SweepRunArgs& a = B ? Ab[blockIdx.z] : A1;
   const int lane = threadIdx.x;
   const int n = a.n, nn = n * n, np = a.nd == 3 ? nn * n : nn;
   const bool act = lane < np;
@@ -640,8 +644,12 @@ __global__ void __launch_bounds__(32) k_sweep_run(const SweepRunArgs a) {
 // meta of the previous op stays in registers (prev / pe / pn) until then.
 // Block maxima rotate over three slots (full-block op c uses slot c mod 3 and
 // clears slot c + 1 before its first barrier).
-template <class T>
-__global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const CoarseArgs a) {
+// B: a batched launch, grid z the instance, arguments Ab[z]
+template <class T, bool B>
+__global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const __grid_constant__ CoarseArgs A1,
+                                                                      const CoarseArgs* __restrict__ Ab) {
+  pdl_wait();
+  const CoarseArgs& a = B ? Ab[blockIdx.z] : A1;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ Plan s_plan[kCoarseThreads / 32];   // full plans (general path only)
   __shared__ unsigned int s_key[3], s_nrm[3];

@@ -91,6 +91,42 @@ __device__ __forceinline__ uint64_t low_shift(i128 z, int64_t t) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel in the stream finishes;
+// pdl_wait() returns once that kernel has completed and its writes are
+// visible (at once when there is no such kernel), so every kernel calls it
+// before its first global memory access.  pdl_trigger() lets the next kernel
+// be scheduled; the kernels call it after their main loop.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// BFP mantissa -> FP64 (the IR update x + m 2^e)
+// ---------------------------------------------------------------------------
+
+// The rare case kept out of line, so that the FP64 pipe is not used speculatively.
+static __device__ __noinline__ double ldexp_slow(int32_t m, int64_t e) {
+  return ldexp((double)m, (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e)));
+}
+
+// m * 2^e as a double, exact for |m| < 2^31 whenever the result is normal
+// (built from its bits); otherwise ldexp.
+__device__ __forceinline__ double mant_pow2(int32_t m, int64_t e) {
+  if (m == 0) return 0.0;
+  const uint64_t sign = m < 0 ? (1ull << 63) : 0ull;
+  const uint32_t a = m < 0 ? (uint32_t)(-(int64_t)m) : (uint32_t)m;
+  const int lz = __clz(a);                                  // a has 32 - lz significant bits
+  const int64_t be = e + (31 - lz) + 1023;                   // biased exponent of the leading bit
+  if (be >= 1 && be <= 2046) {
+    const uint64_t frac = (((uint64_t)a << (lz + 1)) & 0xffffffffull) << 20;   // bits below the leading one
+    return __longlong_as_double((long long)(sign | ((uint64_t)be << 52) | frac));
+  }
+  return ldexp_slow(m, e);
+}
+
+// ---------------------------------------------------------------------------
 // Quantisation plan
 // ---------------------------------------------------------------------------
 

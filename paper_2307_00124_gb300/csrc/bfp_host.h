@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -48,9 +49,98 @@ inline int pick_rows(int heuristic, int cap) {
   return v > 0 ? (v < cap ? v : cap) : heuristic;
 }
 
+// ---- launch records (batched solves) ------------------------------------------
+//
+// While a recorder is installed (thread-local), the launch sites of the kernels
+// that have a batched form, and the zeroing / device-to-device copies of the
+// solver, append a record instead of enqueueing work.  A batched solve records
+// the schedule of every instance, then replays records at the same position of
+// instances with the same schedule as ONE launch of the batched kernel form
+// (blockIdx.z = instance, parameters read from a device array).
+
+using BatchedLaunch = void (*)(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const void* params, int count);
+
+struct LaunchRec {
+  int32_t op = 0;                    // 0: kernel, 1: zero bytes, 2: device-to-device copy
+  BatchedLaunch launch = nullptr;    // op 0: the batched form of the kernel
+  dim3 grid, block;
+  size_t smem = 0;
+  std::vector<unsigned char> params; // op 0: the kernel's parameter struct
+  void* dst = nullptr;               // ops 1, 2
+  const void* src = nullptr;
+  size_t bytes = 0;
+};
+
+std::vector<LaunchRec>*& launch_recorder();
+
+// The batched form of kernel KB (parameters P[count] in device memory, grid z = count).
+// Launch with programmatic stream serialization: the kernel may start while the previous kernel in
+// the stream finishes; every kernel launched this way waits (pdl_wait) before its memory accesses.
+template <class P, void (*K)(const P, const P*)>
+inline void launch_pdl(dim3 g, dim3 b, size_t smem, cudaStream_t s, const P& p, const P* pb) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, K, p, pb);
+}
+
+template <class P, void (*KB)(const P, const P*)>
+void batched_launch(dim3 g, dim3 b, size_t smem, cudaStream_t s, const void* params, int count) {
+  launch_pdl<P, KB>(dim3(g.x, g.y, (unsigned)count), b, smem, s, P{}, reinterpret_cast<const P*>(params));
+}
+
+// Launches K1 with parameters p, or records it (with its batched form KB) while a recorder is installed.
+template <class P, void (*K1)(const P, const P*), void (*KB)(const P, const P*)>
+inline void launch_rec(dim3 g, dim3 b, size_t smem, cudaStream_t s, const P& p) {
+  if (std::vector<LaunchRec>* r = launch_recorder()) {
+    LaunchRec rec;
+    rec.launch = &batched_launch<P, KB>;
+    rec.grid = g;
+    rec.block = b;
+    rec.smem = smem;
+    rec.params.resize(sizeof(P));
+    std::memcpy(rec.params.data(), &p, sizeof(P));
+    r->push_back(std::move(rec));
+    return;
+  }
+  launch_pdl<P, K1>(g, b, smem, s, p, static_cast<const P*>(nullptr));
+}
+
+// cudaMemsetAsync(p, 0, bytes) / a device-to-device cudaMemcpyAsync, or their records.
+inline cudaError_t mem_zero(void* p, size_t bytes, cudaStream_t s) {
+  if (std::vector<LaunchRec>* r = launch_recorder()) {
+    LaunchRec rec;
+    rec.op = 1;
+    rec.dst = p;
+    rec.bytes = bytes;
+    r->push_back(std::move(rec));
+    return cudaSuccess;
+  }
+  return cudaMemsetAsync(p, 0, bytes, s);
+}
+inline cudaError_t mem_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (std::vector<LaunchRec>* r = launch_recorder()) {
+    LaunchRec rec;
+    rec.op = 2;
+    rec.dst = dst;
+    rec.src = src;
+    rec.bytes = bytes;
+    r->push_back(std::move(rec));
+    return cudaSuccess;
+  }
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
 inline cudaError_t zero_accumulators(int64_t* meta_out, cudaStream_t s) {
   if (prezeroed()) return cudaSuccess;
-  return cudaMemsetAsync(meta_out + 1, 0, (BFP_META_WORDS - 1) * sizeof(int64_t), s);
+  return mem_zero(meta_out + 1, (BFP_META_WORDS - 1) * sizeof(int64_t), s);
 }
 
 inline cudaStream_t as_stream(bfp_stream s) { return reinterpret_cast<cudaStream_t>(s); }

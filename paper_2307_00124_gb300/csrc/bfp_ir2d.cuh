@@ -54,9 +54,6 @@ __device__ __forceinline__ bool split_double(double v, int64_t& M, int64_t& E) {
 // Rare-case fallbacks kept out of line: inlined, the compiler would evaluate
 // them speculatively and occupy GB300's low-rate FP64 pipe on every element.
 __device__ __noinline__ double dmul_slow(double v, double factor) { return __dmul_rn(v, factor); }
-__device__ __noinline__ double ldexp_slow(int32_t m, int64_t e) {
-  return ldexp((double)m, (int)(e > 4000 ? 4000 : (e < -4000 ? -4000 : e)));
-}
 
 // v * 2^-k for k >= 0 (exact): exponent-field arithmetic when v and the result
 // are normal, the rounded multiply otherwise (zeros, subnormals, Inf/NaN).
@@ -68,20 +65,6 @@ __device__ __forceinline__ double scale_pow2(double v, int k, double factor) {
   return dmul_slow(v, factor);
 }
 
-// m * 2^e as a double, exact for |m| < 2^31 whenever the result is normal
-// (built from its bits); otherwise ldexp.
-__device__ __forceinline__ double mant_pow2(int32_t m, int64_t e) {
-  if (m == 0) return 0.0;
-  const uint64_t sign = m < 0 ? (1ull << 63) : 0ull;
-  const uint32_t a = m < 0 ? (uint32_t)(-(int64_t)m) : (uint32_t)m;
-  const int lz = __clz(a);                                  // a has 32 - lz significant bits
-  const int64_t be = e + (31 - lz) + 1023;                   // biased exponent of the leading bit
-  if (be >= 1 && be <= 2046) {
-    const uint64_t frac = (((uint64_t)a << (lz + 1)) & 0xffffffffull) << 20;   // bits below the leading one
-    return __longlong_as_double((long long)(sign | ((uint64_t)be << 52) | frac));
-  }
-  return ldexp_slow(m, e);
-}
 
 // floor(M 2^sh) for any sh (caller guarantees the fit when sh > 0)
 __device__ __forceinline__ int64_t fshift(int64_t M, int64_t sh) {
@@ -126,8 +109,18 @@ __device__ __forceinline__ void ir_finish(const IrArgs& a, const IrPlan& p) {
   }
 }
 
-template <bool PASS1>
-__global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
+struct IrP {
+  IrArgs a;
+  int32_t rs;
+};
+
+// B: a batched launch, grid z the instance, parameters Pb[z]
+template <bool PASS1, bool B = false>
+__global__ void __launch_bounds__(128) k_ir2d(const __grid_constant__ IrP P1, const IrP* __restrict__ Pb) {
+  pdl_wait();
+  const IrP& P = B ? Pb[blockIdx.z] : P1;
+  const IrArgs& a = P.a;
+  const int rs = P.rs;
   __shared__ IrPlan sp;
   if (threadIdx.x == 0) sp = ir_plan(a, PASS1);
   __syncthreads();
@@ -247,6 +240,7 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
     }
   }
   if (bad) atomicOr((unsigned long long*)&a.meta[BFP_META_FLAGS], 1ull);
+  pdl_trigger();
   block_commit(red, a.meta, nullptr, PASS1);
   if (!PASS1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ir_finish(a, p);
 }
@@ -254,8 +248,19 @@ __global__ void __launch_bounds__(128) k_ir2d(const IrArgs a, const int rs) {
 // x <- x + m 2^e (FP64 update of Alg. ir): a thread owns one column of
 // kUpdRows consecutive rows and issues all of their loads before any add.
 constexpr int kUpdRows = 8;
-template <class T>
-__global__ void __launch_bounds__(256) k_ir_update2(double* __restrict__ x, const VIn y, const int64_t* meta) {
+struct UpdP {
+  double* x;
+  VIn y;
+  const int64_t* meta;
+};
+
+template <class T, bool B = false>
+__global__ void __launch_bounds__(256) k_ir_update2(const __grid_constant__ UpdP P1, const UpdP* __restrict__ Pb) {
+  pdl_wait();
+  const UpdP& P = B ? Pb[blockIdx.z] : P1;
+  double* __restrict__ x = P.x;
+  const VIn& y = P.y;
+  const int64_t* meta = P.meta;
   const int64_t e = meta[0];
   const int64_t rows = y.ny * y.nz;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -278,9 +278,25 @@ __global__ void __launch_bounds__(256) k_ir_update(double* __restrict__ x, const
 }
 
 // b_c = R~ (bscale * b_f), deltas in lexicographic order (outer axis first)
-template <int ND>
-__global__ void __launch_bounds__(256) k_restrict_f64(const double* __restrict__ bf, double bscale, Grid gf,
-                                                      double* __restrict__ bc, Grid gc, double rscale) {
+struct RestrictF64P {
+  const double* bf;
+  double bscale;
+  Grid gf;
+  double* bc;
+  Grid gc;
+  double rscale;
+};
+
+// B: a batched launch, grid z the instance, parameters Pb[z]
+template <int ND, bool B = false>
+__global__ void __launch_bounds__(256) k_restrict_f64(const __grid_constant__ RestrictF64P P1,
+                                                      const RestrictF64P* __restrict__ Pb) {
+  pdl_wait();
+  const RestrictF64P& P = B ? Pb[blockIdx.z] : P1;
+  const double* __restrict__ bf = P.bf;
+  const double bscale = P.bscale, rscale = P.rscale;
+  const Grid gf = P.gf, gc = P.gc;
+  double* __restrict__ bc = P.bc;
   const int64_t total = gc.nx * gc.ny * gc.nz;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -623,20 +639,23 @@ int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, c
   a.y = vout(y);
   a.y_meta = y->meta;
   a.stats = h->stats;
-  k_sweep_run<<<1, 32, 0, s>>>(a);
+  launch_rec<SweepRunArgs, &k_sweep_run<false>, &k_sweep_run<true>>(dim3(1), dim3(32), 0, s, a);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
 bool allow_coarse_smem(bool is32, int optin) {
   cudaFuncAttributes fa;
-  const cudaError_t e0 = is32 ? cudaFuncGetAttributes(&fa, k_coarse_vcycle<int32_t>)
-                              : cudaFuncGetAttributes(&fa, k_coarse_vcycle<int16_t>);
+  const cudaError_t e0 = is32 ? cudaFuncGetAttributes(&fa, k_coarse_vcycle<int32_t, false>)
+                              : cudaFuncGetAttributes(&fa, k_coarse_vcycle<int16_t, false>);
   if (e0 != cudaSuccess) return false;
   const int dyn = optin - (int)fa.sharedSizeBytes;
-  const cudaError_t e1 =
-      is32 ? cudaFuncSetAttribute(k_coarse_vcycle<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)
-           : cudaFuncSetAttribute(k_coarse_vcycle<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  cudaError_t e1 = is32
+      ? cudaFuncSetAttribute(k_coarse_vcycle<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)
+      : cudaFuncSetAttribute(k_coarse_vcycle<int16_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e1 == cudaSuccess)   // the batched form (one CTA per instance) needs the same shared memory
+    e1 = is32 ? cudaFuncSetAttribute(k_coarse_vcycle<int32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)
+              : cudaFuncSetAttribute(k_coarse_vcycle<int16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   return e1 == cudaSuccess;
 }
 
@@ -735,8 +754,12 @@ int32_t coarse_vcycle(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* 
   a.yout_meta = out->meta;
   a.yout_buf = h->ybuf[i];
   a.stats = h->stats;
-  if (h->coarse_wide) k_coarse_vcycle<int32_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
-  else k_coarse_vcycle<int16_t><<<1, kCoarseThreads, h->smem_bytes, s>>>(a);
+  if (h->coarse_wide)
+    launch_rec<CoarseArgs, &k_coarse_vcycle<int32_t, false>, &k_coarse_vcycle<int32_t, true>>(
+        dim3(1), dim3(kCoarseThreads), h->smem_bytes, s, a);
+  else
+    launch_rec<CoarseArgs, &k_coarse_vcycle<int16_t, false>, &k_coarse_vcycle<int16_t, true>>(
+        dim3(1), dim3(kCoarseThreads), h->smem_bytes, s, a);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -836,7 +859,7 @@ int slots_needed(const bfp_solver_opts& o, bool coarsest) {
 }
 
 cudaError_t zero_arena(bfp_hierarchy* h, cudaStream_t s) {
-  return cudaMemsetAsync(h->arena, 0, h->arena_words * sizeof(int64_t), s);
+  return mem_zero(h->arena, h->arena_words * sizeof(int64_t), s);
 }
 
 Grid grid_of(int nd, int64_t n) { return Grid{n, n, nd == 3 ? n : 1}; }
@@ -879,8 +902,8 @@ int32_t ir_residual_q(bfp_hierarchy* h, int k, const double* b, double bscale, c
     const int rs = pick_rows(g.ny >= 2048 ? 16 : (g.ny >= 1024 ? 8 : (g.ny >= 256 ? 4 : 2)), 64);
     const dim3 grid2((unsigned)((g.nx + kIrCols - 1) / kIrCols),
                      (unsigned)((g.ny + (int64_t)kIrWarps * rs - 1) / ((int64_t)kIrWarps * rs)));
-    k_ir2d<true><<<grid2, 128, 0, s>>>(a, rs);
-    k_ir2d<false><<<grid2, 128, 0, s>>>(a, rs);
+    launch_rec<IrP, &k_ir2d<true>, &k_ir2d<true, true>>(grid2, 128, 0, s, IrP{a, rs});
+    launch_rec<IrP, &k_ir2d<false>, &k_ir2d<false, true>>(grid2, 128, 0, s, IrP{a, rs});
   } else {
     k_ir3d<true><<<gr, 256, 0, s>>>(a, g);
     k_ir3d<false><<<gr, 256, 0, s>>>(a, g);
@@ -895,8 +918,9 @@ int32_t ir_update(double* x, const bfp_vec* y, cudaStream_t s) {
   const int64_t rows = y->n[1] * y->n[2];
   const int64_t rblocks = (rows + kUpdRows - 1) / kUpdRows;
   const dim3 gu((unsigned)((y->n[0] + 255) / 256), (unsigned)(rblocks < 65535 ? rblocks : 65535));
-  if (y->w > 16) k_ir_update2<int32_t><<<gu, 256, 0, s>>>(x, vin(y), y->meta);
-  else k_ir_update2<int16_t><<<gu, 256, 0, s>>>(x, vin(y), y->meta);
+  const UpdP P{x, vin(y), y->meta};
+  if (y->w > 16) launch_rec<UpdP, &k_ir_update2<int32_t>, &k_ir_update2<int32_t, true>>(gu, 256, 0, s, P);
+  else launch_rec<UpdP, &k_ir_update2<int16_t>, &k_ir_update2<int16_t, true>>(gu, 256, 0, s, P);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -1497,17 +1521,19 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
     const double* bf = (k == 1) ? f : F.b;
     const double sc = (k == 1) ? bs0 : 1.0;
     const int64_t tot = Cc.n * Cc.n * (nd == 3 ? Cc.n : 1);
-    if (nd == 2) k_restrict_f64<2><<<grid_for(tot, 256), 256, 0, s>>>(bf, sc, grid_of(nd, F.n), Cc.b, grid_of(nd, Cc.n), rscale);
-    else k_restrict_f64<3><<<grid_for(tot, 256), 256, 0, s>>>(bf, sc, grid_of(nd, F.n), Cc.b, grid_of(nd, Cc.n), rscale);
+    const RestrictF64P P{bf, sc, grid_of(nd, F.n), Cc.b, grid_of(nd, Cc.n), rscale};
+    if (nd == 2)
+      launch_rec<RestrictF64P, &k_restrict_f64<2>, &k_restrict_f64<2, true>>(grid_for(tot, 256), 256, 0, s, P);
+    else k_restrict_f64<3><<<grid_for(tot, 256), 256, 0, s>>>(P, nullptr);
     note_launches(1);
   }
-  if (cudaMemsetAsync(h->ir_gam, 0, nl * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
+  if (mem_zero(h->ir_gam, nl * sizeof(int64_t), s) != cudaSuccess) return BFP_ERR_CUDA;
   for (int k = nl - 1; k >= 0; --k) {
     Level& L = h->lv[k];
     double* xk = (k == 0) ? x : L.x;
     const int64_t tot = L.n * L.n * (nd == 3 ? L.n : 1);
     if (k == nl - 1) {
-      if (cudaMemsetAsync(xk, 0, tot * sizeof(double), s) != cudaSuccess) return BFP_ERR_CUDA;
+      if (mem_zero(xk, tot * sizeof(double), s) != cudaSuccess) return BFP_ERR_CUDA;
     } else {
       Level& Cc = h->lv[k + 1];
       if (is_float(h)) {
@@ -1534,7 +1560,7 @@ int32_t bfp_fmg(bfp_hierarchy* h, const double* f, double* x, bfp_stream stream)
     const double* bk = (k == 0) ? f : L.b;
     const double sc = (k == 0) ? bs0 : 1.0;
     if (k < nl - 1) {   // first step: gamma from the coarser level's last IR residual (i = 1 row)
-      if (cudaMemcpyAsync(h->ir_gam + k, h->ir_gam + k + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+      if (mem_copy(h->ir_gam + k, h->ir_gam + k + 1, sizeof(int64_t), s) !=
           cudaSuccess)
         return BFP_ERR_CUDA;
     }
@@ -1640,6 +1666,10 @@ int32_t ir_solve(bfp_hierarchy* h, const double* f, double* x, const bfp_ir_opts
 
 struct bfp_batch {
   std::vector<bfp_hierarchy*> h;
+  std::vector<bfp_solver_opts> opts;   // per instance (instances with equal options form a group)
+  void* pbuf = nullptr;                 // device copy of the merged launches' parameters
+  size_t pbuf_bytes = 0;
+  int merged_groups = 0, fallback_instances = 0;   // of the last captured solve
   std::vector<cudaStream_t> st;        // one capture branch per instance
   std::vector<cudaEvent_t> join, tend;
   cudaEvent_t fork = nullptr, tstart = nullptr;
@@ -1672,6 +1702,59 @@ int32_t instance_solve(bfp_hierarchy* h, const double* f, double* x, int32_t k, 
   return BFP_OK;
 }
 
+// Zeroing and small device-to-device copies of many instances in one launch (grid z: instance).
+__global__ void __launch_bounds__(256) k_zero_many(void* const* __restrict__ dst, size_t bytes) {
+  unsigned char* d = reinterpret_cast<unsigned char*>(dst[blockIdx.z]);
+  const size_t words = bytes / 8;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+    reinterpret_cast<unsigned long long*>(d)[i] = 0ull;
+  for (size_t i = words * 8 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < bytes;
+       i += (size_t)gridDim.x * blockDim.x)
+    d[i] = 0;
+}
+__global__ void __launch_bounds__(256) k_copy_many(void* const* __restrict__ dst, const void* const* __restrict__ src,
+                                                   size_t bytes) {
+  unsigned char* d = reinterpret_cast<unsigned char*>(dst[blockIdx.z]);
+  const unsigned char* a = reinterpret_cast<const unsigned char*>(src[blockIdx.z]);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < bytes; i += (size_t)gridDim.x * blockDim.x)
+    d[i] = a[i];
+}
+
+// The schedule of one instance (FMG and k IR-V steps) as launch records.  Returns false when any
+// part of it has no batched form: the work the recorder did not take is captured on a private
+// stream instead, and a non-empty capture means the schedule cannot be merged.
+bool record_instance(bfp_hierarchy* h, const double* f, double* x, int32_t k, int32_t fmg, cudaStream_t cap,
+                     std::vector<LaunchRec>* out) {
+  out->clear();
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  launch_recorder() = out;
+  const int32_t rc = instance_solve(h, f, x, k, fmg, cap);
+  launch_recorder() = nullptr;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+  size_t nodes = 1;
+  if (ce == cudaSuccess && g) cudaGraphGetNodes(g, nullptr, &nodes);
+  if (g) cudaGraphDestroy(g);
+  (void)cudaGetLastError();
+  return rc == BFP_OK && ce == cudaSuccess && nodes == 0;
+}
+
+bool same_rec(const LaunchRec& a, const LaunchRec& b) {
+  if (a.op != b.op) return false;
+  if (a.op == 0)
+    return a.launch == b.launch && a.grid.x == b.grid.x && a.grid.y == b.grid.y && a.grid.z == b.grid.z &&
+           a.block.x == b.block.x && a.smem == b.smem && a.params.size() == b.params.size();
+  return a.bytes == b.bytes;
+}
+
+// One position of a group's merged schedule: the members still running there and where their
+// parameters (kernels) or pointers (zeroing, copies) sit in the parameter buffer.
+struct MergedPos {
+  const LaunchRec* rec;          // the first member's record (kind, grid, sizes)
+  int count;                     // members with a record at this position
+  size_t off;                    // byte offset in the parameter buffer
+};
+
 }  // namespace
 
 extern "C" {
@@ -1679,6 +1762,7 @@ extern "C" {
 void bfp_batch_destroy(bfp_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->pbuf) cudaFree(b->pbuf);
   for (auto& o : b->one)
     if (o.g) cudaGraphExecDestroy(o.g);
   for (bfp_hierarchy* h : b->h) bfp_hierarchy_destroy(h);
@@ -1700,6 +1784,7 @@ int32_t bfp_batch_create(const bfp_solver_opts* opts, int32_t count, bfp_batch**
     const int32_t rc = bfp_hierarchy_create(&opts[i], &h);
     if (rc) { bfp_batch_destroy(b); return rc; }
     b->h.push_back(h);
+    b->opts.push_back(opts[i]);
     cudaStream_t s = nullptr;
     cudaEvent_t j = nullptr, t = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1735,19 +1820,129 @@ int32_t bfp_batch_solve(bfp_batch* b, const double* const* f, double* const* x, 
   for (size_t i = 0; same && i < n; ++i) same = b->gf[i] == f[i] && b->gx[i] == x[i] && b->gk[i] == ir_steps[i];
   if (!same) {
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    // groups: instances with equal options run the same schedule (up to their step counts)
+    std::vector<std::vector<int>> groups;
+    for (size_t i = 0; i < n; ++i) {
+      bool placed = false;
+      for (auto& g : groups)
+        if (std::memcmp(&b->opts[g[0]], &b->opts[i], sizeof(bfp_solver_opts)) == 0) {
+          g.push_back((int)i);
+          placed = true;
+          break;
+        }
+      if (!placed) groups.push_back({(int)i});
+    }
+    // record every member's schedule; a group merges when every record has a batched form and the
+    // members' schedules agree position by position (a shorter one is a prefix of the longest)
+    std::vector<std::vector<LaunchRec>> recs(n);
+    std::vector<char> merged(groups.size(), 0);
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return BFP_ERR_CUDA;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      bool ok = true;
+      int longest = groups[gi][0];
+      for (int m : groups[gi]) {
+        ok = ok && record_instance(b->h[m], f[m], x[m], ir_steps[m], fmg, cap, &recs[m]);
+        if (ok && recs[m].size() > recs[longest].size()) longest = m;
+      }
+      const std::vector<LaunchRec>& L = recs[longest];
+      for (int m : groups[gi])
+        for (size_t p2 = 0; ok && p2 < recs[m].size(); ++p2) ok = same_rec(recs[m][p2], L[p2]);
+      merged[gi] = ok ? 1 : 0;
+      if (!ok)
+        for (int m : groups[gi]) recs[m].clear();
+    }
+    cudaStreamDestroy(cap);
+    // the merged launches' parameters (kernels) and pointer arrays (zeroing, copies), position by position
+    std::vector<std::vector<MergedPos>> pos(groups.size());
+    std::vector<unsigned char> host;
+    auto put = [&](const void* p3, size_t bytes) {
+      const size_t off = host.size();
+      host.resize(off + bytes);
+      std::memcpy(host.data() + off, p3, bytes);
+    };
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      if (!merged[gi]) continue;
+      size_t len = 0;
+      for (int m : groups[gi]) len = recs[m].size() > len ? recs[m].size() : len;
+      for (size_t p2 = 0; p2 < len; ++p2) {
+        host.resize((host.size() + 15) / 16 * 16);
+        MergedPos mp{nullptr, 0, host.size()};
+        for (int m : groups[gi]) {
+          if (recs[m].size() <= p2) continue;
+          const LaunchRec& r = recs[m][p2];
+          if (!mp.rec) mp.rec = &r;
+          ++mp.count;
+          if (r.op == 0) put(r.params.data(), r.params.size());
+          else put(&r.dst, sizeof(void*));
+        }
+        if (mp.rec->op == 2)
+          for (int m : groups[gi])
+            if (recs[m].size() > p2) put(&recs[m][p2].src, sizeof(void*));
+        pos[gi].push_back(mp);
+      }
+    }
+    if (host.size() > b->pbuf_bytes) {
+      if (b->pbuf) cudaFree(b->pbuf);
+      b->pbuf = nullptr;
+      b->pbuf_bytes = 0;
+      if (cudaMalloc(&b->pbuf, host.size()) != cudaSuccess) return BFP_ERR_CUDA;
+      b->pbuf_bytes = host.size();
+    }
+    if (!host.empty() && cudaMemcpy(b->pbuf, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return BFP_ERR_CUDA;
+    unsigned char* dev = reinterpret_cast<unsigned char*>(b->pbuf);
+
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return BFP_ERR_CUDA;
     int32_t rc = BFP_OK;
     if (cudaEventRecordWithFlags(b->tstart, s, cudaEventRecordExternal) != cudaSuccess ||
         cudaEventRecord(b->fork, s) != cudaSuccess)
       rc = BFP_ERR_CUDA;
-    for (size_t i = 0; rc == BFP_OK && i < n; ++i) {
-      if (cudaStreamWaitEvent(b->st[i], b->fork, 0) != cudaSuccess) { rc = BFP_ERR_CUDA; break; }
-      rc = instance_solve(b->h[i], f[i], x[i], ir_steps[i], fmg, b->st[i]);
-      if (rc) break;
-      if (cudaEventRecordWithFlags(b->tend[i], b->st[i], cudaEventRecordExternal) != cudaSuccess ||
-          cudaEventRecord(b->join[i], b->st[i]) != cudaSuccess || cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess)
+    int nmerged = 0, nfallback = 0;
+    for (size_t gi = 0; rc == BFP_OK && gi < groups.size(); ++gi) {
+      if (!merged[gi]) {   // one capture branch per member, the single-instance launches
+        for (int m : groups[gi]) {
+          ++nfallback;
+          if (cudaStreamWaitEvent(b->st[m], b->fork, 0) != cudaSuccess) { rc = BFP_ERR_CUDA; break; }
+          rc = instance_solve(b->h[m], f[m], x[m], ir_steps[m], fmg, b->st[m]);
+          if (rc) break;
+          if (cudaEventRecordWithFlags(b->tend[m], b->st[m], cudaEventRecordExternal) != cudaSuccess ||
+              cudaEventRecord(b->join[m], b->st[m]) != cudaSuccess || cudaStreamWaitEvent(s, b->join[m], 0) != cudaSuccess)
+            rc = BFP_ERR_CUDA;
+        }
+        continue;
+      }
+      ++nmerged;
+      const int first = groups[gi][0];
+      cudaStream_t gs = b->st[first];
+      if (cudaStreamWaitEvent(gs, b->fork, 0) != cudaSuccess) { rc = BFP_ERR_CUDA; break; }
+      for (int m : groups[gi])
+        if (recs[m].empty() && cudaEventRecordWithFlags(b->tend[m], gs, cudaEventRecordExternal) != cudaSuccess)
+          rc = BFP_ERR_CUDA;
+      for (size_t p2 = 0; rc == BFP_OK && p2 < pos[gi].size(); ++p2) {
+        const MergedPos& mp = pos[gi][p2];
+        const LaunchRec& r = *mp.rec;
+        if (r.op == 0) {
+          r.launch(r.grid, r.block, r.smem, gs, dev + mp.off, mp.count);
+        } else {
+          const size_t words = (r.bytes + 7) / 8;
+          const unsigned gx = (unsigned)(words / 256 + 1 > 1024 ? 1024 : words / 256 + 1);
+          void* const* dsts = reinterpret_cast<void* const*>(dev + mp.off);
+          if (r.op == 1) k_zero_many<<<dim3(gx, 1, (unsigned)mp.count), 256, 0, gs>>>(dsts, r.bytes);
+          else k_copy_many<<<dim3(gx, 1, (unsigned)mp.count), 256, 0, gs>>>(
+              dsts, reinterpret_cast<const void* const*>(dev + mp.off + mp.count * sizeof(void*)), r.bytes);
+        }
+        note_launches(1);
+        for (int m : groups[gi])   // members whose schedule ends here
+          if (recs[m].size() == p2 + 1 &&
+              cudaEventRecordWithFlags(b->tend[m], gs, cudaEventRecordExternal) != cudaSuccess)
+            rc = BFP_ERR_CUDA;
+      }
+      if (rc == BFP_OK && (cudaEventRecord(b->join[first], gs) != cudaSuccess ||
+                           cudaStreamWaitEvent(s, b->join[first], 0) != cudaSuccess))
         rc = BFP_ERR_CUDA;
     }
+    if (rc == BFP_OK && cudaGetLastError() != cudaSuccess) rc = BFP_ERR_CUDA;
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &g);
     if (rc != BFP_OK || ce != cudaSuccess) {
@@ -1762,6 +1957,8 @@ int32_t bfp_batch_solve(bfp_batch* b, const double* const* f, double* const* x, 
     b->gk.assign(ir_steps, ir_steps + n);
     b->gfmg = fmg;
     b->gs = s;
+    b->merged_groups = nmerged;
+    b->fallback_instances = nfallback;
   }
   return cudaGraphLaunch(b->graph, s) == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -1788,6 +1985,13 @@ int32_t bfp_batch_solve_one(bfp_batch* b, int32_t i, const double* f, double* x,
     o.f = f; o.x = x; o.k = ir_steps; o.fmg = fmg; o.s = s;
   }
   return cudaGraphLaunch(o.g, s) == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
+}
+
+int32_t bfp_batch_info(const bfp_batch* b, int32_t* merged_groups, int32_t* separate_instances) {
+  if (!b || !merged_groups || !separate_instances) return BFP_ERR_ARG;
+  *merged_groups = b->merged_groups;
+  *separate_instances = b->fallback_instances;
+  return BFP_OK;
 }
 
 int32_t bfp_batch_times(bfp_batch* b, float* ms) {

@@ -553,8 +553,10 @@ __device__ __forceinline__ void narrow8(const int32_t* tmp, const Plan& p, const
 }
 
 // Final bookkeeping of a quantised op: e_out and the counters (block (0, 0, 0) only).
-__device__ __forceinline__ void op_epilogue(const QDesc& q, const Plan& p) {
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+// first: this CTA is the op's first block (block (0, 0, 0); in a batched launch (0, 0) of its instance).
+__device__ __forceinline__ void op_epilogue(const QDesc& q, const Plan& p,
+                                            bool first = (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)) {
+  if (first && threadIdx.x == 0) {
     q.meta_out[0] = p.e_out;
     if (q.stats) {
       atomicAdd((unsigned long long*)&q.stats[0], 1ull);

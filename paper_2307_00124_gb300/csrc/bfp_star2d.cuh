@@ -249,15 +249,25 @@ inline int32_t launch_star16(const VIn& y, const VIn& r, int32_t c, int32_t nb, 
   if (!carved) {
     cudaFuncSetAttribute(k_star16<KIND, true, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_star16<KIND, false, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if constexpr (ND == 2) {
+      cudaFuncSetAttribute(k_star16<KIND, true, 2, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_star16<KIND, false, 2, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     carved = true;
   }
   const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
   const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;
   const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1),
                (unsigned)(ND == 3 ? o.nz : 1));
-  const VarRow none{};
-  if (q.mode == kQcomp) k_star16<KIND, true, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, none);
-  k_star16<KIND, false, ND><<<g, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, none);
+  const Star16P P{y, r, c, nb, mw, q, o, rs, VarRow{}};
+  if constexpr (ND == 2) {   // recordable for batched solves
+    if (q.mode == kQcomp)
+      launch_rec<Star16P, &k_star16<KIND, true, 2>, &k_star16<KIND, true, 2, false, true>>(g, 128, 0, s, P);
+    launch_rec<Star16P, &k_star16<KIND, false, 2>, &k_star16<KIND, false, 2, false, true>>(g, 128, 0, s, P);
+  } else {
+    if (q.mode == kQcomp) k_star16<KIND, true, ND><<<g, 128, 0, s>>>(P, nullptr);
+    k_star16<KIND, false, ND><<<g, 128, 0, s>>>(P, nullptr);
+  }
   note_launches(q.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -292,8 +302,9 @@ inline int32_t launch_star16_var(const VIn& y, const VIn& r, const VarRow& va, c
   const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
   const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;
   const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1), 1u);
-  if (q.mode == kQcomp) k_star16<KIND, true, 2, true><<<g, 128, 0, s>>>(y, r, 0, 0, 0, q, o, rs, va);
-  k_star16<KIND, false, 2, true><<<g, 128, 0, s>>>(y, r, 0, 0, 0, q, o, rs, va);
+  const Star16P P{y, r, 0, 0, 0, q, o, rs, va};
+  if (q.mode == kQcomp) k_star16<KIND, true, 2, true><<<g, 128, 0, s>>>(P, nullptr);
+  k_star16<KIND, false, 2, true><<<g, 128, 0, s>>>(P, nullptr);
   note_launches(q.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }

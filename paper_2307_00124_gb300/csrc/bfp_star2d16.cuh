@@ -190,11 +190,32 @@ struct __align__(16) Stage16<3> {
   uint4 zm[N][32], zp[N][32];
 };
 
-// grid: (256-column chunks, strips of 4 * rs rows, planes)
-template <int KIND, bool PASS1, int ND, bool VAR = false>
-__global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const VIn y, const VIn r, const int32_t c,
-                                                                 const int32_t nb, const int32_t mw, const QDesc q,
-                                                                 const VOut out, const int rs, const VarRow va) {
+// Parameters of one star-stencil op (one instance of a batched launch).
+struct Star16P {
+  VIn y, r;
+  int32_t c, nb, mw;
+  QDesc q;
+  VOut out;
+  int32_t rs;
+  VarRow va;
+};
+
+
+// grid: (256-column chunks, strips of 4 * rs rows, planes); B: a batched launch of 2D ops, grid z the
+// instance, parameters Pb[z]
+template <int KIND, bool PASS1, int ND, bool VAR = false, bool B = false>
+__global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const __grid_constant__ Star16P P1,
+                                                                 const Star16P* __restrict__ Pb) {
+  static_assert(!B || ND == 2, "batched launches are 2D");
+  pdl_wait();
+  const Star16P& P = B ? Pb[blockIdx.z] : P1;
+  const VIn& y = P.y;
+  const VIn& r = P.r;
+  const int32_t c = P.c, nb = P.nb, mw = P.mw;
+  const QDesc& q = P.q;
+  const VOut& out = P.out;
+  const int rs = P.rs;
+  const VarRow& va = P.va;
   constexpr int NS = Stage16<ND>::N;
   __shared__ Plan sp;
   __shared__ Stage16<ND> stg[4];
@@ -494,8 +515,9 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   }
   if (PASS1 && ormag) red.key = max(red.key, (long long)(256 + (64 - __clzll((long long)ormag)) + 1));
   if (PASS1 && fast && j0 < j1 && act && ormag == 0 && nvalid > 0) red.key = max(red.key, 257ll);   // all-zero chunk: msb 1
+  pdl_trigger();
   block_commit(red, q.meta_out, q.stats, PASS1);
-  if (!PASS1) op_epilogue(q, p);
+  if (!PASS1) op_epilogue(q, p, blockIdx.x == 0 && blockIdx.y == 0 && (B || blockIdx.z == 0));
 }
 
 }  // namespace bfp

@@ -205,8 +205,25 @@ __device__ __noinline__ void restrict_slow(const VIn& f, const Plan& p, const VO
   slow_hl8<PASS1>(H, L, p, out, tmp, J, c0, red);
 }
 
-template <bool PASS1>
-__global__ void __launch_bounds__(128, 6) k_restrict2d16(const VIn f, const QDesc q, const VOut out, const int rs) {
+// Parameters of one restriction / interpolation op (one instance of a batched launch).
+struct TransferP {
+  VIn f;       // restriction: fine input; interpolation: the coarse d
+  VIn y;       // interpolation: y of the correction
+  QDesc q;
+  VOut out;
+  int32_t rs;
+};
+
+// B: a batched launch of 2D ops, grid z the instance, parameters Pb[z]
+template <bool PASS1, bool B = false>
+__global__ void __launch_bounds__(128, 6) k_restrict2d16(const __grid_constant__ TransferP P1,
+                                                        const TransferP* __restrict__ Pb) {
+  pdl_wait();
+  const TransferP& P = B ? Pb[blockIdx.z] : P1;
+  const VIn& f = P.f;
+  const QDesc& q = P.q;
+  const VOut& out = P.out;
+  const int rs = P.rs;
   __shared__ Plan sp;
   __shared__ StageR stg[4];
   if (threadIdx.x == 0) {
@@ -329,8 +346,9 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const VIn f, const QDes
   }
   if (PASS1) fold_key(red, ormag, any && ec.fast);
   else red.nrm = max(red.nrm, packed_norm(vmax, vmin, out.is32 != 0));
+  pdl_trigger();
   block_commit(red, q.meta_out, q.stats, PASS1);
-  if (!PASS1) op_epilogue(q, p);
+  if (!PASS1) op_epilogue(q, p, blockIdx.x == 0 && blockIdx.y == 0 && (B || blockIdx.z == 0));
 }
 
 // ---------------------------------------------------------------------------
@@ -563,9 +581,17 @@ __device__ __noinline__ void prolong_slow(const VIn& d, const VIn& y, const Plan
 }
 
 // grid: (256-column chunks, strips of 4 * rs row pairs, fine planes)
-template <bool CORR, bool PASS1, int ND>
-__global__ void __launch_bounds__(128, 6) k_prolong16(const VIn d, const VIn y, const QDesc q, const VOut out,
-                                                      const int rs) {
+template <bool CORR, bool PASS1, int ND, bool B = false>
+__global__ void __launch_bounds__(128, 6) k_prolong16(const __grid_constant__ TransferP Pv,
+                                                      const TransferP* __restrict__ Pb) {
+  static_assert(!B || ND == 2, "batched launches are 2D");
+  pdl_wait();
+  const TransferP& P = B ? Pb[blockIdx.z] : Pv;
+  const VIn& d = P.f;
+  const VIn& y = P.y;
+  const QDesc& q = P.q;
+  const VOut& out = P.out;
+  const int rs = P.rs;
   __shared__ Plan sp;
   __shared__ StageP<ND> stg[4];
   if (threadIdx.x == 0) {
@@ -732,8 +758,9 @@ __global__ void __launch_bounds__(128, 6) k_prolong16(const VIn d, const VIn y, 
   }
   if (PASS1) fold_key(red, ormag, any && ec.fast);
   else red.nrm = max(red.nrm, packed_norm(vmax, vmin, out.is32 != 0));
+  pdl_trigger();
   block_commit(red, q.meta_out, q.stats, PASS1);
-  if (!PASS1) op_epilogue(q, p);
+  if (!PASS1) op_epilogue(q, p, blockIdx.x == 0 && blockIdx.y == 0 && (B || blockIdx.z == 0));
 }
 
 }  // namespace bfp

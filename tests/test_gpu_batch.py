@@ -123,3 +123,62 @@ def test_batch_instances_equal_the_oracle():
             xr = s.ir_step(0, bb, xr)
         assert np.array_equal(xs[i].cpu().numpy(), xr), i
     b.close()
+
+
+def test_batch_groups_merge_and_equal_the_oracle():
+    """Instances with equal options run as one group: each op of the shared schedule is one launch
+    over the group's instances still running (different step counts end at different points).
+    Every instance equals the oracle's FMG + K IR-V steps bit for bit, and the per-instance end
+    times are ordered by step count within a group."""
+    from oracle import mg as M
+    spec = [(63, 16, bfp.NNQCOMP, 0, 63)] * 3 + [(127, 16, bfp.QCOMP, 4, 31)] * 3 + [(255, 12, bfp.NNQCOMP, 8, 127)] * 2
+    ks = [1, 3, 2, 0, 2, 1, 2, 1]
+    olist = [opts(*sp) for sp in spec]
+    fh = [smoothed_random_rhs(sp[0], 400 + i) for i, sp in enumerate(spec)]
+    fs = [torch.from_numpy(f).cuda() for f in fh]
+    xs = [torch.zeros_like(f) for f in fs]
+    stream = torch.cuda.Stream()
+    b = bfp.Batch(olist)
+    for rep in range(2):                       # capture, then replay of the captured graph
+        for x in xs:
+            x.zero_()
+        with torch.cuda.stream(stream):
+            b.solve(fs, xs, ks, fmg=True)
+        stream.synchronize()
+        assert b.info() == (3, 0)
+        t = b.times()
+        assert t[1] >= t[2] >= t[0] and t[4] >= t[5] >= t[3] and t[6] >= t[7]
+        for i, (sp, o, k) in enumerate(zip(spec, olist, ks)):
+            s = M.BFPSolver(2, sp[0], w=sp[1], mode="qcomp" if sp[2] == bfp.QCOMP else "nnqcomp",
+                            omega=o.omega, w_omega=o.w_omega)
+            xr = s.fmg(fh[i])
+            bb = s.rhs_hierarchy(fh[i])[0]
+            for _ in range(k):
+                xr = s.ir_step(0, bb, xr)
+            assert np.array_equal(xs[i].cpu().numpy(), xr), (rep, i)
+    b.close()
+
+
+def test_batch_without_batched_form_runs_separately():
+    """A group whose schedule has ops without a batched form (int32 storage at w = 24) runs its
+    instances on branches of their own, with the same results."""
+    spec = [(63, 24, bfp.NNQCOMP, 0, 63)] * 2 + [(63, 16, bfp.NNQCOMP, 0, 63)] * 2
+    olist = [opts(*sp) for sp in spec]
+    fs = [torch.from_numpy(smoothed_random_rhs(sp[0], 500 + i)).cuda() for i, sp in enumerate(spec)]
+    xs = [torch.zeros_like(f) for f in fs]
+    stream = torch.cuda.Stream()
+    b = bfp.Batch(olist)
+    with torch.cuda.stream(stream):
+        b.solve(fs, xs, [2, 2, 2, 2], fmg=True)
+    stream.synchronize()
+    assert b.info() == (1, 2)
+    for i, o in enumerate(olist):
+        h = bfp.Hierarchy(o)
+        xr = torch.zeros_like(fs[i])
+        with torch.cuda.stream(stream):
+            h.fmg(fs[i], xr)
+            h.ir_iterate(fs[i], xr, 2)
+        stream.synchronize()
+        assert torch.equal(xs[i], xr), i
+        h.close()
+    b.close()
