@@ -538,6 +538,7 @@ def c1_time_to_accuracy(bfp, torch, stream, w=16, n=63):
     fh = manufactured_rhs(2, n)
     f = torch.from_numpy(fh).cuda()
     o = bfp.bfp_solver_opts_default(2, n, w)
+    o.mode = bfp.NNQCOMP
     h = bfp.Hierarchy(o)
     x = torch.zeros_like(f)
     with torch.cuda.stream(stream):

@@ -333,6 +333,7 @@ __device__ __forceinline__ void lean_exec(const CoarseOp& op, const CoarseLean& 
   ex.f.dh = (L.two && L.top) ? L.D : 0;
   ex.f.dl = (L.two && !L.top) ? L.D : 0;
   ex.f.t = t < 0 ? 0 : (t > 63 ? 63 : t);
+  ex.f.tl = 0;                  // the on-chip cycle keeps no qcomp window
   ex.f.w = w;
   ex.f.clamp = (!pass1 && clamp) ? 1 : 0;
   ex.m = make_mul(op.kind, ex.f, op);

@@ -262,6 +262,7 @@ struct Fast {
   int32_t ok;           // fast path usable
   int32_t dh, dl;       // left shifts of H and L into Z (one of them is 0)
   int32_t t;            // Z >> t gives the result (pass 2 / nnqcomp) or the window (pass 1)
+  int32_t tl;           // pass 1 with the window below Ez: the window is the low w bits of Z << tl (t = 0)
   int32_t w;            // width that result / window is reduced to
   int32_t clamp;        // nnqcomp saturation (qcomp results fit by construction)
 };
@@ -269,7 +270,11 @@ struct Fast {
 __device__ __forceinline__ Fast make_fast(const Plan& p, bool pass1) {
   Fast f;
   const int64_t t = pass1 ? (p.e_tmp - p.Ez) : (p.e_out - p.Ez);
-  f.ok = (!p.wide && !p.guarded && (t >= 0 || (pass1 && !p.use_tmp))) ? 1 : 0;
+  // qcomp's first pass keeps decr(w_tmp, z* >> lambda_tmp); when lambda_tmp is below the exact result's
+  // exponent that is a left shift, whose low w_tmp bits come from the low bits of Z alone
+  const bool left = pass1 && p.use_tmp && t < 0 && t >= -31;
+  f.ok = (!p.wide && !p.guarded && (t >= 0 || left || (pass1 && !p.use_tmp))) ? 1 : 0;
+  f.tl = left ? (int32_t)(-t) : 0;
   f.dh = (p.two && p.top_is_h) ? p.s_top : 0;
   f.dl = (p.two && !p.top_is_h) ? p.s_top : 0;
   f.t = (int32_t)(t < 0 ? 0 : (t > 63 ? 63 : t));

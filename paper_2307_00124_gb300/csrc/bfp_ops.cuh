@@ -459,7 +459,7 @@ __device__ __forceinline__ void quantvf(const HL& hl, const Plan& p, const Fast&
       const bool valid = k < nvalid;   // padding columns may see a real neighbour: masked
       if (PASS1) {
         if (valid) red.key = max(red.key, (long long)(256 + msb64(Z)));
-        o[k] = valid ? wrap_bits((uint64_t)(Z >> fq.t), fq.w) : 0;
+        o[k] = valid ? wrap_bits((uint64_t)(Z >> fq.t) << fq.tl, fq.w) : 0;
       } else {
         int64_t v = Z >> fq.t;
         if (fq.clamp) {

@@ -71,12 +71,14 @@ struct FastRow {
   int64_t zmax, zmin;   // v > hi  <=>  Z > zmax ;  v < lo  <=>  Z < zmin
   int32_t hi, lo;
   uint32_t t;           // < 32
+  uint32_t tl;          // pass 1: left shift of the window
   int32_t w, clamp;
 };
 
 __device__ __forceinline__ FastRow make_fast_row(const Fast& fq) {
   FastRow f;
   f.t = (uint32_t)fq.t;
+  f.tl = (uint32_t)fq.tl;
   f.w = fq.w;
   f.clamp = fq.clamp;
   f.hi = (int32_t)((1ll << (fq.w - 1)) - 1);
@@ -102,7 +104,7 @@ __device__ __forceinline__ void fast_row(const int64_t (&zc)[3], const int32_t (
     if (PASS1) {
       if (valid) key = max(key, (long long)(256 + msb64(Z)));
       const int s = 32 - fr.w;
-      o[k] = valid ? ((v << s) >> s) : 0;                          // decr to w_tmp bits
+      o[k] = valid ? ((int32_t)((uint32_t)v << fr.tl << s) >> s) : 0;   // decr to w_tmp bits
     } else {
       int32_t vi = v;
       if (fr.clamp) {

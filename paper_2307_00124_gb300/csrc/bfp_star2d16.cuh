@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << (t & 63));   // used only when t < 32
   const uint64_t zrange = (uint64_t)(((uint64_t)1 << ((fq.w - 1 + t) & 63)) * 2 - 1);
   const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
+  const uint32_t tl = (uint32_t)fq.tl;          // pass 1: the window's left shift (window below Ez)
   const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
   const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
   const bool partial = nvalid < 8;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
                                    : (int32_t)(Z >> t);
               if (PASS1) {
                 if (INT || k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
-                o[k] = (int32_t)((uint32_t)v << sh) >> sh;
+                o[k] = (int32_t)(((uint32_t)v << tl) << sh) >> sh;
               } else {
                 o[k] = v;
                 if (!V32 && fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)zmin > zrange) && (INT || k < nvalid);

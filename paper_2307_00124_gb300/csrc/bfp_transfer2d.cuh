@@ -56,6 +56,7 @@ struct EmitC {
   bool v32;           // |Z| < 2^(31 + t): saturation tested on the 32-bit results
   int32_t kh, kl;
   uint32_t t;
+  uint32_t tl;        // pass 1: left shift of the window (window below the exact exponent)
   int w, sh;          // result width, 32 - w (pass 1 window decr)
   uint32_t half;      // 2^(w-1)
   int64_t zmin;
@@ -73,6 +74,7 @@ __device__ __forceinline__ EmitC make_emit(const Fast& fq, const QDesc& q, int32
   e.dl = (uint32_t)fq.dl;
   e.kh = e.fold ? e.kh : hsign;   // unfolded: H carries its sign, Z = (hsign H << dh) + (L << dl)
   e.t = (uint32_t)fq.t;
+  e.tl = (uint32_t)fq.tl;
   const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
   e.v32 = zb - fq.t <= 30;
   e.w = fq.w;
@@ -105,7 +107,7 @@ __device__ __forceinline__ bool emit8(const EmitC& e, const Fast& fq, const int3
                            : (int32_t)(Z >> e.t);
     if (PASS1) {
       if (k < nvalid) ormag |= (uint64_t)(Z ^ (Z >> 63));
-      o[k] = (int32_t)((uint32_t)v << e.sh) >> e.sh;
+      o[k] = (int32_t)(((uint32_t)v << e.tl) << e.sh) >> e.sh;
     } else {
       o[k] = v;
       if (!V32 && fq.clamp) ovf |= ((uint64_t)Z - (uint64_t)e.zmin > e.zrange) && (k < nvalid);

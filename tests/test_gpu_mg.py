@@ -294,3 +294,60 @@ def test_benchmarked_ir_steps_4095(mode):
     assert np.all(r.padding() == 0)
     ir_counters_match(h, s)
     h.close()
+
+
+def test_ir_step_3d_255_bit_exact():
+    """3D at 255^3 (16.6 M DOF, 7 levels, the seven-point kernels' 3D grids over many planes and
+    strips): one IR-V(2,2) step from x = 0 with the default schedule equals the oracle's FP64 iterate
+    bit for bit, with the op and IR counters."""
+    n = 255
+    o = bfp.bfp_solver_opts_default(3, n, 16)
+    o.mode = bfp.NNQCOMP
+    h = bfp.Hierarchy(o)
+    s = mg.BFPSolver(3, n, w=16, mode="nnqcomp", omega=o.omega, w_omega=o.w_omega)
+    f = manufactured_rhs(3, n)
+    ft = torch.from_numpy(f).cuda()
+    xt = torch.zeros_like(ft)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.ir_iterate(ft, xt, 1)
+    stream.synchronize()
+    xr = s.ir_step(0, s.rhs_hierarchy(f)[0], np.zeros_like(f))
+    assert np.array_equal(xt.cpu().numpy(), xr)
+    st = h.stats()
+    assert (st["calls"], st["saturated"]) == (s.stats.calls, s.stats.saturated)
+    ir_counters_match(h, s)
+    h.close()
+
+
+@pytest.mark.parametrize("mode", [bfp.NNQCOMP, bfp.QCOMP])
+def test_ir_resume_from_saved_iterate(mode):
+    """Checkpoint and resume: the whole state of the IR solve is the FP64 iterate.  FMG + 3 IR-V steps,
+    x saved to host memory and the hierarchy destroyed; a new hierarchy loads x and runs 3 more steps.
+    The result equals FMG + 6 steps in one run bit for bit (the IR residual is quantised by Alg. qcomp,
+    whose result does not depend on the window the previous residual set)."""
+    n = 127
+    f = torch.from_numpy(manufactured_rhs(2, n)).cuda()
+    stream = torch.cuda.Stream()
+    h, _ = make(2, n, 16, mode)
+    x = torch.zeros_like(f)
+    with torch.cuda.stream(stream):
+        h.fmg(f, x)
+        h.ir_iterate(f, x, 6)
+    stream.synchronize()
+    h.close()
+    h1, _ = make(2, n, 16, mode)
+    y = torch.zeros_like(f)
+    with torch.cuda.stream(stream):
+        h1.fmg(f, y)
+        h1.ir_iterate(f, y, 3)
+    stream.synchronize()
+    saved = y.cpu().numpy().copy()                      # the checkpoint
+    h1.close()
+    h2, _ = make(2, n, 16, mode)
+    z = torch.from_numpy(saved).cuda()
+    with torch.cuda.stream(stream):
+        h2.ir_iterate(f, z, 3)
+    stream.synchronize()
+    assert torch.equal(z, x)
+    h2.close()
