@@ -828,7 +828,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            ns = n if nd == 2 else min(n, 127)     # 3D: a 127^3 grid of the same problem (per-DOF rate)
+            ns = n if nd == 2 else min(n, 255)     # 3D: a 255^3 grid of the same problem (per-DOF rate)
             orc = OracleRun(ns, w, args.mode, nd)
             nst, wall, cpu_s = 0, 0.0, 0.0
             while nst < 3 and wall < 20.0:         # a bounded sample: up to 3 IR-V steps, ~10-20 s
