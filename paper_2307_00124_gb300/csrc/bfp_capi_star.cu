@@ -20,7 +20,7 @@ template <int KIND, int ND>
 int32_t star_launch(const bfp_vec* yv, const bfp_vec* rv, const QDesc& d, const bfp_vec* out, int64_t c,
                     int64_t n, int64_t mw, bool wide_in, cudaStream_t s) {
   if (ND == 2) {
-    if (wide_in) return launch_star2d<int32_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
+    if (wide_in) return launch_star2d<int32_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s, !yv || yv->w <= 30);
     return launch_star2d<int16_t, KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);
   }
   if (!wide_in && !is32(out)) return launch_star3d16<KIND>(vin(yv), vin(rv), c, n, mw, d, out, s);

@@ -122,7 +122,8 @@ __device__ __forceinline__ void fast_row(const int64_t (&zc)[3], const int32_t (
 
 template <class T, int KIND, bool PASS1>
 __global__ void __launch_bounds__(128, 8) k_star2d(const VIn y, const VIn r, const int32_t c, const int32_t nb,
-                                                   const int32_t mw, const QDesc q, const VOut out, const int rs) {
+                                                   const int32_t mw, const QDesc q, const VOut out, const int rs,
+                                                   const int nsfit) {
   __shared__ Plan sp;
   if (threadIdx.x == 0) {
     build_plan(q, sp);
@@ -152,8 +153,10 @@ __global__ void __launch_bounds__(128, 8) k_star2d(const VIn y, const VIn r, con
     zc[1] = (int64_t)((uint64_t)(int64_t)nb << fq.dh);
     zc[2] = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)(1ull << fq.dl) : (int64_t)((uint64_t)(int64_t)mw << fq.dl));
   }
-  const bool small = zc[0] == (int32_t)zc[0] && zc[1] == (int32_t)zc[1] && zc[2] == (int32_t)zc[2] &&
-                     sizeof(T) == 2;
+  // folded coefficients in 32 bits: Z from 32 x 32 -> 64-bit products (the mantissas and the neighbour
+  // sum are 32-bit: int16 storage, or int32 inputs of at most 30 bits, nsfit)
+  const bool small = zc[0] == (int32_t)zc[0] && zc[1] == (int32_t)zc[1] && zc[2] == (int32_t)zc[2];
+  const bool reg = sizeof(T) == 2 || nsfit != 0;   // register path: the neighbour sum exact in int32
   const RowLoader<T> ly = row_loader<T>(y, c0), lr = row_loader<T>(r, c0);
   const int nvalid = (int)(out.nx - c0 >= kStarV ? kStarV : (out.nx - c0 > 0 ? out.nx - c0 : 0));
 
@@ -208,10 +211,10 @@ __global__ void __launch_bounds__(128, 8) k_star2d(const VIn y, const VIn r, con
       for (int k = 0; k < kStarV; ++k) {
         const uint32_t wk = (uint32_t)(k == 0 ? wv : yc[k - 1]);
         const uint32_t ek = (uint32_t)(k == kStarV - 1 ? ev : yc[k + 1]);
-        ns[k] = sizeof(T) == 2 ? (int32_t)(((wk + ek) + (uint32_t)ym[k]) + (uint32_t)yp[k]) : 0;
+        ns[k] = reg ? (int32_t)(((wk + ek) + (uint32_t)ym[k]) + (uint32_t)yp[k]) : 0;
       }
       if (act) {
-        if (fq.ok && sizeof(T) == 2) {
+        if (fq.ok && reg) {
           int32_t o[kStarV];
           if (small) fast_row<PASS1, true>(zc, yc, ns, rc, fr, nvalid, red.key, nrm32, sat, o);
           else fast_row<PASS1, false>(zc, yc, ns, rc, fr, nvalid, red.key, nrm32, sat, o);
@@ -333,8 +336,9 @@ inline int32_t launch_star3d16(const VIn& y, const VIn& r, int64_t c64, int64_t 
 }
 
 template <class T, int KIND>
+// nsfit: y's mantissas have at most 30 bits, so a sum of four neighbours is exact in int32
 inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb64, int64_t mw64, const QDesc& q,
-                             const bfp_vec* out, cudaStream_t s) {
+                             const bfp_vec* out, cudaStream_t s, bool nsfit = true) {
   if (q.hbits > 62 || (q.two && q.lbits > 62)) return BFP_ERR_WIDTH;
   const int32_t c = (int32_t)c64, nb = (int32_t)nb64, mw = (int32_t)mw64;   // checked < 2^31 by the caller
   const VOut o = vout(out);
@@ -345,8 +349,8 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (sizeof(T) == 2 && !o.is32) return launch_star16<KIND, 2>(y, r, c, nb, mw, q, o, rs, s);
-  if (q.mode == kQcomp) k_star2d<T, KIND, true><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
-  k_star2d<T, KIND, false><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs);
+  if (q.mode == kQcomp) k_star2d<T, KIND, true><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, nsfit ? 1 : 0);
+  k_star2d<T, KIND, false><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, nsfit ? 1 : 0);
   note_launches(q.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
