@@ -219,13 +219,6 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   constexpr int NS = Stage16<ND>::N;
   __shared__ Plan sp;
   __shared__ Stage16<ND> stg[4];
-  if (threadIdx.x == 0) {
-    build_plan(q, sp);
-    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
-  }
-  __syncthreads();
-  const Plan& p = sp;
-  const Fast fq = make_fast(p, PASS1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * kS16Cols + lane * 8;
   const int ny = (int)out.ny;
@@ -234,39 +227,7 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   const int j0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);
   const int j1 = j0 + rs < ny ? j0 + rs : ny;
   const bool act = c0 < out.ld;
-  Red red = {0, 0, 0};
-  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
   constexpr bool kUseY = KIND != kJacobi0, kUseR = KIND != kApply;
-
-  // Z = cy*y + cn*ns + cr*r, the group shifts folded into the coefficients
-  int64_t cy, cn, cr;
-  if (KIND == kJacobi0) {
-    cy = 0; cn = 0; cr = (int64_t)((uint64_t)(int64_t)mw << fq.dh);
-  } else {
-    cy = (int64_t)((uint64_t)(int64_t)c << fq.dh);
-    cn = (int64_t)((uint64_t)(int64_t)nb << fq.dh);
-    cr = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)(1ull << fq.dl) : (int64_t)((uint64_t)(int64_t)mw << fq.dl));
-  }
-  const int32_t cy32 = (int32_t)cy, cn32 = (int32_t)cn, cr32 = (int32_t)cr;
-  const uint32_t t = (uint32_t)fq.t;
-  // |Z| <= 2^zb from the msb bounds of the two groups
-  const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
-  // fast: Z exact in int64 (the plan's fast regime); fold: the group shifts folded into 32-bit
-  // coefficients and t < 32, so Z is three mad.wide and the result one funnel shift (else
-  // Z = (H << dh) + (L << dl) from the plain coefficients and the result Z >> t)
-  const bool fast = fq.ok;
-  const bool fold = !VAR && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr && fq.t < 32;
-  const uint32_t dh = (uint32_t)fq.dh, dl = (uint32_t)fq.dl;
-  // saturation test on the 32-bit results when Z >> t is exact in int32, else on Z
-  const bool v32 = zb - (int)fq.t <= 30;
-  const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << (t & 63));   // used only when t < 32
-  const uint64_t zrange = (uint64_t)(((uint64_t)1 << ((fq.w - 1 + t) & 63)) * 2 - 1);
-  const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
-  const uint32_t tl = (uint32_t)fq.tl;          // pass 1: the window's left shift (window below Ez)
-  const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
-  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
-  const bool partial = nvalid < 8;
-
   // staging: stage s holds y row j0 - 1 + s and r (zm, zp) row j0 - 2 + s
   Stage16<ND>& S = stg[warp];
   const int nyin = kUseY ? ny : 1, nrin = kUseR ? ny : 1;
@@ -335,6 +296,57 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
     return v;
   };
 
+  // the first stages of the ring do not depend on the plan: issued before it is built (nnqcomp and
+  // qcomp's first pass; qcomp's second pass may only narrow the window and loads nothing then)
+  const int nst = j1 - j0 + 2;   // stages with a row that is read: y rows j0 - 1 .. j1
+  const bool early = (PASS1 || q.mode == kNnqcomp) && j0 < j1;
+  auto prologue = [&](auto inttag) {
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+      if (s < nst) issue(s, inttag, s >= 2);
+      else cp_commit();   // the ring's later stages are committed empty: the group count stays the same
+    }
+  };
+  if (early) prologue(std::false_type{});
+  if (threadIdx.x == 0) {
+    build_plan(q, sp);
+    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
+  }
+  __syncthreads();
+  const Plan& p = sp;
+  const Fast fq = make_fast(p, PASS1);
+  Red red = {0, 0, 0};
+  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
+
+  // Z = cy*y + cn*ns + cr*r, the group shifts folded into the coefficients
+  int64_t cy, cn, cr;
+  if (KIND == kJacobi0) {
+    cy = 0; cn = 0; cr = (int64_t)((uint64_t)(int64_t)mw << fq.dh);
+  } else {
+    cy = (int64_t)((uint64_t)(int64_t)c << fq.dh);
+    cn = (int64_t)((uint64_t)(int64_t)nb << fq.dh);
+    cr = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)(1ull << fq.dl) : (int64_t)((uint64_t)(int64_t)mw << fq.dl));
+  }
+  const int32_t cy32 = (int32_t)cy, cn32 = (int32_t)cn, cr32 = (int32_t)cr;
+  const uint32_t t = (uint32_t)fq.t;
+  // |Z| <= 2^zb from the msb bounds of the two groups
+  const int zb = q.two ? max(q.hbits + fq.dh, q.lbits + fq.dl) : q.hbits + fq.dh;
+  // fast: Z exact in int64 (the plan's fast regime); fold: the group shifts folded into 32-bit
+  // coefficients and t < 32, so Z is three mad.wide and the result one funnel shift (else
+  // Z = (H << dh) + (L << dl) from the plain coefficients and the result Z >> t)
+  const bool fast = fq.ok;
+  const bool fold = !VAR && cy == (int32_t)cy && cn == (int32_t)cn && cr == (int32_t)cr && fq.t < 32;
+  const uint32_t dh = (uint32_t)fq.dh, dl = (uint32_t)fq.dl;
+  // saturation test on the 32-bit results when Z >> t is exact in int32, else on Z
+  const bool v32 = zb - (int)fq.t <= 30;
+  const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << (t & 63));   // used only when t < 32
+  const uint64_t zrange = (uint64_t)(((uint64_t)1 << ((fq.w - 1 + t) & 63)) * 2 - 1);
+  const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
+  const uint32_t tl = (uint32_t)fq.tl;          // pass 1: the window's left shift (window below Ez)
+  const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
+  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
+  const bool partial = nvalid < 8;
+
   uint32_t vmax = 0, vmin = 0;                  // packed 16x2 extremes of the results
   uint32_t redo_rows = 0;
   uint64_t ormag = 0;
@@ -346,14 +358,7 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
     auto walk = [&](auto v32tag, auto foldtag, auto inttag) {
       constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
       constexpr bool INT = decltype(inttag)::value;
-      // stages with a row that is read: y rows j0 - 1 .. j1 (stage s = y row j0 - 1 + s); the
-      // ring's later stages are committed empty so that the group count stays the same
-      const int nst = j1 - j0 + 2;
-  #pragma unroll
-      for (int s = 0; s < NS - 1; ++s) {
-        if (s < nst) issue(s, inttag, s >= 2);
-        else cp_commit();
-      }
+      if (!early) prologue(inttag);   // stage s = y row j0 - 1 + s
       // ring slots of stages i, i + 1, i + 2 and i + NS - 1 (= i - 1 mod NS)
       int s0 = 0, s1 = 1, s2 = 2, sn = NS - 1;
       for (int j = j0; j < j1; ++j) {
