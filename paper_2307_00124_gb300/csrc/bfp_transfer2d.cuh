@@ -228,14 +228,6 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const __grid_constant__
   const int rs = P.rs;
   __shared__ Plan sp;
   __shared__ StageR stg[4];
-  if (threadIdx.x == 0) {
-    build_plan(q, sp);
-    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
-  }
-  __syncthreads();
-  const Plan& p = sp;
-  const Fast fq = make_fast(p, PASS1);
-  const EmitC ec = make_emit(fq, q, 1, PASS1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * 256 + lane * 8;
   const int64_t fc = 2 * c0;
@@ -243,8 +235,6 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const __grid_constant__
   const int J0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);
   const int J1 = J0 + rs < ny ? J0 + rs : ny;
   const bool act = c0 < out.ld;
-  Red red = {0, 0, 0};
-  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
   const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
   const bool partial = nvalid < 8;
   // fine columns fc + m, m < 16, beyond nx read as 0 (partial chunks only)
@@ -272,6 +262,28 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const __grid_constant__
     of += f.ld;
     ++jf;
   };
+  // prologue: fine rows 2 J0 .. 2 J0 + 5 in three groups of two; it does not depend on the plan and is
+  // issued before the plan is built (nnqcomp and qcomp's first pass)
+  auto prologue = [&]() {
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      issue(2 * g);
+      issue(2 * g + 1);
+      cp_commit();
+    }
+  };
+  const bool early = (PASS1 || q.mode == kNnqcomp) && J0 < J1;
+  if (early) prologue();
+  if (threadIdx.x == 0) {
+    build_plan(q, sp);
+    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
+  }
+  __syncthreads();
+  const Plan& p = sp;
+  const Fast fq = make_fast(p, PASS1);
+  const EmitC ec = make_emit(fq, q, 1, PASS1);
+  Red red = {0, 0, 0};
+  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
   // h_k = f[2c] + 2 f[2c+1] + f[2c+2] for c = c0 + k of the fine row in `slot`
   auto hrow = [&](int slot, int32_t (&h)[8]) {
     const uint4 a = *reinterpret_cast<const uint4*>(&S.f[slot][4 + 8 * lane]);
@@ -299,13 +311,7 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const __grid_constant__
   } else if (J0 < J1) {
     auto walk = [&](auto v32tag, auto foldtag) {
       constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
-      // prologue: fine rows 2 J0 .. 2 J0 + 5 in three groups of two
-#pragma unroll
-      for (int g = 0; g < 3; ++g) {
-        issue(2 * g);
-        issue(2 * g + 1);
-        cp_commit();
-      }
+      if (!early) prologue();
       cp_wait<2>();
       __syncwarp();
       int32_t hp[8];
@@ -596,14 +602,6 @@ __global__ void __launch_bounds__(128, 6) k_prolong16(const __grid_constant__ Tr
   const int rs = P.rs;
   __shared__ Plan sp;
   __shared__ StageP<ND> stg[4];
-  if (threadIdx.x == 0) {
-    build_plan(q, sp);
-    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
-  }
-  __syncthreads();
-  const Plan& p = sp;
-  const Fast fq = make_fast(p, PASS1);
-  const EmitC ec = make_emit(fq, q, CORR ? -1 : 1, PASS1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * 256 + lane * 8;
   const int64_t C = c0 >> 1;                     // first coarse column of this lane (multiple of 4)
@@ -613,8 +611,6 @@ __global__ void __launch_bounds__(128, 6) k_prolong16(const __grid_constant__ Tr
   const int P0 = (int)(((int64_t)blockIdx.y * 4 + warp) * rs);   // first row pair (fine rows 2P0, 2P0+1)
   const int P1 = min(P0 + rs, (ny + 1) / 2);
   const bool act = c0 < out.ld;
-  Red red = {0, 0, 0};
-  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
   const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
   const bool partial = nvalid < 8;
   // coarse columns C + m (m < 4) beyond d.nx, fine y columns beyond nx: 0 (partial chunks only)
@@ -666,6 +662,25 @@ __global__ void __launch_bounds__(128, 6) k_prolong16(const __grid_constant__ Tr
     ++jc;
     cp_commit();
   };
+  // the first three stages do not depend on the plan: issued before it is built (nnqcomp and qcomp's
+  // first pass)
+  auto prologue = [&]() {
+    issue(0, false);                           // coarse row P0 - 1 only
+    issue(1, true);
+    issue(2, true);
+  };
+  const bool early = (PASS1 || q.mode == kNnqcomp) && P0 < P1;
+  if (early) prologue();
+  if (threadIdx.x == 0) {
+    build_plan(q, sp);
+    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
+  }
+  __syncthreads();
+  const Plan& p = sp;
+  const Fast fq = make_fast(p, PASS1);
+  const EmitC ec = make_emit(fq, q, CORR ? -1 : 1, PASS1);
+  Red red = {0, 0, 0};
+  int32_t* tmp = (PASS1 && p.use_tmp && !p.guarded) ? reinterpret_cast<int32_t*>(q.tmp) : nullptr;
   // coarse columns C - 1 .. C + 3 of the staged row of plane slot pl
   auto dvals = [&](int slot, int pl, int32_t (&dv)[5]) {
     const uint2 u = *reinterpret_cast<const uint2*>(&S.d[slot][pl][4 + 2 * lane]);
@@ -702,9 +717,7 @@ __global__ void __launch_bounds__(128, 6) k_prolong16(const __grid_constant__ Tr
   } else if (P0 < P1) {
     auto walk = [&](auto v32tag, auto foldtag) {
       constexpr bool V32 = decltype(v32tag)::value, FOLD = decltype(foldtag)::value;
-      issue(0, false);                           // coarse row P0 - 1 only
-      issue(1, true);
-      issue(2, true);
+      if (!early) prologue();
       cp_wait<2>();
       __syncwarp();
       int32_t gm[8];
