@@ -66,6 +66,25 @@ __device__ __forceinline__ double scale_pow2(double v, int k, double factor) {
 }
 
 
+// 0.75 v correctly rounded (the centre term of the 3D A'x), computed on the integer pipe: the product of
+// the 53-bit significand m by 3 is exact in 55 bits and is rounded once to 53 bits, to nearest with ties
+// to even, exactly as the IEEE multiply rounds it.  Zero, subnormal, tiny, huge and non-finite v (whose
+// result may leave the normal range) take the rounded multiply, out of line.  Bit for bit
+// __dmul_rn(0.75, v).
+__device__ __forceinline__ double mul_three_quarters(double v) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex < 3 || ex > 2045) return dmul_slow(v, 0.75);
+  const uint64_t M = 3ull * ((bits & ((1ull << 52) - 1)) | (1ull << 52));   // in [3 2^52, 3 2^53)
+  const int sh = (M >> 54) ? 2 : 1;                                          // bits above the 53 kept
+  uint64_t q = M >> sh;
+  const uint64_t rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  int e = ex - 2 + sh;
+  if (q >> 53) { q >>= 1; ++e; }                                             // rounded up to 2^53
+  return __longlong_as_double((long long)((bits & (1ull << 63)) | ((uint64_t)e << 52) | (q & ((1ull << 52) - 1))));
+}
+
 // floor(M 2^sh) for any sh (caller guarantees the fit when sh > 0)
 __device__ __forceinline__ int64_t fshift(int64_t M, int64_t sh) {
   if (sh >= 0) return (int64_t)((uint64_t)M << (sh > 63 ? 63 : sh));

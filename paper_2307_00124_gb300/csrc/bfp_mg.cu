@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(256) k_ir3d(const IrArgs a, const Grid g) {
       s = __dadd_rn(s, at(a.x, g, i, j, k - 1));
       s = __dadd_rn(s, at(a.x, g, i, j, k + 1));
       const int64_t xi = i + g.nx * (j + g.ny * k);
-      const double ax = __dadd_rn(__dmul_rn(a.cdiag, a.x[xi]), -scale_pow2(s, a.nbshift, -a.cnb));
+      const double cx = a.cdiag == 0.75 ? mul_three_quarters(a.x[xi]) : __dmul_rn(a.cdiag, a.x[xi]);
+      const double ax = __dadd_rn(cx, -scale_pow2(s, a.nbshift, -a.cnb));
       const double r = __dsub_rn(scale_pow2(a.b[xi], a.bshift, a.bscale), ax);
       int64_t M = 0, E = -1074;
       if (!split_double(r, M, E)) { bad = true; continue; }
