@@ -14,9 +14,11 @@ bool coarse_of(const bfp_vec* f, const bfp_vec* c) {
   return true;
 }
 
-// rows per warp strip (<= 16: the kernels keep a per-strip mask of general-path rows)
+// Rows per warp strip (<= 16: the kernels keep a per-strip mask of general-path rows): 8 on large
+// levels; below 1024 rows the grid is a few CTAs and a strip's serial row steps set the op's
+// latency, so strips stay at one or two rows there.
 int rows_per_warp(int64_t rows) {
-  return pick_rows(rows >= 1024 ? 8 : (rows >= 256 ? 4 : (rows >= 64 ? 2 : 1)), 16);
+  return pick_rows(rows >= 1024 ? 8 : (rows >= 512 ? 2 : 1), 16);
 }
 
 int32_t launch_checks(const QDesc& d) {

@@ -39,8 +39,39 @@ struct CoarseOp {
   int32_t run;           // on the op at CoarseArgs::run_k: the number of identical solo sweeps (on a
                          // level of <= 32 points, alternating between buffers a and out) it starts
   int64_t c, nb, mw;     // stencil / smoother coefficients
+  // the folded multipliers k0, k1, k2 of the int16 register path (set by set_fold_consts): k_i =
+  // fc[i] 2^dl when bit i of fsel is set, else fc[i] 2^dh; valid while that shift is <= flim[i]
+  int32_t fc[3], flim[3], fsel;
   QDesc q;               // static description (meta pointers unused)
 };
+
+// Host: the folded-multiplier constants of an op from its kind and coefficients.  A coefficient c
+// shifted left by sh stays exact in int32 up to flim = the largest sh <= 30 with (c 2^sh) >> sh == c
+// (the bound only grows down to sh = 0); c = 0 folds at any shift.
+inline void set_fold_consts(CoarseOp& op) {
+  const int32_t c = (int32_t)op.c, nb = (int32_t)op.nb, mw = (int32_t)op.mw;
+  int32_t fc[3] = {0, 0, 0}, fsel = 0;
+  switch (op.kind) {
+    case cJac0: fc[0] = mw; break;
+    case cJac: fc[0] = c; fc[1] = nb; fc[2] = mw; fsel = 4; break;
+    case cRes: fc[0] = c; fc[1] = nb; fc[2] = -1; fsel = 4; break;
+    case cRestrict: fc[0] = 1; break;
+    default: fc[0] = -1; fc[2] = 1; fsel = 4; break;   // prolongation with correction
+  }
+  for (int i = 0; i < 3; ++i) {
+    int lim = 0x7fffffff;
+    if (fc[i] != 0) {
+      lim = 0;
+      for (int sh = 1; sh <= 30; ++sh) {
+        if ((int32_t)((uint32_t)fc[i] << sh) >> sh != fc[i]) break;
+        lim = sh;
+      }
+    }
+    op.fc[i] = fc[i];
+    op.flim[i] = lim;
+  }
+  op.fsel = fsel;
+}
 
 struct CoarseBuf {
   int32_t off;           // byte offset of the (n + 2)^2 padded buffer in dynamic shared memory
@@ -121,15 +152,7 @@ struct CoarseMul {
   uint64_t zrange;      // 2^(w + t): Z in range iff Z - zmin < zrange (unsigned)
 };
 
-// k = c 2^sh when that fits in int32 (c itself fits in int32 by construction)
-__device__ __forceinline__ bool fold_mul(int32_t c, int32_t sh, int32_t& k) {
-  const int32_t s = sh & 31;
-  const int32_t v = (int32_t)((uint32_t)c << s);
-  k = v;
-  return c == 0 || (sh <= 30 && (v >> s) == c);
-}
-
-__device__ __forceinline__ CoarseMul make_mul(int kind, const Fast& f, const CoarseOp& op) {
+__device__ __forceinline__ CoarseMul make_mul(const Fast& f, const CoarseOp& op) {
   CoarseMul m;
   m.k0 = m.k1 = m.k2 = 0;
   m.t = f.t;
@@ -141,13 +164,11 @@ __device__ __forceinline__ CoarseMul make_mul(int kind, const Fast& f, const Coa
   const uint32_t lo = e < 32 ? (1u << (e & 31)) : 0u, hi = e < 32 ? 0u : (1u << ((e - 32) & 31));
   m.zrange = m.clamp ? (((uint64_t)hi << 32) | lo) : 0;
   m.zmin = -(int64_t)(m.zrange >> 1);
-  const int32_t c = (int32_t)op.c, nb = (int32_t)op.nb, mw = (int32_t)op.mw;
-  bool ok;
-  if (kind == cJac0) ok = fold_mul(mw, f.dh, m.k0);
-  else if (kind == cJac) ok = fold_mul(c, f.dh, m.k0) & fold_mul(nb, f.dh, m.k1) & fold_mul(mw, f.dl, m.k2);
-  else if (kind == cRes) ok = fold_mul(c, f.dh, m.k0) & fold_mul(nb, f.dh, m.k1) & fold_mul(-1, f.dl, m.k2);
-  else if (kind == cRestrict) ok = fold_mul(1, f.dh, m.k0);
-  else ok = fold_mul(-1, f.dh, m.k0) & fold_mul(1, f.dl, m.k2);
+  const int32_t s0 = (op.fsel & 1) ? f.dl : f.dh, s1 = (op.fsel & 2) ? f.dl : f.dh, s2 = (op.fsel & 4) ? f.dl : f.dh;
+  m.k0 = (int32_t)((uint32_t)op.fc[0] << (s0 & 31));
+  m.k1 = (int32_t)((uint32_t)op.fc[1] << (s1 & 31));
+  m.k2 = (int32_t)((uint32_t)op.fc[2] << (s2 & 31));
+  const bool ok = s0 <= op.flim[0] && s1 <= op.flim[1] && s2 <= op.flim[2];
   m.ok = (ok && f.ok && f.w <= 32) ? 1 : 0;
   return m;
 }
@@ -336,7 +357,7 @@ __device__ __forceinline__ void lean_exec(const CoarseOp& op, const CoarseLean& 
   ex.f.tl = 0;                  // the on-chip cycle keeps no qcomp window
   ex.f.w = w;
   ex.f.clamp = (!pass1 && clamp) ? 1 : 0;
-  ex.m = make_mul(op.kind, ex.f, op);
+  ex.m = make_mul(ex.f, op);
 }
 
 __device__ __forceinline__ bool lean_first(const CoarseOp& op, int64_t ea64, int64_t na, int64_t eb64, int64_t nb,
@@ -558,7 +579,7 @@ __global__ void __launch_bounds__(32) k_sweep_run(const __grid_constant__ SweepR
     if (!lean) {
       build_plan_v(op.q, ea, na, eb, nb, P);
       ex.f = make_fast(P, qc);
-      ex.m = make_mul(op.kind, ex.f, op);
+      ex.m = make_mul(ex.f, op);
     }
     if (a.var) ex.m.ok = 0;   // folded multipliers need constant coefficients
     // Z on the register path (folded multipliers: the same value as (H << dh) + (L << dl))
@@ -584,7 +605,7 @@ __global__ void __launch_bounds__(32) k_sweep_run(const __grid_constant__ SweepR
         if (lean0) build_plan_v(op.q, ea, na, eb, nb, P);
         plan_from_mu(P, (int64_t)kk);
         ex.f = make_fast(P, false);
-        ex.m = make_mul(op.kind, ex.f, op);
+        ex.m = make_mul(ex.f, op);
       }
       if (a.var) ex.m.ok = 0;
     }
@@ -721,7 +742,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const __gri
       __syncwarp();
       built = true;
       ex.f = make_fast(*pp, qc);
-      ex.m = make_mul(op.kind, ex.f, op);
+      ex.m = make_mul(ex.f, op);
     }
     const int i0 = solo ? (lane & 15) : lane, istep = solo ? 16 : 32;
     const int j0 = solo ? (lane >> 4) : warp, jstep = solo ? 2 : nw;
@@ -751,7 +772,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_vcycle(const __gri
         }
         __syncwarp();
         ex.f = make_fast(*pp, false);
-        ex.m = make_mul(op.kind, ex.f, op);
+        ex.m = make_mul(ex.f, op);
       }
     }
     coarse_dispatch<T, false>(sm, op, bufs, ex, pp, i0, istep, j0, jstep, key, nrm, sat);

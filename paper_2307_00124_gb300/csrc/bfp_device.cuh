@@ -172,16 +172,29 @@ __device__ __forceinline__ int64_t group_exp(int64_t c, int32_t ka, int32_t kb, 
   return c + (ka ? ea : 0) + (kb ? eb : 0);
 }
 
-// msb(gamma_m) + e_gamma for gamma = sum of two non-negative dyadics (exact).
+// bitlen(a1 2^diff + a2) + 1 + e2 for 0 <= diff < 64 in 128-bit arithmetic (out of line: the sums
+// that do not fit 63 bits)
+static __device__ __noinline__ int64_t gamma_msb_wide(uint64_t a1, uint64_t a2, int64_t diff, int64_t e2) {
+  const u128 s = ((u128)a1 << diff) + (u128)a2;
+  return (int64_t)bitlen_u128(s) + 1 + e2;
+}
+
+// msb(gamma_m) + e_gamma for gamma = sum of two non-negative dyadics (exact).  The terms are
+// ordered so that the first is non-zero and the second is zero or has the lower exponent; a second
+// term below 2^e1 (gap >= 64) cannot change the bit length; otherwise the aligned sum is taken in
+// 64 bits when it stays below 2^63, else in 128 bits.
 __device__ __forceinline__ bool gamma_msb(uint64_t a1, int64_t e1, uint64_t a2, int64_t e2, int64_t* out) {
-  if (a1 == 0 && a2 == 0) return false;
-  if (a1 == 0) { a1 = a2; e1 = e2; a2 = 0; }
-  if (a2 == 0) { *out = (int64_t)bitlen_u128((u128)a1) + 1 + e1; return true; }
-  if (e1 < e2) { uint64_t ta = a1; a1 = a2; a2 = ta; int64_t te = e1; e1 = e2; e2 = te; }
-  int64_t diff = e1 - e2;
-  if (diff >= 64) { *out = (int64_t)bitlen_u128((u128)a1) + 1 + e1; return true; }  // a2 2^e2 < 2^e1
-  u128 s = ((u128)a1 << diff) + (u128)a2;
-  *out = (int64_t)bitlen_u128(s) + 1 + e2;
+  const bool swp = a1 == 0 || (a2 != 0 && e1 < e2);
+  const uint64_t A = swp ? a2 : a1, Bv = swp ? a1 : a2;
+  const int64_t EA = swp ? e2 : e1, EB = swp ? e1 : e2;
+  if (A == 0) return false;
+  const int64_t diff = EA - EB;
+  if (Bv == 0 || diff >= 64) { *out = (int64_t)(65 - __clzll((long long)A)) + EA; return true; }
+  if (diff <= 62 && (A >> (62 - diff)) == 0 && (Bv >> 62) == 0) {
+    *out = (int64_t)(65 - __clzll((long long)((A << diff) + Bv))) + EB;
+    return true;
+  }
+  *out = gamma_msb_wide(A, Bv, diff, EB);
   return true;
 }
 

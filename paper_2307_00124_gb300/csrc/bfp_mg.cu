@@ -523,6 +523,7 @@ int32_t make_coarse_op(const bfp_hierarchy* h, int l, int kind, int a, int b, in
   d.w_tmp = w + capped_wadd(rule, h->o.w_add_max);
   d.use_tmp = 0;
   op.solo = h->lv[l + (kind == cRestrict ? 1 : 0)].n <= 15 ? 1 : 0;   // output level size
+  set_fold_consts(op);
   *res = op;
   return BFP_OK;
 }
@@ -618,6 +619,7 @@ int32_t sweep_run(bfp_hierarchy* h, int k, const bfp_vec* r, const bfp_vec* y, c
       op.q.w_out = w;
       op.q.w_tmp = w + capped_wadd(rule, h->o.w_add_max);
       op.q.use_tmp = 0;
+      set_fold_consts(op);
       if (t == 1) a.s = sh;
     }
     a.var = 1;
