@@ -267,6 +267,31 @@ __device__ __forceinline__ void plan_from_mu(Plan& p, int64_t key) {
   p.narrow = p.use_tmp && !p.guarded && !p.overflow && !p.underflow;
 }
 
+// The meta words a plan reads: exponent and max |m| of each input, and the first pass's mu* key for
+// qcomp's second pass (absent inputs read 0).  Loaded by one thread with loads that stay where they
+// are written: the staged kernels issue them ahead of their ring's first copies, so the round trip
+// overlaps those copies instead of following them.
+struct MetaIn {
+  int64_t ea, na, eb, nb, mu;
+};
+__device__ __forceinline__ int64_t ld_meta(const int64_t* p) {
+  int64_t v;
+  asm volatile("ld.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ MetaIn load_meta(const QDesc& q, bool with_mu) {
+  MetaIn m = {0, 0, 0, 0, 0};
+  if (q.meta_a) { m.ea = ld_meta(q.meta_a); m.na = ld_meta(q.meta_a + 1); }
+  if (q.meta_b) { m.eb = ld_meta(q.meta_b); m.nb = ld_meta(q.meta_b + 1); }
+  if (with_mu) m.mu = ld_meta(q.meta_out + kMetaMu);
+  return m;
+}
+// build_plan from preloaded meta words, then plan_from_mu for qcomp's second pass
+__device__ __forceinline__ void build_plan_m(const QDesc& q, const MetaIn& m, bool with_mu, Plan& p) {
+  build_plan_v(q, m.ea, m.na, m.eb, m.nb, p);
+  if (with_mu) plan_from_mu(p, m.mu);
+}
+
 // Register-resident fast path of one op: valid when the exact integer
 // Z = (H << dh) + (L << dl) fits in int64 (no wide / guarded combine) and the
 // output (or window) exponent is at or above Ez, so every element needs only

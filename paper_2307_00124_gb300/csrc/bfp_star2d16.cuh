@@ -307,11 +307,10 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
       else cp_commit();   // the ring's later stages are committed empty: the group count stays the same
     }
   };
+  const bool with_mu = !PASS1 && q.mode == kQcomp;
+  const MetaIn mi = threadIdx.x == 0 ? load_meta(q, with_mu) : MetaIn{0, 0, 0, 0, 0};
   if (early) prologue(std::false_type{});
-  if (threadIdx.x == 0) {
-    build_plan(q, sp);
-    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
-  }
+  if (threadIdx.x == 0) build_plan_m(q, mi, with_mu, sp);
   __syncthreads();
   const Plan& p = sp;
   const Fast fq = make_fast(p, PASS1);

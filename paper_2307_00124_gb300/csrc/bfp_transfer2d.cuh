@@ -273,11 +273,10 @@ __global__ void __launch_bounds__(128, 6) k_restrict2d16(const __grid_constant__
     }
   };
   const bool early = (PASS1 || q.mode == kNnqcomp) && J0 < J1;
+  const bool with_mu = !PASS1 && q.mode == kQcomp;
+  const MetaIn mi = threadIdx.x == 0 ? load_meta(q, with_mu) : MetaIn{0, 0, 0, 0, 0};
   if (early) prologue();
-  if (threadIdx.x == 0) {
-    build_plan(q, sp);
-    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
-  }
+  if (threadIdx.x == 0) build_plan_m(q, mi, with_mu, sp);
   __syncthreads();
   const Plan& p = sp;
   const Fast fq = make_fast(p, PASS1);
@@ -670,11 +669,10 @@ __global__ void __launch_bounds__(128, 6) k_prolong16(const __grid_constant__ Tr
     issue(2, true);
   };
   const bool early = (PASS1 || q.mode == kNnqcomp) && P0 < P1;
+  const bool with_mu = !PASS1 && q.mode == kQcomp;
+  const MetaIn mi = threadIdx.x == 0 ? load_meta(q, with_mu) : MetaIn{0, 0, 0, 0, 0};
   if (early) prologue();
-  if (threadIdx.x == 0) {
-    build_plan(q, sp);
-    if (!PASS1 && q.mode == kQcomp) plan_from_mu(sp, q.meta_out[kMetaMu]);
-  }
+  if (threadIdx.x == 0) build_plan_m(q, mi, with_mu, sp);
   __syncthreads();
   const Plan& p = sp;
   const Fast fq = make_fast(p, PASS1);
