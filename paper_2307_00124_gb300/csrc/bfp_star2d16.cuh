@@ -45,6 +45,13 @@ __device__ __forceinline__ int32_t pk_get(const Pk8& p, int k) {
   return (k & 1) ? ((int32_t)word >> 16) : (int32_t)(int16_t)(word & 0xffffu);
 }
 
+// c + the int16 mantissa k of p (sign-extended), one dp2a (FMA pipe): unpack and add in one instruction
+__device__ __forceinline__ int32_t add_half(const Pk8& p, int k, int32_t c) {
+  int32_t d;
+  asm("dp2a.lo.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(p.w[k >> 1]), "r"((k & 1) ? 0x0100 : 0x0001), "r"(c));
+  return d;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -430,8 +437,8 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
               } else {
                 const int32_t wk = k == 0 ? wv : yv[k - 1];
                 const int32_t ek = k == 7 ? ev : yv[k + 1];
-                int32_t ns = wk + ek + pk_get(ym, k) + pk_get(yp, k);
-                if (ND == 3) ns += pk_get(zm, k) + pk_get(zp, k);
+                int32_t ns = add_half(yp, k, add_half(ym, k, wk + ek));
+                if (ND == 3) ns = add_half(zp, k, add_half(zm, k, ns));
                 if (FOLD) {
                   Z = madw(cn32, ns, mulw(cy32, yv[k]));
                   if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
