@@ -15,9 +15,12 @@ bool coarse_of(const bfp_vec* f, const bfp_vec* c) {
 }
 
 // Rows per warp strip (<= 16: the kernels keep a per-strip mask of general-path rows): 8 on large
-// levels; below 1024 rows the grid is a few CTAs and a strip's serial row steps set the op's
-// latency, so strips stay at one or two rows there.
+// levels; below 1024 rows one op's grid is a few CTAs and a strip's serial row steps set the op's
+// latency, so strips stay at one or two rows there.  A launch recorded for a batched solve runs
+// over many instances at once and fills the GPU anyway: taller strips there (fewer CTAs, each
+// planning and committing once).
 int rows_per_warp(int64_t rows) {
+  if (launch_recorder()) return pick_rows(rows >= 1024 ? 8 : (rows >= 256 ? 4 : (rows >= 64 ? 2 : 1)), 16);
   return pick_rows(rows >= 1024 ? 8 : (rows >= 512 ? 2 : 1), 16);
 }
 
