@@ -246,29 +246,31 @@ __global__ void __launch_bounds__(128, 8) k_star2d(const VIn y, const VIn r, con
   if (!PASS1) op_epilogue(q, p);
 }
 
-// int16 staged kernel, 2D or 3D (zero_accumulators already issued); rs rows per warp
-template <int KIND, int ND>
+// staged kernel (int16 mantissas, 2D or 3D; int32 mantissas, 2D), zero_accumulators already issued;
+// rs rows per warp
+template <int KIND, int ND, class T = int16_t>
 inline int32_t launch_star16(const VIn& y, const VIn& r, int32_t c, int32_t nb, int32_t mw, const QDesc& q,
                              const VOut& o, int rs, cudaStream_t s) {
   static bool carved = false;   // the staging ring wants the shared-memory carveout (7 CTAs / SM in 2D, 5 in 3D)
   if (!carved) {
-    cudaFuncSetAttribute(k_star16<KIND, true, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_star16<KIND, false, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_star16<KIND, true, ND, false, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_star16<KIND, false, ND, false, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if constexpr (ND == 2) {
-      cudaFuncSetAttribute(k_star16<KIND, true, 2, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      cudaFuncSetAttribute(k_star16<KIND, false, 2, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_star16<KIND, true, 2, false, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_star16<KIND, false, 2, false, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     carved = true;
   }
+  constexpr int64_t kCols = sizeof(T) == 4 ? kS16Cols / 2 : kS16Cols;   // 16 bytes per lane and row
   const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
-  const int64_t chunks = (o.ld + kS16Cols - 1) / kS16Cols;
+  const int64_t chunks = (o.ld + kCols - 1) / kCols;
   const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1),
                (unsigned)(ND == 3 ? o.nz : 1));
   const Star16P P{y, r, c, nb, mw, q, o, rs, VarRow{}};
   if constexpr (ND == 2) {   // recordable for batched solves
     if (q.mode == kQcomp)
-      launch_rec<Star16P, &k_star16<KIND, true, 2>, &k_star16<KIND, true, 2, false, true>>(g, 128, 0, s, P);
-    launch_rec<Star16P, &k_star16<KIND, false, 2>, &k_star16<KIND, false, 2, false, true>>(g, 128, 0, s, P);
+      launch_rec<Star16P, &k_star16<KIND, true, 2, false, false, T>, &k_star16<KIND, true, 2, false, true, T>>(g, 128, 0, s, P);
+    launch_rec<Star16P, &k_star16<KIND, false, 2, false, false, T>, &k_star16<KIND, false, 2, false, true, T>>(g, 128, 0, s, P);
   } else {
     if (q.mode == kQcomp) k_star16<KIND, true, ND><<<g, 128, 0, s>>>(P, nullptr);
     k_star16<KIND, false, ND><<<g, 128, 0, s>>>(P, nullptr);
@@ -349,6 +351,10 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   if (sizeof(T) == 2 && !o.is32) return launch_star16<KIND, 2>(y, r, c, nb, mw, q, o, rs, s);
+  // int32 mantissas of at most 30 bits in y and r (one storage class: the callers send mixed storage to
+  // the generic row kernel) and an int32 output: the staged kernel with 128-column chunks (the range
+  // test of its register path needs w_out <= 30)
+  if (sizeof(T) == 4 && o.is32 && nsfit && q.w_out <= 30) return launch_star16<KIND, 2, int32_t>(y, r, c, nb, mw, q, o, rs, s);
   if (q.mode == kQcomp) k_star2d<T, KIND, true><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, nsfit ? 1 : 0);
   k_star2d<T, KIND, false><<<grid, 128, 0, s>>>(y, r, c, nb, mw, q, o, rs, nsfit ? 1 : 0);
   note_launches(q.mode == kQcomp ? 2 : 1);

@@ -52,6 +52,12 @@ __device__ __forceinline__ int32_t add_half(const Pk8& p, int k, int32_t c) {
   return d;
 }
 
+// mantissa k of a lane's 16 bytes: int16 (k < 8) or int32 (k < 4) storage
+template <bool W32>
+__device__ __forceinline__ int32_t vget(const Pk8& p, int k) {
+  return W32 ? (int32_t)p.w[k & 3] : pk_get(p, k);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -116,19 +122,20 @@ struct VarRow {
   int32_t s;
 };
 
-// Inputs of one lane's 8 outputs, for the out-of-line general path.
-struct Row8 {
-  int32_t y[8], ym[8], yp[8], r[8], zm[8], zp[8];
+// Inputs of one lane's NV outputs, for the out-of-line general path.
+template <int NV>
+struct RowIn {
+  int32_t y[NV], ym[NV], yp[NV], r[NV], zm[NV], zp[NV];
   int32_t wv, ev;
 };
 
-// The general path for one lane's 8 outputs of row j of plane kz: reloads its
+// The general path for one lane's NV outputs of row j of plane kz (mantissas of type T): reloads its
 // inputs from global memory (zero outside the grid) and quantises through quantvf.
-template <bool PASS1, int KIND, int ND, bool VAR>
+template <bool PASS1, int KIND, int ND, bool VAR, class T = int16_t, int NV = 8>
 __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p, const Fast& fq, const VOut& out,
                                        int32_t* tmp, int64_t j, int64_t kz, int64_t c0, Red& red, int32_t c,
                                        int32_t nb, int32_t mw, const VarRow& va) {
-  Row8 in;
+  RowIn<NV> in;
   int32_t kf[4][8], qv[8];
   if (VAR) {
     const int64_t row = kz * out.ny + j;
@@ -138,15 +145,15 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
   }
   const int64_t ny = out.ny, row = kz * ny + j;
   if (KIND != kJacobi0) {
-    ldv<int16_t, 8>(y, row, c0, in.y);
-    ldv<int16_t, 8>(y, j > 0 ? row - 1 : -1, c0, in.ym);
-    ldv<int16_t, 8>(y, j + 1 < ny ? row + 1 : -1, c0, in.yp);
-    ldv<int16_t, 8>(y, ND == 3 && kz > 0 ? row - ny : -1, c0, in.zm);
-    ldv<int16_t, 8>(y, ND == 3 && kz + 1 < out.nz ? row + ny : -1, c0, in.zp);
-    in.wv = (int32_t)ld1<int16_t>(y, row, c0 - 1);
-    in.ev = (int32_t)ld1<int16_t>(y, row, c0 + 8);
+    ldv<T, NV>(y, row, c0, in.y);
+    ldv<T, NV>(y, j > 0 ? row - 1 : -1, c0, in.ym);
+    ldv<T, NV>(y, j + 1 < ny ? row + 1 : -1, c0, in.yp);
+    ldv<T, NV>(y, ND == 3 && kz > 0 ? row - ny : -1, c0, in.zm);
+    ldv<T, NV>(y, ND == 3 && kz + 1 < out.nz ? row + ny : -1, c0, in.zp);
+    in.wv = (int32_t)ld1<T>(y, row, c0 - 1);
+    in.ev = (int32_t)ld1<T>(y, row, c0 + NV);
   }
-  if (KIND != kApply) ldv<int16_t, 8>(r, row, c0, in.r);
+  if (KIND != kApply) ldv<T, NV>(r, row, c0, in.r);
   auto hl = [&](int k, int64_t& H, int64_t& L) {
     if (VAR) {
       if (KIND == kJacobi0) {
@@ -156,7 +163,7 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
       }
       const int64_t yk = in.y[k];
       const int64_t ay = (int64_t)kf[0][k] * (yk - (k == 0 ? in.wv : in.y[k - 1])) +
-                         (int64_t)kf[1][k] * (yk - (k == 7 ? in.ev : in.y[k + 1])) +
+                         (int64_t)kf[1][k] * (yk - (k == NV - 1 ? in.ev : in.y[k + 1])) +
                          (int64_t)kf[2][k] * (yk - in.ym[k]) + (int64_t)kf[3][k] * (yk - in.yp[k]);
       if (KIND == kApply) { H = ay; L = 0; }
       else if (KIND == kResidual) { H = ay; L = -(int64_t)in.r[k]; }
@@ -169,12 +176,12 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
       return;
     }
     const int64_t wk = k == 0 ? in.wv : in.y[k - 1];
-    const int64_t ek = k == 7 ? in.ev : in.y[k + 1];
+    const int64_t ek = k == NV - 1 ? in.ev : in.y[k + 1];
     const int64_t ns = wk + ek + in.ym[k] + in.yp[k] + in.zm[k] + in.zp[k];
     H = (int64_t)c * (int64_t)in.y[k] + (int64_t)nb * ns;
     L = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)in.r[k] : (int64_t)mw * (int64_t)in.r[k]);
   };
-  quantvf<PASS1, 8>(hl, p, fq, out, tmp, row, c0, red);
+  quantvf<PASS1, NV>(hl, p, fq, out, tmp, row, c0, red);
 }
 
 // Per-warp staging ring.  A y row is 136 words: 3 pad words, the west halo
@@ -208,12 +215,19 @@ struct Star16P {
 };
 
 
-// grid: (256-column chunks, strips of 4 * rs rows, planes); B: a batched launch of 2D ops, grid z the
-// instance, parameters Pb[z]
-template <int KIND, bool PASS1, int ND, bool VAR = false, bool B = false>
+// grid: (column chunks of 32 lanes x 16 bytes, strips of 4 * rs rows, planes); B: a batched launch of 2D
+// ops, grid z the instance, parameters Pb[z].  T: the mantissa storage of y, r and the output, int16
+// (8 per lane, 256-column chunks) or int32 (4 per lane, 128-column chunks; 2D constant-coefficient ops
+// with mantissas of at most 30 bits, so the neighbour sum is exact in int32)
+template <int KIND, bool PASS1, int ND, bool VAR = false, bool B = false, class T = int16_t>
 __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const __grid_constant__ Star16P P1,
                                                                  const Star16P* __restrict__ Pb) {
   static_assert(!B || ND == 2, "batched launches are 2D");
+  constexpr bool W32 = sizeof(T) == 4;
+  static_assert(!W32 || (ND == 2 && !VAR), "int32 mantissas: 2D constant-coefficient ops");
+  constexpr int NV = W32 ? 4 : 8;                 // mantissas per lane and row (16 bytes)
+  constexpr int kCols = 32 * NV;                  // columns per warp chunk
+  constexpr int64_t kEs = sizeof(T);              // bytes per mantissa
   pdl_wait();
   const Star16P& P = B ? Pb[blockIdx.z] : P1;
   const VIn& y = P.y;
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   __shared__ Plan sp;
   __shared__ Stage16<ND> stg[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t c0 = (int64_t)blockIdx.x * kS16Cols + lane * 8;
+  const int64_t c0 = (int64_t)blockIdx.x * kCols + lane * NV;
   const int ny = (int)out.ny;
   const int kz = ND == 3 ? (int)blockIdx.z : 0;
   const int64_t rowoff = (int64_t)kz * ny;        // global row of the plane's row 0
@@ -239,22 +253,23 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   Stage16<ND>& S = stg[warp];
   const int nyin = kUseY ? ny : 1, nrin = kUseR ? ny : 1;
   const bool ycol = kUseY && c0 < y.nx && c0 < y.ld, rcol = kUseR && c0 < r.nx && c0 < r.ld;
-  const int16_t* ybase = kUseY ? reinterpret_cast<const int16_t*>(y.m) : nullptr;
-  const int16_t* rbase = kUseR ? reinterpret_cast<const int16_t*>(r.m) : nullptr;
-  // halo pairs: lane 0 copies (c0-2, c0-1) into word 3, lane 31 (c0+8, c0+9) into word 132
-  const int64_t ecol = lane == 0 ? c0 - 2 : c0 + 8;
-  const bool eok = kUseY && (lane == 0 ? (c0 >= 2 && c0 - 1 < y.nx) : (lane == 31 && c0 + 8 < y.nx));
+  const T* ybase = kUseY ? reinterpret_cast<const T*>(y.m) : nullptr;
+  const T* rbase = kUseR ? reinterpret_cast<const T*>(r.m) : nullptr;
+  // halo words: lane 0 copies (c0-2, c0-1) (int16; int32: c0-1) into word 3, lane 31 (c0+8, c0+9)
+  // (int32: c0+4) into word 132
+  const int64_t ecol = lane == 0 ? c0 - (W32 ? 1 : 2) : c0 + NV;
+  const bool eok = kUseY && (lane == 0 ? (c0 >= (W32 ? 1 : 2) && c0 - 1 < y.nx) : (lane == 31 && c0 + NV < y.nx));
   const int eword = lane == 0 ? 3 : kRowWords - 4;
   // the next stage to issue: y row jy at byte offset oy, r row jy - 1 at byte offset orr (rows
   // outside the grid and lanes past the row are zero-filled)
   int jy = j0 - 1;
-  int64_t oy = kUseY ? ((rowoff + jy) * y.ld + c0) * 2 : 0, orr = kUseR ? ((rowoff + jy - 1) * r.ld + c0) * 2 : 0;
-  const int64_t ystride = kUseY ? y.ld * 2 : 0, rstride = kUseR ? r.ld * 2 : 0;
+  int64_t oy = kUseY ? ((rowoff + jy) * y.ld + c0) * kEs : 0, orr = kUseR ? ((rowoff + jy - 1) * r.ld + c0) * kEs : 0;
+  const int64_t ystride = kUseY ? y.ld * kEs : 0, rstride = kUseR ? r.ld * kEs : 0;
   // 3D: row jy - 1 of planes kz - 1 and kz + 1 (offsets used only when that plane exists)
   const bool zmok = ND == 3 && kUseY && kz > 0, zpok = ND == 3 && kUseY && kz + 1 < (int)out.nz;
   int64_t ozm = ND == 3 && kUseY ? ((rowoff - ny + jy - 1) * y.ld + c0) * 2 : 0;
   const int64_t zdelta = 2 * (int64_t)ny * y.ld * 2;
-  const int64_t edelta = (ecol - c0) * 2;
+  const int64_t edelta = (ecol - c0) * kEs;
   const bool edge_lane = lane == 0 || lane == 31;
   const uint32_t ybytes = 16u, rbytes = 16u;
   const char* yb = reinterpret_cast<const char*>(ybase);
@@ -347,18 +362,19 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   const bool v32 = zb - (int)fq.t <= 30;
   const int64_t zmin = (int64_t)((uint64_t)(-(1ll << (fq.w - 1))) << (t & 63));   // used only when t < 32
   const uint64_t zrange = (uint64_t)(((uint64_t)1 << ((fq.w - 1 + t) & 63)) * 2 - 1);
-  const int sh = 32 - fq.w;                     // decr to fq.w bits (pass 1 window)
+  const int sh = fq.w < 32 ? 32 - fq.w : 0;    // decr to fq.w bits (pass 1 window; wider windows are not kept)
   const uint32_t tl = (uint32_t)fq.tl;          // pass 1: the window's left shift (window below Ez)
   const uint32_t half = 1u << ((fq.w - 1) & 31);   // v in X_w iff v + 2^(w-1) in [0, 2^w)
-  const int nvalid = (int)(out.nx - c0 < 8 ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : 8);
-  const bool partial = nvalid < 8;
+  const int nvalid = (int)(out.nx - c0 < NV ? (out.nx - c0 < 0 ? 0 : out.nx - c0) : NV);
+  const bool partial = nvalid < NV;
 
-  uint32_t vmax = 0, vmin = 0;                  // packed 16x2 extremes of the results
+  uint32_t vmax = 0, vmin = 0;                  // packed 16x2 extremes of the results (int16)
+  int32_t imax = 0, imin = 0;                   // extremes of the results (int32)
   uint32_t redo_rows = 0;
   uint64_t ormag = 0;
   if (!PASS1 && p.narrow) {
     for (int j = j0; j < j1; ++j)
-      if (act) narrowv<8>(reinterpret_cast<const int32_t*>(q.tmp), p, out, rowoff + j, c0, red);
+      if (act) narrowv<NV>(reinterpret_cast<const int32_t*>(q.tmp), p, out, rowoff + j, c0, red);
   } else if (j0 < j1) {
     // the row walk, instantiated for both saturation tests (a uniform choice per CTA)
     auto walk = [&](auto v32tag, auto foldtag, auto inttag) {
@@ -382,21 +398,27 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
         cp_wait<NS - 3>();                        // stages <= i + 2 have landed (own copies)
         __syncwarp();                             // ... and the other lanes' (neighbours, halo)
         Pk8 ym, yc, yp, rc, zm, zp;
-        int32_t yv[8], wv = 0, ev = 0;
+        int32_t yv[NV], wv = 0, ev = 0;
         if (kUseY) {
           ym = rd(*reinterpret_cast<const uint4*>(&S.y[s0][4 + 4 * lane]));
           yc = rd(*reinterpret_cast<const uint4*>(&S.y[s1][4 + 4 * lane]));
           yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
   #pragma unroll
-          for (int k = 0; k < 8; ++k) yv[k] = pk_get(yc, k);
+          for (int k = 0; k < NV; ++k) yv[k] = vget<W32>(yc, k);
           if (!INT && partial) {   // padding columns may hold anything: the east neighbour of the last column is 0
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+            for (int k = 0; k < NV; ++k)
               if (k >= nvalid) yv[k] = 0;
           }
-          const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
-          wv = row[7 + 8 * lane];                 // column c0 - 1
-          ev = row[16 + 8 * lane];                // column c0 + 8
+          if constexpr (W32) {
+            const int32_t* roww = reinterpret_cast<const int32_t*>(&S.y[s1][0]);
+            wv = roww[3 + 4 * lane];              // column c0 - 1
+            ev = roww[8 + 4 * lane];              // column c0 + 4
+          } else {
+            const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
+            wv = row[7 + 8 * lane];               // column c0 - 1
+            ev = row[16 + 8 * lane];              // column c0 + 8
+          }
           if constexpr (ND == 3) {
             zm = rd(S.zm[s2][lane]);
             zp = rd(S.zp[s2][lane]);
@@ -409,43 +431,48 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
         s2 = s2 + 1 == NS ? 0 : s2 + 1;
         if (INT || act) {
           bool redo = !fast;
-          int32_t o[8];
+          int32_t o[NV];
           bool ovf = false;
           if (fast) {
   #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < NV; ++k) {
               int64_t Z;
               if constexpr (VAR) {
                 if (KIND == kJacobi0) {
-                  Z = (int64_t)((uint64_t)mulw(qv[k], pk_get(rc, k)) << dh);
+                  Z = (int64_t)((uint64_t)mulw(qv[k], vget<W32>(rc, k)) << dh);
                 } else {
                   const int32_t yk = yv[k];
                   int64_t ay = mulw(kf[0][k], yk - (k == 0 ? wv : yv[k - 1]));
-                  ay = madw(kf[1][k], yk - (k == 7 ? ev : yv[k + 1]), ay);
-                  ay = madw(kf[2][k], yk - pk_get(ym, k), ay);
-                  ay = madw(kf[3][k], yk - pk_get(yp, k), ay);
+                  ay = madw(kf[1][k], yk - (k == NV - 1 ? ev : yv[k + 1]), ay);
+                  ay = madw(kf[2][k], yk - vget<W32>(ym, k), ay);
+                  ay = madw(kf[3][k], yk - vget<W32>(yp, k), ay);
                   int64_t H = ay, L = 0;
-                  if (KIND == kResidual) L = -(int64_t)pk_get(rc, k);
+                  if (KIND == kResidual) L = -(int64_t)vget<W32>(rc, k);
                   if (KIND == kJacobi) {
                     H = (int64_t)((uint64_t)(int64_t)yk << va.s) - (int64_t)qv[k] * ay;
-                    L = mulw(qv[k], pk_get(rc, k));
+                    L = mulw(qv[k], vget<W32>(rc, k));
                   }
                   Z = (int64_t)((uint64_t)H << dh) + (int64_t)((uint64_t)L << dl);
                 }
               } else if (KIND == kJacobi0) {
-                Z = FOLD ? mulw(cr32, pk_get(rc, k)) : (int64_t)((uint64_t)mulw(mw, pk_get(rc, k)) << dh);
+                Z = FOLD ? mulw(cr32, vget<W32>(rc, k)) : (int64_t)((uint64_t)mulw(mw, vget<W32>(rc, k)) << dh);
               } else {
                 const int32_t wk = k == 0 ? wv : yv[k - 1];
-                const int32_t ek = k == 7 ? ev : yv[k + 1];
-                int32_t ns = add_half(yp, k, add_half(ym, k, wk + ek));
-                if (ND == 3) ns = add_half(zp, k, add_half(zm, k, ns));
+                const int32_t ek = k == NV - 1 ? ev : yv[k + 1];
+                int32_t ns;
+                if constexpr (W32) {
+                  ns = wk + ek + vget<W32>(ym, k) + vget<W32>(yp, k);
+                } else {
+                  ns = add_half(yp, k, add_half(ym, k, wk + ek));
+                  if (ND == 3) ns = add_half(zp, k, add_half(zm, k, ns));
+                }
                 if (FOLD) {
                   Z = madw(cn32, ns, mulw(cy32, yv[k]));
-                  if (KIND != kApply) Z = madw(cr32, pk_get(rc, k), Z);
+                  if (KIND != kApply) Z = madw(cr32, vget<W32>(rc, k), Z);
                 } else {
                   const int64_t H = madw(nb, ns, mulw(c, yv[k]));
-                  const int64_t L = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)pk_get(rc, k)
-                                                                              : mulw(mw, pk_get(rc, k)));
+                  const int64_t L = KIND == kApply ? 0 : (KIND == kResidual ? -(int64_t)vget<W32>(rc, k)
+                                                                              : mulw(mw, vget<W32>(rc, k)));
                   Z = (int64_t)((uint64_t)H << dh) + (int64_t)((uint64_t)L << dl);
                 }
               }
@@ -461,14 +488,14 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
             }
             if (!INT && partial) {
   #pragma unroll
-              for (int k = 0; k < 8; ++k)
+              for (int k = 0; k < NV; ++k)
                 if (k >= nvalid) o[k] = 0;
             }
             if (!PASS1 && fq.clamp) {
               if (V32) {
                 uint32_t acc = 0;
   #pragma unroll
-                for (int k = 0; k < 8; ++k) acc |= (uint32_t)o[k] + half;
+                for (int k = 0; k < NV; ++k) acc |= (uint32_t)o[k] + half;
                 redo = (acc >> fq.w) != 0u;
               } else {
                 redo = ovf;
@@ -482,14 +509,19 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
             if (tmp) {
               int4* d = reinterpret_cast<int4*>(tmp + (rowoff + j) * out.ld + c0);
               d[0] = make_int4(o[0], o[1], o[2], o[3]);
-              d[1] = make_int4(o[4], o[5], o[6], o[7]);
+              if constexpr (!W32) d[1] = make_int4(o[NV > 4 ? 4 : 0], o[NV > 4 ? 5 : 0], o[NV > 4 ? 6 : 0], o[NV > 4 ? 7 : 0]);
             }
+          } else if constexpr (W32) {
+            imax = max(imax, max(max(o[0], o[1]), max(o[2], o[3])));
+            imin = min(imin, min(min(o[0], o[1]), min(o[2], o[3])));
+            *reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(out.m) + (rowoff + j) * out.ld + c0) =
+                make_int4(o[0], o[1], o[2], o[3]);
           } else {
             uint4 u;
             u.x = __byte_perm((uint32_t)o[0], (uint32_t)o[1], 0x5410);
             u.y = __byte_perm((uint32_t)o[2], (uint32_t)o[3], 0x5410);
-            u.z = __byte_perm((uint32_t)o[4], (uint32_t)o[5], 0x5410);
-            u.w = __byte_perm((uint32_t)o[6], (uint32_t)o[7], 0x5410);
+            u.z = __byte_perm((uint32_t)o[NV > 4 ? 4 : 0], (uint32_t)o[NV > 4 ? 5 : 0], 0x5410);
+            u.w = __byte_perm((uint32_t)o[NV > 4 ? 6 : 0], (uint32_t)o[NV > 4 ? 7 : 0], 0x5410);
             vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
             vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
             *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (rowoff + j) * out.ld + c0) = u;
@@ -498,8 +530,8 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
       }
       cp_wait<0>();
     };
-    // interior strip: y rows j0 - 1 .. j1 inside the plane, the chunk's 256 columns inside the row
-    const bool xfull = (int64_t)blockIdx.x * kS16Cols + kS16Cols <= out.nx;
+    // interior strip: y rows j0 - 1 .. j1 inside the plane, the chunk's columns inside the row
+    const bool xfull = (int64_t)blockIdx.x * kCols + kCols <= out.nx;
     const bool interior = xfull && (!kUseY || (j0 >= 1 && j1 < ny));
     const std::false_type no;
     if constexpr (VAR) {   // per-point coefficients: no folded constants
@@ -517,13 +549,17 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
     // rows a warp sent to the general path (warp-uniform mask; rs <= 32)
     for (uint32_t m = redo_rows; m != 0u; m &= m - 1u) {
       const int j = j0 + __ffs(m) - 1;
-      if (act) slow_row8<PASS1, KIND, ND, VAR>(y, r, p, fq, out, tmp, j, kz, c0, red, c, nb, mw, va);
+      if (act) slow_row8<PASS1, KIND, ND, VAR, T, NV>(y, r, p, fq, out, tmp, j, kz, c0, red, c, nb, mw, va);
     }
   }
   if (!PASS1) {
-    const int32_t mx = max((int32_t)vmax >> 16, (int32_t)(int16_t)(vmax & 0xffffu));
-    const int32_t mn = min((int32_t)vmin >> 16, (int32_t)(int16_t)(vmin & 0xffffu));
-    red.nrm = max(red.nrm, (long long)max(mx, -mn));
+    if constexpr (W32) {
+      red.nrm = max(red.nrm, max((long long)imax, -(long long)imin));
+    } else {
+      const int32_t mx = max((int32_t)vmax >> 16, (int32_t)(int16_t)(vmax & 0xffffu));
+      const int32_t mn = min((int32_t)vmin >> 16, (int32_t)(int16_t)(vmin & 0xffffu));
+      red.nrm = max(red.nrm, (long long)max(mx, -mn));
+    }
   }
   if (PASS1 && ormag) red.key = max(red.key, (long long)(256 + (64 - __clzll((long long)ormag)) + 1));
   if (PASS1 && fast && j0 < j1 && act && ormag == 0 && nvalid > 0) red.key = max(red.key, 257ll);   // all-zero chunk: msb 1
