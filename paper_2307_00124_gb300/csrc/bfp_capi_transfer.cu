@@ -29,27 +29,30 @@ int32_t launch_checks(const QDesc& d) {
   return BFP_OK;
 }
 
+// T: the fine mantissas (int16; or int32 of at most 27 bits with an int32 output)
+template <class T = int16_t>
 int32_t restrict2d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaStream_t s) {
   int32_t e = launch_checks(d);
   if (e) return e;
   const int64_t ny = rc->n[1];
   const int rs = rows_per_warp(ny);
   const int64_t strips = (ny + 4 * rs - 1) / (4 * rs);
-  const dim3 grid((unsigned)((rc->ld + 255) / 256), (unsigned)(strips > 0 ? strips : 1));
+  const int64_t cols = sizeof(T) == 4 ? 128 : 256;   // coarse columns per warp chunk
+  const dim3 grid((unsigned)((rc->ld + cols - 1) / cols), (unsigned)(strips > 0 ? strips : 1));
   const VOut o = vout(rc);
   static bool carved = false;   // the staging rings want the shared-memory carveout
   if (!carved) {
-    cudaFuncSetAttribute(k_restrict2d16<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_restrict2d16<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_restrict2d16<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_restrict2d16<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<true, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<false, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<true, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_restrict2d16<false, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     carved = true;
   }
   if (zero_accumulators(d.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
   const TransferP P{vin(rf), vin(rf), d, o, rs};
   if (d.mode == kQcomp)
-    launch_rec<TransferP, &k_restrict2d16<true>, &k_restrict2d16<true, true>>(grid, 128, 0, s, P);
-  launch_rec<TransferP, &k_restrict2d16<false>, &k_restrict2d16<false, true>>(grid, 128, 0, s, P);
+    launch_rec<TransferP, &k_restrict2d16<true, false, T>, &k_restrict2d16<true, true, T>>(grid, 128, 0, s, P);
+  launch_rec<TransferP, &k_restrict2d16<false, false, T>, &k_restrict2d16<false, true, T>>(grid, 128, 0, s, P);
   note_launches(d.mode == kQcomp ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
@@ -77,8 +80,8 @@ int32_t restrict3d16(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaS
   return cudaGetLastError() == cudaSuccess ? BFP_OK : BFP_ERR_CUDA;
 }
 
-// staged int16 interpolation, 2D or 3D (grid z: fine planes)
-template <bool CORR, int ND>
+// staged interpolation, int16 (2D or 3D, grid z: fine planes) or int32 mantissas (2D)
+template <bool CORR, int ND, class T = int16_t>
 int32_t prolong16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const QDesc& d, cudaStream_t s) {
   int32_t e = launch_checks(d);
   if (e) return e;
@@ -87,17 +90,18 @@ int32_t prolong16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const
   const int64_t nzf = ND == 3 ? out->n[2] : 1;
   if (nzf > 65535) return BFP_ERR_SHAPE;
   const int64_t strips = (pairs + 4 * rs - 1) / (4 * rs);
-  const dim3 grid((unsigned)((out->ld + 255) / 256), (unsigned)(strips > 0 ? strips : 1), (unsigned)nzf);
+  const int64_t cols = sizeof(T) == 4 ? 128 : 256;   // fine columns per warp chunk
+  const dim3 grid((unsigned)((out->ld + cols - 1) / cols), (unsigned)(strips > 0 ? strips : 1), (unsigned)nzf);
   const VOut o = vout(out);
   VIn yv = vin(y ? y : out);
   if (!CORR) yv.m = nullptr;
   static bool carved = false;
   if (!carved) {
-    cudaFuncSetAttribute(k_prolong16<CORR, true, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_prolong16<CORR, false, ND>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_prolong16<CORR, true, ND, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_prolong16<CORR, false, ND, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if constexpr (ND == 2) {
-      cudaFuncSetAttribute(k_prolong16<CORR, true, 2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      cudaFuncSetAttribute(k_prolong16<CORR, false, 2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_prolong16<CORR, true, 2, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_prolong16<CORR, false, 2, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     carved = true;
   }
@@ -105,8 +109,8 @@ int32_t prolong16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const
   const TransferP P{vin(dc), yv, d, o, rs};
   if constexpr (ND == 2) {   // recordable for batched solves
     if (d.mode == kQcomp)
-      launch_rec<TransferP, &k_prolong16<CORR, true, 2>, &k_prolong16<CORR, true, 2, true>>(grid, 128, 0, s, P);
-    launch_rec<TransferP, &k_prolong16<CORR, false, 2>, &k_prolong16<CORR, false, 2, true>>(grid, 128, 0, s, P);
+      launch_rec<TransferP, &k_prolong16<CORR, true, 2, false, T>, &k_prolong16<CORR, true, 2, true, T>>(grid, 128, 0, s, P);
+    launch_rec<TransferP, &k_prolong16<CORR, false, 2, false, T>, &k_prolong16<CORR, false, 2, true, T>>(grid, 128, 0, s, P);
   } else {
     if (d.mode == kQcomp) k_prolong16<CORR, true, ND><<<grid, 128, 0, s>>>(P, nullptr);
     k_prolong16<CORR, false, ND><<<grid, 128, 0, s>>>(P, nullptr);
@@ -118,6 +122,8 @@ int32_t prolong16(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, const
 template <int ND>
 int32_t restrict_launch(const bfp_vec* rf, const bfp_vec* rc, const QDesc& d, cudaStream_t s) {
   if (ND == 2 && !is32(rf)) return restrict2d16(rf, rc, d, s);
+  // int32 fine mantissas of at most 27 bits (the nine-point sum exact in int32) into an int32 output
+  if (ND == 2 && is32(rf) && !is64(rf) && is32(rc) && !is64(rc) && rf->w <= 27) return restrict2d16<int32_t>(rf, rc, d, s);
   if (ND == 3 && !is32(rf)) return restrict3d16(rf, rc, d, s);
   if (is32(rf)) return launch_quant(OpRestrict<int32_t, ND>{vin(rf), rc->n[1]}, d, rc, s);
   return launch_quant(OpRestrict<int16_t, ND>{vin(rf), rc->n[1]}, d, rc, s);
@@ -130,6 +136,11 @@ int32_t prolong_launch(const bfp_vec* dc, const bfp_vec* y, const bfp_vec* out, 
     return launch_quant(OpProlong<int16_t, ND, true, int64_t>{vin(dc), vin(y), esize(y)}, d, out, s);
   }
   if (!is32(dc)) return prolong16<CORR, ND>(dc, y, out, d, s);
+  // int32 mantissas (d of at most 29 bits: P_m d exact in int32; y int32 when corrected) into an int32 output
+  if constexpr (ND == 2) {
+    if (!is64(dc) && dc->w <= 29 && is32(out) && !is64(out) && (!CORR || !is64(y)))
+      return prolong16<CORR, ND, int32_t>(dc, y, out, d, s);
+  }
   VIn yv = vin(y ? y : out);   // carries the fine shape; not read when CORR is false
   if (!CORR) yv.m = nullptr;
   if (is32(dc)) return launch_quant(OpProlong<int32_t, ND, CORR>{vin(dc), yv}, d, out, s);

@@ -142,7 +142,7 @@ def test_laplace_stencil_matches_oracle():
 
 
 # 3D: several strips of rows per plane, two column chunks, ragged tails in x and y
-STAR_SHAPES = [(37, 45), (1, 1), (2, 3), (63, 63), (5, 6, 7), (3, 3, 3), (9, 70, 300), (3, 260, 17)]
+STAR_SHAPES = [(37, 45), (1, 1), (2, 3), (63, 63), (70, 300), (5, 6, 7), (3, 3, 3), (9, 70, 300), (3, 260, 17)]
 
 
 @pytest.mark.parametrize("shape", STAR_SHAPES)
@@ -197,12 +197,13 @@ def test_jacobi(shape, w, mode, zero_guess):
     check(yo, ref, st, rs)
 
 
-# coarse shapes; the 3D ones span several strips of rows and two column chunks of the fine grid
-TRANSFER_SHAPES = [(1, 1), (3, 3), (20, 33), (2, 2, 2), (4, 3, 5), (5, 40, 140), (3, 70, 9), (0, 0), (0, 0, 0)]
+# coarse shapes; (70, 300) and the 3D ones span several strips of rows and column chunks of the fine grid
+TRANSFER_SHAPES = [(1, 1), (3, 3), (20, 33), (70, 300), (2, 2, 2), (4, 3, 5), (5, 40, 140), (3, 70, 9), (0, 0),
+                   (0, 0, 0)]
 
 
 @pytest.mark.parametrize("nc", TRANSFER_SHAPES)
-@pytest.mark.parametrize("w", [8, 16, 32])
+@pytest.mark.parametrize("w", [8, 16, 24, 27, 32])   # int32 fine mantissas of <= 27 bits take the staged kernel
 @pytest.mark.parametrize("mode", MODES)
 def test_restrict(nc, w, mode):
     nf = tuple(2 * c + 1 for c in nc)
@@ -217,7 +218,7 @@ def test_restrict(nc, w, mode):
 
 
 @pytest.mark.parametrize("nc", TRANSFER_SHAPES)
-@pytest.mark.parametrize("w", [8, 16, 32])
+@pytest.mark.parametrize("w", [8, 16, 24, 29, 32])   # int32 coarse mantissas of <= 29 bits take the staged kernel
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("correct", [True, False])
 def test_prolong(nc, w, mode, correct):
