@@ -1,8 +1,11 @@
 // bfp_star2d16.cuh -- five- and seven-point stencil ops on int16 mantissas
-// (w <= 16), the finest-level hot path of the V-cycle.
+// (w <= 16), the finest-level hot path of the V-cycle, and the 2D five-point ops
+// on int32 mantissas of at most 30 bits (the same kernel with half the values
+// per lane).
 //
 // A warp owns a 256-column chunk of a strip of rows of one plane: each lane 8
-// consecutive mantissas (16 bytes per row and input).  Rows are staged through
+// consecutive mantissas (16 bytes per row and input; int32: 128 columns, 4 per
+// lane).  Rows are staged through
 // a per-lane ring of NS slots in shared memory with cp.async (16-byte copies,
 // zero-filled outside the grid), issued NS - 3 rows ahead of the three-row
 // window the lane reads back (rows j-1, j, j+1 of y and row j of r; in 3D also

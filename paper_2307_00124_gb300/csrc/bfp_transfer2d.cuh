@@ -1,10 +1,10 @@
-// bfp_transfer2d.cuh -- 2D grid transfers on int16 mantissas: full-weighting
-// restriction (Alg. v-cycle restriction line) and bilinear interpolation with
-// or without the correction y - P d (Alg. v-cycle correction line, Alg. fmg
-// interpolation line).
+// bfp_transfer2d.cuh -- grid transfers on int16 mantissas (2D and 3D) and on
+// int32 mantissas (2D): full-weighting restriction (Alg. v-cycle restriction
+// line) and bilinear interpolation with or without the correction y - P d
+// (Alg. v-cycle correction line, Alg. fmg interpolation line).
 //
-// Same structure as bfp_star2d16.cuh: a warp owns a 256-column chunk of a
-// strip of output rows, input rows are staged per warp through a cp.async
+// Same structure as bfp_star2d16.cuh: a warp owns a 256-column chunk (int32:
+// 128) of a strip of output rows, input rows are staged per warp through a cp.async
 // ring in shared memory (with halo words for the one neighbour mantissa a
 // chunk needs from the next / previous chunk), the exact groups H (the
 // transfer stencil) and L (the correction's y) are combined as
