@@ -28,7 +28,7 @@ __device__ __forceinline__ int64_t ld1(const VIn& v, int64_t row, int64_t col) {
   return (int64_t)__ldg(reinterpret_cast<const T*>(v.m) + row * v.ld + col);
 }
 
-// V consecutive mantissas (V = 4 or 8) of one row starting at c0 (c0 % V == 0).
+// V consecutive mantissas (V = 4, 8, or 16 for int16) of one row starting at c0 (c0 % V == 0).
 // Entries at columns >= nx, rows outside the vector, or chunks past ld read as
 // 0 (zero Dirichlet halo and padding).
 template <class T, int V>
@@ -39,7 +39,16 @@ __device__ __forceinline__ void ldv(const VIn& v, int64_t row, int64_t c0, int32
     return;
   }
   const T* p = reinterpret_cast<const T*>(v.m) + row * v.ld + c0;
-  if (sizeof(T) == 2) {
+  if (sizeof(T) == 2 && V == 16) {   // the second half only inside the row (ld is a multiple of 8)
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint4 b = c0 + 8 < v.ld ? __ldg(reinterpret_cast<const uint4*>(p) + 1) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      o[(2 * k) % V] = (int32_t)(int16_t)(w[k] & 0xffffu);
+      o[(2 * k + 1) % V] = (int32_t)(int16_t)(w[k] >> 16);
+    }
+  } else if (sizeof(T) == 2) {
     uint32_t w[V / 2];
     if (V == 8) {
       const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
@@ -76,6 +85,14 @@ __device__ __forceinline__ void ld8(const VIn& v, int64_t row, int64_t c0, int32
 
 template <int V>
 __device__ __forceinline__ void stv(const VOut& v, int64_t row, int64_t c0, const int32_t (&o)[V]) {
+  if constexpr (V == 16) {   // two halves of 8; the second only inside the row (ld is a multiple of 8)
+    int32_t lo[8], hi[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { lo[k] = o[k]; hi[k] = o[(k + 8) % V]; }
+    stv<8>(v, row, c0, lo);
+    if (c0 + 8 < v.ld) stv<8>(v, row, c0 + 8, hi);
+    return;
+  }
   if (v.is32) {
     int4* p = reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(v.m) + row * v.ld + c0);
     p[0] = make_int4(o[0], o[1], o[2], o[3]);
@@ -506,8 +523,9 @@ __device__ __forceinline__ void quantvf(const HL& hl, const Plan& p, const Fast&
   if (PASS1) {
     if (tmp && store) {
       int4* q = reinterpret_cast<int4*>(tmp + row * out.ld + c0);
-      q[0] = make_int4(o[0], o[1], o[2], o[3]);
-      if (V == 8) q[1] = make_int4(o[V == 8 ? 4 : 0], o[V == 8 ? 5 : 1], o[V == 8 ? 6 : 2], o[V == 8 ? 7 : 3]);
+#pragma unroll
+      for (int g = 0; g < V / 4; ++g)   // (past column c0 + 8 only inside the row: ld is a multiple of 8)
+        if (g < 2 || c0 + 8 < out.ld) q[g] = make_int4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
     }
   } else {
 #pragma unroll
@@ -531,11 +549,10 @@ __device__ __forceinline__ void narrowv(const int32_t* tmp, const Plan& p, const
                                         Red& red) {
   const int4* src = reinterpret_cast<const int4*>(tmp + row * out.ld + c0);
   int32_t t[V];
-  const int4 a = src[0];
-  t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w;
-  if (V == 8) {
-    const int4 b = src[1];
-    t[V == 8 ? 4 : 0] = b.x; t[V == 8 ? 5 : 1] = b.y; t[V == 8 ? 6 : 2] = b.z; t[V == 8 ? 7 : 3] = b.w;
+#pragma unroll
+  for (int g = 0; g < V / 4; ++g) {   // (past column c0 + 8 only inside the row: ld is a multiple of 8)
+    const int4 a = (g < 2 || c0 + 8 < out.ld) ? src[g] : make_int4(0, 0, 0, 0);
+    t[4 * g] = a.x; t[4 * g + 1] = a.y; t[4 * g + 2] = a.z; t[4 * g + 3] = a.w;
   }
   const int s = (int)(p.e_out - p.e_tmp);
   int32_t o[V];

@@ -261,7 +261,8 @@ inline int32_t launch_star16(const VIn& y, const VIn& r, int32_t c, int32_t nb, 
     }
     carved = true;
   }
-  constexpr int64_t kCols = sizeof(T) == 4 ? kS16Cols / 2 : kS16Cols;   // 16 bytes per lane and row
+  // columns per warp chunk: 4 int32, 16 int16 (2D) or 8 int16 (3D) mantissas per lane
+  constexpr int64_t kCols = sizeof(T) == 4 ? kS16Cols / 2 : (ND == 2 ? 2 * kS16Cols : kS16Cols);
   const int64_t strips = (o.ny + 4 * (int64_t)rs - 1) / (4 * (int64_t)rs);
   const int64_t chunks = (o.ld + kCols - 1) / kCols;
   const dim3 g((unsigned)(chunks > 0 ? chunks : 1), (unsigned)(strips > 0 ? strips : 1),
@@ -346,11 +347,13 @@ inline int32_t launch_star2d(const VIn& y, const VIn& r, int64_t c64, int64_t nb
   const VOut o = vout(out);
   const int64_t ny = out->n[1];
   const int rs = pick_rows(ny >= 2048 ? 16 : (ny >= 1024 ? 8 : (ny >= 256 ? 4 : 2)), 32);   // <= 32: row masks
+  // the int16 staged kernel's lanes take 16 columns: half the rows per strip keep a level's CTA count
+  const int rs16 = pick_rows(ny >= 2048 ? 8 : (ny >= 1024 ? 4 : (ny >= 256 ? 2 : 1)), 32);
   const int64_t chunks = (out->ld + kStarCols - 1) / kStarCols;
   const int64_t strips = (ny + (int64_t)kStarWarps * rs - 1) / ((int64_t)kStarWarps * rs);
   const dim3 grid((unsigned)chunks, (unsigned)(strips > 0 ? strips : 1));
   if (zero_accumulators(q.meta_out, s) != cudaSuccess) return BFP_ERR_CUDA;
-  if (sizeof(T) == 2 && !o.is32) return launch_star16<KIND, 2>(y, r, c, nb, mw, q, o, rs, s);
+  if (sizeof(T) == 2 && !o.is32) return launch_star16<KIND, 2>(y, r, c, nb, mw, q, o, rs16, s);
   // int32 mantissas of at most 30 bits in y and r (one storage class: the callers send mixed storage to
   // the generic row kernel) and an int32 output: the staged kernel with 128-column chunks (the range
   // test of its register path needs w_out <= 30)

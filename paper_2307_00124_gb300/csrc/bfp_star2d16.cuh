@@ -39,8 +39,9 @@ constexpr int kS16Cols = 256;   // columns per warp chunk (32 lanes x 8)
 constexpr int kStages = 6;      // ring slots per lane (2D): the 3-row window + 3 rows in flight
 constexpr int kStages3 = 5;     // 3D (four rows per stage): the window + 2 rows in flight
 
+// A lane's mantissas of one row: 4 words (8 int16 or 4 int32) or 8 words (16 int16)
 struct Pk8 {
-  uint32_t w[4];
+  uint32_t w[8];
 };
 
 __device__ __forceinline__ int32_t pk_get(const Pk8& p, int k) {
@@ -140,7 +141,7 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
                                        int32_t nb, int32_t mw, const VarRow& va) {
   RowIn<NV> in;
   int32_t kf[4][8], qv[8];
-  if (VAR) {
+  if constexpr (VAR) {
     const int64_t row = kz * out.ny + j;
 #pragma unroll
     for (int f = 0; f < 4; ++f) ldv<int16_t, 8>(va.k[f], row, c0, kf[f]);
@@ -158,7 +159,7 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
   }
   if (KIND != kApply) ldv<T, NV>(r, row, c0, in.r);
   auto hl = [&](int k, int64_t& H, int64_t& L) {
-    if (VAR) {
+    if constexpr (VAR) {
       if (KIND == kJacobi0) {
         H = (int64_t)qv[k] * in.r[k];
         L = 0;
@@ -192,15 +193,17 @@ __device__ __noinline__ void slow_row8(const VIn& y, const VIn& r, const Plan& p
 // east halo pair (columns c+256, c+257), 3 pad words; lane slots stay 16-byte
 // aligned, and every west / east neighbour is one int16 load from the row.
 // In 3D a stage also holds row j of the planes below (zm) and above (zp).
+// LW: words per lane and row (4, or 8 for 16 int16 mantissas per lane); a y row is 8 + 32 LW words.
 constexpr int kRowWords = 136;
-template <int ND>
+template <int ND, int LW = 4>
 struct __align__(16) Stage16 {
-  static constexpr int N = kStages;
-  uint32_t y[N][kRowWords];
-  uint4 r[N][32];
+  // wide lanes: the window + 2 rows in flight (four warps' stages stay within 48 KB of static shared memory)
+  static constexpr int N = LW == 8 ? kStages3 : kStages;
+  uint32_t y[N][8 + 32 * LW];
+  uint4 r[N][8 * LW];
 };
 template <>
-struct __align__(16) Stage16<3> {
+struct __align__(16) Stage16<3, 4> {
   static constexpr int N = kStages3;
   uint32_t y[N][kRowWords];
   uint4 r[N][32];
@@ -223,12 +226,17 @@ struct Star16P {
 // (8 per lane, 256-column chunks) or int32 (4 per lane, 128-column chunks; 2D constant-coefficient ops
 // with mantissas of at most 30 bits, so the neighbour sum is exact in int32)
 template <int KIND, bool PASS1, int ND, bool VAR = false, bool B = false, class T = int16_t>
-__global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const __grid_constant__ Star16P P1,
-                                                                 const Star16P* __restrict__ Pb) {
+__global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : (sizeof(T) == 2 ? 4 : 7))
+    k_star16(const __grid_constant__ Star16P P1, const Star16P* __restrict__ Pb) {
   static_assert(!B || ND == 2, "batched launches are 2D");
   constexpr bool W32 = sizeof(T) == 4;
   static_assert(!W32 || (ND == 2 && !VAR), "int32 mantissas: 2D constant-coefficient ops");
-  constexpr int NV = W32 ? 4 : 8;                 // mantissas per lane and row (16 bytes)
+  // 2D constant-coefficient int16 ops: 16 mantissas per lane (32 bytes per row and input), so that a
+  // row's fixed per-lane work (copies, waits, loads, the range vote, stores) covers twice the points
+  constexpr bool WIDE = !W32 && ND == 2 && !VAR;
+  constexpr int NV = W32 ? 4 : (WIDE ? 16 : 8);   // mantissas per lane and row
+  constexpr int LW = WIDE ? 8 : 4;                // words per lane and row
+  constexpr int kRowW = 8 + 32 * LW;              // words of a staged y row
   constexpr int kCols = 32 * NV;                  // columns per warp chunk
   constexpr int64_t kEs = sizeof(T);              // bytes per mantissa
   pdl_wait();
@@ -240,9 +248,9 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   const VOut& out = P.out;
   const int rs = P.rs;
   const VarRow& va = P.va;
-  constexpr int NS = Stage16<ND>::N;
+  constexpr int NS = Stage16<ND, LW>::N;
   __shared__ Plan sp;
-  __shared__ Stage16<ND> stg[4];
+  __shared__ Stage16<ND, LW> stg[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * kCols + lane * NV;
   const int ny = (int)out.ny;
@@ -253,16 +261,19 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   const bool act = c0 < out.ld;
   constexpr bool kUseY = KIND != kJacobi0, kUseR = KIND != kApply;
   // staging: stage s holds y row j0 - 1 + s and r (zm, zp) row j0 - 2 + s
-  Stage16<ND>& S = stg[warp];
+  Stage16<ND, LW>& S = stg[warp];
   const int nyin = kUseY ? ny : 1, nrin = kUseR ? ny : 1;
   const bool ycol = kUseY && c0 < y.nx && c0 < y.ld, rcol = kUseR && c0 < r.nx && c0 < r.ld;
+  // the second 16 bytes of a wide lane (columns c0 + 8 ..)
+  const bool ycol1 = WIDE && kUseY && c0 + 8 < y.nx && c0 + 8 < y.ld;
+  const bool rcol1 = WIDE && kUseR && c0 + 8 < r.nx && c0 + 8 < r.ld;
   const T* ybase = kUseY ? reinterpret_cast<const T*>(y.m) : nullptr;
   const T* rbase = kUseR ? reinterpret_cast<const T*>(r.m) : nullptr;
-  // halo words: lane 0 copies (c0-2, c0-1) (int16; int32: c0-1) into word 3, lane 31 (c0+8, c0+9)
-  // (int32: c0+4) into word 132
+  // halo words: lane 0 copies (c0-2, c0-1) (int16; int32: c0-1) into word 3, lane 31 (c0+NV, c0+NV+1)
+  // (int32: c0+4) into word kRowW - 4
   const int64_t ecol = lane == 0 ? c0 - (W32 ? 1 : 2) : c0 + NV;
   const bool eok = kUseY && (lane == 0 ? (c0 >= (W32 ? 1 : 2) && c0 - 1 < y.nx) : (lane == 31 && c0 + NV < y.nx));
-  const int eword = lane == 0 ? 3 : kRowWords - 4;
+  const int eword = lane == 0 ? 3 : kRowW - 4;
   // the next stage to issue: y row jy at byte offset oy, r row jy - 1 at byte offset orr (rows
   // outside the grid and lanes past the row are zero-filled)
   int jy = j0 - 1;
@@ -277,9 +288,9 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
   const uint32_t ybytes = 16u, rbytes = 16u;
   const char* yb = reinterpret_cast<const char*>(ybase);
   const char* rb = reinterpret_cast<const char*>(rbase);
-  constexpr uint32_t kYRowBytes = kRowWords * 4, kRRowBytes = 32 * 16;
-  const uint32_t ydst = smem_u32(&S.y[0][4 + 4 * lane]), edst = smem_u32(&S.y[0][eword]);
-  const uint32_t rdst = smem_u32(&S.r[0][lane]);
+  constexpr uint32_t kYRowBytes = kRowW * 4, kRRowBytes = 32 * LW * 4;
+  const uint32_t ydst = smem_u32(&S.y[0][4 + LW * lane]), edst = smem_u32(&S.y[0][eword]);
+  const uint32_t rdst = smem_u32(&S.r[0][(LW / 4) * lane]);
   uint32_t zmdst = 0, zpdst = 0;
   if constexpr (ND == 3) {
     zmdst = smem_u32(&S.zm[0][lane]);
@@ -294,14 +305,23 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
       const bool in = INT || (unsigned)jy < (unsigned)nyin;
       const bool ok = INT || (in && ycol);
       cp16u(ydst + (uint32_t)slot * kYRowBytes, yb + (ok ? oy : 0), ok ? ybytes : 0u);
+      if constexpr (WIDE) {
+        const bool ok1 = INT || (in && ycol1);
+        cp16u(ydst + (uint32_t)slot * kYRowBytes + 16u, yb + (ok1 ? oy + 16 : 0), ok1 ? 16u : 0u);
+      }
       const bool ek = eok && in;
       cp4u_if(edge_lane, edst + (uint32_t)slot * kYRowBytes, yb + (ek ? oy + edelta : 0), ek ? 4u : 0u);
       oy += ystride;
     }
     if (kUseR) {
       if (with_r) {
-        const bool ok = INT || (rcol && (unsigned)(jy - 1) < (unsigned)nrin);
+        const bool rin = (unsigned)(jy - 1) < (unsigned)nrin;
+        const bool ok = INT || (rcol && rin);
         cp16u(rdst + (uint32_t)slot * kRRowBytes, rb + (ok ? orr : 0), ok ? rbytes : 0u);
+        if constexpr (WIDE) {
+          const bool ok1 = INT || (rcol1 && rin);
+          cp16u(rdst + (uint32_t)slot * kRRowBytes + 16u, rb + (ok1 ? orr + 16 : 0), ok1 ? 16u : 0u);
+        }
       }
       orr += rstride;
     }
@@ -314,6 +334,27 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
     }
     ++jy;
     cp_commit();
+  };
+  // a lane's mantissas of the staged y / r row in `slot` (one or two 16-byte halves)
+  auto rdy = [&](int slot) {
+    Pk8 v;
+    const uint4 a = *reinterpret_cast<const uint4*>(&S.y[slot][4 + LW * lane]);
+    v.w[0] = a.x; v.w[1] = a.y; v.w[2] = a.z; v.w[3] = a.w;
+    if constexpr (LW == 8) {
+      const uint4 b = *reinterpret_cast<const uint4*>(&S.y[slot][8 + LW * lane]);
+      v.w[LW - 4] = b.x; v.w[LW - 3] = b.y; v.w[LW - 2] = b.z; v.w[LW - 1] = b.w;
+    }
+    return v;
+  };
+  auto rdr = [&](int slot) {
+    Pk8 v;
+    const uint4 a = S.r[slot][(LW / 4) * lane];
+    v.w[0] = a.x; v.w[1] = a.y; v.w[2] = a.z; v.w[3] = a.w;
+    if constexpr (LW == 8) {
+      const uint4 b = S.r[slot][(LW / 4) * lane + 1];
+      v.w[LW - 4] = b.x; v.w[LW - 3] = b.y; v.w[LW - 2] = b.z; v.w[LW - 1] = b.w;
+    }
+    return v;
   };
   auto rd = [&](const uint4& u) {
     Pk8 v;
@@ -403,9 +444,9 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
         Pk8 ym, yc, yp, rc, zm, zp;
         int32_t yv[NV], wv = 0, ev = 0;
         if (kUseY) {
-          ym = rd(*reinterpret_cast<const uint4*>(&S.y[s0][4 + 4 * lane]));
-          yc = rd(*reinterpret_cast<const uint4*>(&S.y[s1][4 + 4 * lane]));
-          yp = rd(*reinterpret_cast<const uint4*>(&S.y[s2][4 + 4 * lane]));
+          ym = rdy(s0);
+          yc = rdy(s1);
+          yp = rdy(s2);
   #pragma unroll
           for (int k = 0; k < NV; ++k) yv[k] = vget<W32>(yc, k);
           if (!INT && partial) {   // padding columns may hold anything: the east neighbour of the last column is 0
@@ -419,15 +460,15 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
             ev = roww[8 + 4 * lane];              // column c0 + 4
           } else {
             const int16_t* row = reinterpret_cast<const int16_t*>(&S.y[s1][0]);
-            wv = row[7 + 8 * lane];               // column c0 - 1
-            ev = row[16 + 8 * lane];              // column c0 + 8
+            wv = row[7 + NV * lane];              // column c0 - 1
+            ev = row[8 + NV * (lane + 1)];        // column c0 + NV
           }
           if constexpr (ND == 3) {
             zm = rd(S.zm[s2][lane]);
             zp = rd(S.zp[s2][lane]);
           }
         }
-        if (kUseR) rc = rd(S.r[s2][lane]);
+        if (kUseR) rc = rdr(s2);
         sn = s0;
         s0 = s1;
         s1 = s2;
@@ -511,8 +552,9 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
           } else if (PASS1) {
             if (tmp) {
               int4* d = reinterpret_cast<int4*>(tmp + (rowoff + j) * out.ld + c0);
-              d[0] = make_int4(o[0], o[1], o[2], o[3]);
-              if constexpr (!W32) d[1] = make_int4(o[NV > 4 ? 4 : 0], o[NV > 4 ? 5 : 0], o[NV > 4 ? 6 : 0], o[NV > 4 ? 7 : 0]);
+#pragma unroll
+              for (int g = 0; g < NV / 4; ++g)   // (a wide lane's second half only inside the row)
+                if (g < 2 || c0 + 8 < out.ld) d[g] = make_int4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
             }
           } else if constexpr (W32) {
             imax = max(imax, max(max(o[0], o[1]), max(o[2], o[3])));
@@ -520,14 +562,18 @@ __global__ void __launch_bounds__(128, (ND == 3 || VAR) ? 5 : 7) k_star16(const 
             *reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(out.m) + (rowoff + j) * out.ld + c0) =
                 make_int4(o[0], o[1], o[2], o[3]);
           } else {
-            uint4 u;
-            u.x = __byte_perm((uint32_t)o[0], (uint32_t)o[1], 0x5410);
-            u.y = __byte_perm((uint32_t)o[2], (uint32_t)o[3], 0x5410);
-            u.z = __byte_perm((uint32_t)o[NV > 4 ? 4 : 0], (uint32_t)o[NV > 4 ? 5 : 0], 0x5410);
-            u.w = __byte_perm((uint32_t)o[NV > 4 ? 6 : 0], (uint32_t)o[NV > 4 ? 7 : 0], 0x5410);
-            vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
-            vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
-            *reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (rowoff + j) * out.ld + c0) = u;
+            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<int16_t*>(out.m) + (rowoff + j) * out.ld + c0);
+#pragma unroll
+            for (int g = 0; g < NV / 8; ++g) {
+              uint4 u;
+              u.x = __byte_perm((uint32_t)o[8 * g], (uint32_t)o[8 * g + 1], 0x5410);
+              u.y = __byte_perm((uint32_t)o[8 * g + 2], (uint32_t)o[8 * g + 3], 0x5410);
+              u.z = __byte_perm((uint32_t)o[8 * g + 4], (uint32_t)o[8 * g + 5], 0x5410);
+              u.w = __byte_perm((uint32_t)o[8 * g + 6], (uint32_t)o[8 * g + 7], 0x5410);
+              vmax = max_s16x2(vmax, max_s16x2(max_s16x2(u.x, u.y), max_s16x2(u.z, u.w)));
+              vmin = min_s16x2(vmin, min_s16x2(min_s16x2(u.x, u.y), min_s16x2(u.z, u.w)));
+              if (g == 0 || c0 + 8 < out.ld) dst[g] = u;   // a wide lane's second half only inside the row
+            }
           }
         }
       }
